@@ -1,0 +1,104 @@
+"""Workload recipes: seeded synthetic cut circuits shaped like the
+benchmarked configurations, with their subcircuit variant outputs and qubit
+roles.  The recipes state their shapes explicitly; roles are "the lowest a_i
+data qubits of each subcircuit active, the rest merged", with a_i given per
+recipe (the tests check that this equals what Algorithm 2 assigns)."""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .circuits import CutCircuit, chain_grid_circuit, chain_line_circuit, random_block_circuit
+from .qpu import random_variant_probs, subcircuit_variant_probs
+
+ACTIVE, MERGED, ZOOM0, ZOOM1 = 0, 1, 2, 3
+
+
+@dataclass
+class Workload:
+    name: str
+    circuit: CutCircuit
+    probs: list[np.ndarray]            # per subcircuit [4^k_i, 2^w_i]
+    roles: np.ndarray                  # int8 per original qubit
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_active(self) -> int:
+        return int((self.roles == ACTIVE).sum())
+
+
+def lowest_active_roles(c: CutCircuit, a: list[int], zoom: dict[int, int] | None = None) -> np.ndarray:
+    zoom = zoom or {}
+    roles = np.full(c.n_qubits, MERGED, dtype=np.int8)
+    for q, v in zoom.items():
+        roles[q] = ZOOM1 if v else ZOOM0
+    for i, dq in enumerate(c.data_qubits):
+        free = [q for q in dq if q not in zoom]
+        for q in free[:a[i]]:
+            roles[q] = ACTIVE
+    return roles
+
+
+def _exact_probs(c: CutCircuit, dtype) -> list[np.ndarray]:
+    return [subcircuit_variant_probs(c, i).astype(dtype) for i in range(c.n_subcircuits)]
+
+
+def full_state_12q(seed: int = 1) -> Workload:
+    """12-qubit line circuit, 8 brickwork layers per block, cut at K=2 into
+    two 7-qubit subcircuits; FP64 variants; every qubit active (2^12 bins)."""
+    c = chain_line_circuit(seed, [7, 7], [2], 8)
+    roles = np.zeros(c.n_qubits, dtype=np.int8)
+    return Workload("line12_K2_full", c, _exact_probs(c, np.float64), roles,
+                    {"seed": seed, "precision": "fp64 inputs"})
+
+
+def merged_30q(seed: int = 2) -> Workload:
+    """30-qubit line circuit of depth 10, cut at K=8 (3,2,3) into 4
+    subcircuits of width 10,10,10,8; FP32 variants from exact simulation;
+    20 active qubits (5 per subcircuit) and 10 merged: 2^20 bins."""
+    c = chain_line_circuit(seed, [10, 10, 10, 8], [3, 2, 3], 10)
+    roles = lowest_active_roles(c, [5, 5, 5, 5])
+    return Workload("line30_K8_a20", c, _exact_probs(c, np.float32), roles, {"seed": seed})
+
+
+def grid_40q(seed: int = 3) -> Workload:
+    """40-qubit 5x8 grid circuit of depth 8, cut at K=12 (3,3,3,3) into 5
+    subcircuits of width 8,11,11,11,11; FP32 variants from exact simulation;
+    22 active qubits (4,4,4,5,5): 2^22 bins."""
+    c = chain_grid_circuit(seed, 5, 8, [8, 11, 11, 11, 11], [3, 3, 3, 3], 8)
+    roles = lowest_active_roles(c, [4, 4, 4, 5, 5])
+    return Workload("grid40_K12_a22", c, _exact_probs(c, np.float32), roles, {"seed": seed})
+
+
+def small_random(seed: int, n_qubits: int = 9, n_blocks: int = 4, max_block: int = 5, depth: int = 2,
+                 dtype=np.float64, roles: str = "active") -> Workload:
+    """Tiny random cut circuit with an arbitrary compute graph (exact
+    variants).  roles: 'active' (all active), or 'mixed' (seeded random
+    active / merged / zoom0 / zoom1 per qubit)."""
+    c = random_block_circuit(seed, n_qubits, n_blocks, max_block, depth, p_reuse=0.8)
+    if roles == "active":
+        r = np.zeros(c.n_qubits, dtype=np.int8)
+    else:
+        rng = np.random.default_rng(seed + 1000)
+        r = rng.choice([ACTIVE, ACTIVE, MERGED, ZOOM0, ZOOM1], size=c.n_qubits).astype(np.int8)
+    return Workload(f"random{n_qubits}_s{seed}", c, _exact_probs(c, dtype), r, {"seed": seed})
+
+
+def random_line_chain(seed: int, widths: list[int], handoffs: list[int], depth: int, active: list[int],
+                      dtype=np.float32, zoom_bits: int = 0) -> Workload:
+    """A chain of line blocks with random numbers in place of QPU outputs
+    (as in the paper's timing runs); used where exact simulation of every
+    variant would be too slow.  The first `zoom_bits` data qubits of the
+    circuit's subcircuits (lowest original index first) are zoomed to seeded
+    random values."""
+    c = chain_line_circuit(seed, widths, handoffs, depth)
+    rng = np.random.default_rng(seed)
+    probs = [random_variant_probs(c, i, rng).astype(dtype) for i in range(c.n_subcircuits)]
+    zoom = {}
+    if zoom_bits:
+        for i, dq in enumerate(c.data_qubits):
+            for q in dq[:zoom_bits]:
+                zoom[q] = int(rng.integers(2))
+    roles = lowest_active_roles(c, active, zoom)
+    return Workload(f"randline{c.n_qubits}_s{seed}", c, probs, roles, {"seed": seed, "outputs": "random"})
