@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the states-merging reconstruction on GB300.
+
+A step is one pass of the whole hot path over one batch of synthetic input
+already resident in HBM: attribution of the subcircuit variant outputs
+(new QPU results, Algorithm 1), merge/zoom of every subcircuit (Algorithm
+2), the contraction steps (Section 6) with the 2^-K scale and the FP64
+probability check, and the selection of the largest bins.  The default
+workload is the 30-qubit line circuit cut at K=8 into 4 subcircuits with
+20 active and 10 merged qubits (2^20 bins, FP32).
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA
+events on the launching stream; the inputs fit in L2, so a 256 MiB buffer
+is written between steps (outside the events) to flush it.  One JSON line
+on rank 0.  --impl reference times the FP64 CPU oracle on the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+if "reference" in sys.argv:
+    # the oracle baseline runs single-threaded so that its core count is exact
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "line30_K8_a20": "merged_30q",
+    "grid40_K12_a22": "grid_40q",
+    "line12_K2_full": "full_state_12q",
+}
+METRIC = "recon bins/s"
+UNIT = "bins/s"
+TOPK = 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="line30_K8_a20", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str, seed_offset: int = 0):
+    from synthetic import workloads as W
+    fn = getattr(W, WORKLOADS[name])
+    import inspect
+    seed = inspect.signature(fn).parameters["seed"].default + seed_offset
+    return fn(seed)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---- clocks during the timed region ---------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- the oracle on the host cores --------------------------------------------------
+
+def oracle_step(w, g, probs64, k):
+    import oracle as O
+    P = O.reconstruct(g, probs64, w.roles)
+    O.top_bins(P, k)
+    O.total_probability(P)
+    return P
+
+
+def cpu_baseline(name: str, budget_s: float = 12.0) -> dict:
+    """Time the oracle, as it stands, on a bounded sample of the same
+    workload in a single-threaded subprocess."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import bench, oracle as O
+w = bench.make_workload({name!r})
+g = O.Graph.from_arrays(w.circuit.n_qubits, *w.circuit.graph_arrays())
+probs = [p.astype(np.float64) for p in w.probs]
+bench.oracle_step(w, g, probs, bench.TOPK)
+n, t0 = 0, time.perf_counter()
+while True:
+    bench.oracle_step(w, g, probs, bench.TOPK)
+    n += 1
+    dt = time.perf_counter() - t0
+    if dt >= {budget_s} or n >= 200:
+        break
+print(json.dumps({{"reps": n, "seconds": dt, "bins": 1 << w.n_active}}))
+"""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["reps"] * d["bins"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['reps']} full reconstructions (attribution, merge, pairwise contraction, top-{TOPK}, "
+                      f"FP64 sum) of {name}, {d['seconds']:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    w = make_workload(args.workload)
+    g = O.Graph.from_arrays(w.circuit.n_qubits, *w.circuit.graph_arrays())
+    probs = [p.astype(np.float64) for p in w.probs]
+    for _ in range(args.warmup):
+        oracle_step(w, g, probs, TOPK)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(w, g, probs, TOPK)
+        times.append(time.perf_counter() - t0)
+    bins = 1 << w.n_active
+    tot = sum(times)
+    value = bins * len(times) / tot
+    import multiprocessing
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "bins": bins, "topk": TOPK},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{len(times)} full reconstructions of {args.workload} "
+                                       f"({multiprocessing.cpu_count()} host cores present; numpy oracle)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- our arm -------------------------------------------------------------------------
+
+def algorithmic_bytes(w, steps, out_elem_bytes):
+    """Bytes the method itself must move per step, per stage."""
+    c = w.circuit
+    in_b = w.probs[0].dtype.itemsize
+    attr = sum(p.size * in_b + (p.shape[0] << len(c.data_qubits[i])) * 4 for i, p in enumerate(w.probs))
+    merge = 0
+    for i in range(c.n_subcircuits):
+        k = len(c.incident[i])
+        dq = c.data_qubits[i]
+        z = sum(1 for q in dq if w.roles[q] in (2, 3))
+        a = sum(1 for q in dq if w.roles[q] == 0)
+        merge += (4 ** k) * (1 << (len(dq) - z)) * 4 + (4 ** k) * (1 << a) * 4
+    contract = sum(4 * (M * K + K * N) + 4 * M * N for (M, N, K) in steps[:-1])
+    M, N, K = steps[-1] if steps else (1, 1, 1)
+    final = 4 * (M * K + K * N) + out_elem_bytes * M * N
+    select = (1 << w.n_active) * out_elem_bytes
+    return {"attribute": attr, "merge": merge, "contract": contract, "final": final, "select": select}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2207_00933_gb300 import Context
+
+    w = make_workload(args.workload, seed_offset=rank)      # weak scaling: an independent circuit per rank
+    c = w.circuit
+    out_dtype = torch.float64 if args.workload == "grid40_K12_a22" else torch.float32
+    out_b = 8 if out_dtype == torch.float64 else 4
+    stream = torch.cuda.current_stream(dev)
+    ctx = Context(local)
+    probs_dev = [torch.from_numpy(p).to(dev) for p in w.probs]
+    probs_host = [torch.from_numpy(p).pin_memory() for p in w.probs]
+    cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), probs_host)   # host-staged (e2e path)
+    qid, na = ctx.set_qubit_roles(cid, w.roles)
+    bins = 1 << na
+    out = torch.empty(bins, dtype=out_dtype, device=dev)
+    tot = torch.zeros(1, dtype=torch.float64, device=dev)
+    kb = torch.empty(TOPK, dtype=torch.int64, device=dev)
+    kp = torch.empty(TOPK, dtype=torch.float64, device=dev)
+    kn = torch.empty(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.update_subcircuit_outputs(cid, probs_dev)
+        ctx.reconstruct(qid, out, "fp32", tot)
+        ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # correctness of the timed configuration against the FP64 oracle
+    import oracle as O
+    g = O.Graph.from_arrays(c.n_qubits, *c.graph_arrays())
+    ref = O.reconstruct(g, [p.astype(np.float64) for p in w.probs], w.roles)
+    err = float(np.abs(out.double().cpu().numpy() - ref).max())
+
+    steps_shape = ctx.query_steps(qid)
+    info = ctx.query_info(qid)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    ctx.profile_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * bins * args.steps / (total_ms * 1e-3)
+
+    # roofline of the dominant stage
+    algo = algorithmic_bytes(w, steps_shape, out_b)
+    stage_ms = {k: v / max(1, prof["calls"][k]) for k, v in prof["ms"].items() if prof["calls"][k]}
+    share = {k: prof["ms"][k] / max(1e-12, sum(prof["ms"].values())) for k in prof["ms"]}
+    dom = max(stage_ms, key=lambda k: prof["ms"][k])
+    hbm, src = peaks()
+    achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    kernel_of = {"attribute": "fold_kernel+mix_kernel", "merge": "merge_kernel", "contract": "gemm_simt_kernel",
+                 "final": "gemm_simt_kernel (last step)", "select": "radix_pass+compact+sort_emit"}
+    roofline = {"bound": "hbm", "kernel": kernel_of[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "stages": {k: {"us": 1e3 * stage_ms[k], "share": share[k],
+                               "GBps": algo[k] / (stage_ms[k] * 1e-3) / 1e9} for k in stage_ms}}
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    h_bins = torch.empty(TOPK, dtype=torch.int64).pin_memory()
+    h_probs = torch.empty(TOPK, dtype=torch.float64).pin_memory()
+    h_n = torch.empty(1, dtype=torch.int32).pin_memory()
+    h_tot = torch.empty(1, dtype=torch.float64).pin_memory()
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ctx.update_subcircuit_outputs(cid, probs_host)            # H2D of this step's inputs inside
+        ctx.reconstruct(qid, out, "fp32", tot)
+        ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
+        h_bins.copy_(kb, non_blocking=True)
+        h_probs.copy_(kp, non_blocking=True)
+        h_n.copy_(kn, non_blocking=True)
+        h_tot.copy_(tot, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    h2d = sum(p.nbytes for p in w.probs)
+    d2h = TOPK * 8 * 2 + 4 + 8
+
+    if rank == 0:
+        step_sorted = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "bins": bins, "active_qubits": na, "cuts": c.n_edges,
+                       "subcircuits": c.n_subcircuits, "topk": TOPK, "out_dtype": str(out_dtype).split(".")[-1],
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": f"{world} independent circuits" if world > 1 else "1 gpu",
+                       "seed": w.meta.get("seed")},
+            "max_abs_err_vs_fp64": err,
+            "tflops": info["flops"] / (ms_per_step * 1e-3) / 1e12,
+            "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
+                           "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
+            "wall_s": wall,
+            "gpu_launches": prof["launches"],
+            "roofline": roofline,
+            "clocks": clocks,
+            "e2e": {"value": world * bins * args.steps / (e2e_total * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

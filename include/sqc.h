@@ -1,0 +1,228 @@
+/*
+ * sqc.h -- C ABI of the GB300 states-merging reconstruction library.
+ *
+ * The library reconstructs the output of a cut quantum circuit from its
+ * subcircuits' outputs (ScaleQC, arXiv 2207.00933):
+ *
+ *   P[b] = 2^-K  sum_{e in {I,X,Y,Z}^K}  prod_i  T_i[e|_i, b|_i]      (Eq. 1)
+ *
+ * where T_i is subcircuit i's output attributed to the I/X/Y/Z labels of its
+ * cut edges and merged into bins (Section 4, Algorithm 2), and the sum is
+ * evaluated as a sequence of pairwise tensor contractions over the compute
+ * graph (Section 6, Fig. 4-5).  All device work is hand-written CUDA for
+ * sm_103a; there is no CPU fallback: calls fail with SQC_ECUDA when no
+ * usable GPU is present.
+ *
+ * Conventions for every call:
+ *   - Every function returns an sqc_status and never aborts the process.
+ *     sqc_last_error() returns a description of the last failure on the
+ *     context (or of a failed sqc_create when passed NULL).
+ *   - A context is used from one host thread at a time.
+ *   - Device work is enqueued on the caller's `stream` (a cudaStream_t
+ *     passed as void*; NULL = the legacy default stream) and is
+ *     asynchronous unless stated otherwise.
+ *   - "device pointer" arguments point to memory on the context's GPU that
+ *     the caller owns and keeps alive until the work on `stream` completes.
+ *
+ * Index conventions (the input layout a QPU runner produces):
+ *   - Edges are numbered 0..K-1.  Subcircuit i's incident edges are taken
+ *     in ascending edge id.
+ *   - Variant index of subcircuit i: one base-4 digit per incident edge, the
+ *     lowest edge id most significant.  For an edge leaving i (i measures
+ *     the wire) the digit is the measurement basis 0=I, 1=X, 2=Y, 3=Z; for an
+ *     edge entering i (i initialises the wire) it is the prepared state
+ *     0=|0>, 1=|1>, 2=|+>, 3=|+i>.  X is measured after H, Y after S^dagger
+ *     then H; outcome 0 counts +1.
+ *   - Output index of subcircuit i: y = x | c << n_i, x little-endian over
+ *     i's data qubits in the order given by data_qubit[], c little-endian
+ *     over i's outgoing edges in ascending edge id.
+ *   - Reconstructed bin index: little-endian over the ACTIVE original
+ *     qubits in ascending original index.
+ */
+#ifndef SQC_H
+#define SQC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SQC_API __attribute__((visibility("default")))
+
+typedef int32_t sqc_status;
+enum {
+  SQC_OK = 0,
+  SQC_EINVAL = 1,    /* malformed argument or graph                    */
+  SQC_ENOMEM = 2,    /* a device allocation failed                     */
+  SQC_ESHAPE = 3,    /* buffer too small / sizes beyond the limits     */
+  SQC_ECUDA = 4,     /* a CUDA call failed (includes "no GPU")         */
+  SQC_ETIMEOUT = 5,  /* a bounded device wait ran out                  */
+  SQC_EBUSY = 6,     /* admission refused: over the HBM budget         */
+  SQC_ENOTFOUND = 7  /* unknown circuit or query handle                */
+};
+
+typedef enum { SQC_F32 = 0, SQC_F64 = 1 } sqc_dtype;
+
+/* Arithmetic of the contraction steps.  FP32: SIMT FP32 FMA.  SPLIT_BF16:
+ * every operand split into three BF16 terms (hi + mid + lo) and multiplied
+ * on the tcgen05 tensor cores with FP32 accumulation, keeping the six
+ * products of order <= 2 (about FP32 accuracy). */
+typedef enum { SQC_PREC_FP32 = 0, SQC_PREC_SPLIT_BF16 = 1 } sqc_precision;
+
+/* Qubit roles (Section 4): ACTIVE qubits index the output bins, MERGED
+ * qubits are summed inside each bin, ZOOM0/ZOOM1 qubits are fixed to 0/1
+ * (the bin chosen by an earlier recursion). */
+enum { SQC_ROLE_ACTIVE = 0, SQC_ROLE_MERGED = 1, SQC_ROLE_ZOOM0 = 2, SQC_ROLE_ZOOM1 = 3 };
+
+typedef struct sqc_ctx sqc_ctx;
+typedef int64_t sqc_circuit_id;
+typedef int64_t sqc_query_id;
+
+typedef struct {
+  /* Device memory the context may hold for resident subcircuit tensors and
+   * query plans; 0 = no limit.  Exceeding it makes loads and role settings
+   * fail with SQC_EBUSY (admission by HBM footprint). */
+  uint64_t hbm_budget_bytes;
+  /* Largest number of active qubits a query may ask for (2^this bins). */
+  int32_t max_active_qubits;
+  /* Number of cut edges K from which the last contraction step sums its
+   * shared index in FP32 chunks added up in FP64 (the cross-chunk sum). */
+  int32_t fp64_chunk_min_edges;
+  /* FP32 terms summed per chunk before the FP64 addition (>= 16, power of 2). */
+  int32_t chunk_terms;
+  int32_t reserved[5];
+} sqc_config;
+
+/* Compute graph (Section 5, Fig. 3d).  Vertices are subcircuits 0..n_C-1;
+ * edge k runs from subcircuit edge_up[k] (which measures the wire) to
+ * edge_down[k] (which initialises it).  Subcircuit i owns n_data[i] data
+ * qubits; data_qubit[] lists them, subcircuit-major, as original qubit
+ * indices; every original qubit 0..n_qubits-1 appears exactly once.
+ * Limits: n_C <= 64, K <= 60, 4^{k_i} * 2^{w_i} < 2^40 per subcircuit. */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_subcircuits;
+  int32_t n_edges;
+  const int32_t* edge_up;     /* [n_edges]       */
+  const int32_t* edge_down;   /* [n_edges]       */
+  const int32_t* n_data;      /* [n_subcircuits] */
+  const int32_t* data_qubit;  /* [n_qubits]      */
+} sqc_graph;
+
+/* Fill `cfg` with the defaults (no budget, 32 active qubits, FP64 chunking
+ * from 12 edges, 256 terms per chunk). */
+SQC_API void sqc_default_config(sqc_config* cfg);
+
+/* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
+ * Fails with SQC_ECUDA when the device cannot be used.  *out is NULL on
+ * failure; sqc_last_error(NULL) then says why. */
+SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg);
+
+/* Destroy a context and free every device buffer it holds (synchronises
+ * the device first).  NULL is ignored. */
+SQC_API void sqc_destroy(sqc_ctx* ctx);
+
+/* Description of the last failure on ctx (NULL: of the last sqc_create). */
+SQC_API const char* sqc_last_error(const sqc_ctx* ctx);
+
+/* Load one circuit: validate the graph, copy it, and attribute every
+ * subcircuit's variant outputs to its cut-edge labels (Eq. 1; the weights
+ * of Section 2.1 with the I/X/Y/Z expansion of Peng et al.), producing the
+ * resident tensors A_i[4^{k_i}][2^{n_i}] (FP32) that later queries merge.
+ *   probs[i]: subcircuit i's outputs, [4^{k_i}][2^{w_i}] row-major,
+ *             w_i = n_data[i] + #outgoing edges of i, in `dtype`;
+ *             host pointers if probs_on_device == 0 (copied, then
+ *             synchronised), else device pointers (read on `stream`).
+ * On success *out_id names the circuit until sqc_unload. */
+SQC_API sqc_status sqc_load_subcircuit_outputs(sqc_ctx* ctx, const sqc_graph* graph,
+                                               const void* const* probs, sqc_dtype dtype,
+                                               int probs_on_device, sqc_circuit_id* out_id,
+                                               void* stream);
+
+/* Replace a loaded circuit's subcircuit outputs with new ones of the same
+ * shapes (the next recursion's QPU results, Algorithm 1) and re-run the
+ * attribution; allocates nothing.  Same argument meaning as above. */
+SQC_API sqc_status sqc_update_subcircuit_outputs(sqc_ctx* ctx, sqc_circuit_id id,
+                                                 const void* const* probs, sqc_dtype dtype,
+                                                 int probs_on_device, void* stream);
+
+/* Free a circuit and every query made on it. */
+SQC_API sqc_status sqc_unload(sqc_ctx* ctx, sqc_circuit_id id);
+
+/* Fix the qubit roles of one reconstruction (one recursion of Algorithm 1,
+ * bins assigned as in Algorithm 2) and plan it: per-subcircuit merge,
+ * contraction order (greedy on the Section 6.2 cost), layouts, workspace.
+ *   roles: [n_qubits] of SQC_ROLE_*.
+ * Outputs: *out_q (query handle), *n_active (log2 of the bin count).
+ * Fails with SQC_ESHAPE when n_active > cfg.max_active_qubits and with
+ * SQC_EBUSY when the plan's workspace would exceed the HBM budget. */
+SQC_API sqc_status sqc_set_qubit_roles(sqc_ctx* ctx, sqc_circuit_id id, const int8_t* roles,
+                                       sqc_query_id* out_q, int32_t* n_active);
+
+/* Release a query and its workspace. */
+SQC_API sqc_status sqc_release_query(sqc_ctx* ctx, sqc_query_id q);
+
+/* Reconstruct the bin probabilities of query q (Eq. 1 by compute-graph
+ * contraction, Section 6):
+ *   out_bins: device pointer, 2^{n_active} values of out_dtype, bin index
+ *             as in the header comment; out_bytes its size (checked).
+ *   total_prob: nullable device pointer to one double; receives the FP64
+ *             sum of all bins (the per-level probability check).
+ * Merges every subcircuit (Algorithm 2), runs the planned contraction
+ * steps, scales by 2^-K, writes the bins.  With out_dtype = SQC_F64 and
+ * K >= cfg.fp64_chunk_min_edges the last step's shared index is summed in
+ * FP32 chunks accumulated in FP64.  Asynchronous on `stream`. */
+SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id q, sqc_precision precision,
+                                   void* out_bins, sqc_dtype out_dtype, uint64_t out_bytes,
+                                   double* total_prob, void* stream);
+
+/* Select bins (Algorithm 1: keep the largest bins): among the n values at
+ * device pointer `probs` (dtype), those >= threshold, ordered by value
+ * descending then bin index ascending, at most k (1 <= k <= 16384).
+ * Outputs are device pointers: bins_out[k] (uint64), probs_out[k] (double),
+ * n_found[1] (int32).  Uses query q's workspace; calls on the same query
+ * must not overlap on the GPU.  Asynchronous on `stream`. */
+SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id q, const void* probs, sqc_dtype dtype,
+                                uint64_t n, int32_t k, double threshold, uint64_t* bins_out,
+                                double* probs_out, int32_t* n_found, void* stream);
+
+/* Introspection of a planned query (host values, no device work):
+ * n_steps contraction steps; flops = sum of 2*M*N*K over the steps;
+ * merge_bytes = bytes the merge reads and writes; work_bytes = device
+ * workspace held. */
+SQC_API sqc_status sqc_query_info(const sqc_ctx* ctx, sqc_query_id q, int32_t* n_steps, double* flops,
+                                  double* merge_bytes, uint64_t* work_bytes);
+
+/* Shape of contraction step `step` (0-based, in launch order) of query q:
+ * the step computes C[M][N] = sum over Kd of A[M][Kd] * B[N][Kd]
+ * (Section 6.1, Fig. 4a).  Host values, no device work. */
+SQC_API sqc_status sqc_query_step(const sqc_ctx* ctx, sqc_query_id q, int32_t step, int64_t* M, int64_t* N,
+                                  int64_t* Kd);
+
+/* Stage timing (tracing).  When enabled, the library records a pair of CUDA
+ * events on the caller's stream around each stage it launches and counts
+ * its kernel launches.  Stages: */
+enum {
+  SQC_STAGE_ATTRIBUTE = 0,  /* attribution of variant outputs (load/update) */
+  SQC_STAGE_MERGE = 1,      /* merge/zoom of all subcircuits                */
+  SQC_STAGE_CONTRACT = 2,   /* contraction steps except the last            */
+  SQC_STAGE_FINAL = 3,      /* last contraction step (scaled bins, K7 sum)  */
+  SQC_STAGE_SELECT = 4,     /* bin selection                                 */
+  SQC_STAGE_COUNT = 5
+};
+
+/* Turn stage timing on (1) or off (0); turning it on clears the record. */
+SQC_API sqc_status sqc_profile_enable(sqc_ctx* ctx, int on);
+
+/* Read and clear the record: ms[SQC_STAGE_COUNT] total milliseconds per
+ * stage, calls[SQC_STAGE_COUNT] how many times each stage ran, *launches the
+ * number of kernels launched.  Synchronises with the recorded events.  Any
+ * output may be NULL. */
+SQC_API sqc_status sqc_profile_read(sqc_ctx* ctx, double* ms, int64_t* calls, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SQC_H */

@@ -1,0 +1,299 @@
+"""GB300 states-merging reconstruction (ScaleQC, arXiv 2207.00933).
+
+Thin Python binding over the C ABI in ``include/sqc.h``: argument
+marshalling only.  Every step of the reconstruction runs in the CUDA
+library ``libsqc.so`` built from ``csrc/``; PyTorch supplies device memory
+and streams.  Importing works without a GPU; creating a ``Context`` needs
+one and the built library, and fails loudly otherwise (there is no CPU
+fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Sequence
+
+import numpy as np
+
+__all__ = ["Context", "SQCError", "lib_path", "load_library", "ROLE_ACTIVE", "ROLE_MERGED", "ROLE_ZOOM0",
+           "ROLE_ZOOM1", "STATUS"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+ROLE_ACTIVE, ROLE_MERGED, ROLE_ZOOM0, ROLE_ZOOM1 = 0, 1, 2, 3
+F32, F64 = 0, 1
+PREC = {"fp32": 0, "split_bf16": 1}
+STATUS = {0: "SQC_OK", 1: "SQC_EINVAL", 2: "SQC_ENOMEM", 3: "SQC_ESHAPE", 4: "SQC_ECUDA", 5: "SQC_ETIMEOUT",
+          6: "SQC_EBUSY", 7: "SQC_ENOTFOUND"}
+
+
+class SQCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_active_qubits", ctypes.c_int32),
+                ("fp64_chunk_min_edges", ctypes.c_int32), ("chunk_terms", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_subcircuits", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("edge_up", ctypes.POINTER(ctypes.c_int32)), ("edge_down", ctypes.POINTER(ctypes.c_int32)),
+                ("n_data", ctypes.POINTER(ctypes.c_int32)), ("data_qubit", ctypes.POINTER(ctypes.c_int32))]
+
+
+_c = ctypes
+_P = ctypes.c_void_p
+_SIGS = {
+    "sqc_default_config": (None, [_P]),
+    "sqc_create": (_c.c_int32, [_c.POINTER(_P), _c.c_int, _P]),
+    "sqc_destroy": (None, [_P]),
+    "sqc_last_error": (_c.c_char_p, [_P]),
+    "sqc_load_subcircuit_outputs": (_c.c_int32, [_P, _P, _c.POINTER(_P), _c.c_int, _c.c_int,
+                                                 _c.POINTER(_c.c_int64), _P]),
+    "sqc_update_subcircuit_outputs": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_P), _c.c_int, _c.c_int, _P]),
+    "sqc_unload": (_c.c_int32, [_P, _c.c_int64]),
+    "sqc_set_qubit_roles": (_c.c_int32, [_P, _c.c_int64, _P, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int32)]),
+    "sqc_release_query": (_c.c_int32, [_P, _c.c_int64]),
+    "sqc_reconstruct": (_c.c_int32, [_P, _c.c_int64, _c.c_int, _P, _c.c_int, _c.c_uint64, _P, _P]),
+    "sqc_top_bins": (_c.c_int32, [_P, _c.c_int64, _P, _c.c_int, _c.c_uint64, _c.c_int32, _c.c_double, _P, _P,
+                                  _P, _P]),
+    "sqc_query_info": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_double),
+                                    _c.POINTER(_c.c_double), _c.POINTER(_c.c_uint64)]),
+    "sqc_query_step": (_c.c_int32, [_P, _c.c_int64, _c.c_int32, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64),
+                                    _c.POINTER(_c.c_int64)]),
+    "sqc_profile_enable": (_c.c_int32, [_P, _c.c_int]),
+    "sqc_profile_read": (_c.c_int32, [_P, _P, _P, _P]),
+}
+
+STAGES = ("attribute", "merge", "contract", "final", "select")
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libsqc.so")
+
+
+def load_library():
+    """Load libsqc.so (built by ``_build.build()``); raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _ptr(t) -> int:
+    """Device or host address of a torch tensor or numpy array."""
+    if t is None:
+        return 0
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(t) -> int:
+    name = str(t.dtype)
+    if name.endswith("float32"):
+        return F32
+    if name.endswith("float64"):
+        return F64
+    raise TypeError(f"unsupported dtype {t.dtype}: float32 or float64")
+
+
+class Context:
+    """One library context on one GPU (C ABI: sqc_create / sqc_destroy)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_active_qubits: int = 32,
+                 fp64_chunk_min_edges: int = 12, chunk_terms: int = 256):
+        self._lib = load_library()
+        cfg = _Config()
+        self._lib.sqc_default_config(ctypes.byref(cfg))
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.max_active_qubits = max_active_qubits
+        cfg.fp64_chunk_min_edges = fp64_chunk_min_edges
+        cfg.chunk_terms = chunk_terms
+        h = _P()
+        st = self._lib.sqc_create(ctypes.byref(h), device, ctypes.byref(cfg))
+        if st != 0:
+            raise SQCError(st, self._lib.sqc_last_error(None).decode())
+        self._h = h
+        self.device = device
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sqc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int):
+        if st != 0:
+            raise SQCError(st, self._lib.sqc_last_error(self._h).decode())
+
+    # -- circuits ---------------------------------------------------------
+    def load_subcircuit_outputs(self, n_qubits: int, edge_up: Sequence[int], edge_down: Sequence[int],
+                                n_data: Sequence[int], data_qubit: Sequence[int], probs: list, stream=None) -> int:
+        """Attribute and keep resident one circuit's subcircuit outputs.
+        probs: per subcircuit a [4^k_i, 2^w_i] float32/float64 tensor, all on
+        the GPU or all on the host (torch CPU tensor or numpy array)."""
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.int32)) for a in (edge_up, edge_down, n_data, data_qubit)]
+        g = _Graph()
+        g.n_qubits = n_qubits
+        g.n_subcircuits = len(arrs[2])
+        g.n_edges = len(arrs[0])
+        ip = ctypes.POINTER(ctypes.c_int32)
+        g.edge_up, g.edge_down, g.n_data, g.data_qubit = (a.ctypes.data_as(ip) for a in arrs)
+        on_dev, ptrs, dt = self._prob_ptrs(probs)
+        cid = ctypes.c_int64()
+        self._check(self._lib.sqc_load_subcircuit_outputs(self._h, ctypes.byref(g), ptrs, dt, on_dev,
+                                                          ctypes.byref(cid), _stream_handle(stream)))
+        return cid.value
+
+    def update_subcircuit_outputs(self, circuit: int, probs: list, stream=None):
+        on_dev, ptrs, dt = self._prob_ptrs(probs)
+        self._check(self._lib.sqc_update_subcircuit_outputs(self._h, circuit, ptrs, dt, on_dev,
+                                                            _stream_handle(stream)))
+
+    @staticmethod
+    def _prob_ptrs(probs):
+        on_dev = None
+        dt = None
+        ptrs = (ctypes.c_void_p * len(probs))()
+        for i, p in enumerate(probs):
+            dev = (not isinstance(p, np.ndarray)) and p.is_cuda
+            if on_dev is None:
+                on_dev = dev
+            if dev != on_dev:
+                raise ValueError("probs must be all on the GPU or all on the host")
+            d = _dtype_code(p)
+            if dt is None:
+                dt = d
+            if d != dt:
+                raise ValueError("probs must share one dtype")
+            if not (p.flags["C_CONTIGUOUS"] if isinstance(p, np.ndarray) else p.is_contiguous()):
+                raise ValueError("probs must be contiguous")
+            ptrs[i] = _ptr(p)
+        return int(bool(on_dev)), ptrs, dt
+
+    def unload(self, circuit: int):
+        self._check(self._lib.sqc_unload(self._h, circuit))
+
+    # -- queries ----------------------------------------------------------
+    def set_qubit_roles(self, circuit: int, roles) -> tuple[int, int]:
+        r = np.ascontiguousarray(np.asarray(roles, dtype=np.int8))
+        q = ctypes.c_int64()
+        na = ctypes.c_int32()
+        self._check(self._lib.sqc_set_qubit_roles(self._h, circuit, r.ctypes.data, ctypes.byref(q),
+                                                  ctypes.byref(na)))
+        return q.value, na.value
+
+    def release_query(self, query: int):
+        self._check(self._lib.sqc_release_query(self._h, query))
+
+    def query_info(self, query: int) -> dict:
+        ns, fl, mb, wb = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        self._check(self._lib.sqc_query_info(self._h, query, ctypes.byref(ns), ctypes.byref(fl), ctypes.byref(mb),
+                                             ctypes.byref(wb)))
+        return {"n_steps": ns.value, "flops": fl.value, "merge_bytes": mb.value, "work_bytes": wb.value}
+
+    def query_steps(self, query: int) -> list[tuple[int, int, int]]:
+        """(M, N, Kd) of every contraction step, in launch order."""
+        out = []
+        for s in range(self.query_info(query)["n_steps"]):
+            m, n, k = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+            self._check(self._lib.sqc_query_step(self._h, query, s, ctypes.byref(m), ctypes.byref(n), ctypes.byref(k)))
+            out.append((m.value, n.value, k.value))
+        return out
+
+    def reconstruct(self, query: int, out, precision: str = "fp32", total_prob=None, stream=None):
+        """Bins of `query` into the device tensor `out` (float32/float64,
+        2^n_active elements); total_prob: optional device float64 tensor of
+        one element receiving the FP64 sum of the bins."""
+        if not out.is_cuda:
+            raise ValueError("out must be a device tensor")
+        if total_prob is not None and (not total_prob.is_cuda or str(total_prob.dtype) != "torch.float64"):
+            raise ValueError("total_prob must be a device float64 tensor")
+        self._check(self._lib.sqc_reconstruct(self._h, query, PREC[precision], _ptr(out), _dtype_code(out),
+                                              out.numel() * out.element_size(), _ptr(total_prob),
+                                              _stream_handle(stream)))
+
+    def top_bins(self, query: int, probs, k: int, threshold: float = -math.inf, bins_out=None, probs_out=None,
+                 n_found=None, stream=None):
+        """Largest bins of the device tensor `probs` (value descending, bin
+        ascending, values >= threshold, at most k).  Outputs are device
+        tensors (allocated here when not given): (bins int64 [k], probs
+        float64 [k], n_found int32 [1])."""
+        import torch
+        dev = probs.device
+        if bins_out is None:
+            bins_out = torch.empty(k, dtype=torch.int64, device=dev)
+        if probs_out is None:
+            probs_out = torch.empty(k, dtype=torch.float64, device=dev)
+        if n_found is None:
+            n_found = torch.empty(1, dtype=torch.int32, device=dev)
+        self._check(self._lib.sqc_top_bins(self._h, query, _ptr(probs), _dtype_code(probs), probs.numel(), k,
+                                           float(threshold), _ptr(bins_out), _ptr(probs_out), _ptr(n_found),
+                                           _stream_handle(stream)))
+        return bins_out, probs_out, n_found
+
+
+def _profile_enable(self, on: bool = True):
+    """Stage timing on/off (sqc_profile_enable); turning it on clears it."""
+    self._check(self._lib.sqc_profile_enable(self._h, int(on)))
+
+
+def _profile_read(self) -> dict:
+    """Per-stage milliseconds and call counts since the last read, and the
+    number of kernels launched (sqc_profile_read)."""
+    ms = (ctypes.c_double * len(STAGES))()
+    calls = (ctypes.c_int64 * len(STAGES))()
+    launches = ctypes.c_int64()
+    self._check(self._lib.sqc_profile_read(self._h, ms, calls, ctypes.byref(launches)))
+    return {"ms": dict(zip(STAGES, list(ms))), "calls": dict(zip(STAGES, list(calls))),
+            "launches": launches.value}
+
+
+Context.profile_enable = _profile_enable
+Context.profile_read = _profile_read
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared with SQC_API in include/sqc.h."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "sqc.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"SQC_API\s+[\w\s\*]*?\b(sqc_\w+)\s*\(", text)))

@@ -1,0 +1,914 @@
+// C ABI of the reconstruction library: contexts, resident circuits, query
+// planning (merge descriptors, contraction order, layouts) and the
+// per-query launch sequence.  See include/sqc.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/sqc.h"
+#include "internal.h"
+
+using namespace sqc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kBinBase = 1 << 16;   // layout codes: edge bit = 2*eid + (hi?1:0); bin bit = kBinBase + position
+constexpr int kMaxK = 16;           // cut edges per subcircuit
+constexpr int kMaxSub = 64;
+
+struct Circuit {
+  int n_qubits = 0, nC = 0, K = 0;
+  std::vector<int> eu, ed, ndata, dq_flat;
+  std::vector<std::vector<int>> dq, inc, ins, outs;
+  std::vector<int64_t> V;        // 4^k_i
+  std::vector<int> w;            // n_i + kout_i
+  std::vector<float*> A;         // [V_i][2^n_i], data index bit-reversed
+  void* staging = nullptr;       // device copy of one subcircuit's host input
+  size_t staging_bytes = 0;
+  float* scratch = nullptr;      // fold output for subcircuits with incoming edges
+  size_t scratch_floats = 0;
+  size_t bytes = 0;
+};
+
+struct Tensor {
+  std::vector<int> bits;         // unordered set of logical bit codes
+  std::set<int> edges;           // open cut edges
+  std::vector<int> layout;       // layout[p] = code stored at address bit p
+  int producer_sub = -1;         // merge of this subcircuit, or
+  int producer_step = -1;        // output of this step
+  float* buf = nullptr;          // FP32 storage (intermediates)
+};
+
+struct Step {
+  int x = -1, y = -1, z = -1;    // operand tensors (x = A rows, y = B cols after layout) and result
+  std::vector<int> shared;       // shared edge ids
+  int64_t M = 1, N = 1, Kd = 1;
+  uint64_t* rowmap = nullptr;    // device
+  uint64_t* colmap = nullptr;
+  int vec4 = 0;
+};
+
+struct Query {
+  sqc_circuit_id circuit = 0;
+  std::vector<int8_t> roles;
+  int n_active = 0;
+  int64_t out_elems = 1;
+  std::vector<Tensor> tensors;
+  std::vector<Step> steps;
+  int final_tensor = -1;
+  std::vector<MergeDesc> merge_host;
+  MergeDesc* merge_dev = nullptr;
+  int64_t merge_blocks = 0;
+  int final_merge = -1;          // descriptor index writing the output when there are no steps
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  SelectWork sel{};
+  double flops = 0.0, merge_bytes = 0.0;
+};
+
+}  // namespace
+
+struct StageMark {
+  int stage;
+  cudaEvent_t start, stop;
+};
+
+struct sqc_ctx {
+  int device = 0;
+  bool prof = false;
+  std::vector<StageMark> marks;
+  std::vector<cudaEvent_t> event_pool;
+  int64_t launches = 0;
+  sqc_config cfg{};
+  std::string err;
+  size_t bytes = 0;
+  int64_t next_id = 1;
+  std::map<int64_t, std::unique_ptr<Circuit>> circuits;
+  std::map<int64_t, std::unique_ptr<Query>> queries;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+sqc_status fail(sqc_ctx* ctx, sqc_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg; else g_create_error = msg;
+  return st;
+}
+
+sqc_status cuda_fail(sqc_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, SQC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
+  } while (0)
+
+cudaEvent_t take_event(sqc_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Scope that brackets one stage with events when timing is on.
+struct StageScope {
+  sqc_ctx* ctx;
+  cudaStream_t s;
+  int stage;
+  cudaEvent_t a = nullptr, b = nullptr;
+  StageScope(sqc_ctx* c, cudaStream_t st, int stg) : ctx(c), s(st), stage(stg) {
+    if (ctx->prof) {
+      a = take_event(ctx);
+      b = take_event(ctx);
+      if (a) cudaEventRecord(a, s);
+    }
+  }
+  ~StageScope() {
+    if (a && b) {
+      cudaEventRecord(b, s);
+      ctx->marks.push_back({stage, a, b});
+    }
+  }
+};
+
+sqc_status dev_alloc(sqc_ctx* ctx, void** p, size_t bytes, bool admit = true) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (admit && ctx->cfg.hbm_budget_bytes && ctx->bytes + bytes > ctx->cfg.hbm_budget_bytes)
+    return fail(ctx, SQC_EBUSY, "HBM budget exceeded: " + std::to_string(ctx->bytes + bytes) + " > " +
+                                     std::to_string(ctx->cfg.hbm_budget_bytes) + " bytes");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, SQC_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  ctx->bytes += bytes;
+  return SQC_OK;
+}
+
+void dev_free(sqc_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  cudaFree(p);
+  ctx->bytes = ctx->bytes >= bytes ? ctx->bytes - bytes : 0;
+}
+
+inline int popc32(uint32_t x) { return __builtin_popcount(x); }
+
+// ---- graph validation ---------------------------------------------------------
+
+sqc_status build_circuit(sqc_ctx* ctx, const sqc_graph* g, Circuit* c) {
+  if (!g || g->n_qubits < 1 || g->n_subcircuits < 1 || g->n_edges < 0)
+    return fail(ctx, SQC_EINVAL, "graph: need n_qubits >= 1, n_subcircuits >= 1, n_edges >= 0");
+  if (g->n_subcircuits > kMaxSub) return fail(ctx, SQC_ESHAPE, "graph: more than 64 subcircuits");
+  if (g->n_edges > 60) return fail(ctx, SQC_ESHAPE, "graph: more than 60 cut edges");
+  if (!g->n_data || !g->data_qubit || (g->n_edges > 0 && (!g->edge_up || !g->edge_down)))
+    return fail(ctx, SQC_EINVAL, "graph: null array");
+  c->n_qubits = g->n_qubits;
+  c->nC = g->n_subcircuits;
+  c->K = g->n_edges;
+  c->eu.assign(g->edge_up, g->edge_up + g->n_edges);
+  c->ed.assign(g->edge_down, g->edge_down + g->n_edges);
+  c->ndata.assign(g->n_data, g->n_data + g->n_subcircuits);
+  int64_t tot = 0;
+  for (int i = 0; i < c->nC; ++i) {
+    if (c->ndata[i] < 0 || c->ndata[i] > 30) return fail(ctx, SQC_ESHAPE, "graph: n_data[i] must be in [0, 30]");
+    tot += c->ndata[i];
+  }
+  if (tot != c->n_qubits) return fail(ctx, SQC_EINVAL, "graph: sum of n_data must equal n_qubits");
+  c->dq_flat.assign(g->data_qubit, g->data_qubit + c->n_qubits);
+  std::vector<int> seen(c->n_qubits, 0);
+  c->dq.resize(c->nC);
+  int off = 0;
+  for (int i = 0; i < c->nC; ++i) {
+    for (int t = 0; t < c->ndata[i]; ++t) {
+      const int q = c->dq_flat[off + t];
+      if (q < 0 || q >= c->n_qubits || seen[q]) return fail(ctx, SQC_EINVAL, "graph: data_qubit must be a permutation of 0..n_qubits-1");
+      seen[q] = 1;
+      c->dq[i].push_back(q);
+    }
+    off += c->ndata[i];
+  }
+  c->inc.assign(c->nC, {});
+  c->ins.assign(c->nC, {});
+  c->outs.assign(c->nC, {});
+  for (int e = 0; e < c->K; ++e) {
+    const int u = c->eu[e], d = c->ed[e];
+    if (u < 0 || u >= c->nC || d < 0 || d >= c->nC) return fail(ctx, SQC_EINVAL, "graph: edge endpoint out of range");
+    if (u == d) return fail(ctx, SQC_EINVAL, "graph: an edge must join two different subcircuits");
+    c->outs[u].push_back(e);
+    c->ins[d].push_back(e);
+  }
+  c->V.resize(c->nC);
+  c->w.resize(c->nC);
+  for (int i = 0; i < c->nC; ++i) {
+    std::set<int> s(c->ins[i].begin(), c->ins[i].end());
+    s.insert(c->outs[i].begin(), c->outs[i].end());
+    c->inc[i].assign(s.begin(), s.end());
+    const int k = int(c->inc[i].size());
+    if (k > kMaxK) return fail(ctx, SQC_ESHAPE, "graph: more than 16 cut edges on one subcircuit");
+    c->V[i] = int64_t(1) << (2 * k);
+    c->w[i] = c->ndata[i] + int(c->outs[i].size());
+    if (2 * k + c->w[i] >= 40) return fail(ctx, SQC_ESHAPE, "graph: subcircuit input beyond 2^40 values");
+  }
+  return SQC_OK;
+}
+
+int digit_shift(const Circuit& c, int i, int eid) {
+  const auto& inc = c.inc[i];
+  const int k = int(inc.size());
+  const int p = int(std::find(inc.begin(), inc.end(), eid) - inc.begin());
+  return 2 * (k - 1 - p);
+}
+
+sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc_dtype dtype, int on_device,
+                         cudaStream_t s) {
+  const size_t esz = dtype == SQC_F64 ? 8 : 4;
+  for (int i = 0; i < c->nC; ++i)
+    if (!probs[i]) return fail(ctx, SQC_EINVAL, "probs[i] is null");
+  StageScope scope(ctx, s, SQC_STAGE_ATTRIBUTE);
+  for (int i = 0; i < c->nC; ++i) {
+    const size_t nbytes = size_t(c->V[i]) * (size_t(1) << c->w[i]) * esz;
+    const void* src = probs[i];
+    if (!on_device) {
+      CK(cudaMemcpyAsync(c->staging, probs[i], nbytes, cudaMemcpyHostToDevice, s));
+      src = c->staging;
+    }
+    const int n = c->ndata[i];
+    FoldArgs fa{};
+    fa.p = src;
+    fa.in_f64 = dtype == SQC_F64;
+    fa.V = c->V[i];
+    fa.n = n;
+    fa.kout = int(c->outs[i].size());
+    for (int u = 0; u < fa.kout; ++u) fa.outshift[u] = digit_shift(*c, i, c->outs[i][u]);
+    const int kin = int(c->ins[i].size());
+    fa.B = kin ? c->scratch : c->A[i];
+    CK(launch_fold(fa, s));
+    ctx->launches += 1;
+    if (kin) {
+      MixArgs ma{};
+      ma.B = c->scratch;
+      ma.A = c->A[i];
+      ma.rows = c->V[i];
+      ma.n = n;
+      ma.kin = kin;
+      for (int t = 0; t < kin; ++t) ma.inshift[t] = digit_shift(*c, i, c->ins[i][t]);
+      CK(launch_mix(ma, s));
+      ctx->launches += 1;
+    }
+  }
+  if (!on_device) CK(cudaStreamSynchronize(s));
+  return SQC_OK;
+}
+
+void free_query(sqc_ctx* ctx, Query* q) {
+  dev_free(ctx, q->work, q->work_bytes);
+  q->work = nullptr;
+}
+
+void free_circuit(sqc_ctx* ctx, Circuit* c) {
+  for (int i = 0; i < c->nC; ++i)
+    if (c->A[i]) dev_free(ctx, c->A[i], size_t(c->V[i]) * (size_t(1) << c->ndata[i]) * 4);
+  dev_free(ctx, c->staging, c->staging_bytes);
+  dev_free(ctx, c->scratch, c->scratch_floats * 4);
+}
+
+// ---- planning -------------------------------------------------------------------
+
+struct MapBuild {
+  std::vector<uint64_t> host;   // all maps, concatenated
+  size_t add(const std::vector<uint64_t>& m) {
+    const size_t off = host.size();
+    host.insert(host.end(), m.begin(), m.end());
+    return off;
+  }
+};
+
+// offset contribution of an index whose bit p holds logical code codes[p]
+std::vector<uint64_t> make_map(const std::vector<int>& codes, const std::map<int, int>& pos) {
+  const size_t n = size_t(1) << codes.size();
+  std::vector<uint64_t> m(n, 0);
+  std::vector<uint64_t> w(codes.size());
+  for (size_t p = 0; p < codes.size(); ++p) w[p] = uint64_t(1) << pos.at(codes[p]);
+  for (size_t i = 1; i < n; ++i) m[i] = m[i & (i - 1)] | w[size_t(__builtin_ctzll(i))];
+  return m;
+}
+
+std::map<int, int> positions(const std::vector<int>& layout) {
+  std::map<int, int> pos;
+  for (size_t p = 0; p < layout.size(); ++p) pos[layout[p]] = int(p);
+  return pos;
+}
+
+sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
+  const int nC = c.nC;
+  // canonical position of each active qubit
+  std::vector<int> canon(c.n_qubits, -1);
+  int na = 0;
+  for (int qb = 0; qb < c.n_qubits; ++qb)
+    if (q->roles[qb] == SQC_ROLE_ACTIVE) canon[qb] = na++;
+  q->n_active = na;
+  q->out_elems = int64_t(1) << na;
+
+  // subcircuit tensors T_i and the merge index codes
+  q->tensors.assign(nC, Tensor{});
+  std::vector<std::vector<int>> row_codes(nC), col_codes(nC);
+  q->merge_host.assign(nC, MergeDesc{});
+  for (int i = 0; i < nC; ++i) {
+    const int n = c.ndata[i];
+    const int k = int(c.inc[i].size());
+    uint32_t act = 0, mer = 0, zval = 0;
+    for (int t = 0; t < n; ++t) {
+      const int qb = c.dq[i][t];
+      const uint32_t bit = 1u << (n - 1 - t);   // storage order is bit-reversed
+      switch (q->roles[qb]) {
+        case SQC_ROLE_ACTIVE: act |= bit; break;
+        case SQC_ROLE_MERGED: mer |= bit; break;
+        case SQC_ROLE_ZOOM1: zval |= bit; break;
+        default: break;
+      }
+    }
+    Tensor& T = q->tensors[i];
+    T.producer_sub = i;
+    // row index e: incident edge p's digit at bits 2(k-1-p) (lo) and 2(k-1-p)+1 (hi)
+    row_codes[i].assign(2 * k, 0);
+    for (int p = 0; p < k; ++p) {
+      const int eid = c.inc[i][p];
+      row_codes[i][2 * (k - 1 - p)] = 2 * eid;
+      row_codes[i][2 * (k - 1 - p) + 1] = 2 * eid + 1;
+      T.edges.insert(eid);
+    }
+    // column index b: u-th lowest active storage bit
+    for (int sp = 0; sp < n; ++sp)
+      if ((act >> sp) & 1) {
+        const int t = n - 1 - sp;
+        col_codes[i].push_back(kBinBase + canon[c.dq[i][t]]);
+      }
+    T.bits = row_codes[i];
+    T.bits.insert(T.bits.end(), col_codes[i].begin(), col_codes[i].end());
+    MergeDesc& d = q->merge_host[i];
+    d.A = c.A[i];
+    d.rows = c.V[i];
+    d.n = n;
+    d.act_mask = act;
+    d.mer_mask = mer;
+    d.zoom_val = zval;
+    d.a = popc32(act);
+    d.m = popc32(mer);
+    d.fast = (mer == ((1u << d.m) - 1u)) && (act == (((1u << d.a) - 1u) << d.m));
+    const uint32_t run = 1u << d.m;
+    int lanes = d.fast ? int(run / 16) : int(run / 4);
+    lanes = std::max(1, std::min(32, lanes));
+    d.lanes = lanes;
+    d.alpha = 1.0;
+    q->merge_bytes += double(d.rows) * double(int64_t(1) << (d.a + d.m)) * 4.0 + double(d.rows << d.a) * 4.0;
+  }
+
+  // greedy contraction order on the Section 6.2 cost (multiplications)
+  std::vector<int> alive;
+  for (int i = 0; i < nC; ++i) alive.push_back(i);
+  while (alive.size() > 1) {
+    int bx = -1, by = -1;
+    double best = 0, best_out = 0;
+    bool best_conn = false;
+    for (size_t a = 0; a < alive.size(); ++a)
+      for (size_t b = a + 1; b < alive.size(); ++b) {
+        const Tensor& X = q->tensors[alive[a]];
+        const Tensor& Y = q->tensors[alive[b]];
+        int sh = 0;
+        for (int e : X.edges) sh += Y.edges.count(e);
+        const bool conn = sh > 0;
+        const double fx = double(X.bits.size()) - 2.0 * sh, fy = double(Y.bits.size()) - 2.0 * sh;
+        const double out = std::ldexp(1.0, int(fx + fy));
+        const double cost = std::ldexp(1.0, int(fx + fy + 2 * sh));
+        bool better;
+        if (bx < 0) better = true;
+        else if (conn != best_conn) better = conn;
+        else better = cost < best || (cost == best && out < best_out);
+        if (better) {
+          bx = alive[a]; by = alive[b]; best = cost; best_out = out; best_conn = conn;
+        }
+      }
+    Step st;
+    st.x = bx;
+    st.y = by;
+    Tensor Z;
+    const Tensor& X = q->tensors[bx];
+    const Tensor& Y = q->tensors[by];
+    for (int e : X.edges)
+      if (Y.edges.count(e)) st.shared.push_back(e);
+    std::set<int> shcodes;
+    for (int e : st.shared) { shcodes.insert(2 * e); shcodes.insert(2 * e + 1); }
+    for (int b : X.bits) if (!shcodes.count(b)) Z.bits.push_back(b);
+    for (int b : Y.bits) if (!shcodes.count(b)) Z.bits.push_back(b);
+    for (int e : X.edges) if (!Y.edges.count(e)) Z.edges.insert(e);
+    for (int e : Y.edges) if (!X.edges.count(e)) Z.edges.insert(e);
+    Z.producer_step = int(q->steps.size());
+    st.z = int(q->tensors.size());
+    q->tensors.push_back(Z);
+    q->steps.push_back(st);
+    alive.erase(std::find(alive.begin(), alive.end(), bx));
+    alive.erase(std::find(alive.begin(), alive.end(), by));
+    alive.push_back(st.z);
+  }
+  q->final_tensor = alive[0];
+  {
+    Tensor& F = q->tensors[q->final_tensor];
+    if (!F.edges.empty()) return fail(ctx, SQC_EINVAL, "plan: open edges left after contraction");
+    F.layout.resize(na);
+    for (int p = 0; p < na; ++p) F.layout[p] = kBinBase + p;
+    if (int(F.bits.size()) != na) return fail(ctx, SQC_EINVAL, "plan: result bits do not match active qubits");
+  }
+
+  // layouts, from the result backwards; maps and dimensions of every step
+  MapBuild maps;
+  std::vector<std::pair<size_t, size_t>> step_map_off(q->steps.size());
+  for (int s = int(q->steps.size()) - 1; s >= 0; --s) {
+    Step& st = q->steps[s];
+    const Tensor& Z = q->tensors[st.z];
+    const std::map<int, int> zpos = positions(Z.layout);
+    std::set<int> shcodes;
+    for (int e : st.shared) { shcodes.insert(2 * e); shcodes.insert(2 * e + 1); }
+    auto free_of = [&](int t) {
+      std::vector<int> f;
+      for (int b : q->tensors[t].bits) if (!shcodes.count(b)) f.push_back(b);
+      std::sort(f.begin(), f.end(), [&](int a, int b) { return zpos.at(a) < zpos.at(b); });
+      return f;
+    };
+    std::vector<int> fx = free_of(st.x), fy = free_of(st.y);
+    // B (columns) = the operand that owns the result's lowest address bit,
+    // so that consecutive columns land on consecutive addresses
+    bool swap = false;
+    if (!Z.layout.empty()) {
+      const int low = Z.layout[0];
+      swap = std::find(fx.begin(), fx.end(), low) != fx.end();
+    } else {
+      swap = fx.size() < fy.size();
+    }
+    if (swap) { std::swap(st.x, st.y); std::swap(fx, fy); }
+    std::vector<int> sh(shcodes.begin(), shcodes.end());
+    q->tensors[st.x].layout = sh;
+    q->tensors[st.x].layout.insert(q->tensors[st.x].layout.end(), fx.begin(), fx.end());
+    q->tensors[st.y].layout = sh;
+    q->tensors[st.y].layout.insert(q->tensors[st.y].layout.end(), fy.begin(), fy.end());
+    st.Kd = int64_t(1) << sh.size();
+    st.M = int64_t(1) << fx.size();
+    st.N = int64_t(1) << fy.size();
+    const std::vector<uint64_t> rm = make_map(fx, zpos), cm = make_map(fy, zpos);
+    bool v4 = st.N % 4 == 0;
+    for (size_t j = 0; v4 && j < cm.size(); ++j)
+      if (cm[j] != cm[j & ~size_t(3)] + (j & 3) || (cm[j & ~size_t(3)] & 3)) v4 = false;
+    for (size_t i = 0; v4 && i < rm.size(); ++i)
+      if (rm[i] & 3) v4 = false;
+    st.vec4 = v4;
+    step_map_off[s] = {maps.add(rm), maps.add(cm)};
+    q->flops += 2.0 * double(st.M) * double(st.N) * double(st.Kd);
+  }
+  std::vector<std::pair<size_t, size_t>> merge_map_off(nC);
+  for (int i = 0; i < nC; ++i) {
+    const std::map<int, int> tpos = positions(q->tensors[i].layout);
+    merge_map_off[i] = {maps.add(make_map(row_codes[i], tpos)), maps.add(make_map(col_codes[i], tpos))};
+  }
+
+  // workspace: descriptors | maps | tensors | partials + counter | selection
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t off_desc = off; off = align(off + sizeof(MergeDesc) * nC);
+  const size_t off_maps = off; off = align(off + sizeof(uint64_t) * maps.host.size());
+  std::vector<size_t> off_tensor(q->tensors.size(), 0);
+  for (size_t t = 0; t < q->tensors.size(); ++t) {
+    if (int(t) == q->final_tensor) continue;
+    off_tensor[t] = off;
+    off = align(off + sizeof(float) * (size_t(1) << q->tensors[t].bits.size()));
+  }
+  int64_t max_tiles = 1024;
+  for (const Step& st : q->steps) max_tiles = std::max<int64_t>(max_tiles, ((st.M + 31) / 32) * ((st.N + 31) / 32));
+  const size_t off_part = off; off = align(off + sizeof(double) * size_t(max_tiles));
+  const size_t off_cnt = off; off = align(off + 64);
+  const int sel_blocks = 1024;
+  const size_t off_sel = off; off = align(off + select_work_bytes(0, sel_blocks));
+  q->work_bytes = off;
+  sqc_status st = dev_alloc(ctx, &q->work, off);
+  if (st != SQC_OK) return st;
+  char* base = static_cast<char*>(q->work);
+  q->merge_dev = reinterpret_cast<MergeDesc*>(base + off_desc);
+  uint64_t* maps_dev = reinterpret_cast<uint64_t*>(base + off_maps);
+  for (size_t t = 0; t < q->tensors.size(); ++t)
+    if (int(t) != q->final_tensor) q->tensors[t].buf = reinterpret_cast<float*>(base + off_tensor[t]);
+  q->partials = reinterpret_cast<double*>(base + off_part);
+  q->counter = reinterpret_cast<unsigned*>(base + off_cnt);
+  select_work_carve(base + off_sel, 0, sel_blocks, &q->sel);
+
+  for (size_t s = 0; s < q->steps.size(); ++s) {
+    q->steps[s].rowmap = maps_dev + step_map_off[s].first;
+    q->steps[s].colmap = maps_dev + step_map_off[s].second;
+  }
+  int64_t blocks = 0;
+  for (int i = 0; i < nC; ++i) {
+    MergeDesc& d = q->merge_host[i];
+    d.rowmap = maps_dev + merge_map_off[i].first;
+    d.colmap = maps_dev + merge_map_off[i].second;
+    d.dst = q->tensors[i].buf;          // null for the result (set per call)
+    d.kind = OUT_F32;
+    d.plane_stride = 0;
+    d.block_begin = blocks;
+    const int64_t outs = d.rows << d.a;
+    const int64_t per = 256 / d.lanes;
+    blocks += (outs + per - 1) / per;
+  }
+  q->merge_blocks = blocks;
+  q->final_merge = q->steps.empty() ? 0 : -1;
+  cudaError_t e = cudaMemcpy(maps_dev, maps.host.data(), sizeof(uint64_t) * maps.host.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nC > 0)
+    e = cudaMemcpy(q->merge_dev, q->merge_host.data(), sizeof(MergeDesc) * nC, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(base + off_cnt, 0, 64);
+  if (e == cudaSuccess) e = cudaMemset(base + off_sel, 0, select_work_bytes(0, sel_blocks));
+  if (e != cudaSuccess) {
+    free_query(ctx, q);
+    return cuda_fail(ctx, e, "plan upload");
+  }
+  return SQC_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI =====
+
+extern "C" {
+
+SQC_API void sqc_default_config(sqc_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->hbm_budget_bytes = 0;
+  cfg->max_active_qubits = 32;
+  cfg->fp64_chunk_min_edges = 12;
+  cfg->chunk_terms = 256;
+}
+
+SQC_API const char* sqc_last_error(const sqc_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg) {
+  if (!out) return fail(nullptr, SQC_EINVAL, "out is null");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(nullptr, SQC_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= n) return fail(nullptr, SQC_EINVAL, "device index out of range");
+  cudaDeviceProp prop{};
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return fail(nullptr, SQC_ECUDA, cudaGetErrorString(e));
+  if (prop.major < 10) return fail(nullptr, SQC_ECUDA, std::string("device is not a Blackwell GPU: ") + prop.name);
+  auto ctx = std::make_unique<sqc_ctx>();
+  ctx->device = device;
+  sqc_default_config(&ctx->cfg);
+  if (cfg) ctx->cfg = *cfg;
+  if (ctx->cfg.max_active_qubits < 0 || ctx->cfg.max_active_qubits > 40)
+    return fail(nullptr, SQC_EINVAL, "max_active_qubits must be in [0, 40]");
+  if (ctx->cfg.chunk_terms < 16 || (ctx->cfg.chunk_terms & (ctx->cfg.chunk_terms - 1)))
+    return fail(nullptr, SQC_EINVAL, "chunk_terms must be a power of two >= 16");
+  DeviceGuard g(device);
+  e = select_configure();
+  if (e != cudaSuccess) return fail(nullptr, SQC_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(e));
+  *out = ctx.release();
+  return SQC_OK;
+}
+
+SQC_API void sqc_destroy(sqc_ctx* ctx) {
+  if (!ctx) return;
+  {
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->queries) free_query(ctx, kv.second.get());
+    for (auto& kv : ctx->circuits) free_circuit(ctx, kv.second.get());
+    for (auto& m : ctx->marks) {
+      cudaEventDestroy(m.start);
+      cudaEventDestroy(m.stop);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  }
+  delete ctx;
+}
+
+SQC_API sqc_status sqc_load_subcircuit_outputs(sqc_ctx* ctx, const sqc_graph* graph, const void* const* probs,
+                                               sqc_dtype dtype, int probs_on_device, sqc_circuit_id* out_id,
+                                               void* stream) {
+  if (!ctx || !out_id || !probs) return fail(ctx, SQC_EINVAL, "null argument");
+  if (dtype != SQC_F32 && dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "dtype must be SQC_F32 or SQC_F64");
+  DeviceGuard g(ctx->device);
+  auto c = std::make_unique<Circuit>();
+  sqc_status st = build_circuit(ctx, graph, c.get());
+  if (st != SQC_OK) return st;
+  c->A.assign(c->nC, nullptr);
+  size_t stage = 0, scratch = 0;
+  for (int i = 0; i < c->nC; ++i) {
+    stage = std::max(stage, size_t(c->V[i]) * (size_t(1) << c->w[i]) * (dtype == SQC_F64 ? 8 : 4));
+    if (!c->ins[i].empty()) scratch = std::max(scratch, size_t(c->V[i]) << c->ndata[i]);
+  }
+  auto cleanup = [&](sqc_status s) {
+    free_circuit(ctx, c.get());
+    return s;
+  };
+  for (int i = 0; i < c->nC; ++i) {
+    void* p = nullptr;
+    st = dev_alloc(ctx, &p, size_t(c->V[i]) * (size_t(1) << c->ndata[i]) * 4);
+    if (st != SQC_OK) return cleanup(st);
+    c->A[i] = static_cast<float*>(p);
+  }
+  if (!probs_on_device) {
+    c->staging_bytes = stage;
+    st = dev_alloc(ctx, &c->staging, stage);
+    if (st != SQC_OK) return cleanup(st);
+  }
+  if (scratch) {
+    c->scratch_floats = scratch;
+    void* p = nullptr;
+    st = dev_alloc(ctx, &p, scratch * 4);
+    if (st != SQC_OK) return cleanup(st);
+    c->scratch = static_cast<float*>(p);
+  }
+  st = attribute_all(ctx, c.get(), probs, dtype, probs_on_device, static_cast<cudaStream_t>(stream));
+  if (st != SQC_OK) return cleanup(st);
+  const int64_t id = ctx->next_id++;
+  ctx->circuits[id] = std::move(c);
+  *out_id = id;
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_update_subcircuit_outputs(sqc_ctx* ctx, sqc_circuit_id id, const void* const* probs,
+                                                 sqc_dtype dtype, int probs_on_device, void* stream) {
+  if (!ctx || !probs) return fail(ctx, SQC_EINVAL, "null argument");
+  auto it = ctx->circuits.find(id);
+  if (it == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "unknown circuit");
+  Circuit* c = it->second.get();
+  if (dtype != SQC_F32 && dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "dtype must be SQC_F32 or SQC_F64");
+  if (!probs_on_device) {
+    size_t need = 0;
+    for (int i = 0; i < c->nC; ++i)
+      need = std::max(need, size_t(c->V[i]) * (size_t(1) << c->w[i]) * (dtype == SQC_F64 ? 8 : 4));
+    if (need > c->staging_bytes)
+      return fail(ctx, SQC_ESHAPE, "host-input update needs the circuit loaded from host data in this dtype");
+  }
+  DeviceGuard g(ctx->device);
+  return attribute_all(ctx, c, probs, dtype, probs_on_device, static_cast<cudaStream_t>(stream));
+}
+
+SQC_API sqc_status sqc_unload(sqc_ctx* ctx, sqc_circuit_id id) {
+  if (!ctx) return SQC_EINVAL;
+  auto it = ctx->circuits.find(id);
+  if (it == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "unknown circuit");
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto q = ctx->queries.begin(); q != ctx->queries.end();) {
+    if (q->second->circuit == id) {
+      free_query(ctx, q->second.get());
+      q = ctx->queries.erase(q);
+    } else {
+      ++q;
+    }
+  }
+  free_circuit(ctx, it->second.get());
+  ctx->circuits.erase(it);
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_set_qubit_roles(sqc_ctx* ctx, sqc_circuit_id id, const int8_t* roles, sqc_query_id* out_q,
+                                       int32_t* n_active) {
+  if (!ctx || !roles || !out_q) return fail(ctx, SQC_EINVAL, "null argument");
+  auto it = ctx->circuits.find(id);
+  if (it == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "unknown circuit");
+  const Circuit& c = *it->second;
+  int na = 0;
+  for (int qb = 0; qb < c.n_qubits; ++qb) {
+    if (roles[qb] < SQC_ROLE_ACTIVE || roles[qb] > SQC_ROLE_ZOOM1) return fail(ctx, SQC_EINVAL, "role out of range");
+    na += roles[qb] == SQC_ROLE_ACTIVE;
+  }
+  if (na > ctx->cfg.max_active_qubits)
+    return fail(ctx, SQC_ESHAPE, "active qubits " + std::to_string(na) + " > max_active_qubits");
+  DeviceGuard g(ctx->device);
+  auto q = std::make_unique<Query>();
+  q->circuit = id;
+  q->roles.assign(roles, roles + c.n_qubits);
+  sqc_status st = plan_query(ctx, c, q.get());
+  if (st != SQC_OK) return st;
+  const int64_t qid = ctx->next_id++;
+  if (n_active) *n_active = q->n_active;
+  ctx->queries[qid] = std::move(q);
+  *out_q = qid;
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_release_query(sqc_ctx* ctx, sqc_query_id qid) {
+  if (!ctx) return SQC_EINVAL;
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  free_query(ctx, it->second.get());
+  ctx->queries.erase(it);
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_query_info(const sqc_ctx* cctx, sqc_query_id qid, int32_t* n_steps, double* flops,
+                                  double* merge_bytes, uint64_t* work_bytes) {
+  sqc_ctx* ctx = const_cast<sqc_ctx*>(cctx);
+  if (!ctx) return SQC_EINVAL;
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  const Query& q = *it->second;
+  if (n_steps) *n_steps = int32_t(q.steps.size());
+  if (flops) *flops = q.flops;
+  if (merge_bytes) *merge_bytes = q.merge_bytes;
+  if (work_bytes) *work_bytes = q.work_bytes;
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_query_step(const sqc_ctx* cctx, sqc_query_id qid, int32_t step, int64_t* M, int64_t* N,
+                                  int64_t* Kd) {
+  sqc_ctx* ctx = const_cast<sqc_ctx*>(cctx);
+  if (!ctx) return SQC_EINVAL;
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  const Query& q = *it->second;
+  if (step < 0 || step >= int32_t(q.steps.size())) return fail(ctx, SQC_EINVAL, "step out of range");
+  if (M) *M = q.steps[step].M;
+  if (N) *N = q.steps[step].N;
+  if (Kd) *Kd = q.steps[step].Kd;
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
+                                   sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream) {
+  if (!ctx || !out_bins) return fail(ctx, SQC_EINVAL, "null argument");
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  Query& q = *it->second;
+  auto cit = ctx->circuits.find(q.circuit);
+  if (cit == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "circuit of the query was unloaded");
+  const Circuit& c = *cit->second;
+  if (out_dtype != SQC_F32 && out_dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "out_dtype must be F32 or F64");
+  if (precision != SQC_PREC_FP32)
+    return fail(ctx, SQC_EINVAL, "precision: only SQC_PREC_FP32 is available in this build");
+  const uint64_t need = uint64_t(q.out_elems) * (out_dtype == SQC_F64 ? 8 : 4);
+  if (out_bytes < need)
+    return fail(ctx, SQC_ESHAPE, "out_bytes " + std::to_string(out_bytes) + " < " + std::to_string(need));
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int out_kind = out_dtype == SQC_F64 ? OUT_F64 : OUT_F32;
+  const double alpha = std::ldexp(1.0, -c.K);
+
+  if (q.steps.empty()) {
+    // one subcircuit: the merge writes the bins directly
+    MergeDesc d = q.merge_host[0];
+    d.dst = out_bins;
+    d.kind = out_kind;
+    d.alpha = alpha;
+    CK(cudaMemcpyAsync(q.merge_dev, &d, sizeof(MergeDesc), cudaMemcpyHostToDevice, s));
+    {
+      StageScope scope(ctx, s, SQC_STAGE_MERGE);
+      CK(launch_merge_blocks(q.merge_dev, int(q.merge_host.size()), q.merge_blocks, s));
+      ctx->launches += 1;
+    }
+    if (total_prob) {
+      StageScope scope(ctx, s, SQC_STAGE_FINAL);
+      CK(launch_sum(out_bins, out_dtype == SQC_F64, uint64_t(q.out_elems), q.partials, q.counter, total_prob, s));
+      ctx->launches += 1;
+    }
+    return SQC_OK;
+  }
+  {
+    StageScope scope(ctx, s, SQC_STAGE_MERGE);
+    CK(launch_merge_blocks(q.merge_dev, int(q.merge_host.size()), q.merge_blocks, s));
+    ctx->launches += 1;
+  }
+  for (size_t si = 0; si < q.steps.size(); ++si) {
+    const Step& st = q.steps[si];
+    const bool last = int(si) == int(q.steps.size()) - 1;
+    GemmArgs a{};
+    a.A = q.tensors[st.x].buf;
+    a.B = q.tensors[st.y].buf;
+    a.M = st.M;
+    a.N = st.N;
+    a.K = st.Kd;
+    a.rowmap = st.rowmap;
+    a.colmap = st.colmap;
+    a.vec4 = st.vec4;
+    if (last) {
+      a.C = out_bins;
+      a.kind = out_kind;
+      a.alpha = alpha;
+      a.chunk = (out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
+                    ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
+                    : 0;
+      a.partials = total_prob ? q.partials : nullptr;
+      a.counter = q.counter;
+      a.total = total_prob;
+    } else {
+      a.C = q.tensors[st.z].buf;
+      a.kind = OUT_F32;
+      a.alpha = 1.0;
+      a.chunk = 0;
+    }
+    StageScope scope(ctx, s, last ? SQC_STAGE_FINAL : SQC_STAGE_CONTRACT);
+    CK(launch_gemm_simt(a, s));
+    ctx->launches += 1;
+  }
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* probs, sqc_dtype dtype, uint64_t n,
+                                int32_t k, double threshold, uint64_t* bins_out, double* probs_out, int32_t* n_found,
+                                void* stream) {
+  if (!ctx || !probs || !bins_out || !probs_out || !n_found) return fail(ctx, SQC_EINVAL, "null argument");
+  if (k < 1 || k > kSelectMaxK) return fail(ctx, SQC_ESHAPE, "k must be in [1, 4096]");
+  if (dtype != SQC_F32 && dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "dtype must be F32 or F64");
+  if (std::isnan(threshold)) return fail(ctx, SQC_EINVAL, "threshold is NaN");
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  DeviceGuard g(ctx->device);
+  StageScope scope(ctx, static_cast<cudaStream_t>(stream), SQC_STAGE_SELECT);
+  ctx->launches += (dtype == SQC_F64 ? 8 : 4) + 4;
+  CK(launch_select(it->second->sel, probs, dtype == SQC_F64, n, k, threshold,
+                   reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found,
+                   static_cast<cudaStream_t>(stream)));
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_profile_enable(sqc_ctx* ctx, int on) {
+  if (!ctx) return SQC_EINVAL;
+  DeviceGuard g(ctx->device);
+  for (auto& m : ctx->marks) {
+    cudaEventSynchronize(m.stop);
+    ctx->event_pool.push_back(m.start);
+    ctx->event_pool.push_back(m.stop);
+  }
+  ctx->marks.clear();
+  ctx->launches = 0;
+  ctx->prof = on != 0;
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_profile_read(sqc_ctx* ctx, double* ms, int64_t* calls, int64_t* launches) {
+  if (!ctx) return SQC_EINVAL;
+  DeviceGuard g(ctx->device);
+  double acc[SQC_STAGE_COUNT] = {0};
+  int64_t cnt[SQC_STAGE_COUNT] = {0};
+  for (auto& m : ctx->marks) {
+    cudaError_t e = cudaEventSynchronize(m.stop);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventSynchronize");
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, m.start, m.stop);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventElapsedTime");
+    if (m.stage >= 0 && m.stage < SQC_STAGE_COUNT) {
+      acc[m.stage] += t;
+      cnt[m.stage] += 1;
+    }
+    ctx->event_pool.push_back(m.start);
+    ctx->event_pool.push_back(m.stop);
+  }
+  ctx->marks.clear();
+  if (ms) for (int i = 0; i < SQC_STAGE_COUNT; ++i) ms[i] = acc[i];
+  if (calls) for (int i = 0; i < SQC_STAGE_COUNT; ++i) calls[i] = cnt[i];
+  if (launches) *launches = ctx->launches;
+  ctx->launches = 0;
+  return SQC_OK;
+}
+
+}  // extern "C"

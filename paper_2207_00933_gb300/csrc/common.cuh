@@ -1,0 +1,88 @@
+// Device helpers shared by the library's kernels.
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace sqc {
+
+// Write one result element in the destination's number format: FP32, FP64,
+// or three BF16 planes hi + mid + lo (each the round-to-nearest of what the
+// previous planes left), the operand format of the split-BF16 steps.
+__device__ __forceinline__ void store_out(void* dst, int kind, int64_t plane_stride, uint64_t off, double v) {
+  if (kind == OUT_F32) {
+    static_cast<float*>(dst)[off] = float(v);
+  } else if (kind == OUT_F64) {
+    static_cast<double*>(dst)[off] = v;
+  } else {
+    const float f = float(v);
+    __nv_bfloat16* p = static_cast<__nv_bfloat16*>(dst);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const float r1 = f - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    p[off] = hi;
+    p[off + plane_stride] = mid;
+    p[off + 2 * plane_stride] = lo;
+  }
+}
+
+// The value a store_out of kind `kind` represents (what the next reader sees).
+__device__ __forceinline__ double stored_value(int kind, double v) {
+  return kind == OUT_F64 ? v : double(float(v));
+}
+
+// Scatter the low bits of src to the set bits of mask (bit deposit).
+__device__ __forceinline__ uint32_t deposit(uint32_t src, uint32_t mask) {
+  uint32_t r = 0;
+  for (uint32_t bit = 1; mask; bit <<= 1) {
+    const uint32_t low = mask & (0u - mask);
+    if (src & bit) r |= low;
+    mask &= mask - 1;
+  }
+  return r;
+}
+
+// Block-wide FP64 sum in a fixed order; the result is valid in thread 0.
+// Every thread of the block must call it.  red: blockDim/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// Each CTA stores its partial sum; the CTA that finishes last adds all
+// partials in CTA order (so the total does not depend on scheduling),
+// writes *total and re-arms the counter for the next launch.
+__device__ __forceinline__ void finish_total(double mine, double* partials, unsigned* counter, double* total,
+                                             double* red) {
+  __shared__ bool is_last;
+  const double bs = block_sum(mine, red);
+  const unsigned nblocks = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x == 0) {
+    partials[bid] = bs;
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == nblocks - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned i = threadIdx.x; i < nblocks; i += blockDim.x) s += static_cast<volatile double*>(partials)[i];
+  const double tot = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    *total = tot;
+    *counter = 0u;
+  }
+}
+
+}  // namespace sqc

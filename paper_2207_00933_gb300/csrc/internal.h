@@ -1,0 +1,127 @@
+// Internal kernel interfaces of the reconstruction library (not part of the
+// C ABI).  Every tensor index here is a plain linear index into a
+// power-of-two sized array; layouts are expressed as "maps": an output
+// element (row r, column c) of a producer goes to offset rowmap[r] +
+// colmap[c] of its destination, which lets each producer write the layout
+// its consumer wants (no separate transpose passes).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sqc {
+
+enum OutKind : int { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16X3 = 2 };
+
+// ---- attribution (Eq. 1, Section 2.1) --------------------------------------
+// fold: B[v][rev_n(x)] = sum_c prod_u W[v_u][c_u] * p[v][x | c << n]
+//   (outgoing cut wires: outcome weights; the basis is the variant digit)
+struct FoldArgs {
+  const void* p;
+  int in_f64;
+  float* B;          // [V][2^n], data index stored bit-reversed
+  int64_t V;
+  int n;             // data qubits
+  int kout;          // outgoing edges
+  int outshift[16];  // bit shift of each outgoing edge's digit in v
+};
+cudaError_t launch_fold(const FoldArgs& a, cudaStream_t s);
+
+// mix: A[e][xs] = sum_s prod_t D[e_t][s_t] * B[v(e with in-digits := s)][xs]
+//   (incoming cut wires: prepared-state coefficients)
+struct MixArgs {
+  const float* B;
+  float* A;          // [rows][2^n]
+  int64_t rows;      // 4^k
+  int n;
+  int kin;
+  int inshift[16];   // bit shift of each incoming edge's digit in e / v
+};
+cudaError_t launch_mix(const MixArgs& a, cudaStream_t s);
+
+// ---- merge / zoom (Section 4, Algorithm 2) ----------------------------------
+// T[e][b] = sum over data states with the zoom bits fixed and active bits
+// spelling b of A[e][state]; written to dst + rowmap[e] + colmap[b].
+struct MergeDesc {
+  const float* A;
+  int64_t rows;
+  int n;
+  uint32_t act_mask, mer_mask, zoom_val;  // storage-order bit masks
+  int a, m;                               // active / merged bit counts
+  int fast;                               // mer_mask == low m bits, act_mask == next a bits
+  int lanes;                              // threads cooperating on one output (1..32, pow2)
+  const uint64_t* rowmap;                 // [rows]
+  const uint64_t* colmap;                 // [2^a]
+  void* dst;
+  int kind;                               // OutKind
+  int64_t plane_stride;                   // OUT_BF16X3: elements between planes
+  double alpha;
+  int64_t block_begin;                    // first CTA of this descriptor
+};
+constexpr int kMaxMerge = 64;
+// descs: device array of n descriptors; total_blocks = CTAs over all of them
+cudaError_t launch_merge_blocks(const MergeDesc* descs, int n, int64_t total_blocks, cudaStream_t s);
+
+// ---- contraction step, FP32 SIMT (Section 6.1: C = A B over the shared index)
+struct GemmArgs {
+  const float* A;           // [M][K]
+  const float* B;           // [N][K]
+  int64_t M, N, K;
+  const uint64_t* rowmap;   // [M]
+  const uint64_t* colmap;   // [N]
+  void* C;
+  int kind;                 // OutKind
+  int64_t plane_stride;
+  double alpha;
+  int64_t chunk;            // FP32 terms per chunk before the FP64 add (0 = plain FP32)
+  int vec4;                 // colmap[4j..4j+3] contiguous and 4-aligned for all j
+  double* partials;         // per-CTA sums of the written values (nullable)
+  unsigned* counter;        // zero-initialised; last CTA writes *total and resets it
+  double* total;
+};
+cudaError_t launch_gemm_simt(const GemmArgs& a, cudaStream_t s);
+
+// ---- contraction step, split-BF16 on tcgen05 ---------------------------------
+struct GemmTcArgs {
+  const void* A;            // bf16 planes [3][Mp][Kp] (hi, mid, lo), K-contiguous
+  const void* B;            // bf16 planes [3][Np][Kp]
+  int64_t M, N, K;          // logical sizes
+  int64_t Mp, Np, Kp;       // padded (Mp, Np multiples of 128; Kp multiple of 64)
+  const uint64_t* rowmap;
+  const uint64_t* colmap;
+  void* C;
+  int kind;
+  int64_t plane_stride;
+  double alpha;
+  int64_t chunk;
+  double* partials;
+  unsigned* counter;
+  double* total;
+  int* err;                 // device error flag (bounded waits)
+};
+cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s);
+bool gemm_tc_available();
+
+// ---- probability check: FP64 sum of n values ---------------------------------
+cudaError_t launch_sum(const void* x, int is_f64, uint64_t n, double* partials, unsigned* counter,
+                       double* total, cudaStream_t s);
+
+// ---- bin selection (Algorithm 1: keep the largest bins) ----------------------
+struct SelectWork {
+  unsigned* hist;          // [kPasses][kRadix]
+  unsigned* state;         // small control block, see select.cu
+  unsigned long long* cand_key;  // [cap]
+  unsigned long long* cand_idx;  // [cap]
+  unsigned* tie_count;     // [max_blocks]
+  int cap;
+  int max_blocks;
+};
+size_t select_work_bytes(int cap, int max_blocks);
+void select_work_carve(void* base, int cap, int max_blocks, SelectWork* w);
+cudaError_t launch_select(const SelectWork& w, const void* x, int is_f64, uint64_t n, int k,
+                          double threshold, unsigned long long* bins_out, double* probs_out,
+                          int* n_found, cudaStream_t s);
+// one-time per-device kernel attributes (large shared memory for the sort)
+cudaError_t select_configure();
+constexpr int kSelectMaxK = 4096;
+
+}  // namespace sqc

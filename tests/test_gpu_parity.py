@@ -1,0 +1,241 @@
+"""GPU parity: the CUDA reconstruction through the C ABI against the FP64
+oracle on the same seeded inputs.
+
+Tolerance: 1e-6 max-abs probability error (the stated target), and a
+relative bound derived from the arithmetic: every bin is a sum of products
+accumulated in FP32 (unit roundoff 6e-8) over at most a few hundred terms
+per step, so the error stays below ~1e-5 of the largest bin; tighter where
+noted.  Bin selection and indexing are compared exactly."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synthetic import full_circuit_probs, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ABS_TOL = 1e-6
+REL_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2207_00933_gb300 import Context, _build
+    _build.build()
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def graph_of(c):
+    return O.Graph.from_arrays(c.n_qubits, *c.graph_arrays())
+
+
+def gpu_run(ctx, w, roles=None, out_dtype="float32", precision="fp32", host_inputs=False):
+    import torch
+    c = w.circuit
+    roles = w.roles if roles is None else roles
+    eu, ed, nd, dq = c.graph_arrays()
+    probs = [p if host_inputs else torch.from_numpy(np.ascontiguousarray(p)).cuda() for p in w.probs]
+    cid = ctx.load_subcircuit_outputs(c.n_qubits, eu, ed, nd, dq, probs)
+    qid, na = ctx.set_qubit_roles(cid, roles)
+    out = torch.empty(1 << na, dtype=getattr(torch, out_dtype), device="cuda")
+    tot = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.reconstruct(qid, out, precision, tot)
+    torch.cuda.synchronize()
+    res = out.double().cpu().numpy(), float(tot.item())
+    ctx.unload(cid)
+    return res
+
+
+def oracle_run(w, roles=None):
+    roles = w.roles if roles is None else roles
+    probs = [p.astype(np.float64) for p in w.probs]
+    return O.reconstruct(graph_of(w.circuit), probs, roles)
+
+
+def check(P, ref, rel=REL_TOL):
+    err = np.abs(P - ref).max()
+    scale = np.abs(ref).max()
+    assert err <= ABS_TOL, err
+    assert err <= rel * scale, (err, scale)
+    return err
+
+
+def test_full_state_12q(ctx):
+    w = W.full_state_12q()
+    P, tot = gpu_run(ctx, w)
+    ref = oracle_run(w)
+    check(P, ref)
+    assert np.abs(P - full_circuit_probs(w.circuit)).max() < 1e-6
+    assert abs(tot - 1.0) < 1e-5
+    assert abs(tot - math.fsum(P)) < 1e-9
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_graphs_mixed_roles(ctx, seed):
+    w = W.small_random(seed, roles="mixed")
+    P, _ = gpu_run(ctx, w)
+    check(P, oracle_run(w))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_graphs_all_active_vs_statevector(ctx, seed):
+    w = W.small_random(seed + 100, n_qubits=10, n_blocks=5, roles="active")
+    P, tot = gpu_run(ctx, w, out_dtype="float64")
+    check(P, full_circuit_probs(w.circuit))
+    assert abs(tot - 1.0) < 1e-5
+
+
+def test_merged_30q_all_bins(ctx):
+    w = W.merged_30q()
+    P, tot = gpu_run(ctx, w)
+    ref = oracle_run(w)
+    assert P.size == 1 << 20
+    check(P, ref)
+    assert abs(tot - O.total_probability(ref)) < 1e-6
+
+
+def test_merged_30q_host_inputs_fp64_out(ctx):
+    w = W.merged_30q()
+    P, _ = gpu_run(ctx, w, out_dtype="float64", host_inputs=True)
+    check(P, oracle_run(w))
+
+
+def test_grid_40q_fp64_chunked(ctx):
+    w = W.grid_40q()
+    P, tot = gpu_run(ctx, w, out_dtype="float64")
+    ref = oracle_run(w)
+    assert P.size == 1 << 22
+    check(P, ref)
+    assert abs(tot - O.total_probability(ref)) < 1e-6
+
+
+def test_zoomed_children_sum_to_parent(ctx):
+    w = W.merged_30q()
+    q = w.circuit.data_qubits[2][6]
+    assert w.roles[q] == O.MERGED
+    parent, _ = gpu_run(ctx, w)
+    kids = []
+    for role in (O.ZOOM0, O.ZOOM1):
+        r = w.roles.copy()
+        r[q] = role
+        kids.append(gpu_run(ctx, w, roles=r)[0])
+        check(kids[-1], oracle_run(w, r))
+    assert np.abs(kids[0] + kids[1] - parent).max() < 1e-9
+
+
+def test_single_subcircuit_no_cuts(ctx):
+    from synthetic.circuits import Block, CutCircuit
+    from synthetic.workloads import Workload
+    from synthetic import subcircuit_variant_probs
+    c = CutCircuit(6, [Block(list(range(6)), [("h", 0), ("cz", 0, 1), ("sx", 3), ("t", 1), ("sy", 5)])]).finalize()
+    w = Workload("one", c, [subcircuit_variant_probs(c, 0)], np.array([0, 1, 0, 2, 0, 3], dtype=np.int8))
+    P, tot = gpu_run(ctx, w)
+    check(P, oracle_run(w))
+
+
+def test_all_merged_gives_one(ctx):
+    w = W.full_state_12q(4)
+    roles = np.full(w.circuit.n_qubits, O.MERGED, dtype=np.int8)
+    P, tot = gpu_run(ctx, w, roles=roles, out_dtype="float64")
+    assert P.shape == (1,)
+    assert abs(P[0] - 1.0) < 1e-6 and abs(tot - 1.0) < 1e-6
+
+
+def test_top_bins_matches_oracle_exactly(ctx):
+    import torch
+    w = W.merged_30q()
+    c = w.circuit
+    probs = [torch.from_numpy(p).cuda() for p in w.probs]
+    cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), probs)
+    qid, na = ctx.set_qubit_roles(cid, w.roles)
+    out = torch.empty(1 << na, dtype=torch.float32, device="cuda")
+    ctx.reconstruct(qid, out)
+    P = out.double().cpu().numpy()
+    for k, thr in ((1, -math.inf), (10, -math.inf), (1000, -math.inf), (4096, -math.inf), (50, 3e-6),
+                   (4096, 1e-6)):
+        b, v, n = ctx.top_bins(qid, out, k, thr)
+        torch.cuda.synchronize()
+        nf = int(n.item())
+        eb, ev = O.top_bins(P, k, thr)          # same FP32 values, compared as FP64
+        assert nf == eb.size
+        assert b[:nf].cpu().numpy().tolist() == eb.tolist()
+        assert np.array_equal(v[:nf].cpu().numpy(), ev)
+    # the GPU's selection agrees with the FP64 oracle's up to near-ties
+    ref = oracle_run(w)
+    eb, ev = O.top_bins(ref, 64)
+    b, v, n = ctx.top_bins(qid, out, 64)
+    gb = b.cpu().numpy()
+    err = np.abs(P - ref).max()
+    gap_ok = np.abs(ev[-1] - ref[gb[-1]]) <= 2 * err
+    assert set(gb.tolist()) == set(eb.tolist()) or gap_ok
+    ctx.unload(cid)
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_top_bins_ties_and_edges(ctx, dtype):
+    import torch
+    rng = np.random.default_rng(5)
+    n = 300_000
+    x = rng.integers(0, 7, n).astype(dtype) * 0.125        # heavy exact ties
+    x[rng.integers(0, n, 40)] = 2.0
+    w = W.full_state_12q()
+    c = w.circuit
+    cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in w.probs])
+    qid, _ = ctx.set_qubit_roles(cid, w.roles)
+    xd = torch.from_numpy(x).cuda()
+    for k, thr in ((1, -math.inf), (37, -math.inf), (100, -math.inf), (4096, -math.inf), (4096, 0.7),
+                   (5, 3.0), (4096, 0.0)):
+        b, v, nf = ctx.top_bins(qid, xd, k, thr)
+        torch.cuda.synchronize()
+        eb, ev = O.top_bins(x.astype(np.float64), k, thr)
+        m = int(nf.item())
+        assert m == eb.size
+        assert b[:m].cpu().numpy().tolist() == eb.tolist()
+        assert np.array_equal(v[:m].cpu().numpy(), ev)
+    # empty and tiny inputs
+    for m in (1, 3):
+        y = torch.from_numpy(x[:m].copy()).cuda()
+        b, v, nf = ctx.top_bins(qid, y, 10)
+        torch.cuda.synchronize()
+        assert int(nf.item()) == m
+    ctx.unload(cid)
+
+
+def test_errors_are_reported(ctx):
+    import torch
+    from paper_2207_00933_gb300 import SQCError
+    w = W.full_state_12q()
+    c = w.circuit
+    cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in w.probs])
+    with pytest.raises(SQCError) as ei:
+        ctx.set_qubit_roles(cid, np.full(c.n_qubits, 7, dtype=np.int8))
+    assert ei.value.status == 1
+    qid, na = ctx.set_qubit_roles(cid, w.roles)
+    small = torch.empty(10, dtype=torch.float32, device="cuda")
+    with pytest.raises(SQCError) as ei:
+        ctx.reconstruct(qid, small)
+    assert ei.value.status == 3
+    with pytest.raises(SQCError) as ei:
+        ctx.top_bins(qid, small, 0)
+    assert ei.value.status == 3
+    ctx.unload(cid)
+    with pytest.raises(SQCError) as ei:
+        ctx.reconstruct(qid, small)
+    assert ei.value.status == 7
+
+
+def test_hbm_budget_admission(ctx):
+    import torch
+    from paper_2207_00933_gb300 import Context, SQCError
+    w = W.merged_30q()
+    c = w.circuit
+    with Context(0, hbm_budget_bytes=4 << 20) as small:
+        with pytest.raises(SQCError) as ei:
+            small.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in w.probs])
+        assert ei.value.status == 6
