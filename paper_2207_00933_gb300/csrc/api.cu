@@ -856,8 +856,9 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
 SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* probs, sqc_dtype dtype, uint64_t n,
                                 int32_t k, double threshold, uint64_t* bins_out, double* probs_out, int32_t* n_found,
                                 void* stream) {
-  if (!ctx || !probs || !bins_out || !probs_out || !n_found) return fail(ctx, SQC_EINVAL, "null argument");
+  if (!ctx) return SQC_EINVAL;
   if (k < 1 || k > kSelectMaxK) return fail(ctx, SQC_ESHAPE, "k must be in [1, 4096]");
+  if (!probs || !bins_out || !probs_out || !n_found) return fail(ctx, SQC_EINVAL, "null argument");
   if (dtype != SQC_F32 && dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "dtype must be F32 or F64");
   if (std::isnan(threshold)) return fail(ctx, SQC_EINVAL, "threshold is NaN");
   auto it = ctx->queries.find(qid);

@@ -62,7 +62,9 @@ def check(P, ref, rel=REL_TOL):
     err = np.abs(P - ref).max()
     scale = np.abs(ref).max()
     assert err <= ABS_TOL, err
-    assert err <= rel * scale, (err, scale)
+    # relative to the largest bin, with a floor for bins that are exactly
+    # zero in exact arithmetic (the oracle's FP64 rounding leaves ~1e-17)
+    assert err <= rel * scale + 1e-12, (err, scale)
     return err
 
 
@@ -235,7 +237,7 @@ def test_hbm_budget_admission(ctx):
     from paper_2207_00933_gb300 import Context, SQCError
     w = W.merged_30q()
     c = w.circuit
-    with Context(0, hbm_budget_bytes=4 << 20) as small:
+    with Context(0, hbm_budget_bytes=1 << 20) as small:   # the circuit needs ~2.7 MB
         with pytest.raises(SQCError) as ei:
             small.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in w.probs])
         assert ei.value.status == 6
