@@ -188,6 +188,28 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id q, const void* probs,
                                 uint64_t n, int32_t k, double threshold, uint64_t* bins_out,
                                 double* probs_out, int32_t* n_found, void* stream);
 
+/* Allocation-free bin selection.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code
+ * embedded in a host application that owns every device allocation, or a
+ * latency-critical loop in which a cudaMalloc (which can synchronise the
+ * device) is not acceptable.  It returns exactly what sqc_top_bins returns
+ * for the same arguments, needs no context and no query, and allocates
+ * nothing: its scratch is one static device array of about 140 KiB in the
+ * library (held on every GPU that loads the library until the process
+ * exits).
+ *   device: the GPU that holds `probs` and the outputs (made current for
+ *           the call).  The first call on a device looks up the array's
+ *           device address and sets kernel attributes; make that first call
+ *           before any stream capture.
+ *   k must be in [1, 4096] (the scratch's capacity); larger k fails with
+ *   SQC_ESHAPE.  Other arguments as in sqc_top_bins.
+ * Every call shares the one array: calls whose GPU work may overlap (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Errors are reported through sqc_last_error(NULL). */
+SQC_API sqc_status sqc_top_bins_noalloc(int device, const void* probs, sqc_dtype dtype, uint64_t n, int32_t k,
+                                        double threshold, uint64_t* bins_out, double* probs_out,
+                                        int32_t* n_found, void* stream);
+
 /* Introspection of a planned query (host values, no device work):
  * n_steps contraction steps; flops = sum of 2*M*N*K over the steps;
  * merge_bytes = bytes the merge reads and writes; work_bytes = device

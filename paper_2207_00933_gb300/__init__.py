@@ -66,6 +66,8 @@ _SIGS = {
                                     _c.POINTER(_c.c_double), _c.POINTER(_c.c_uint64)]),
     "sqc_query_step": (_c.c_int32, [_P, _c.c_int64, _c.c_int32, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64),
                                     _c.POINTER(_c.c_int64)]),
+    "sqc_top_bins_noalloc": (_c.c_int32, [_c.c_int, _P, _c.c_int, _c.c_uint64, _c.c_int32, _c.c_double, _P, _P,
+                                          _P, _P]),
     "sqc_profile_enable": (_c.c_int32, [_P, _c.c_int]),
     "sqc_profile_read": (_c.c_int32, [_P, _P, _P, _P]),
 }
@@ -289,6 +291,27 @@ def _profile_read(self) -> dict:
 
 Context.profile_enable = _profile_enable
 Context.profile_read = _profile_read
+
+
+def top_bins_noalloc(probs, k: int, threshold: float = -math.inf, bins_out=None, probs_out=None, n_found=None,
+                     stream=None):
+    """Allocation-free selection (sqc_top_bins_noalloc): same result as
+    Context.top_bins, scratch in the library's static device array, no
+    context needed.  Calls that may overlap on the GPU must be serialised."""
+    import torch
+    lib = load_library()
+    dev = probs.device
+    if bins_out is None:
+        bins_out = torch.empty(k, dtype=torch.int64, device=dev)
+    if probs_out is None:
+        probs_out = torch.empty(k, dtype=torch.float64, device=dev)
+    if n_found is None:
+        n_found = torch.empty(1, dtype=torch.int32, device=dev)
+    st = lib.sqc_top_bins_noalloc(dev.index or 0, _ptr(probs), _dtype_code(probs), probs.numel(), k, float(threshold),
+                                  _ptr(bins_out), _ptr(probs_out), _ptr(n_found), _stream_handle(stream))
+    if st != 0:
+        raise SQCError(st, lib.sqc_last_error(None).decode())
+    return bins_out, probs_out, n_found
 
 
 def declared_symbols() -> list[str]:

@@ -872,6 +872,34 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* prob
   return SQC_OK;
 }
 
+SQC_API sqc_status sqc_top_bins_noalloc(int device, const void* probs, sqc_dtype dtype, uint64_t n, int32_t k,
+                                        double threshold, uint64_t* bins_out, double* probs_out, int32_t* n_found,
+                                        void* stream) {
+  if (k < 1 || k > kSelectMaxK)
+    return fail(nullptr, SQC_ESHAPE, "k must be in [1, 4096]: the static scratch holds at most 4096 selected bins");
+  if (!probs || !bins_out || !probs_out || !n_found) return fail(nullptr, SQC_EINVAL, "null argument");
+  if (dtype != SQC_F32 && dtype != SQC_F64) return fail(nullptr, SQC_EINVAL, "dtype must be F32 or F64");
+  if (std::isnan(threshold)) return fail(nullptr, SQC_EINVAL, "threshold is NaN");
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return fail(nullptr, e != cudaSuccess ? SQC_ECUDA : SQC_EINVAL, "no such CUDA device");
+  }
+  DeviceGuard g(device);
+  static thread_local bool configured[64] = {false};
+  if (device < 64 && !configured[device]) {
+    e = select_configure();
+    if (e != cudaSuccess) return fail(nullptr, SQC_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(e));
+    configured[device] = true;
+  }
+  e = launch_select_static(device, probs, dtype == SQC_F64, n, k, threshold,
+                           reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found,
+                           static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, SQC_ECUDA, std::string("selection: ") + cudaGetErrorString(e));
+  return SQC_OK;
+}
+
 SQC_API sqc_status sqc_profile_enable(sqc_ctx* ctx, int on) {
   if (!ctx) return SQC_EINVAL;
   DeviceGuard g(ctx->device);

@@ -120,6 +120,11 @@ void select_work_carve(void* base, int cap, int max_blocks, SelectWork* w);
 cudaError_t launch_select(const SelectWork& w, const void* x, int is_f64, uint64_t n, int k,
                           double threshold, unsigned long long* bins_out, double* probs_out,
                           int* n_found, cudaStream_t s);
+// Selection with scratch in a static device array instead of a workspace
+// (the caller has made `device` current); select_static_bytes() is its size.
+cudaError_t launch_select_static(int device, const void* x, int is_f64, uint64_t n, int k, double threshold,
+                                 unsigned long long* bins_out, double* probs_out, int* n_found, cudaStream_t s);
+size_t select_static_bytes();
 // one-time per-device kernel attributes (large shared memory for the sort)
 cudaError_t select_configure();
 constexpr int kSelectMaxK = 4096;

@@ -18,6 +18,8 @@
 //     the first k.
 // The FP64 probability sum is a grid reduction with a fixed summation
 // order (per-CTA partials added by the last CTA in CTA order).
+#include <mutex>
+
 #include "common.cuh"
 
 namespace sqc {
@@ -328,6 +330,50 @@ cudaError_t launch_select(const SelectWork& w, const void* x, int is_f64, uint64
   const size_t smem = 2 * sizeof(unsigned long long) * kMaxSort;
   sort_emit<<<1, kSortThreads, smem, s>>>(x, is_f64, st, w.cand_key, w.cand_idx, bins_out, probs_out, n_found);
   return cudaGetLastError();
+}
+
+// ---- allocation-free variant -------------------------------------------------
+// Fixed scratch for sqc_top_bins_noalloc: the same layout launch_select
+// carves from a query's workspace (control block, candidate list, radix
+// histograms, tie counts), sized for k <= kSelectMaxK and 1024 tie ranges.
+constexpr int kStaticSelectBlocks = 1024;
+constexpr size_t kStaticSelectBytes = sizeof(unsigned long long) * ST_WORDS +
+                                      2 * sizeof(unsigned long long) * kMaxSort +
+                                      sizeof(unsigned) * kPasses * kRadix +
+                                      sizeof(unsigned) * kStaticSelectBlocks + 256;
+static __device__ __align__(256) unsigned char g_select_scratch[kStaticSelectBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_scratch_addr[kMaxDevices];
+static std::mutex g_scratch_mu;
+
+size_t select_static_bytes() { return kStaticSelectBytes; }
+
+// The caller has made `device` current.  The array's name is only a host
+// stand-in for the device symbol, so its device address is looked up once
+// per device and cached.
+cudaError_t launch_select_static(int device, const void* x, int is_f64, uint64_t n, int k, double threshold,
+                                 unsigned long long* bins_out, double* probs_out, int* n_found, cudaStream_t s) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[device]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
+      if (e != cudaSuccess) return e;
+      g_scratch_addr[device] = p;
+    }
+    base = g_scratch_addr[device];
+  }
+  SelectWork w{};
+  select_work_carve(base, 0, kStaticSelectBlocks, &w);
+  // the control block and the histograms must start at zero; the array keeps
+  // whatever the previous call left
+  cudaError_t e = cudaMemsetAsync(w.state, 0, sizeof(unsigned long long) * ST_WORDS, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.hist, 0, sizeof(unsigned) * kPasses * kRadix, s);
+  if (e != cudaSuccess) return e;
+  return launch_select(w, x, is_f64, n, k, threshold, bins_out, probs_out, n_found, s);
 }
 
 cudaError_t select_configure() {
