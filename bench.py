@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="line30_K8_a20", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
     return ap.parse_args()
 
 
@@ -285,8 +286,27 @@ def main():
     steps_shape = ctx.query_steps(qid)
     info = ctx.query_info(qid)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    use_graph = not args.no_graph
+    if use_graph:
+        # the whole step (attribution, merge, contraction steps, selection)
+        # captured once and replayed; stage events become graph nodes
+        ctx.profile_enable(2)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize(dev)
+        run = graph.replay
+        for _ in range(max(3, args.warmup)):
+            run()
+        torch.cuda.synchronize(dev)
+        ctx.profile_read()
+    else:
+        ctx.profile_enable(True)
+        run = step
+    stage_total = {k: 0.0 for k in ("attribute", "merge", "contract", "final", "select")}
+    stage_calls = {k: 0 for k in stage_total}
+    launches = 0
     sampler = ClockSampler(local)
-    ctx.profile_enable(True)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -296,13 +316,24 @@ def main():
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        step()
+        run()
         ev[i][1].record(stream)
+        if use_graph:
+            # stage events of this replay are read before the next one
+            torch.cuda.synchronize(dev)
+            pr = ctx.profile_read()
+            for k in stage_total:
+                stage_total[k] += pr["ms"][k]
+                stage_calls[k] += pr["calls"][k]
+            launches += pr["launches"]
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
-    prof = ctx.profile_read()
+    if not use_graph:
+        pr = ctx.profile_read()
+        stage_total, stage_calls, launches = dict(pr["ms"]), dict(pr["calls"]), pr["launches"]
     ctx.profile_enable(False)
+    prof = {"ms": stage_total, "calls": stage_calls, "launches": launches}
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if world > 1:
@@ -362,6 +393,7 @@ def main():
             "config": {"workload": args.workload, "bins": bins, "active_qubits": na, "cuts": c.n_edges,
                        "subcircuits": c.n_subcircuits, "topk": TOPK, "out_dtype": str(out_dtype).split(".")[-1],
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "cuda_graph": use_graph,
                        "parallelism": f"{world} independent circuits" if world > 1 else "1 gpu",
                        "seed": w.meta.get("seed")},
             "max_abs_err_vs_fp64": err,

@@ -235,10 +235,14 @@ enum {
   SQC_STAGE_COUNT = 5
 };
 
-/* Turn stage timing on (1) or off (0); turning it on clears the record. */
+/* Turn stage timing on (1) or off (0); turning it on clears the record.
+ * Mode 2 is for work captured into a CUDA graph: the event pairs recorded
+ * during capture become graph nodes and are kept; every sqc_profile_read
+ * then reports the times of the most recent replay, and *launches the
+ * kernels recorded during capture (one replay's worth). */
 SQC_API sqc_status sqc_profile_enable(sqc_ctx* ctx, int on);
 
-/* Read and clear the record: ms[SQC_STAGE_COUNT] total milliseconds per
+/* Read (and, outside mode 2, clear) the record: ms[SQC_STAGE_COUNT] total milliseconds per
  * stage, calls[SQC_STAGE_COUNT] how many times each stage ran, *launches the
  * number of kernels launched.  Synchronises with the recorded events.  Any
  * output may be NULL. */

@@ -273,8 +273,10 @@ class Context:
         return bins_out, probs_out, n_found
 
 
-def _profile_enable(self, on: bool = True):
-    """Stage timing on/off (sqc_profile_enable); turning it on clears it."""
+def _profile_enable(self, on=True):
+    """Stage timing on/off (sqc_profile_enable); turning it on clears it.
+    on=2: graph mode (events captured into a CUDA graph are kept; each read
+    reports the latest replay)."""
     self._check(self._lib.sqc_profile_enable(self._h, int(on)))
 
 

@@ -40,22 +40,48 @@ struct Circuit {
   size_t bytes = 0;
 };
 
+constexpr int kPad = -1;           // layout code of a padding bit (never written, zero)
+
 struct Tensor {
   std::vector<int> bits;         // unordered set of logical bit codes
   std::set<int> edges;           // open cut edges
-  std::vector<int> layout;       // layout[p] = code stored at address bit p
+  std::vector<int> layout;       // layout[p] = code stored at address bit p (kPad: padding)
   int producer_sub = -1;         // merge of this subcircuit, or
   int producer_step = -1;        // output of this step
-  float* buf = nullptr;          // FP32 storage (intermediates)
+  int kind = OUT_F32;            // storage: FP32, or three BF16 planes for a tensor-core step
+  int64_t plane_stride = 0;      // elements per BF16 plane
+  void* buf = nullptr;
+  size_t bytes = 0;
 };
 
 struct Step {
   int x = -1, y = -1, z = -1;    // operand tensors (x = A rows, y = B cols after layout) and result
   std::vector<int> shared;       // shared edge ids
   int64_t M = 1, N = 1, Kd = 1;
+  bool tc = false;               // split-BF16 on tcgen05
+  int64_t Kp = 1;                // shared index padded to the tensor-core K block
   uint64_t* rowmap = nullptr;    // device
   uint64_t* colmap = nullptr;
   int vec4 = 0;
+};
+
+// Everything one precision needs to run a query: contraction order, layouts,
+// maps, buffers.  Built on first use of that precision.
+struct Plan {
+  bool built = false;
+  bool split = false;
+  std::vector<Tensor> tensors;
+  std::vector<Step> steps;
+  int final_tensor = -1;
+  std::vector<MergeDesc> merge_host;
+  MergeDesc* merge_dev = nullptr;
+  int64_t merge_blocks = 0;
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  int* err = nullptr;            // set by bounded device waits that gave up
+  double flops = 0.0;
 };
 
 struct Query {
@@ -63,19 +89,11 @@ struct Query {
   std::vector<int8_t> roles;
   int n_active = 0;
   int64_t out_elems = 1;
-  std::vector<Tensor> tensors;
-  std::vector<Step> steps;
-  int final_tensor = -1;
-  std::vector<MergeDesc> merge_host;
-  MergeDesc* merge_dev = nullptr;
-  int64_t merge_blocks = 0;
-  int final_merge = -1;          // descriptor index writing the output when there are no steps
-  void* work = nullptr;
-  size_t work_bytes = 0;
-  double* partials = nullptr;
-  unsigned* counter = nullptr;
+  Plan plans[2];                 // [SQC_PREC_FP32], [SQC_PREC_SPLIT_BF16]
+  void* sel_mem = nullptr;
+  size_t sel_bytes = 0;
   SelectWork sel{};
-  double flops = 0.0, merge_bytes = 0.0;
+  double merge_bytes = 0.0;
 };
 
 }  // namespace
@@ -88,6 +106,7 @@ struct StageMark {
 struct sqc_ctx {
   int device = 0;
   bool prof = false;
+  bool prof_keep = false;       // marks belong to a captured graph: keep them across reads
   std::vector<StageMark> marks;
   std::vector<cudaEvent_t> event_pool;
   int64_t launches = 0;
@@ -145,16 +164,25 @@ struct StageScope {
   cudaStream_t s;
   int stage;
   cudaEvent_t a = nullptr, b = nullptr;
+  // inside a stream capture the records become graph nodes that must be
+  // observable outside the graph (external event records)
+  static void record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, s);
+  }
   StageScope(sqc_ctx* c, cudaStream_t st, int stg) : ctx(c), s(st), stage(stg) {
     if (ctx->prof) {
       a = take_event(ctx);
       b = take_event(ctx);
-      if (a) cudaEventRecord(a, s);
+      if (a) record(a, s);
     }
   }
   ~StageScope() {
     if (a && b) {
-      cudaEventRecord(b, s);
+      record(b, s);
       ctx->marks.push_back({stage, a, b});
     }
   }
@@ -259,44 +287,100 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
   for (int i = 0; i < c->nC; ++i)
     if (!probs[i]) return fail(ctx, SQC_EINVAL, "probs[i] is null");
   StageScope scope(ctx, s, SQC_STAGE_ATTRIBUTE);
+  // device addresses of every subcircuit's input (host inputs are staged
+  // back to back so that one launch can attribute all subcircuits)
+  std::vector<const void*> src(c->nC);
+  size_t off = 0;
   for (int i = 0; i < c->nC; ++i) {
     const size_t nbytes = size_t(c->V[i]) * (size_t(1) << c->w[i]) * esz;
-    const void* src = probs[i];
-    if (!on_device) {
-      CK(cudaMemcpyAsync(c->staging, probs[i], nbytes, cudaMemcpyHostToDevice, s));
-      src = c->staging;
+    if (on_device) {
+      src[i] = probs[i];
+    } else {
+      char* dst = static_cast<char*>(c->staging) + off;
+      CK(cudaMemcpyAsync(dst, probs[i], nbytes, cudaMemcpyHostToDevice, s));
+      src[i] = dst;
+      off += (nbytes + 255) & ~size_t(255);
     }
+  }
+  AttrLaunch L{};
+  int64_t blocks = 0;
+  int smem = 0;
+  auto flush = [&]() -> sqc_status {
+    if (L.n == 0) return SQC_OK;
+    CK(launch_attr_fused(L, blocks, smem, s));
+    ctx->launches += 1;
+    L = AttrLaunch{};
+    blocks = 0;
+    smem = 0;
+    return SQC_OK;
+  };
+  for (int i = 0; i < c->nC; ++i) {
     const int n = c->ndata[i];
+    const int kin = int(c->ins[i].size());
+    const int kout = int(c->outs[i].size());
+    if (kin <= kMaxFusedIn) {
+      AttrDesc& d = L.d[L.n];
+      d.p = src[i];
+      d.A = c->A[i];
+      d.in_f64 = dtype == SQC_F64;
+      d.n = n;
+      d.kin = kin;
+      d.kout = kout;
+      int L2 = std::min(3, n / 2), L1 = std::min(3, n - L2);
+      const int64_t S = int64_t(1) << (2 * kin);
+      while ((S << (L1 + L2)) > kAttrSmemMax / 4) {
+        if (L1 >= L2 && L1 > 0) --L1;
+        else if (L2 > 0) --L2;
+        else break;
+      }
+      d.L1 = L1;
+      d.L2 = L2;
+      for (int t = 0; t < kin; ++t) d.inshift[t] = digit_shift(*c, i, c->ins[i][t]);
+      for (int u = 0; u < kout; ++u) d.outshift[u] = digit_shift(*c, i, c->outs[i][u]);
+      d.block_begin = blocks;
+      blocks += (int64_t(1) << (n - L1 - L2)) << (2 * kout);
+      smem = std::max(smem, int(S << (L1 + L2)) * 4);
+      if (++L.n == kAttrPerLaunch) {
+        sqc_status st = flush();
+        if (st != SQC_OK) return st;
+      }
+      continue;
+    }
+    // many incoming edges: outcome fold, then a per-output prepared-state mix
     FoldArgs fa{};
-    fa.p = src;
+    fa.p = src[i];
     fa.in_f64 = dtype == SQC_F64;
     fa.V = c->V[i];
     fa.n = n;
-    fa.kout = int(c->outs[i].size());
-    for (int u = 0; u < fa.kout; ++u) fa.outshift[u] = digit_shift(*c, i, c->outs[i][u]);
-    const int kin = int(c->ins[i].size());
-    fa.B = kin ? c->scratch : c->A[i];
+    fa.kout = kout;
+    for (int u = 0; u < kout; ++u) fa.outshift[u] = digit_shift(*c, i, c->outs[i][u]);
+    fa.B = c->scratch;
     CK(launch_fold(fa, s));
-    ctx->launches += 1;
-    if (kin) {
-      MixArgs ma{};
-      ma.B = c->scratch;
-      ma.A = c->A[i];
-      ma.rows = c->V[i];
-      ma.n = n;
-      ma.kin = kin;
-      for (int t = 0; t < kin; ++t) ma.inshift[t] = digit_shift(*c, i, c->ins[i][t]);
-      CK(launch_mix(ma, s));
-      ctx->launches += 1;
-    }
+    MixArgs ma{};
+    ma.B = c->scratch;
+    ma.A = c->A[i];
+    ma.rows = c->V[i];
+    ma.n = n;
+    ma.kin = kin;
+    for (int t = 0; t < kin; ++t) ma.inshift[t] = digit_shift(*c, i, c->ins[i][t]);
+    CK(launch_mix(ma, s));
+    ctx->launches += 2;
   }
+  sqc_status st = flush();
+  if (st != SQC_OK) return st;
   if (!on_device) CK(cudaStreamSynchronize(s));
   return SQC_OK;
 }
 
+void free_plan(sqc_ctx* ctx, Plan* p) {
+  dev_free(ctx, p->work, p->work_bytes);
+  *p = Plan{};
+}
+
 void free_query(sqc_ctx* ctx, Query* q) {
-  dev_free(ctx, q->work, q->work_bytes);
-  q->work = nullptr;
+  for (Plan& p : q->plans) free_plan(ctx, &p);
+  dev_free(ctx, q->sel_mem, q->sel_bytes);
+  q->sel_mem = nullptr;
 }
 
 void free_circuit(sqc_ctx* ctx, Circuit* c) {
@@ -329,24 +413,35 @@ std::vector<uint64_t> make_map(const std::vector<int>& codes, const std::map<int
 
 std::map<int, int> positions(const std::vector<int>& layout) {
   std::map<int, int> pos;
-  for (size_t p = 0; p < layout.size(); ++p) pos[layout[p]] = int(p);
+  for (size_t p = 0; p < layout.size(); ++p)
+    if (layout[p] != kPad) pos[layout[p]] = int(p);
   return pos;
 }
 
-sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
+int ilog2(int64_t x) { return 63 - __builtin_clzll(uint64_t(x)); }
+
+// Per-query roles: the bins (canonical positions) and, per subcircuit, the
+// merge masks in storage order.
+void resolve_roles(const Circuit& c, Query* q) {
+  int na = 0;
+  for (int qb = 0; qb < c.n_qubits; ++qb) na += q->roles[qb] == SQC_ROLE_ACTIVE;
+  q->n_active = na;
+  q->out_elems = int64_t(1) << na;
+}
+
+sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan* P) {
   const int nC = c.nC;
-  // canonical position of each active qubit
   std::vector<int> canon(c.n_qubits, -1);
   int na = 0;
   for (int qb = 0; qb < c.n_qubits; ++qb)
     if (q->roles[qb] == SQC_ROLE_ACTIVE) canon[qb] = na++;
-  q->n_active = na;
-  q->out_elems = int64_t(1) << na;
 
   // subcircuit tensors T_i and the merge index codes
-  q->tensors.assign(nC, Tensor{});
+  P->split = split;
+  P->tensors.assign(nC, Tensor{});
   std::vector<std::vector<int>> row_codes(nC), col_codes(nC);
-  q->merge_host.assign(nC, MergeDesc{});
+  P->merge_host.assign(nC, MergeDesc{});
+  double merge_bytes = 0.0;
   for (int i = 0; i < nC; ++i) {
     const int n = c.ndata[i];
     const int k = int(c.inc[i].size());
@@ -361,7 +456,7 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
         default: break;
       }
     }
-    Tensor& T = q->tensors[i];
+    Tensor& T = P->tensors[i];
     T.producer_sub = i;
     // row index e: incident edge p's digit at bits 2(k-1-p) (lo) and 2(k-1-p)+1 (hi)
     row_codes[i].assign(2 * k, 0);
@@ -373,13 +468,10 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
     }
     // column index b: u-th lowest active storage bit
     for (int sp = 0; sp < n; ++sp)
-      if ((act >> sp) & 1) {
-        const int t = n - 1 - sp;
-        col_codes[i].push_back(kBinBase + canon[c.dq[i][t]]);
-      }
+      if ((act >> sp) & 1) col_codes[i].push_back(kBinBase + canon[c.dq[i][n - 1 - sp]]);
     T.bits = row_codes[i];
     T.bits.insert(T.bits.end(), col_codes[i].begin(), col_codes[i].end());
-    MergeDesc& d = q->merge_host[i];
+    MergeDesc& d = P->merge_host[i];
     d.A = c.A[i];
     d.rows = c.V[i];
     d.n = n;
@@ -391,11 +483,11 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
     d.fast = (mer == ((1u << d.m) - 1u)) && (act == (((1u << d.a) - 1u) << d.m));
     const uint32_t run = 1u << d.m;
     int lanes = d.fast ? int(run / 16) : int(run / 4);
-    lanes = std::max(1, std::min(32, lanes));
-    d.lanes = lanes;
+    d.lanes = std::max(1, std::min(32, lanes));
     d.alpha = 1.0;
-    q->merge_bytes += double(d.rows) * double(int64_t(1) << (d.a + d.m)) * 4.0 + double(d.rows << d.a) * 4.0;
+    merge_bytes += double(d.rows) * double(int64_t(1) << (d.a + d.m)) * 4.0 + double(d.rows << d.a) * 4.0;
   }
+  q->merge_bytes = merge_bytes;
 
   // greedy contraction order on the Section 6.2 cost (multiplications)
   std::vector<int> alive;
@@ -406,10 +498,10 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
     bool best_conn = false;
     for (size_t a = 0; a < alive.size(); ++a)
       for (size_t b = a + 1; b < alive.size(); ++b) {
-        const Tensor& X = q->tensors[alive[a]];
-        const Tensor& Y = q->tensors[alive[b]];
+        const Tensor& X = P->tensors[alive[a]];
+        const Tensor& Y = P->tensors[alive[b]];
         int sh = 0;
-        for (int e : X.edges) sh += Y.edges.count(e);
+        for (int e : X.edges) sh += int(Y.edges.count(e));
         const bool conn = sh > 0;
         const double fx = double(X.bits.size()) - 2.0 * sh, fy = double(Y.bits.size()) - 2.0 * sh;
         const double out = std::ldexp(1.0, int(fx + fy));
@@ -426,8 +518,8 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
     st.x = bx;
     st.y = by;
     Tensor Z;
-    const Tensor& X = q->tensors[bx];
-    const Tensor& Y = q->tensors[by];
+    const Tensor& X = P->tensors[bx];
+    const Tensor& Y = P->tensors[by];
     for (int e : X.edges)
       if (Y.edges.count(e)) st.shared.push_back(e);
     std::set<int> shcodes;
@@ -436,17 +528,17 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
     for (int b : Y.bits) if (!shcodes.count(b)) Z.bits.push_back(b);
     for (int e : X.edges) if (!Y.edges.count(e)) Z.edges.insert(e);
     for (int e : Y.edges) if (!X.edges.count(e)) Z.edges.insert(e);
-    Z.producer_step = int(q->steps.size());
-    st.z = int(q->tensors.size());
-    q->tensors.push_back(Z);
-    q->steps.push_back(st);
+    Z.producer_step = int(P->steps.size());
+    st.z = int(P->tensors.size());
+    P->tensors.push_back(Z);
+    P->steps.push_back(st);
     alive.erase(std::find(alive.begin(), alive.end(), bx));
     alive.erase(std::find(alive.begin(), alive.end(), by));
     alive.push_back(st.z);
   }
-  q->final_tensor = alive[0];
+  P->final_tensor = alive[0];
   {
-    Tensor& F = q->tensors[q->final_tensor];
+    Tensor& F = P->tensors[P->final_tensor];
     if (!F.edges.empty()) return fail(ctx, SQC_EINVAL, "plan: open edges left after contraction");
     F.layout.resize(na);
     for (int p = 0; p < na; ++p) F.layout[p] = kBinBase + p;
@@ -454,17 +546,18 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
   }
 
   // layouts, from the result backwards; maps and dimensions of every step
+  const bool tc_ok = split && gemm_tc_available();
   MapBuild maps;
-  std::vector<std::pair<size_t, size_t>> step_map_off(q->steps.size());
-  for (int s = int(q->steps.size()) - 1; s >= 0; --s) {
-    Step& st = q->steps[s];
-    const Tensor& Z = q->tensors[st.z];
+  std::vector<std::pair<size_t, size_t>> step_map_off(P->steps.size());
+  for (int s = int(P->steps.size()) - 1; s >= 0; --s) {
+    Step& st = P->steps[s];
+    const Tensor& Z = P->tensors[st.z];
     const std::map<int, int> zpos = positions(Z.layout);
     std::set<int> shcodes;
     for (int e : st.shared) { shcodes.insert(2 * e); shcodes.insert(2 * e + 1); }
     auto free_of = [&](int t) {
       std::vector<int> f;
-      for (int b : q->tensors[t].bits) if (!shcodes.count(b)) f.push_back(b);
+      for (int b : P->tensors[t].bits) if (!shcodes.count(b)) f.push_back(b);
       std::sort(f.begin(), f.end(), [&](int a, int b) { return zpos.at(a) < zpos.at(b); });
       return f;
     };
@@ -472,21 +565,30 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
     // B (columns) = the operand that owns the result's lowest address bit,
     // so that consecutive columns land on consecutive addresses
     bool swap = false;
-    if (!Z.layout.empty()) {
-      const int low = Z.layout[0];
-      swap = std::find(fx.begin(), fx.end(), low) != fx.end();
-    } else {
-      swap = fx.size() < fy.size();
-    }
+    int low = kPad;
+    for (int code : Z.layout)
+      if (code != kPad) { low = code; break; }
+    if (low != kPad) swap = std::find(fx.begin(), fx.end(), low) != fx.end();
+    else swap = fx.size() < fy.size();
     if (swap) { std::swap(st.x, st.y); std::swap(fx, fy); }
     std::vector<int> sh(shcodes.begin(), shcodes.end());
-    q->tensors[st.x].layout = sh;
-    q->tensors[st.x].layout.insert(q->tensors[st.x].layout.end(), fx.begin(), fx.end());
-    q->tensors[st.y].layout = sh;
-    q->tensors[st.y].layout.insert(q->tensors[st.y].layout.end(), fy.begin(), fy.end());
     st.Kd = int64_t(1) << sh.size();
     st.M = int64_t(1) << fx.size();
     st.N = int64_t(1) << fy.size();
+    // tensor cores for the big steps: M, N >= 128 (one UMMA tile), and a
+    // shared index short enough to be one FP32 chunk
+    st.tc = tc_ok && st.M >= gemm_tc_min_rows() && st.N >= gemm_tc_min_rows() &&
+            (st.Kd <= ctx->cfg.chunk_terms || c.K < ctx->cfg.fp64_chunk_min_edges);
+    st.Kp = st.tc ? std::max<int64_t>(st.Kd, gemm_tc_k_align()) : st.Kd;
+    std::vector<int> lay = sh;
+    for (int p = ilog2(st.Kd); p < ilog2(st.Kp); ++p) lay.push_back(kPad);
+    for (Tensor* T : {&P->tensors[st.x], &P->tensors[st.y]}) {
+      T->layout = lay;
+      const std::vector<int>& f = (T == &P->tensors[st.x]) ? fx : fy;
+      T->layout.insert(T->layout.end(), f.begin(), f.end());
+      T->kind = st.tc ? OUT_BF16X3 : OUT_F32;
+      T->plane_stride = int64_t(1) << T->layout.size();
+    }
     const std::vector<uint64_t> rm = make_map(fx, zpos), cm = make_map(fy, zpos);
     bool v4 = st.N % 4 == 0;
     for (size_t j = 0; v4 && j < cm.size(); ++j)
@@ -495,71 +597,90 @@ sqc_status plan_query(sqc_ctx* ctx, const Circuit& c, Query* q) {
       if (rm[i] & 3) v4 = false;
     st.vec4 = v4;
     step_map_off[s] = {maps.add(rm), maps.add(cm)};
-    q->flops += 2.0 * double(st.M) * double(st.N) * double(st.Kd);
+    P->flops += 2.0 * double(st.M) * double(st.N) * double(st.Kd);
   }
   std::vector<std::pair<size_t, size_t>> merge_map_off(nC);
   for (int i = 0; i < nC; ++i) {
-    const std::map<int, int> tpos = positions(q->tensors[i].layout);
+    const std::map<int, int> tpos = positions(P->tensors[i].layout);
     merge_map_off[i] = {maps.add(make_map(row_codes[i], tpos)), maps.add(make_map(col_codes[i], tpos))};
   }
 
-  // workspace: descriptors | maps | tensors | partials + counter | selection
-  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  // workspace: descriptors | maps | tensors | partials + counter + error flag
+  auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
   size_t off = 0;
   const size_t off_desc = off; off = align(off + sizeof(MergeDesc) * nC);
   const size_t off_maps = off; off = align(off + sizeof(uint64_t) * maps.host.size());
-  std::vector<size_t> off_tensor(q->tensors.size(), 0);
-  for (size_t t = 0; t < q->tensors.size(); ++t) {
-    if (int(t) == q->final_tensor) continue;
+  std::vector<size_t> off_tensor(P->tensors.size(), 0);
+  size_t zero_begin = 0, zero_end = 0;
+  for (size_t t = 0; t < P->tensors.size(); ++t) {
+    Tensor& T = P->tensors[t];
+    if (int(t) == P->final_tensor) continue;
+    const size_t elems = size_t(1) << T.layout.size();
+    T.bytes = T.kind == OUT_BF16X3 ? 3 * elems * 2 : elems * 4;
     off_tensor[t] = off;
-    off = align(off + sizeof(float) * (size_t(1) << q->tensors[t].bits.size()));
+    if (T.kind == OUT_BF16X3) {
+      if (!zero_end) zero_begin = off;
+      zero_end = off + T.bytes;
+    }
+    off = align(off + T.bytes);
   }
   int64_t max_tiles = 1024;
-  for (const Step& st : q->steps) max_tiles = std::max<int64_t>(max_tiles, ((st.M + 31) / 32) * ((st.N + 31) / 32));
+  for (const Step& st : P->steps) max_tiles = std::max<int64_t>(max_tiles, ((st.M + 31) / 32) * ((st.N + 31) / 32));
   const size_t off_part = off; off = align(off + sizeof(double) * size_t(max_tiles));
   const size_t off_cnt = off; off = align(off + 64);
-  const int sel_blocks = 1024;
-  const size_t off_sel = off; off = align(off + select_work_bytes(0, sel_blocks));
-  q->work_bytes = off;
-  sqc_status st = dev_alloc(ctx, &q->work, off);
+  P->work_bytes = off;
+  sqc_status st = dev_alloc(ctx, &P->work, off);
   if (st != SQC_OK) return st;
-  char* base = static_cast<char*>(q->work);
-  q->merge_dev = reinterpret_cast<MergeDesc*>(base + off_desc);
+  char* base = static_cast<char*>(P->work);
+  P->merge_dev = reinterpret_cast<MergeDesc*>(base + off_desc);
   uint64_t* maps_dev = reinterpret_cast<uint64_t*>(base + off_maps);
-  for (size_t t = 0; t < q->tensors.size(); ++t)
-    if (int(t) != q->final_tensor) q->tensors[t].buf = reinterpret_cast<float*>(base + off_tensor[t]);
-  q->partials = reinterpret_cast<double*>(base + off_part);
-  q->counter = reinterpret_cast<unsigned*>(base + off_cnt);
-  select_work_carve(base + off_sel, 0, sel_blocks, &q->sel);
+  for (size_t t = 0; t < P->tensors.size(); ++t)
+    if (int(t) != P->final_tensor) P->tensors[t].buf = base + off_tensor[t];
+  P->partials = reinterpret_cast<double*>(base + off_part);
+  P->counter = reinterpret_cast<unsigned*>(base + off_cnt);
+  P->err = reinterpret_cast<int*>(base + off_cnt + 16);
 
-  for (size_t s = 0; s < q->steps.size(); ++s) {
-    q->steps[s].rowmap = maps_dev + step_map_off[s].first;
-    q->steps[s].colmap = maps_dev + step_map_off[s].second;
+  for (size_t s = 0; s < P->steps.size(); ++s) {
+    P->steps[s].rowmap = maps_dev + step_map_off[s].first;
+    P->steps[s].colmap = maps_dev + step_map_off[s].second;
   }
   int64_t blocks = 0;
   for (int i = 0; i < nC; ++i) {
-    MergeDesc& d = q->merge_host[i];
+    MergeDesc& d = P->merge_host[i];
     d.rowmap = maps_dev + merge_map_off[i].first;
     d.colmap = maps_dev + merge_map_off[i].second;
-    d.dst = q->tensors[i].buf;          // null for the result (set per call)
-    d.kind = OUT_F32;
-    d.plane_stride = 0;
+    d.dst = P->tensors[i].buf;          // null for the result (set per call)
+    d.kind = P->tensors[i].kind;
+    d.plane_stride = P->tensors[i].plane_stride;
     d.block_begin = blocks;
     const int64_t outs = d.rows << d.a;
     const int64_t per = 256 / d.lanes;
     blocks += (outs + per - 1) / per;
   }
-  q->merge_blocks = blocks;
-  q->final_merge = q->steps.empty() ? 0 : -1;
+  P->merge_blocks = blocks;
   cudaError_t e = cudaMemcpy(maps_dev, maps.host.data(), sizeof(uint64_t) * maps.host.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nC > 0)
-    e = cudaMemcpy(q->merge_dev, q->merge_host.data(), sizeof(MergeDesc) * nC, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(P->merge_dev, P->merge_host.data(), sizeof(MergeDesc) * nC, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(base + off_cnt, 0, 64);
-  if (e == cudaSuccess) e = cudaMemset(base + off_sel, 0, select_work_bytes(0, sel_blocks));
+  // BF16 operand padding (shared-index columns beyond K) must read as zero
+  if (e == cudaSuccess && zero_end > zero_begin) e = cudaMemset(base + zero_begin, 0, zero_end - zero_begin);
   if (e != cudaSuccess) {
-    free_query(ctx, q);
+    free_plan(ctx, P);
     return cuda_fail(ctx, e, "plan upload");
   }
+  P->built = true;
+  return SQC_OK;
+}
+
+sqc_status ensure_select_work(sqc_ctx* ctx, Query* q) {
+  if (q->sel_mem) return SQC_OK;
+  const int sel_blocks = 1024;
+  q->sel_bytes = select_work_bytes(0, sel_blocks);
+  sqc_status st = dev_alloc(ctx, &q->sel_mem, q->sel_bytes);
+  if (st != SQC_OK) return st;
+  select_work_carve(q->sel_mem, 0, sel_blocks, &q->sel);
+  cudaError_t e = cudaMemset(q->sel_mem, 0, q->sel_bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "selection workspace");
   return SQC_OK;
 }
 
@@ -606,6 +727,8 @@ SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg) 
     return fail(nullptr, SQC_EINVAL, "chunk_terms must be a power of two >= 16");
   DeviceGuard g(device);
   e = select_configure();
+  if (e == cudaSuccess) e = attr_configure();
+  if (e == cudaSuccess) e = gemm_tc_configure();
   if (e != cudaSuccess) return fail(nullptr, SQC_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(e));
   *out = ctx.release();
   return SQC_OK;
@@ -639,8 +762,8 @@ SQC_API sqc_status sqc_load_subcircuit_outputs(sqc_ctx* ctx, const sqc_graph* gr
   c->A.assign(c->nC, nullptr);
   size_t stage = 0, scratch = 0;
   for (int i = 0; i < c->nC; ++i) {
-    stage = std::max(stage, size_t(c->V[i]) * (size_t(1) << c->w[i]) * (dtype == SQC_F64 ? 8 : 4));
-    if (!c->ins[i].empty()) scratch = std::max(scratch, size_t(c->V[i]) << c->ndata[i]);
+    stage += (size_t(c->V[i]) * (size_t(1) << c->w[i]) * (dtype == SQC_F64 ? 8 : 4) + 255) & ~size_t(255);
+    if (int(c->ins[i].size()) > kMaxFusedIn) scratch = std::max(scratch, size_t(c->V[i]) << c->ndata[i]);
   }
   auto cleanup = [&](sqc_status s) {
     free_circuit(ctx, c.get());
@@ -682,7 +805,7 @@ SQC_API sqc_status sqc_update_subcircuit_outputs(sqc_ctx* ctx, sqc_circuit_id id
   if (!probs_on_device) {
     size_t need = 0;
     for (int i = 0; i < c->nC; ++i)
-      need = std::max(need, size_t(c->V[i]) * (size_t(1) << c->w[i]) * (dtype == SQC_F64 ? 8 : 4));
+      need += (size_t(c->V[i]) * (size_t(1) << c->w[i]) * (dtype == SQC_F64 ? 8 : 4) + 255) & ~size_t(255);
     if (need > c->staging_bytes)
       return fail(ctx, SQC_ESHAPE, "host-input update needs the circuit loaded from host data in this dtype");
   }
@@ -726,8 +849,13 @@ SQC_API sqc_status sqc_set_qubit_roles(sqc_ctx* ctx, sqc_circuit_id id, const in
   auto q = std::make_unique<Query>();
   q->circuit = id;
   q->roles.assign(roles, roles + c.n_qubits);
-  sqc_status st = plan_query(ctx, c, q.get());
-  if (st != SQC_OK) return st;
+  resolve_roles(c, q.get());
+  sqc_status st = build_plan(ctx, c, q.get(), false, &q->plans[SQC_PREC_FP32]);
+  if (st == SQC_OK) st = ensure_select_work(ctx, q.get());
+  if (st != SQC_OK) {
+    free_query(ctx, q.get());
+    return st;
+  }
   const int64_t qid = ctx->next_id++;
   if (n_active) *n_active = q->n_active;
   ctx->queries[qid] = std::move(q);
@@ -753,10 +881,11 @@ SQC_API sqc_status sqc_query_info(const sqc_ctx* cctx, sqc_query_id qid, int32_t
   auto it = ctx->queries.find(qid);
   if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
   const Query& q = *it->second;
-  if (n_steps) *n_steps = int32_t(q.steps.size());
-  if (flops) *flops = q.flops;
+  const Plan& P = q.plans[SQC_PREC_FP32];
+  if (n_steps) *n_steps = int32_t(P.steps.size());
+  if (flops) *flops = P.flops;
   if (merge_bytes) *merge_bytes = q.merge_bytes;
-  if (work_bytes) *work_bytes = q.work_bytes;
+  if (work_bytes) *work_bytes = q.plans[0].work_bytes + q.plans[1].work_bytes + q.sel_bytes;
   return SQC_OK;
 }
 
@@ -766,11 +895,11 @@ SQC_API sqc_status sqc_query_step(const sqc_ctx* cctx, sqc_query_id qid, int32_t
   if (!ctx) return SQC_EINVAL;
   auto it = ctx->queries.find(qid);
   if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
-  const Query& q = *it->second;
-  if (step < 0 || step >= int32_t(q.steps.size())) return fail(ctx, SQC_EINVAL, "step out of range");
-  if (M) *M = q.steps[step].M;
-  if (N) *N = q.steps[step].N;
-  if (Kd) *Kd = q.steps[step].Kd;
+  const Plan& P = it->second->plans[SQC_PREC_FP32];
+  if (step < 0 || step >= int32_t(P.steps.size())) return fail(ctx, SQC_EINVAL, "step out of range");
+  if (M) *M = P.steps[step].M;
+  if (N) *N = P.steps[step].N;
+  if (Kd) *Kd = P.steps[step].Kd;
   return SQC_OK;
 }
 
@@ -784,70 +913,102 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
   if (cit == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "circuit of the query was unloaded");
   const Circuit& c = *cit->second;
   if (out_dtype != SQC_F32 && out_dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "out_dtype must be F32 or F64");
-  if (precision != SQC_PREC_FP32)
-    return fail(ctx, SQC_EINVAL, "precision: only SQC_PREC_FP32 is available in this build");
+  if (precision != SQC_PREC_FP32 && precision != SQC_PREC_SPLIT_BF16)
+    return fail(ctx, SQC_EINVAL, "precision must be SQC_PREC_FP32 or SQC_PREC_SPLIT_BF16");
   const uint64_t need = uint64_t(q.out_elems) * (out_dtype == SQC_F64 ? 8 : 4);
   if (out_bytes < need)
     return fail(ctx, SQC_ESHAPE, "out_bytes " + std::to_string(out_bytes) + " < " + std::to_string(need));
   DeviceGuard g(ctx->device);
+  Plan& P = q.plans[precision];
+  if (!P.built) {
+    // the first split-BF16 call on a query plans that precision (allocates)
+    sqc_status st = build_plan(ctx, c, &q, precision == SQC_PREC_SPLIT_BF16, &P);
+    if (st != SQC_OK) return st;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int out_kind = out_dtype == SQC_F64 ? OUT_F64 : OUT_F32;
   const double alpha = std::ldexp(1.0, -c.K);
 
-  if (q.steps.empty()) {
+  if (P.steps.empty()) {
     // one subcircuit: the merge writes the bins directly
-    MergeDesc d = q.merge_host[0];
+    MergeDesc d = P.merge_host[0];
     d.dst = out_bins;
     d.kind = out_kind;
     d.alpha = alpha;
-    CK(cudaMemcpyAsync(q.merge_dev, &d, sizeof(MergeDesc), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.merge_dev, &d, sizeof(MergeDesc), cudaMemcpyHostToDevice, s));
     {
       StageScope scope(ctx, s, SQC_STAGE_MERGE);
-      CK(launch_merge_blocks(q.merge_dev, int(q.merge_host.size()), q.merge_blocks, s));
+      CK(launch_merge_blocks(P.merge_dev, int(P.merge_host.size()), P.merge_blocks, s));
       ctx->launches += 1;
     }
     if (total_prob) {
       StageScope scope(ctx, s, SQC_STAGE_FINAL);
-      CK(launch_sum(out_bins, out_dtype == SQC_F64, uint64_t(q.out_elems), q.partials, q.counter, total_prob, s));
+      CK(launch_sum(out_bins, out_dtype == SQC_F64, uint64_t(q.out_elems), P.partials, P.counter, total_prob, s));
       ctx->launches += 1;
     }
     return SQC_OK;
   }
   {
     StageScope scope(ctx, s, SQC_STAGE_MERGE);
-    CK(launch_merge_blocks(q.merge_dev, int(q.merge_host.size()), q.merge_blocks, s));
+    CK(launch_merge_blocks(P.merge_dev, int(P.merge_host.size()), P.merge_blocks, s));
     ctx->launches += 1;
   }
-  for (size_t si = 0; si < q.steps.size(); ++si) {
-    const Step& st = q.steps[si];
-    const bool last = int(si) == int(q.steps.size()) - 1;
-    GemmArgs a{};
-    a.A = q.tensors[st.x].buf;
-    a.B = q.tensors[st.y].buf;
-    a.M = st.M;
-    a.N = st.N;
-    a.K = st.Kd;
-    a.rowmap = st.rowmap;
-    a.colmap = st.colmap;
-    a.vec4 = st.vec4;
-    if (last) {
-      a.C = out_bins;
-      a.kind = out_kind;
-      a.alpha = alpha;
-      a.chunk = (out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
-                    ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
-                    : 0;
-      a.partials = total_prob ? q.partials : nullptr;
-      a.counter = q.counter;
-      a.total = total_prob;
-    } else {
-      a.C = q.tensors[st.z].buf;
-      a.kind = OUT_F32;
-      a.alpha = 1.0;
-      a.chunk = 0;
-    }
+  for (size_t si = 0; si < P.steps.size(); ++si) {
+    const Step& st = P.steps[si];
+    const bool last = int(si) == int(P.steps.size()) - 1;
+    const Tensor& Z = P.tensors[st.z];
+    void* C = last ? out_bins : Z.buf;
+    const int kind = last ? out_kind : Z.kind;
     StageScope scope(ctx, s, last ? SQC_STAGE_FINAL : SQC_STAGE_CONTRACT);
-    CK(launch_gemm_simt(a, s));
+    if (st.tc) {
+      GemmTcArgs a{};
+      a.A = P.tensors[st.x].buf;
+      a.B = P.tensors[st.y].buf;
+      a.M = st.M;
+      a.N = st.N;
+      a.K = st.Kd;
+      a.Mp = st.M;
+      a.Np = st.N;
+      a.Kp = st.Kp;
+      a.rowmap = st.rowmap;
+      a.colmap = st.colmap;
+      a.C = C;
+      a.kind = kind;
+      a.plane_stride = last ? 0 : Z.plane_stride;
+      a.alpha = last ? alpha : 1.0;
+      a.chunk = 0;
+      a.partials = (last && total_prob) ? P.partials : nullptr;
+      a.counter = P.counter;
+      a.total = total_prob;
+      a.err = P.err;
+      CK(launch_gemm_tc(a, s));
+    } else {
+      GemmArgs a{};
+      a.A = static_cast<const float*>(P.tensors[st.x].buf);
+      a.B = static_cast<const float*>(P.tensors[st.y].buf);
+      a.M = st.M;
+      a.N = st.N;
+      a.K = st.Kd;
+      a.rowmap = st.rowmap;
+      a.colmap = st.colmap;
+      a.vec4 = st.vec4;
+      a.C = C;
+      a.kind = kind;
+      a.plane_stride = last ? 0 : Z.plane_stride;
+      if (last) {
+        a.alpha = alpha;
+        a.chunk = (out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
+                      ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
+                      : 0;
+        a.partials = total_prob ? P.partials : nullptr;
+        a.counter = P.counter;
+        a.total = total_prob;
+      } else {
+        a.alpha = 1.0;
+        a.chunk = 0;
+      }
+      CK(launch_gemm_simt(a, s));
+    }
     ctx->launches += 1;
   }
   return SQC_OK;
@@ -911,6 +1072,7 @@ SQC_API sqc_status sqc_profile_enable(sqc_ctx* ctx, int on) {
   ctx->marks.clear();
   ctx->launches = 0;
   ctx->prof = on != 0;
+  ctx->prof_keep = on == 2;
   return SQC_OK;
 }
 
@@ -929,14 +1091,16 @@ SQC_API sqc_status sqc_profile_read(sqc_ctx* ctx, double* ms, int64_t* calls, in
       acc[m.stage] += t;
       cnt[m.stage] += 1;
     }
-    ctx->event_pool.push_back(m.start);
-    ctx->event_pool.push_back(m.stop);
+    if (!ctx->prof_keep) {
+      ctx->event_pool.push_back(m.start);
+      ctx->event_pool.push_back(m.stop);
+    }
   }
-  ctx->marks.clear();
+  if (!ctx->prof_keep) ctx->marks.clear();
   if (ms) for (int i = 0; i < SQC_STAGE_COUNT; ++i) ms[i] = acc[i];
   if (calls) for (int i = 0; i < SQC_STAGE_COUNT; ++i) calls[i] = cnt[i];
   if (launches) *launches = ctx->launches;
-  ctx->launches = 0;
+  if (!ctx->prof_keep) ctx->launches = 0;
   return SQC_OK;
 }
 

@@ -28,9 +28,23 @@ __device__ __forceinline__ void store_out(void* dst, int kind, int64_t plane_str
   }
 }
 
-// The value a store_out of kind `kind` represents (what the next reader sees).
-__device__ __forceinline__ double stored_value(int kind, double v) {
-  return kind == OUT_F64 ? v : double(float(v));
+// FP32 result: FP64 conversion only when the destination is FP64 (the FP64
+// pipe is narrow on this GPU).
+__device__ __forceinline__ void store_out_f(void* dst, int kind, int64_t plane_stride, uint64_t off, float f) {
+  if (kind == OUT_F32) {
+    static_cast<float*>(dst)[off] = f;
+  } else if (kind == OUT_F64) {
+    static_cast<double*>(dst)[off] = double(f);
+  } else {
+    __nv_bfloat16* p = static_cast<__nv_bfloat16*>(dst);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+    const float r1 = f - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    p[off] = hi;
+    p[off + plane_stride] = mid;
+    p[off + 2 * plane_stride] = lo;
+  }
 }
 
 // Scatter the low bits of src to the set bits of mask (bit deposit).

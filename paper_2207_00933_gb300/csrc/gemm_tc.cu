@@ -1,0 +1,316 @@
+// One contraction step (Section 6.1: C = A B^T over the shared cut-edge
+// index) on the tcgen05 tensor cores in split-BF16.
+//
+// Every operand is held as three BF16 planes x = hi + mid + lo (each plane
+// the round-to-nearest of what the previous ones left).  The product keeps
+// the six terms of order <= 2 -- hi*hi, hi*mid, mid*hi, hi*lo, mid*mid,
+// lo*hi -- all accumulated in one FP32 accumulator in tensor memory, which
+// gives about FP32 accuracy for the signed I/X/Y/Z sums.
+//
+// Per CTA: one 128 x 128 output tile, 6 warps.
+//   warp 0 (one thread): TMA producer -- for each 64-wide block of the
+//     shared index it loads the three A planes and three B planes
+//     (128 x 64 BF16 each, 128-byte swizzle) into one pipeline stage;
+//   warp 1 (one thread): allocates 128 TMEM columns and issues
+//     tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 128, K = 16):
+//     6 plane pairs x 4 K-slices per stage, then commits the stage back to
+//     the producer;
+//   warps 2-5: epilogue -- wait for the last commit, read the accumulator
+//     rows with tcgen05.ld (warp w reads TMEM lanes 32*(w%4) .. +31), scale
+//     by alpha, write through rowmap/colmap (FP32, FP64 or BF16 planes) and
+//     add the written values into the per-CTA probability sum.
+// Every mbarrier wait is bounded; on timeout the CTA records an error code,
+// drains its own copies (bounded) and frees its TMEM before returning.
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace sqc {
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBN = 128;
+constexpr int kBK = 64;            // 64 BF16 = 128 bytes: one swizzle row
+constexpr int kStages = 2;
+constexpr int kTileA = kBM * kBK * 2;
+constexpr int kTileB = kBN * kBK * 2;
+constexpr int kStageBytes = 3 * kTileA + 3 * kTileB;
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 128;
+constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (i > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile of 8-row x 128-byte swizzle
+// atoms (128-byte swizzle), atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= uint64_t((addr & 0x3FFFFu) >> 4);   // start address
+  d |= uint64_t(1) << 16;                  // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;          // stride byte offset: next 8-row group
+  d |= uint64_t(1) << 46;                  // descriptor version
+  d |= uint64_t(2) << 61;                  // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D = FP32, A = B = BF16, both K-major, M x N.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kBN >> 3) << 17) |
+                            (uint32_t(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmTcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* accf = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  __shared__ double red[kThreads / 32];
+  __shared__ int failed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles_n = a.Np / kBN;
+  const int tn_shift = __ffsll(tiles_n) - 1;
+  const int64_t tile = blockIdx.x;
+  const int m0 = int((tile >> tn_shift) * kBM);
+  const int n0 = int((tile & (tiles_n - 1)) * kBN);
+  const int nk = int(a.Kp / kBK);
+
+  if (threadIdx.x == 0) {
+    failed = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  float sum_f = 0.f;
+  double sum_d = 0.0;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      const int use = kb / kStages;
+      if (use > 0 && !mbar_wait(&empty[s], uint32_t((use - 1) & 1))) {
+        atomicExch(&failed, 1);
+        break;
+      }
+      if (failed) break;
+      uint8_t* st = smem + s * kStageBytes;
+      mbar_expect_tx(&full[s], kStageBytes);
+      for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
+      for (int p = 0; p < 3; ++p) tma_load_3d(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
+      issued = kb + 1;
+    }
+    // drain: every stage we filled must have landed before the CTA exits
+    for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
+      if (!mbar_wait(&full[kb % kStages], uint32_t((kb / kStages) & 1))) atomicExch(&failed, 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
+    constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
+    bool ok = true;
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % kStages;
+      if (!mbar_wait(&full[s], uint32_t((kb / kStages) & 1)) || failed) {
+        atomicExch(&failed, 1);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const uint64_t da = smem_desc(base + pa[q] * kTileA);
+        const uint64_t db = smem_desc(base + 3 * kTileA + pb[q] * kTileB);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk)   // K = 16 per instruction: +32 bytes = +2 in the address field
+          mma_bf16(tmem, da + 2 * kk, db + 2 * kk, (kb | q | kk) != 0);
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accf);
+  } else if (warp >= 2) {
+    // ---- epilogue
+    if (mbar_wait(accf, 0) && !failed) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int quad = warp & 3;
+      const int r = quad * 32 + lane;
+      const int64_t row = int64_t(m0) + r;
+      const float alpha_f = float(a.alpha);
+      const bool row_ok = row < a.M;
+      const uint64_t rbase = row_ok ? a.rowmap[row] : 0;
+      for (int c0 = 0; c0 < kBN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
+        if (!row_ok) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t col = int64_t(n0) + c0 + j;
+          if (col >= a.N) continue;
+          const float f = v[j] * alpha_f;
+          if (a.kind == OUT_F64) sum_d += double(f); else sum_f += f;
+          store_out_f(a.C, a.kind, a.plane_stride, rbase + a.colmap[col], f);
+        }
+      }
+    } else {
+      atomicExch(&failed, 1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+  if (failed && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+  if (a.partials) finish_total(sum_d + double(sum_f), a.partials, a.counter, a.total, red);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3-D map over BF16 planes [3][rows][Kp], box 64 x 128 x 1, 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t Kp) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {cuuint64_t(Kp), cuuint64_t(rows), 3};
+  const cuuint64_t strides[2] = {cuuint64_t(Kp) * 2, cuuint64_t(rows) * cuuint64_t(Kp) * 2};
+  const cuuint32_t box[3] = {kBK, kBM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool gemm_tc_available() { return encode_fn() != nullptr; }
+
+int gemm_tc_min_rows() { return kBM; }
+int gemm_tc_k_align() { return kBK; }
+
+cudaError_t gemm_tc_configure() {
+  return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+}
+
+cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s) {
+  // shape contract: Mp, Np multiples of 128 (they are the powers of two M, N
+  // >= 128), Kp a multiple of 64; checked here so that no TMA coordinate or
+  // TMEM lane can leave the operands
+  if (a.Mp % kBM || a.Np % kBN || a.Kp % kBK || a.Kp <= 0 || a.M > a.Mp || a.N > a.Np || a.K > a.Kp)
+    return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 1023) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a.A, a.Mp, a.Kp) || !make_map(&mb, a.B, a.Np, a.Kp)) return cudaErrorInvalidValue;
+  const int64_t tiles = (a.Mp / kBM) * (a.Np / kBN);
+  gemm_tc_kernel<<<unsigned(tiles), kThreads, kSmemBytes, s>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+}  // namespace sqc

@@ -38,6 +38,27 @@ struct MixArgs {
 };
 cudaError_t launch_mix(const MixArgs& a, cudaStream_t s);
 
+// fused fold + mix, shared-memory tiled (subcircuits with kin <= 7)
+constexpr int kMaxFusedIn = 7;
+constexpr int kAttrSmemMax = 64 * 1024;
+constexpr int kAttrPerLaunch = 16;
+struct AttrDesc {
+  const void* p;
+  float* A;
+  int in_f64;
+  int n, kin, kout;
+  int L1, L2;                 // x tile: 2^L1 low values x 2^L2 top-bit values
+  int inshift[kMaxFusedIn];
+  int outshift[16];
+  int64_t block_begin;
+};
+struct AttrLaunch {
+  AttrDesc d[kAttrPerLaunch];
+  int n;
+};
+cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s);
+cudaError_t attr_configure();
+
 // ---- merge / zoom (Section 4, Algorithm 2) ----------------------------------
 // T[e][b] = sum over data states with the zoom bits fixed and active bits
 // spelling b of A[e][state]; written to dst + rowmap[e] + colmap[b].
@@ -99,7 +120,10 @@ struct GemmTcArgs {
   int* err;                 // device error flag (bounded waits)
 };
 cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s);
-bool gemm_tc_available();
+bool gemm_tc_available();          // the driver's tensor-map encoder is reachable
+int gemm_tc_min_rows();            // M and N of a tensor-core step must be >= this
+int gemm_tc_k_align();             // the shared index is padded to a multiple of this
+cudaError_t gemm_tc_configure();   // one-time kernel attributes (dynamic shared memory)
 
 // ---- probability check: FP64 sum of n values ---------------------------------
 cudaError_t launch_sum(const void* x, int is_f64, uint64_t n, double* partials, unsigned* counter,

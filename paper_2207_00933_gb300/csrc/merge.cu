@@ -25,9 +25,9 @@ __global__ void __launch_bounds__(256) merge_kernel(const MergeDesc* __restrict_
     d = descs[lo];
   }
   __syncthreads();
-  const int lanes = d.lanes;
-  const int per_block = 256 / lanes;
-  const int64_t o = (int64_t(blockIdx.x) - d.block_begin) * per_block + threadIdx.x / lanes;
+  const int lanes = d.lanes;                       // power of two
+  const int lshift = __ffs(lanes) - 1;
+  const int64_t o = ((int64_t(blockIdx.x) - d.block_begin) << (8 - lshift)) + (threadIdx.x >> lshift);
   const int lane = threadIdx.x & (lanes - 1);
   const int64_t total = d.rows << d.a;
   const bool valid = o < total;
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) merge_kernel(const MergeDesc* __restrict_
   if (valid && lane == 0) {
     const int64_t e = o >> d.a;
     const uint32_t b = uint32_t(o & ((int64_t(1) << d.a) - 1));
-    store_out(d.dst, d.kind, d.plane_stride, d.rowmap[e] + d.colmap[b], d.alpha * double(acc));
+    store_out_f(d.dst, d.kind, d.plane_stride, d.rowmap[e] + d.colmap[b], acc * float(d.alpha));
   }
 }
 

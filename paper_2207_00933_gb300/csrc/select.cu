@@ -14,10 +14,14 @@
 //     to a candidate list;
 //  3. if more than `cap` values share the exact k-th key, those ties are
 //     taken in ascending bin order by an ordered block scan instead;
-//  4. one CTA sorts the candidates (bitonic, in shared memory) and writes
-//     the first k.
+//  4. every candidate finds its rank in the final order by counting the
+//     candidates ahead of it (many CTAs, shared-memory tiles) and the
+//     first k are written at their ranks.
 // The FP64 probability sum is a grid reduction with a fixed summation
 // order (per-CTA partials added by the last CTA in CTA order).
+#include <cmath>
+#include <cstring>
+#include <limits>
 #include <mutex>
 
 #include "common.cuh"
@@ -30,7 +34,6 @@ constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kPasses = 8;          // 64-bit keys
 constexpr int kSelThreads = 256;
-constexpr int kSortThreads = 1024;
 constexpr int kMaxSort = 8192;      // candidates sorted in shared memory
 
 // control block layout (unsigned long long words)
@@ -45,23 +48,110 @@ enum : int {
   ST_WORDS = 8
 };
 
-__device__ __forceinline__ unsigned long long key_of(const void* x, int is_f64, uint64_t i, double* val) {
-  if (is_f64) {
-    const double v = static_cast<const double*>(x)[i];
-    *val = v;
-    const unsigned long long u = __double_as_longlong(v);
-    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
-  }
-  const float f = static_cast<const float*>(x)[i];
-  *val = double(f);
+__device__ __forceinline__ unsigned long long key_f32(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned k = (u >> 31) ? ~u : (u | 0x80000000u);
   return (unsigned long long)k << 32;
 }
 
+__device__ __forceinline__ unsigned long long key_f64(double v) {
+  const unsigned long long u = __double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ unsigned long long key_of(const void* x, int is_f64, uint64_t i, double* val) {
+  if (is_f64) {
+    const double v = static_cast<const double*>(x)[i];
+    *val = v;
+    return key_f64(v);
+  }
+  const float f = static_cast<const float*>(x)[i];
+  *val = double(f);
+  return key_f32(f);
+}
+
+// Values i0 .. i0+kVec-1 (fewer at the tail) with one or two vector loads,
+// so that every thread keeps kVec independent loads in flight.  The
+// threshold test is done on the order-preserving keys (integer compares,
+// no FP64 pipe): ok = !isnan(v) && key(v) >= key_thr, where key_thr is the
+// key of the smallest value of the input's type that is >= threshold.
+constexpr int kVec = 4;
+struct Chunk {
+  unsigned long long key[kVec];
+  bool ok[kVec];
+  int cnt;
+};
+
+template <bool is_f64>
+__device__ __forceinline__ void load_chunk(const void* x, int aligned, uint64_t n, uint64_t i0,
+                                           unsigned long long key_thr, Chunk* c) {
+  c->cnt = 0;
+#pragma unroll
+  for (int q = 0; q < kVec; ++q) {
+    c->ok[q] = false;
+    c->key[q] = 0ull;
+  }
+  if (i0 >= n) return;
+  const int cnt = (n - i0 >= kVec) ? kVec : int(n - i0);
+  c->cnt = cnt;
+  if constexpr (is_f64) {
+    const double* p = static_cast<const double*>(x) + i0;
+    double v[kVec];
+    if (aligned && cnt == kVec) {
+      const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+      const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+      for (int q = 0; q < cnt; ++q) v[q] = p[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kVec; ++q) {
+      const unsigned long long u = __double_as_longlong(v[q]);
+      const bool nan = (u & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+      c->key[q] = key_f64(v[q]);
+      c->ok[q] = q < cnt && !nan && c->key[q] >= key_thr;
+    }
+  } else {
+    const float* p = static_cast<const float*>(x) + i0;
+    float f[kVec];
+    if (aligned && cnt == kVec) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+      f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+    } else {
+      for (int q = 0; q < cnt; ++q) f[q] = p[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kVec; ++q) {
+      const unsigned u = __float_as_uint(f[q]);
+      const bool nan = (u & 0x7fffffffu) > 0x7f800000u;
+      c->key[q] = key_f32(f[q]);
+      c->ok[q] = q < cnt && !nan && c->key[q] >= key_thr;
+    }
+  }
+}
+
+// Aggregate equal digits across a warp: one shared atomic per distinct
+// digit.  The common case (every active lane has the same digit, as in the
+// exponent bytes of probabilities) takes one ballot and one compare.
+__device__ __forceinline__ void warp_hist_add(unsigned* sh, bool ok, unsigned dig, int lane) {
+  const unsigned active = __ballot_sync(0xffffffffu, ok);
+  if (!active) return;
+  const int leader = __ffs(active) - 1;
+  const unsigned d0 = __shfl_sync(0xffffffffu, dig, leader);
+  if (__all_sync(0xffffffffu, !ok || dig == d0)) {
+    if (lane == leader) atomicAdd(&sh[d0], unsigned(__popc(active)));
+    return;
+  }
+  if (ok) {
+    const unsigned peers = __match_any_sync(active, dig);
+    if (__ffs(peers) - 1 == lane) atomicAdd(&sh[dig], unsigned(__popc(peers)));
+  }
+}
+
+template <bool is_f64>
 __global__ void __launch_bounds__(kSelThreads)
-radix_pass(const void* x, int is_f64, uint64_t n, double thr, int k, int pass, int last_pass, int cap,
-           unsigned* hist_all, unsigned long long* st) {
+radix_pass(const void* x, int aligned, uint64_t n, unsigned long long key_thr, int k, int pass,
+           int last_pass, int cap, unsigned* hist_all, unsigned long long* st) {
   __shared__ unsigned sh[kRadix];
   __shared__ bool is_last;
   if (st[ST_DONE] != 0) return;
@@ -69,86 +159,134 @@ radix_pass(const void* x, int is_f64, uint64_t n, double thr, int k, int pass, i
   __syncthreads();
   const int shift = 64 - kRadixBits * (pass + 1);
   const unsigned long long prefix = st[ST_PREFIX];
-  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
-    double v;
-    const unsigned long long key = key_of(x, is_f64, i, &v);
-    if (!(v >= thr)) continue;
-    if (pass > 0 && (key >> (shift + kRadixBits)) != (prefix >> (shift + kRadixBits))) continue;
-    atomicAdd(&sh[(key >> shift) & (kRadix - 1)], 1u);
+  const int lane = threadIdx.x & 31;
+  const uint64_t span = uint64_t(blockDim.x) * kVec;
+  const uint64_t stride = uint64_t(gridDim.x) * span * 2;
+  // the loop bound is uniform across the block, so whole warps iterate
+  // together and can aggregate equal digits into one shared atomic; two
+  // chunks per iteration keep 2 x kVec loads in flight per thread
+  for (uint64_t base = uint64_t(blockIdx.x) * span * 2; base < n; base += stride) {
+    Chunk c[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      load_chunk<is_f64>(x, aligned, n, base + h * span + uint64_t(threadIdx.x) * kVec, key_thr, &c[h]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < kVec; ++q) {
+        const unsigned long long key = c[h].key[q];
+        const bool ok =
+            c[h].ok[q] && (pass == 0 || (key >> (shift + kRadixBits)) == (prefix >> (shift + kRadixBits)));
+        warp_hist_add(sh, ok, unsigned((key >> shift) & (kRadix - 1)), lane);
+      }
   }
   __syncthreads();
   unsigned* hist = hist_all + pass * kRadix;
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
     if (sh[d]) atomicAdd(&hist[d], sh[d]);
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned long long t = atomicAdd(&st[ST_COUNTER], 1ull);
     is_last = (t == gridDim.x - 1);
   }
   __syncthreads();
-  if (!is_last || threadIdx.x != 0) return;
+  if (!is_last) return;
+  // the last CTA: copy the global histogram (and re-arm it), then one warp
+  // finds the digit holding the k-th largest value with a suffix scan
   __threadfence();
-  volatile unsigned* h = hist;
-  unsigned long long total = 0;
-  for (int d = 0; d < kRadix; ++d) total += h[d];
-  unsigned long long krem = (pass == 0) ? (unsigned long long)k : st[ST_KREM];
-  if (pass == 0) {
-    st[ST_TAKE] = total < (unsigned long long)k ? total : (unsigned long long)k;
-    if (total <= (unsigned long long)k) {
-      st[ST_DONE] = 2;
-    }
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+    sh[d] = static_cast<volatile unsigned*>(hist)[d];
+    hist[d] = 0;
   }
-  if (st[ST_DONE] == 0) {
-    unsigned long long cum = 0;
-    int d = kRadix - 1;
-    for (; d > 0; --d) {
-      if (cum + h[d] >= krem) break;
-      cum += h[d];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  constexpr int kPer = kRadix / 32;
+  unsigned long long part = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) part += sh[lane * kPer + q];
+  unsigned long long suf = part;              // sum over lanes >= this lane
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long t = __shfl_down_sync(0xffffffffu, suf, off);
+    if (lane + off < 32) suf += t;
+  }
+  const unsigned long long total = __shfl_sync(0xffffffffu, suf, 0);
+  const unsigned long long krem = (pass == 0) ? (unsigned long long)k : st[ST_KREM];
+  if (pass == 0 && lane == 0) {
+    st[ST_TAKE] = total < (unsigned long long)k ? total : (unsigned long long)k;
+    if (total <= (unsigned long long)k) st[ST_DONE] = 2;
+  }
+  __syncwarp();
+  const bool refine = !(pass == 0 && total <= (unsigned long long)k);
+  // digits are scanned from the top: the k-th largest lies in the highest
+  // lane whose suffix count reaches krem
+  const unsigned reach = __ballot_sync(0xffffffffu, suf >= krem);
+  const int L = reach ? 31 - __clz(reach) : 0;
+  if (refine && lane == L) {
+    unsigned long long cum = suf - part;
+    int d = lane * kPer + kPer - 1;
+    for (; d > lane * kPer; --d) {
+      if (cum + sh[d] >= krem) break;
+      cum += sh[d];
     }
     st[ST_PREFIX] = prefix | ((unsigned long long)d << shift);
     st[ST_BITS] = (unsigned long long)(kRadixBits * (pass + 1));
     st[ST_KREM] = krem - cum;
-    if (h[d] <= (unsigned)cap)
+    if (sh[d] <= (unsigned)cap)
       st[ST_DONE] = 1;
     else if (last_pass)
       st[ST_DONE] = 3;
   }
-  for (int d = 0; d < kRadix; ++d) h[d] = 0;
-  st[ST_COUNTER] = 0;
+  if (lane == 0) st[ST_COUNTER] = 0;
 }
 
 // Copy the values that are certainly selected, and the current bucket
 // (unless it is an oversized group of exact ties), to the candidate list.
+template <bool is_f64>
 __global__ void __launch_bounds__(kSelThreads)
-compact(const void* x, int is_f64, uint64_t n, double thr, unsigned long long* st, unsigned long long* ck,
-        unsigned long long* ci) {
+compact(const void* x, int aligned, uint64_t n, unsigned long long key_thr, unsigned long long* st,
+        unsigned long long* ck, unsigned long long* ci) {
   const unsigned long long done = st[ST_DONE];
   const int bits = int(st[ST_BITS]);
   const unsigned long long pv = bits ? (st[ST_PREFIX] >> (64 - bits)) : 0ull;
-  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
-    double v;
-    const unsigned long long key = key_of(x, is_f64, i, &v);
-    if (!(v >= thr)) continue;
-    bool take;
-    if (done == 2) {
-      take = true;
-    } else {
-      const unsigned long long hb = key >> (64 - bits);
-      take = (done == 3) ? (hb > pv) : (hb >= pv);
-    }
-    if (take) {
-      const unsigned long long slot = atomicAdd(&st[ST_NCAND], 1ull);
-      ck[slot] = key;
-      ci[slot] = i;
+  const int lane = threadIdx.x & 31;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kVec;
+  for (uint64_t base = uint64_t(blockIdx.x) * blockDim.x * kVec; base < n; base += stride) {
+    Chunk c;
+    const uint64_t i0 = base + uint64_t(threadIdx.x) * kVec;
+    load_chunk<is_f64>(x, aligned, n, i0, key_thr, &c);
+#pragma unroll
+    for (int q = 0; q < kVec; ++q) {
+      bool take = false;
+      if (c.ok[q]) {
+        if (done == 2) {
+          take = true;
+        } else {
+          const unsigned long long hb = c.key[q] >> (64 - bits);
+          take = (done == 3) ? (hb > pv) : (hb >= pv);
+        }
+      }
+      // one global atomic per warp
+      const unsigned m = __ballot_sync(0xffffffffu, take);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long slot = 0;
+        if (lane == leader) slot = atomicAdd(&st[ST_NCAND], (unsigned long long)__popc(m));
+        slot = __shfl_sync(0xffffffffu, slot, leader);
+        if (take) {
+          const unsigned long long r = slot + __popc(m & ((1u << lane) - 1u));
+          ck[r] = c.key[q];
+          ci[r] = i0 + q;
+        }
+      }
     }
   }
 }
 
 // Exact ties beyond capacity: count them per contiguous range ...
 __global__ void __launch_bounds__(kSelThreads)
-tie_count(const void* x, int is_f64, uint64_t n, double thr, const unsigned long long* st, unsigned* counts,
-          uint64_t range) {
+tie_count(const void* x, int is_f64, uint64_t n, unsigned long long key_thr, const unsigned long long* st,
+          unsigned* counts, uint64_t range) {
   if (st[ST_DONE] != 3) return;
   __shared__ unsigned s;
   if (threadIdx.x == 0) s = 0;
@@ -160,7 +298,7 @@ tie_count(const void* x, int is_f64, uint64_t n, double thr, const unsigned long
   for (uint64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
     double v;
     const unsigned long long key = key_of(x, is_f64, i, &v);
-    if (v >= thr && key == tkey) ++c;
+    if (key >= key_thr && !isnan(v) && key == tkey) ++c;
   }
   atomicAdd(&s, c);
   __syncthreads();
@@ -169,8 +307,8 @@ tie_count(const void* x, int is_f64, uint64_t n, double thr, const unsigned long
 
 // ... then append the first KREM of them in ascending bin order.
 __global__ void __launch_bounds__(kSelThreads)
-tie_write(const void* x, int is_f64, uint64_t n, double thr, unsigned long long* st, const unsigned* counts,
-          uint64_t range, unsigned long long* ck, unsigned long long* ci) {
+tie_write(const void* x, int is_f64, uint64_t n, unsigned long long key_thr, unsigned long long* st,
+          const unsigned* counts, uint64_t range, unsigned long long* ck, unsigned long long* ci) {
   if (st[ST_DONE] != 3) return;
   __shared__ unsigned long long base;
   __shared__ unsigned wsum[kSelThreads / 32];
@@ -193,7 +331,7 @@ tie_write(const void* x, int is_f64, uint64_t n, double thr, unsigned long long*
     if (i < e0) {
       double v;
       const unsigned long long key = key_of(x, is_f64, i, &v);
-      tie = (v >= thr && key == tkey);
+      tie = (key >= key_thr && !isnan(v) && key == tkey);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, tie);
     if (lane == 0) wsum[warp] = __popc(bal);
@@ -213,56 +351,63 @@ tie_write(const void* x, int is_f64, uint64_t n, double thr, unsigned long long*
   }
 }
 
-// Sort the candidates by (key descending, index ascending) and emit the
-// first TAKE as (bin, probability).
-__global__ void __launch_bounds__(kSortThreads)
-sort_emit(const void* x, int is_f64, unsigned long long* st, const unsigned long long* ck,
+// Place every candidate by its rank in the order (key descending, index
+// ascending): rank = number of candidates that come before it.  The order
+// is total (indices are distinct), so ranks are distinct; candidates whose
+// rank is below TAKE are written out.  A CTA owns 32 candidates (one per
+// lane); each of its warps counts against one slice of all candidates,
+// read coalesced and broadcast by shuffles.  The last CTA re-arms the
+// control block for the next call.
+constexpr int kRankWarps = 8;
+constexpr int kRankGrid = kMaxSort / 32;
+__global__ void __launch_bounds__(32 * kRankWarps)
+rank_emit(const void* x, int is_f64, unsigned long long* st, const unsigned long long* ck,
           const unsigned long long* ci, unsigned long long* bins_out, double* probs_out, int* n_found) {
-  extern __shared__ unsigned long long sm[];
+  __shared__ unsigned long long part[kRankWarps][32];
+  __shared__ bool is_last;
   const unsigned long long done = st[ST_DONE];
   unsigned long long nc = st[ST_NCAND];
   if (done == 3) nc += st[ST_KREM];
   if (nc > kMaxSort) nc = kMaxSort;
-  unsigned P = 1;
-  while (P < nc) P <<= 1;
-  unsigned long long* keys = sm;
-  unsigned long long* idx = sm + kMaxSort;
-  for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
-    if (i < nc) {
-      keys[i] = ck[i];
-      idx[i] = ci[i];
-    } else {
-      keys[i] = 0ull;
-      idx[i] = ~0ull;
+  const unsigned long long take = st[ST_TAKE];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long me = uint64_t(blockIdx.x) * 32 + lane;
+  if (uint64_t(blockIdx.x) * 32 < nc) {
+    const bool have = me < nc;
+    const unsigned long long mk = have ? ck[me] : 0ull, mi = have ? ci[me] : 0ull;
+    const unsigned long long per = (nc + kRankWarps - 1) / kRankWarps;
+    const unsigned long long j0 = per * warp, j1 = (j0 + per < nc) ? j0 + per : nc;
+    unsigned long long rank = 0;
+    for (unsigned long long jb = j0; jb < j1; jb += 32) {
+      const unsigned long long j = jb + lane;
+      const bool ok = j < j1;
+      const unsigned long long kj = ok ? ck[j] : 0ull, ij = ok ? ci[j] : 0ull;
+      const int m = int((j1 - jb) < 32 ? (j1 - jb) : 32);
+      for (int r = 0; r < m; ++r) {
+        const unsigned long long kr = __shfl_sync(0xffffffffu, kj, r);
+        const unsigned long long ir = __shfl_sync(0xffffffffu, ij, r);
+        rank += (kr > mk) || (kr == mk && ir < mi);
+      }
+    }
+    part[warp][lane] = rank;
+    __syncthreads();
+    if (warp == 0 && have) {
+      unsigned long long r = 0;
+      for (int w = 0; w < kRankWarps; ++w) r += part[w][lane];
+      if (r < take) {
+        bins_out[r] = mi;
+        probs_out[r] = is_f64 ? static_cast<const double*>(x)[mi] : double(static_cast<const float*>(x)[mi]);
+      }
     }
   }
   __syncthreads();
-  // bitonic sort: "a before b" <=> a.key > b.key || (a.key == b.key && a.idx < b.idx)
-  for (unsigned size = 2; size <= P; size <<= 1) {
-    for (unsigned stride = size >> 1; stride > 0; stride >>= 1) {
-      for (unsigned i = threadIdx.x; i < P; i += blockDim.x) {
-        const unsigned j = i ^ stride;
-        if (j > i) {
-          const bool up = ((i & size) == 0);
-          const unsigned long long ka = keys[i], kb = keys[j];
-          const unsigned long long ia = idx[i], ib = idx[j];
-          const bool a_first = (ka > kb) || (ka == kb && ia < ib);
-          if (a_first != up) {
-            keys[i] = kb; keys[j] = ka;
-            idx[i] = ib; idx[j] = ia;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  const unsigned long long take = st[ST_TAKE];
-  for (unsigned i = threadIdx.x; i < take; i += blockDim.x) {
-    const unsigned long long b = idx[i];
-    bins_out[i] = b;
-    probs_out[i] = is_f64 ? static_cast<const double*>(x)[b] : double(static_cast<const float*>(x)[b]);
-  }
   if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long t = atomicAdd(&st[ST_COUNTER], 1ull);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
     *n_found = int(take);
     for (int w = 0; w < ST_WORDS; ++w) st[w] = 0;   // re-arm for the next call
   }
@@ -275,6 +420,31 @@ sum_kernel(const void* x, int is_f64, uint64_t n, double* partials, unsigned* co
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
     s += is_f64 ? static_cast<const double*>(x)[i] : double(static_cast<const float*>(x)[i]);
   finish_total(s, partials, counter, total, red);
+}
+
+// Key of the smallest value of the input type that is >= thr (host side,
+// same order-preserving transform as the kernels).
+unsigned long long threshold_key(int is_f64, double thr) {
+  if (is_f64) {
+    unsigned long long u;
+    std::memcpy(&u, &thr, 8);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+  }
+  float f = float(thr);                       // round to nearest, then up if below
+  if (double(f) < thr) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+  unsigned u;
+  std::memcpy(&u, &f, 4);
+  const unsigned k = (u >> 31) ? ~u : (u | 0x80000000u);
+  return (unsigned long long)k << 32;
+}
+
+// Up to two CTAs per SM: every CTA adds its histogram into the global one
+// with same-address atomics, so fewer, longer-lived CTAs are cheaper.
+inline int vec_grid(uint64_t n) {
+  uint64_t g = (n + uint64_t(kSelThreads) * kVec - 1) / (uint64_t(kSelThreads) * kVec);
+  if (g < 1) g = 1;
+  if (g > 152 * 2) g = 152 * 2;
+  return int(g);
 }
 
 inline int stream_grid(uint64_t n, int max_blocks) {
@@ -316,19 +486,27 @@ cudaError_t launch_select(const SelectWork& w, const void* x, int is_f64, uint64
   // bucket size at which refinement stops: the sort then sees <= k + cap values
   const int cap = (k > 512 ? k : 512) < kMaxSort - k ? (k > 512 ? k : 512) : kMaxSort - k;
   unsigned long long* st = reinterpret_cast<unsigned long long*>(w.state);
-  const int g = stream_grid(n, w.max_blocks);
+  const int aligned = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+  const unsigned long long kt = threshold_key(is_f64, threshold);
+  const int g = vec_grid(n);
   const int passes = is_f64 ? kPasses : 4;
-  for (int p = 0; p < passes; ++p)
-    radix_pass<<<g, kSelThreads, 0, s>>>(x, is_f64, n, threshold, k, p, p == passes - 1, cap, w.hist, st);
-  compact<<<g, kSelThreads, 0, s>>>(x, is_f64, n, threshold, st, w.cand_key, w.cand_idx);
+  for (int p = 0; p < passes; ++p) {
+    if (is_f64)
+      radix_pass<true><<<g, kSelThreads, 0, s>>>(x, aligned, n, kt, k, p, p == passes - 1, cap, w.hist, st);
+    else
+      radix_pass<false><<<g, kSelThreads, 0, s>>>(x, aligned, n, kt, k, p, p == passes - 1, cap, w.hist, st);
+  }
+  if (is_f64)
+    compact<true><<<g, kSelThreads, 0, s>>>(x, aligned, n, kt, st, w.cand_key, w.cand_idx);
+  else
+    compact<false><<<g, kSelThreads, 0, s>>>(x, aligned, n, kt, st, w.cand_key, w.cand_idx);
   const uint64_t range = (n + w.max_blocks - 1) / w.max_blocks;
   const unsigned tb = unsigned((n + range - 1) / (range ? range : 1));
   const uint64_t rng = range ? range : 1;
-  tie_count<<<tb ? tb : 1, kSelThreads, 0, s>>>(x, is_f64, n, threshold, st, w.tie_count, rng);
-  tie_write<<<tb ? tb : 1, kSelThreads, 0, s>>>(x, is_f64, n, threshold, st, w.tie_count, rng, w.cand_key,
-                                               w.cand_idx);
-  const size_t smem = 2 * sizeof(unsigned long long) * kMaxSort;
-  sort_emit<<<1, kSortThreads, smem, s>>>(x, is_f64, st, w.cand_key, w.cand_idx, bins_out, probs_out, n_found);
+  tie_count<<<tb ? tb : 1, kSelThreads, 0, s>>>(x, is_f64, n, kt, st, w.tie_count, rng);
+  tie_write<<<tb ? tb : 1, kSelThreads, 0, s>>>(x, is_f64, n, kt, st, w.tie_count, rng, w.cand_key, w.cand_idx);
+  rank_emit<<<kRankGrid, 32 * kRankWarps, 0, s>>>(x, is_f64, st, w.cand_key, w.cand_idx, bins_out, probs_out,
+                                                 n_found);
   return cudaGetLastError();
 }
 
@@ -376,10 +554,7 @@ cudaError_t launch_select_static(int device, const void* x, int is_f64, uint64_t
   return launch_select(w, x, is_f64, n, k, threshold, bins_out, probs_out, n_found, s);
 }
 
-cudaError_t select_configure() {
-  return cudaFuncSetAttribute(sort_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(2 * sizeof(unsigned long long) * kMaxSort));
-}
+cudaError_t select_configure() { return cudaSuccess; }
 
 cudaError_t launch_sum(const void* x, int is_f64, uint64_t n, double* partials, unsigned* counter, double* total,
                        cudaStream_t s) {

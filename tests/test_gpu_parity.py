@@ -117,6 +117,28 @@ def test_grid_40q_fp64_chunked(ctx):
     assert abs(tot - O.total_probability(ref)) < 1e-6
 
 
+@pytest.mark.parametrize("wl,out", [("merged_30q", "float32"), ("grid_40q", "float64"), ("full_state_12q", "float32")])
+def test_split_bf16_matches_oracle(ctx, wl, out):
+    # split-BF16 (three BF16 planes, six products) on tcgen05 for the steps
+    # with M, N >= 128; FP32 SIMT for the rest
+    w = getattr(W, wl)()
+    P, tot = gpu_run(ctx, w, out_dtype=out, precision="split_bf16")
+    ref = oracle_run(w)
+    check(P, ref)
+    assert abs(tot - O.total_probability(ref)) < 1e-6
+
+
+def test_split_bf16_contraction_bound_step(ctx):
+    # two subcircuits sharing 4 cut edges: one 1024 x 1024 x 256 step on the
+    # tensor cores (four 64-wide K blocks through the two-stage pipeline)
+    w = W.random_line_chain(7, [14, 14], [4], 2, [10, 10])
+    assert w.circuit.n_edges == 4 and w.n_active == 20
+    ref = oracle_run(w)
+    for prec in ("split_bf16", "fp32"):
+        P, tot = gpu_run(ctx, w, precision=prec)
+        check(P, ref)
+
+
 def test_zoomed_children_sum_to_parent(ctx):
     w = W.merged_30q()
     q = w.circuit.data_qubits[2][6]
