@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--workload", default="line30_K8_a20", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the split-BF16 variant and the tensor microbench")
     return ap.parse_args()
 
 
@@ -77,6 +79,58 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s) for a kernel timed alone: the
+    measured burst figure, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def tensor_microbench(dev, reps: int = 20) -> dict:
+    """A contraction-bound step: two subcircuits sharing 4 cut edges, 12
+    active qubits each, so the last step is C[4096 x 4096] = A[4096 x 256]
+    B^T (Section 6.1, Fig. 4a).  Times that step (stage events) in
+    split-BF16 on the tensor cores and in FP32 SIMT; hardware flops of the
+    split form = 6 products x 2MNK."""
+    import torch
+    import oracle as O
+    from paper_2207_00933_gb300 import Context
+    from synthetic import workloads as W
+    w = W.random_line_chain(11, [16, 16], [4], 1, [12, 12])
+    c = w.circuit
+    g = O.Graph.from_arrays(c.n_qubits, *c.graph_arrays())
+    ref = O.reconstruct(g, [p.astype(np.float64) for p in w.probs], w.roles)
+    out = {}
+    with Context(dev.index or 0) as ctx:
+        cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).to(dev) for p in w.probs])
+        qid, na = ctx.set_qubit_roles(cid, w.roles)
+        M, N, K = ctx.query_steps(qid)[-1]
+        res = torch.empty(1 << na, dtype=torch.float32, device=dev)
+        for prec in ("split_bf16", "fp32"):
+            for _ in range(3):
+                ctx.reconstruct(qid, res, prec)
+            torch.cuda.synchronize(dev)
+            ctx.profile_enable(True)
+            for _ in range(reps):
+                ctx.reconstruct(qid, res, prec)
+            pr = ctx.profile_read()
+            ctx.profile_enable(False)
+            ms = pr["ms"]["final"] / max(1, pr["calls"]["final"])
+            err = float(np.abs(res.double().cpu().numpy() - ref).max())
+            alg = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+            d = {"ms": ms, "alg_tflops": alg, "max_abs_err_vs_fp64": err}
+            if prec == "split_bf16":
+                peak, src = bf16_peak()
+                d.update({"hw_tflops": 6 * alg, "peak_tflops": peak, "peak_source": src,
+                          "tensor_frac": 6 * alg / peak})
+            out[prec] = d
+        ctx.unload(cid)
+    return {"shape": {"M": M, "N": N, "K": K}, "workload": "randline32_K4_a24 (two subcircuits, 4 shared cuts)", **out}
 
 
 # ---- clocks during the timed region ---------------------------------------------
@@ -268,9 +322,11 @@ def main():
     kn = torch.empty(1, dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    prec = args.precision
+
     def step():
         ctx.update_subcircuit_outputs(cid, probs_dev)
-        ctx.reconstruct(qid, out, "fp32", tot)
+        ctx.reconstruct(qid, out, prec, tot)
         ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
 
     for _ in range(max(3, args.warmup)):
@@ -368,7 +424,7 @@ def main():
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         ctx.update_subcircuit_outputs(cid, probs_host)            # H2D of this step's inputs inside
-        ctx.reconstruct(qid, out, "fp32", tot)
+        ctx.reconstruct(qid, out, prec, tot)
         ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
         h_bins.copy_(kb, non_blocking=True)
         h_probs.copy_(kp, non_blocking=True)
@@ -389,7 +445,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16x3", "data": "synthetic",
             "config": {"workload": args.workload, "bins": bins, "active_qubits": na, "cuts": c.n_edges,
                        "subcircuits": c.n_subcircuits, "topk": TOPK, "out_dtype": str(out_dtype).split(".")[-1],
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
@@ -407,6 +463,9 @@ def main():
             "e2e": {"value": world * bins * args.steps / (e2e_total * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         }
+        line["config"]["precision"] = prec
+        if world == 1 and not args.no_extras:
+            line["tensor_microbench"] = tensor_microbench(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

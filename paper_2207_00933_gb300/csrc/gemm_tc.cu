@@ -7,18 +7,21 @@
 // lo*hi -- all accumulated in one FP32 accumulator in tensor memory, which
 // gives about FP32 accuracy for the signed I/X/Y/Z sums.
 //
-// Per CTA: one 128 x 128 output tile, 6 warps.
+// Persistent CTAs (one per SM) walk the 128 x 128 output tiles; 6 warps:
 //   warp 0 (one thread): TMA producer -- for each 64-wide block of the
 //     shared index it loads the three A planes and three B planes
-//     (128 x 64 BF16 each, 128-byte swizzle) into one pipeline stage;
-//   warp 1 (one thread): allocates 128 TMEM columns and issues
+//     (128 x 64 BF16 each, 128-byte swizzle) into one of two pipeline stages;
+//   warp 1 (one thread): allocates 2 x 128 TMEM columns and issues
 //     tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 128, K = 16):
 //     6 plane pairs x 4 K-slices per stage, then commits the stage back to
 //     the producer;
-//   warps 2-5: epilogue -- wait for the last commit, read the accumulator
-//     rows with tcgen05.ld (warp w reads TMEM lanes 32*(w%4) .. +31), scale
-//     by alpha, write through rowmap/colmap (FP32, FP64 or BF16 planes) and
-//     add the written values into the per-CTA probability sum.
+//   warps 2-5: epilogue -- wait for a tile's last commit, read the
+//     accumulator rows with tcgen05.ld (warp w reads TMEM lanes 32*(w%4) ..
+//     +31), scale by alpha, write through rowmap/colmap (vector stores where
+//     the 16 columns are contiguous; FP32, FP64 or BF16 planes), add the
+//     written values into the per-CTA probability sum, and hand the TMEM
+//     buffer back.  Two accumulator buffers let the epilogue of one tile run
+//     under the MMAs of the next.
 // Every mbarrier wait is bounded; on timeout the CTA records an error code,
 // drains its own copies (bounded) and frees its TMEM before returning.
 #include <cuda.h>
@@ -31,7 +34,7 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBN = 128;
-constexpr int kBK = 64;            // 64 BF16 = 128 bytes: one swizzle row
+constexpr int kBK = 64;            // 64 BF16 = 128 bytes: one 128-byte swizzle row
 constexpr int kStages = 2;
 constexpr int kTileA = kBM * kBK * 2;
 constexpr int kTileB = kBN * kBK * 2;
@@ -130,23 +133,48 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Store 16 consecutive columns of one output row.  `contig`: the columns'
+// offsets are consecutive and 16-byte aligned, so vector stores are used.
+__device__ __forceinline__ void store16(const GemmTcArgs& a, uint64_t off, bool contig, const float* f,
+                                        const uint64_t* colmap, int64_t col0, uint64_t rbase, int ncols) {
+  if (contig && ncols == 16) {
+    if (a.kind == OUT_F32) {
+      float4* p = reinterpret_cast<float4*>(static_cast<float*>(a.C) + off);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) p[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+      return;
+    }
+    if (a.kind == OUT_F64) {
+      double2* p = reinterpret_cast<double2*>(static_cast<double*>(a.C) + off);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) p[q] = make_double2(double(f[2 * q]), double(f[2 * q + 1]));
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (j < ncols) store_out_f(a.C, a.kind, a.plane_stride, rbase + colmap[col0 + j], f[j]);
+}
+
+// Persistent: grid = min(tiles, SMs); CTA b takes tiles b, b + grid, ...
+// The accumulator is double-buffered in TMEM (2 x 128 columns) so that the
+// epilogue of one tile overlaps the loads and MMAs of the next.
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmTcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* accf = empty + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* acc_full = empty + kStages;      // [2]: MMA -> epilogue
+  uint64_t* acc_empty = acc_full + 2;        // [2]: epilogue -> MMA
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   __shared__ double red[kThreads / 32];
   __shared__ int failed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tiles_n = a.Np / kBN;
   const int tn_shift = __ffsll(tiles_n) - 1;
-  const int64_t tile = blockIdx.x;
-  const int m0 = int((tile >> tn_shift) * kBM);
-  const int n0 = int((tile & (tiles_n - 1)) * kBN);
+  const int64_t ntiles = (a.Mp / kBM) * tiles_n;
   const int nk = int(a.Kp / kBK);
 
   if (threadIdx.x == 0) {
@@ -155,14 +183,17 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);            // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
+                 "r"(2 * kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -175,82 +206,111 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   double sum_d = 0.0;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      const int use = kb / kStages;
-      if (use > 0 && !mbar_wait(&empty[s], uint32_t((use - 1) & 1))) {
-        atomicExch(&failed, 1);
-        break;
+    // ---- TMA producer: one continuous ring of stages across all tiles
+    int64_t it = 0, issued = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+      const int m0 = int((tile >> tn_shift) * kBM);
+      const int n0 = int((tile & (tiles_n - 1)) * kBN);
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = int(it % kStages);
+        const int64_t use = it / kStages;
+        if (use > 0 && !mbar_wait(&empty[s], uint32_t((use - 1) & 1))) {
+          atomicExch(&failed, 1);
+          break;
+        }
+        uint8_t* st = smem + s * kStageBytes;
+        mbar_expect_tx(&full[s], kStageBytes);
+        for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
+        for (int p = 0; p < 3; ++p) tma_load_3d(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
+        issued = it + 1;
       }
-      if (failed) break;
-      uint8_t* st = smem + s * kStageBytes;
-      mbar_expect_tx(&full[s], kStageBytes);
-      for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
-      for (int p = 0; p < 3; ++p) tma_load_3d(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
-      issued = kb + 1;
     }
     // drain: every stage we filled must have landed before the CTA exits
-    for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
-      if (!mbar_wait(&full[kb % kStages], uint32_t((kb / kStages) & 1))) atomicExch(&failed, 1);
+    for (int64_t j = (issued > kStages ? issued - kStages : 0); j < issued; ++j)
+      if (!mbar_wait(&full[j % kStages], uint32_t((j / kStages) & 1))) atomicExch(&failed, 1);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
     constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
     constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
-    bool ok = true;
-    for (int kb = 0; kb < nk && ok; ++kb) {
-      const int s = kb % kStages;
-      if (!mbar_wait(&full[s], uint32_t((kb / kStages) & 1)) || failed) {
+    int64_t it = 0, t = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++t) {
+      const int buf = int(t & 1);
+      const int64_t use = t >> 1;
+      if (use > 0 && !mbar_wait(&acc_empty[buf], uint32_t((use - 1) & 1))) {
         atomicExch(&failed, 1);
-        ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(smem + s * kStageBytes);
+      const uint32_t dacc = tmem + uint32_t(buf * kTmemCols);
+      bool ok = true;
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = int(it % kStages);
+        if (!mbar_wait(&full[s], uint32_t((it / kStages) & 1)) || failed) {
+          atomicExch(&failed, 1);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = smem_u32(smem + s * kStageBytes);
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        const uint64_t da = smem_desc(base + pa[q] * kTileA);
-        const uint64_t db = smem_desc(base + 3 * kTileA + pb[q] * kTileB);
+        for (int q = 0; q < 6; ++q) {
+          const uint64_t da = smem_desc(base + pa[q] * kTileA);
+          const uint64_t db = smem_desc(base + 3 * kTileA + pb[q] * kTileB);
 #pragma unroll
-        for (int kk = 0; kk < kBK / 16; ++kk)   // K = 16 per instruction: +32 bytes = +2 in the address field
-          mma_bf16(tmem, da + 2 * kk, db + 2 * kk, (kb | q | kk) != 0);
+          for (int kk = 0; kk < kBK / 16; ++kk)   // K = 16 per instruction: +32 bytes = +2 in the address field
+            mma_bf16(dacc, da + 2 * kk, db + 2 * kk, (kb | q | kk) != 0);
+        }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&empty[s]);
+      mma_commit(&acc_full[buf]);
+      if (!ok) break;
     }
-    mma_commit(accf);
   } else if (warp >= 2) {
     // ---- epilogue
-    if (mbar_wait(accf, 0) && !failed) {
+    const int quad = warp & 3;
+    const float alpha_f = float(a.alpha);
+    int64_t t = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+      const int buf = int(t & 1);
+      if (!mbar_wait(&acc_full[buf], uint32_t((t >> 1) & 1)) || failed) {
+        atomicExch(&failed, 1);
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int quad = warp & 3;
-      const int r = quad * 32 + lane;
-      const int64_t row = int64_t(m0) + r;
-      const float alpha_f = float(a.alpha);
+      const int64_t m0 = (tile >> tn_shift) * kBM;
+      const int64_t n0 = (tile & (tiles_n - 1)) * kBN;
+      const int64_t row = m0 + quad * 32 + lane;
       const bool row_ok = row < a.M;
       const uint64_t rbase = row_ok ? a.rowmap[row] : 0;
       for (int c0 = 0; c0 < kBN; c0 += 16) {
         float v[16];
-        tmem_ld16(tmem + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
-        if (!row_ok) continue;
+        tmem_ld16(tmem + uint32_t(buf * kTmemCols) + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
+        const int64_t col0 = n0 + c0;
+        const int ncols = int(a.N - col0 < 16 ? (a.N - col0 > 0 ? a.N - col0 : 0) : 16);
+        if (!row_ok || ncols == 0) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int64_t col = int64_t(n0) + c0 + j;
-          if (col >= a.N) continue;
-          const float f = v[j] * alpha_f;
-          if (a.kind == OUT_F64) sum_d += double(f); else sum_f += f;
-          store_out_f(a.C, a.kind, a.plane_stride, rbase + a.colmap[col], f);
+          v[j] *= alpha_f;
+          if (j < ncols) {
+            if (a.kind == OUT_F64) sum_d += double(v[j]); else sum_f += v[j];
+          }
         }
+        const uint64_t c_first = a.colmap[col0];
+        const bool contig = ncols == 16 && a.colmap[col0 + 15] == c_first + 15 &&
+                            ((rbase + c_first) & (a.kind == OUT_F64 ? 1 : 3)) == 0;
+        store16(a, rbase + c_first, contig, v, a.colmap, col0, rbase, ncols);
       }
-    } else {
-      atomicExch(&failed, 1);
+      // hand the accumulator back to the MMA warp
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
   }
   if (failed && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
   if (a.partials) finish_total(sum_d + double(sum_f), a.partials, a.counter, a.total, red);
@@ -309,7 +369,8 @@ cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s) {
   CUtensorMap ma, mb;
   if (!make_map(&ma, a.A, a.Mp, a.Kp) || !make_map(&mb, a.B, a.Np, a.Kp)) return cudaErrorInvalidValue;
   const int64_t tiles = (a.Mp / kBM) * (a.Np / kBN);
-  gemm_tc_kernel<<<unsigned(tiles), kThreads, kSmemBytes, s>>>(ma, mb, a);
+  const int64_t grid = tiles < 152 ? tiles : 152;    // persistent: at most one CTA per SM
+  gemm_tc_kernel<<<unsigned(grid), kThreads, kSmemBytes, s>>>(ma, mb, a);
   return cudaGetLastError();
 }
 
