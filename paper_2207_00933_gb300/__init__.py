@@ -68,6 +68,10 @@ _SIGS = {
                                     _c.POINTER(_c.c_int64)]),
     "sqc_top_bins_noalloc": (_c.c_int32, [_c.c_int, _P, _c.c_int, _c.c_uint64, _c.c_int32, _c.c_double, _P, _P,
                                           _P, _P]),
+    "sqc_batch_create": (_c.c_int32, [_P, _c.c_int32, _P, _P, _c.c_int, _P, _c.POINTER(_c.c_int64)]),
+    "sqc_batch_run": (_c.c_int32, [_P, _c.c_int64, _P]),
+    "sqc_batch_status": (_c.c_int32, [_P, _c.c_int64]),
+    "sqc_batch_release": (_c.c_int32, [_P, _c.c_int64]),
     "sqc_profile_enable": (_c.c_int32, [_P, _c.c_int]),
     "sqc_profile_read": (_c.c_int32, [_P, _P, _P, _P]),
 }
@@ -252,6 +256,30 @@ class Context:
         self._check(self._lib.sqc_reconstruct(self._h, query, PREC[precision], _ptr(out), _dtype_code(out),
                                               out.numel() * out.element_size(), _ptr(total_prob),
                                               _stream_handle(stream)))
+
+    # -- batches ----------------------------------------------------------
+    def batch_create(self, queries: list[int], outs: list, totals=None) -> int:
+        """One persistent launch for many queries (sqc_batch_create): outs[j]
+        is the device tensor receiving query j's bins (all float32 or all
+        float64); totals: optional device float64 tensor [len(queries)]."""
+        n = len(queries)
+        qa = (ctypes.c_int64 * n)(*queries)
+        oa = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        dt = _dtype_code(outs[0])
+        if any(_dtype_code(o) != dt for o in outs):
+            raise ValueError("batch outputs must share one dtype")
+        b = ctypes.c_int64()
+        self._check(self._lib.sqc_batch_create(self._h, n, qa, oa, dt, _ptr(totals), ctypes.byref(b)))
+        return b.value
+
+    def batch_run(self, batch: int, stream=None):
+        self._check(self._lib.sqc_batch_run(self._h, batch, _stream_handle(stream)))
+
+    def batch_status(self, batch: int):
+        self._check(self._lib.sqc_batch_status(self._h, batch))
+
+    def batch_release(self, batch: int):
+        self._check(self._lib.sqc_batch_release(self._h, batch))
 
     def top_bins(self, query: int, probs, k: int, threshold: float = -math.inf, bins_out=None, probs_out=None,
                  n_found=None, stream=None):

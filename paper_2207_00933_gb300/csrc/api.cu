@@ -84,6 +84,14 @@ struct Plan {
   double flops = 0.0;
 };
 
+struct Batch {
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  BatchLaunch L{};
+  int grid = 0;
+  std::vector<sqc_query_id> queries;
+};
+
 struct Query {
   sqc_circuit_id circuit = 0;
   std::vector<int8_t> roles;
@@ -116,6 +124,7 @@ struct sqc_ctx {
   int64_t next_id = 1;
   std::map<int64_t, std::unique_ptr<Circuit>> circuits;
   std::map<int64_t, std::unique_ptr<Query>> queries;
+  std::map<int64_t, std::unique_ptr<Batch>> batches;
 };
 
 namespace {
@@ -729,6 +738,7 @@ SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg) 
   e = select_configure();
   if (e == cudaSuccess) e = attr_configure();
   if (e == cudaSuccess) e = gemm_tc_configure();
+  if (e == cudaSuccess) e = batch_configure();
   if (e != cudaSuccess) return fail(nullptr, SQC_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(e));
   *out = ctx.release();
   return SQC_OK;
@@ -741,6 +751,7 @@ SQC_API void sqc_destroy(sqc_ctx* ctx) {
     cudaDeviceSynchronize();
     for (auto& kv : ctx->queries) free_query(ctx, kv.second.get());
     for (auto& kv : ctx->circuits) free_circuit(ctx, kv.second.get());
+    for (auto& kv : ctx->batches) dev_free(ctx, kv.second->work, kv.second->work_bytes);
     for (auto& m : ctx->marks) {
       cudaEventDestroy(m.start);
       cudaEventDestroy(m.stop);
@@ -1030,6 +1041,188 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* prob
   CK(launch_select(it->second->sel, probs, dtype == SQC_F64, n, k, threshold,
                    reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found,
                    static_cast<cudaStream_t>(stream)));
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
+                                    sqc_dtype out_dtype, double* totals, sqc_batch_id* out_b) {
+  if (!ctx || !qs || !outs || !out_b || n < 1) return fail(ctx, SQC_EINVAL, "batch: null argument or n < 1");
+  if (out_dtype != SQC_F32 && out_dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "out_dtype must be F32 or F64");
+  DeviceGuard g(ctx->device);
+  const int out_kind = out_dtype == SQC_F64 ? OUT_F64 : OUT_F32;
+  std::vector<MergeDesc> mdescs;
+  std::vector<BatchStep> steps;
+  std::vector<unsigned> expected;
+  struct Pending { BatchItem it; int level; };
+  std::vector<Pending> items;
+  std::vector<int64_t> part_off;     // per batch step with a probability sum: offset into partials
+  int64_t n_parts = 0;
+  for (int j = 0; j < n; ++j) {
+    auto it = ctx->queries.find(qs[j]);
+    if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "batch: unknown query");
+    Query& q = *it->second;
+    auto cit = ctx->circuits.find(q.circuit);
+    if (cit == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "batch: circuit of a query was unloaded");
+    const Circuit& c = *cit->second;
+    Plan& P = q.plans[SQC_PREC_FP32];
+    if (P.steps.empty()) return fail(ctx, SQC_EINVAL, "batch: every query needs at least two subcircuits");
+    if (!outs[j]) return fail(ctx, SQC_EINVAL, "batch: null output");
+    // tensor slots of this query
+    std::vector<int> slot(P.tensors.size(), -1), level(P.tensors.size(), 0);
+    for (size_t t = 0; t < P.tensors.size(); ++t) {
+      if (int(t) == P.final_tensor) continue;
+      slot[t] = int(expected.size());
+      expected.push_back(0);
+    }
+    for (int i = 0; i < c.nC; ++i) {
+      const int di = int(mdescs.size());
+      mdescs.push_back(P.merge_host[i]);
+      const MergeDesc& d = P.merge_host[i];
+      const int64_t per = 256 / d.lanes;
+      const int64_t nblk = ((d.rows << d.a) + per - 1) / per;
+      for (int64_t b = 0; b < nblk; ++b) items.push_back({{kItemMerge, di, b, -1, -1, slot[i]}, 0});
+      expected[slot[i]] = unsigned(nblk);
+    }
+    const double alpha = std::ldexp(1.0, -c.K);
+    for (size_t si = 0; si < P.steps.size(); ++si) {
+      const Step& st = P.steps[si];
+      const bool last = si + 1 == P.steps.size();
+      BatchStep bs{};
+      GemmArgs& a = bs.a;
+      a.A = static_cast<const float*>(P.tensors[st.x].buf);
+      a.B = static_cast<const float*>(P.tensors[st.y].buf);
+      a.M = st.M;
+      a.N = st.N;
+      a.K = st.Kd;
+      a.rowmap = st.rowmap;
+      a.colmap = st.colmap;
+      a.vec4 = st.vec4;
+      a.C = last ? outs[j] : P.tensors[st.z].buf;
+      a.kind = last ? out_kind : OUT_F32;
+      a.alpha = last ? alpha : 1.0;
+      a.chunk = (last && out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
+                    ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
+                    : 0;
+      int64_t bm = 0, bn = 0;
+      bs.cfg = batch_tile_cfg(a.M, a.N, a.K, a.chunk > 0, a.chunk, &bm, &bn);
+      bs.ntiles = ((a.M + bm - 1) / bm) * ((a.N + bn - 1) / bn);
+      if (last && totals) {
+        part_off.push_back(n_parts);
+        bs.total = totals + j;
+        n_parts += bs.ntiles;
+      } else {
+        part_off.push_back(-1);
+      }
+      const int lvl = 1 + std::max(level[st.x], level[st.y]);
+      level[st.z] = lvl;
+      const int si_b = int(steps.size());
+      steps.push_back(bs);
+      for (int64_t t = 0; t < bs.ntiles; ++t)
+        items.push_back({{kItemGemm, si_b, t, slot[st.x], slot[st.y], last ? -1 : slot[st.z]}, lvl});
+      if (!last) expected[slot[st.z]] = unsigned(bs.ntiles);
+    }
+  }
+  // dependency order: merges, then steps level by level (stable)
+  std::stable_sort(items.begin(), items.end(), [](const Pending& a, const Pending& b) { return a.level < b.level; });
+
+  auto B = std::make_unique<Batch>();
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t o_items = off; off = align(off + sizeof(BatchItem) * items.size());
+  const size_t o_md = off; off = align(off + sizeof(MergeDesc) * mdescs.size());
+  const size_t o_st = off; off = align(off + sizeof(BatchStep) * steps.size());
+  const size_t o_cnt = off; off = align(off + sizeof(unsigned) * expected.size());
+  const size_t o_exp = off; off = align(off + sizeof(unsigned) * expected.size());
+  const size_t o_part = off; off = align(off + sizeof(double) * size_t(std::max<int64_t>(n_parts, 1)));
+  const size_t o_pc = off; off = align(off + sizeof(unsigned) * steps.size());
+  const size_t o_ctl = off; off = align(off + 64);
+  B->work_bytes = off;
+  sqc_status st = dev_alloc(ctx, &B->work, off);
+  if (st != SQC_OK) return st;
+  char* base = static_cast<char*>(B->work);
+  for (size_t k = 0; k < steps.size(); ++k) {
+    steps[k].counter = reinterpret_cast<unsigned*>(base + o_pc) + k;
+    if (part_off[k] >= 0) {
+      steps[k].partials = reinterpret_cast<double*>(base + o_part) + part_off[k];
+      steps[k].a.partials = steps[k].partials;     // marks the query's last step
+      steps[k].a.counter = steps[k].counter;
+      steps[k].a.total = steps[k].total;
+    }
+  }
+  std::vector<BatchItem> flat(items.size());
+  for (size_t k = 0; k < items.size(); ++k) flat[k] = items[k].it;
+  cudaError_t e = cudaMemcpy(base + o_items, flat.data(), sizeof(BatchItem) * flat.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !mdescs.empty())
+    e = cudaMemcpy(base + o_md, mdescs.data(), sizeof(MergeDesc) * mdescs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + o_st, steps.data(), sizeof(BatchStep) * steps.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + o_exp, expected.data(), sizeof(unsigned) * expected.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(base + o_cnt, 0, sizeof(unsigned) * expected.size());
+  if (e == cudaSuccess) e = cudaMemset(base + o_pc, 0, sizeof(unsigned) * steps.size());
+  if (e == cudaSuccess) e = cudaMemset(base + o_ctl, 0, 64);
+  if (e != cudaSuccess) {
+    dev_free(ctx, B->work, B->work_bytes);
+    return cuda_fail(ctx, e, "batch upload");
+  }
+  BatchLaunch& L = B->L;
+  L.items = reinterpret_cast<const BatchItem*>(base + o_items);
+  L.n_items = int64_t(flat.size());
+  L.mdescs = reinterpret_cast<const MergeDesc*>(base + o_md);
+  L.steps = reinterpret_cast<const BatchStep*>(base + o_st);
+  L.counts = reinterpret_cast<unsigned*>(base + o_cnt);
+  L.expected = reinterpret_cast<const unsigned*>(base + o_exp);
+  L.n_slots = int64_t(expected.size());
+  L.head = reinterpret_cast<unsigned long long*>(base + o_ctl);
+  L.done = reinterpret_cast<unsigned*>(base + o_ctl + 8);
+  L.abort = reinterpret_cast<int*>(base + o_ctl + 16);
+  L.err = reinterpret_cast<int*>(base + o_ctl + 20);
+  int sms = 152, per = 2;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  B->grid = int(std::min<int64_t>(int64_t(sms) * per, L.n_items));
+  B->queries.assign(qs, qs + n);
+  const int64_t id = ctx->next_id++;
+  ctx->batches[id] = std::move(B);
+  *out_b = id;
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_batch_run(sqc_ctx* ctx, sqc_batch_id b, void* stream) {
+  if (!ctx) return SQC_EINVAL;
+  auto it = ctx->batches.find(b);
+  if (it == ctx->batches.end()) return fail(ctx, SQC_ENOTFOUND, "unknown batch");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StageScope scope(ctx, s, SQC_STAGE_CONTRACT);
+  CK(launch_batch(it->second->L, it->second->grid, s));
+  ctx->launches += 1;
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_batch_status(sqc_ctx* ctx, sqc_batch_id b) {
+  if (!ctx) return SQC_EINVAL;
+  auto it = ctx->batches.find(b);
+  if (it == ctx->batches.end()) return fail(ctx, SQC_ENOTFOUND, "unknown batch");
+  DeviceGuard g(ctx->device);
+  CK(cudaDeviceSynchronize());
+  int err = 0;
+  CK(cudaMemcpy(&err, it->second->L.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    const int zero = 0;
+    CK(cudaMemcpy(it->second->L.err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    return fail(ctx, SQC_ETIMEOUT, "batch: a bounded device wait gave up");
+  }
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b) {
+  if (!ctx) return SQC_EINVAL;
+  auto it = ctx->batches.find(b);
+  if (it == ctx->batches.end()) return fail(ctx, SQC_ENOTFOUND, "unknown batch");
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  dev_free(ctx, it->second->work, it->second->work_bytes);
+  ctx->batches.erase(it);
   return SQC_OK;
 }
 

@@ -1,0 +1,173 @@
+// Device-side bodies shared by the per-step kernels and the persistent
+// batched kernel: one merge CTA-block and one SIMT contraction tile.
+#pragma once
+#include "common.cuh"
+
+namespace sqc {
+
+constexpr int kOpThreads = 256;
+
+// One CTA-block of the merge of descriptor d (Section 4, Algorithm 2):
+// blk is the block index relative to the descriptor's first block.
+__device__ __forceinline__ void merge_block(const MergeDesc& d, int64_t blk) {
+  const int lanes = d.lanes;                       // power of two
+  const int lshift = __ffs(lanes) - 1;
+  const int64_t o = (blk << (8 - lshift)) + (threadIdx.x >> lshift);
+  const int lane = threadIdx.x & (lanes - 1);
+  const int64_t total = d.rows << d.a;
+  const bool valid = o < total;
+  float acc = 0.f;
+  if (valid) {
+    const int64_t e = o >> d.a;
+    const uint32_t b = uint32_t(o & ((int64_t(1) << d.a) - 1));
+    const float* row = d.A + (e << d.n);
+    const uint32_t run = 1u << d.m;
+    if (d.fast) {
+      const float* src = row + (d.zoom_val | (b << d.m));
+      if (run >= 4u * lanes) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+        for (uint32_t r = lane; r < run / 4; r += lanes) {
+          const float4 q = __ldg(s4 + r);
+          acc += (q.x + q.y) + (q.z + q.w);
+        }
+      } else {
+        for (uint32_t r = lane; r < run; r += lanes) acc += __ldg(src + r);
+      }
+    } else {
+      const uint32_t xb = deposit(b, d.act_mask) | d.zoom_val;
+      for (uint32_t r = lane; r < run; r += lanes) acc += __ldg(row + (xb | deposit(r, d.mer_mask)));
+    }
+  }
+  for (int off = lanes >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (valid && lane == 0) {
+    const int64_t e = o >> d.a;
+    const uint32_t b = uint32_t(o & ((int64_t(1) << d.a) - 1));
+    store_out_f(d.dst, d.kind, d.plane_stride, d.rowmap[e] + d.colmap[b], acc * float(d.alpha));
+  }
+}
+
+// Shared memory (floats) one SIMT tile needs for its A and B stages.
+template <int BM, int BN, int kBK>
+constexpr int gemm_tile_smem_floats() {
+  return kBK * (BM + 4) + kBK * (BN + 4);
+}
+
+// One BM x BN tile (origin m0, n0) of C = A B^T (Section 6.1) on 256 threads,
+// epilogue through the layout maps; returns this thread's sum of the values
+// it wrote (for the probability check).  smem_a / smem_b: kBK x (BM+4) and
+// kBK x (BN+4) floats of shared memory.
+template <int BM, int BN, int TM, int TN, bool CHUNKED, int kBK>
+__device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64_t n0, float* smem_a,
+                                            float* smem_b) {
+  constexpr int kThreads = kOpThreads;
+  static_assert((BM / TM) * (BN / TN) == kThreads, "tile shape");
+  constexpr int TX = BN / TN;
+  float (*As)[BM + 4] = reinterpret_cast<float (*)[BM + 4]>(smem_a);
+  float (*Bs)[BN + 4] = reinterpret_cast<float (*)[BN + 4]>(smem_b);
+
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+
+  // alpha is a power of two: scaling an FP32 partial by it is exact
+  const float alpha_f = float(a.alpha);
+  float acc[TM][TN];
+  double acc64[CHUNKED ? TM : 1][CHUNKED ? TN : 1];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  if constexpr (CHUNKED) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc64[i][j] = 0.0;
+  }
+
+  for (int64_t k0 = 0; k0 < a.K; k0 += kBK) {
+    for (int idx = tid; idx < BM * kBK; idx += kThreads) {
+      const int r = idx / kBK, kk = idx % kBK;
+      float v = 0.f;
+      if (m0 + r < a.M && k0 + kk < a.K) v = __ldg(a.A + (m0 + r) * a.K + k0 + kk);
+      As[kk][r] = v;
+    }
+    for (int idx = tid; idx < BN * kBK; idx += kThreads) {
+      const int r = idx / kBK, kk = idx % kBK;
+      float v = 0.f;
+      if (n0 + r < a.N && k0 + kk < a.K) v = __ldg(a.B + (n0 + r) * a.K + k0 + kk);
+      Bs[kk][r] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      float af[TM], bf[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) af[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) bf[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(af[i], bf[j], acc[i][j]);
+    }
+    __syncthreads();
+    if constexpr (CHUNKED) {
+      const int64_t done = k0 + kBK;
+      if ((done & (a.chunk - 1)) == 0 || done >= a.K) {
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) {
+            acc64[i][j] += double(acc[i][j] * alpha_f);
+            acc[i][j] = 0.f;
+          }
+      }
+    }
+  }
+
+  // FP32 outputs are scaled and summed in FP32; only FP64 outputs use the
+  // FP64 pipe per element
+  float sum_f = 0.f;
+  double sum_d = 0.0;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t row = m0 + ty * TM + i;
+    if (row >= a.M) continue;
+    const uint64_t rbase = a.rowmap[row];
+    const int64_t c0 = n0 + tx * TN;
+    if (!CHUNKED && a.kind == OUT_F32) {
+      if (a.vec4 && (TN % 4) == 0 && c0 + TN <= a.N) {
+#pragma unroll
+        for (int j = 0; j < TN; j += 4) {
+          float4 q;
+          q.x = acc[i][j] * alpha_f; q.y = acc[i][j + 1] * alpha_f;
+          q.z = acc[i][j + 2] * alpha_f; q.w = acc[i][j + 3] * alpha_f;
+          sum_f += (q.x + q.y) + (q.z + q.w);
+          *reinterpret_cast<float4*>(static_cast<float*>(a.C) + rbase + a.colmap[c0 + j]) = q;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+          const int64_t col = c0 + j;
+          if (col >= a.N) continue;
+          const float v = acc[i][j] * alpha_f;
+          sum_f += v;
+          static_cast<float*>(a.C)[rbase + a.colmap[col]] = v;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int64_t col = c0 + j;
+        if (col >= a.N) continue;
+        double v;
+        if constexpr (CHUNKED) v = acc64[i][j]; else v = double(acc[i][j] * alpha_f);
+        if (a.kind == OUT_F64) sum_d += v; else sum_f += float(v);
+        store_out(a.C, a.kind, a.plane_stride, rbase + a.colmap[col], v);
+      }
+    }
+  }
+  return sum_d + double(sum_f);
+}
+
+
+}  // namespace sqc

@@ -125,6 +125,42 @@ int gemm_tc_min_rows();            // M and N of a tensor-core step must be >= t
 int gemm_tc_k_align();             // the shared index is padded to a multiple of this
 cudaError_t gemm_tc_configure();   // one-time kernel attributes (dynamic shared memory)
 
+// ---- batched recursion level: one persistent launch over many queries -------
+enum : int { kItemMerge = 0, kItemGemm = 1 };
+struct BatchItem {
+  int type;          // kItemMerge / kItemGemm
+  int idx;           // merge descriptor or step index in the batch arrays
+  int64_t tile;      // merge block (relative to the descriptor) or output tile
+  int dep0, dep1;    // tensor slots that must be complete first (-1: none)
+  int out;           // tensor slot this item writes (-1: none)
+};
+struct BatchStep {
+  GemmArgs a;        // a.partials != null: the query's last step (probability sum)
+  int cfg;           // tile configuration id (batch_tile_cfg)
+  int64_t ntiles;
+  double* partials;  // per-tile partial sums of the query's bins
+  unsigned* counter;
+  double* total;
+};
+struct BatchLaunch {
+  const BatchItem* items;
+  int64_t n_items;
+  const MergeDesc* mdescs;
+  const BatchStep* steps;
+  unsigned* counts;          // [n_slots] completion counters (zero between launches)
+  const unsigned* expected;  // [n_slots]
+  int64_t n_slots;
+  unsigned long long* head;
+  unsigned* done;
+  int* abort;
+  int* err;
+};
+cudaError_t launch_batch(const BatchLaunch& L, int grid, cudaStream_t s);
+cudaError_t batch_configure();
+int batch_smem_bytes();
+// tile configuration for a step of the batch kernel; *bm, *bn its tile
+int batch_tile_cfg(int64_t M, int64_t N, int64_t K, bool chunked, int64_t chunk, int64_t* bm, int64_t* bn);
+
 // ---- probability check: FP64 sum of n values ---------------------------------
 cudaError_t launch_sum(const void* x, int is_f64, uint64_t n, double* partials, unsigned* counter,
                        double* total, cudaStream_t s);

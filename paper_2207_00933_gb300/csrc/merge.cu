@@ -10,7 +10,7 @@
 // shuffle tree.  Other role patterns take the generic bit-deposit path.
 // The result goes straight into the layout the first contraction step reads
 // (rowmap/colmap), in FP32, FP64 or as three BF16 planes.
-#include "common.cuh"
+#include "device_ops.cuh"
 
 namespace sqc {
 
@@ -25,40 +25,7 @@ __global__ void __launch_bounds__(256) merge_kernel(const MergeDesc* __restrict_
     d = descs[lo];
   }
   __syncthreads();
-  const int lanes = d.lanes;                       // power of two
-  const int lshift = __ffs(lanes) - 1;
-  const int64_t o = ((int64_t(blockIdx.x) - d.block_begin) << (8 - lshift)) + (threadIdx.x >> lshift);
-  const int lane = threadIdx.x & (lanes - 1);
-  const int64_t total = d.rows << d.a;
-  const bool valid = o < total;
-  float acc = 0.f;
-  if (valid) {
-    const int64_t e = o >> d.a;
-    const uint32_t b = uint32_t(o & ((int64_t(1) << d.a) - 1));
-    const float* row = d.A + (e << d.n);
-    const uint32_t run = 1u << d.m;
-    if (d.fast) {
-      const float* src = row + (d.zoom_val | (b << d.m));
-      if (run >= 4u * lanes) {
-        const float4* s4 = reinterpret_cast<const float4*>(src);
-        for (uint32_t r = lane; r < run / 4; r += lanes) {
-          const float4 q = __ldg(s4 + r);
-          acc += (q.x + q.y) + (q.z + q.w);
-        }
-      } else {
-        for (uint32_t r = lane; r < run; r += lanes) acc += __ldg(src + r);
-      }
-    } else {
-      const uint32_t xb = deposit(b, d.act_mask) | d.zoom_val;
-      for (uint32_t r = lane; r < run; r += lanes) acc += __ldg(row + (xb | deposit(r, d.mer_mask)));
-    }
-  }
-  for (int off = lanes >> 1; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (valid && lane == 0) {
-    const int64_t e = o >> d.a;
-    const uint32_t b = uint32_t(o & ((int64_t(1) << d.a) - 1));
-    store_out_f(d.dst, d.kind, d.plane_stride, d.rowmap[e] + d.colmap[b], acc * float(d.alpha));
-  }
+  merge_block(d, int64_t(blockIdx.x) - d.block_begin);
 }
 
 }  // namespace

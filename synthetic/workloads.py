@@ -102,3 +102,83 @@ def random_line_chain(seed: int, widths: list[int], handoffs: list[int], depth: 
                 zoom[q] = int(rng.integers(2))
     roles = lowest_active_roles(c, active, zoom)
     return Workload(f"randline{c.n_qubits}_s{seed}", c, probs, roles, {"seed": seed, "outputs": "random"})
+
+
+@dataclass
+class BatchWorkload:
+    """Many zoom queries over a few resident circuits."""
+    name: str
+    circuits: list                     # CutCircuit
+    probs: list                        # per circuit: list of per-subcircuit arrays
+    queries: list                      # (circuit index, roles int8 array)
+    meta: dict = field(default_factory=dict)
+
+
+def _chain_shape(rng, n_sub: int, K: int, max_log_input: int, max_width: int, min_qubits: int):
+    """Random chain: hand-offs h (sum K, each >= 1) and block widths w with
+    4^{k_b} 2^{w_b} <= 2^max_log_input (k_b = h_{b-1} + h_b) and at least two
+    data qubits per block; retried until the circuit has >= min_qubits."""
+    for _ in range(1000):
+        cuts = np.sort(rng.choice(np.arange(1, K), n_sub - 2, replace=False)) if n_sub > 2 else np.array([], int)
+        h = np.diff(np.concatenate([[0], cuts, [K]])).astype(int).tolist()
+        widths = []
+        ok = True
+        for b in range(n_sub):
+            hin = h[b - 1] if b > 0 else 0
+            hout = h[b] if b < n_sub - 1 else 0
+            kb = hin + hout
+            wmax = min(max_width, max_log_input - 2 * kb)
+            wmin = max(hin + hout + 2, hin + 1)
+            if wmax < wmin:
+                ok = False
+                break
+            widths.append(int(rng.integers(max(wmin, wmax - 2), wmax + 1)))
+        if ok and sum(widths) - K >= min_qubits:
+            return widths, h
+    raise ValueError("no chain shape satisfies the constraints")
+
+
+def batch_level(seed: int = 4, n_circuits: int = 4, n_queries: int = 256, a_range=(10, 20),
+                n_sub_range=(5, 6), K_range=(6, 10), max_width: int = 16, max_log_input: int = 22,
+                min_qubits: int = 60, dtype=np.float32) -> BatchWorkload:
+    """Batched recursion level: `n_queries` zoomed bins, each with an active
+    count drawn uniformly from a_range, over `n_circuits` seeded random line
+    circuits cut into n_sub_range subcircuits at K_range wires.  Subcircuit
+    outputs are random numbers (as in the paper's timing runs).  Within each
+    subcircuit a query zooms a random number (up to a third) of the lowest
+    data qubits to random bits, makes the next ones active (the active count
+    spread over the subcircuits at random) and merges the rest."""
+    rng = np.random.default_rng(seed)
+    circuits, probs = [], []
+    for ci in range(n_circuits):
+        n_sub = int(rng.integers(n_sub_range[0], n_sub_range[1] + 1))
+        K = int(rng.integers(max(K_range[0], n_sub - 1), K_range[1] + 1))
+        widths, h = _chain_shape(rng, n_sub, K, max_log_input, max_width, min_qubits)
+        c = chain_line_circuit(seed * 1000 + ci, widths, h, 2)
+        circuits.append(c)
+        probs.append([random_variant_probs(c, i, rng).astype(dtype) for i in range(c.n_subcircuits)])
+    queries = []
+    for _ in range(n_queries):
+        ci = int(rng.integers(n_circuits))
+        c = circuits[ci]
+        a_total = int(rng.integers(a_range[0], a_range[1] + 1))
+        roles = np.full(c.n_qubits, MERGED, dtype=np.int8)
+        zoom_n, act_n = [], []
+        for dq in c.data_qubits:
+            z = int(rng.integers(0, len(dq) // 3 + 1))
+            zoom_n.append(z)
+            act_n.append(0)
+        for _ in range(a_total):
+            cand = [i for i, dq in enumerate(c.data_qubits) if zoom_n[i] + act_n[i] < len(dq)]
+            if not cand:
+                break
+            act_n[int(rng.choice(cand))] += 1
+        for i, dq in enumerate(c.data_qubits):
+            for q in dq[:zoom_n[i]]:
+                roles[q] = ZOOM1 if rng.integers(2) else ZOOM0
+            for q in dq[zoom_n[i]:zoom_n[i] + act_n[i]]:
+                roles[q] = ACTIVE
+        queries.append((ci, roles))
+    return BatchWorkload(f"batch{n_queries}_s{seed}", circuits, probs, queries,
+                         {"seed": seed, "n_qubits": [c.n_qubits for c in circuits],
+                          "cuts": [c.n_edges for c in circuits], "subcircuits": [c.n_subcircuits for c in circuits]})

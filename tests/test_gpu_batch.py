@@ -1,0 +1,78 @@
+"""GPU: the batched recursion level -- many zoom queries over several
+resident circuits in one persistent launch -- against the FP64 oracle and
+against the same queries run one at a time (which must give the very same
+bins: every bin is summed by one thread in the same order either way)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synthetic import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    from paper_2207_00933_gb300 import Context, _build
+    _build.build()
+    ctx = Context(0)
+    b = W.batch_level(seed=5, n_circuits=3, n_queries=24, a_range=(6, 12), max_log_input=18, min_qubits=30)
+    cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in ps])
+            for c, ps in zip(b.circuits, b.probs)]
+    qs = [ctx.set_qubit_roles(cids[ci], roles) for ci, roles in b.queries]
+    yield ctx, b, qs
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+def _oracle(b, j):
+    ci, roles = b.queries[j]
+    c = b.circuits[ci]
+    g = O.Graph.from_arrays(c.n_qubits, *c.graph_arrays())
+    return O.reconstruct(g, [p.astype(np.float64) for p in b.probs[ci]], roles)
+
+
+def test_batch_matches_oracle_and_single_queries(setup):
+    import torch
+    ctx, b, qs = setup
+    outs = [torch.full((1 << na,), -1.0, dtype=torch.float32, device="cuda") for _, na in qs]
+    totals = torch.zeros(len(qs), dtype=torch.float64, device="cuda")
+    bid = ctx.batch_create([q for q, _ in qs], outs, totals)
+    for _ in range(2):                              # the launch re-arms itself
+        ctx.batch_run(bid)
+    ctx.batch_status(bid)
+    for j, (q, na) in enumerate(qs):
+        ref = _oracle(b, j)
+        P = outs[j].double().cpu().numpy()
+        err = np.abs(P - ref).max()
+        assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-12, (j, err)
+        single = torch.empty_like(outs[j])
+        tot1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.reconstruct(q, single, "fp32", tot1)
+        torch.cuda.synchronize()
+        assert torch.equal(single, outs[j]), j
+        assert abs(tot1.item() - totals[j].item()) <= 1e-12 * max(1.0, abs(tot1.item())) + 1e-15
+    ctx.batch_release(bid)
+
+
+def test_batch_replays_from_a_cuda_graph(setup):
+    import torch
+    ctx, b, qs = setup
+    outs = [torch.zeros((1 << na,), dtype=torch.float64, device="cuda") for _, na in qs]
+    bid = ctx.batch_create([q for q, _ in qs], outs)
+    ctx.batch_run(bid)
+    torch.cuda.synchronize()
+    first = [o.clone() for o in outs]
+    for o in outs:
+        o.zero_()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx.batch_run(bid)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    ctx.batch_status(bid)
+    for o, f in zip(outs, first):
+        assert torch.equal(o, f)
+    ctx.batch_release(bid)
