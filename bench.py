@@ -232,6 +232,76 @@ print(json.dumps({{"reps": n, "seconds": dt, "bins": 1 << w.n_active}}))
                       f"FP64 sum) of {name}, {d['seconds']:.1f} s"}
 
 
+def batch_bench(dev, reps: int = 10) -> dict:
+    """Batched recursion level: 256 zoom queries (10-20 active qubits) over 4
+    resident random-output circuits of 60-70 qubits (5-6 subcircuits, 7-10
+    cuts).  Times (CUDA events, L2 flushed between repetitions) the one-launch
+    persistent batch (FP32, replayed from a CUDA graph) against the plain
+    form -- every query's own launches, one query after another -- in FP32
+    and in split-BF16.  Each form's bins are checked on 8 sampled queries
+    against the FP64 oracle."""
+    import torch
+    import oracle as O
+    from paper_2207_00933_gb300 import Context
+    from synthetic import workloads as W
+    b = W.batch_level()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": f"{len(b.queries)} queries, circuits {b.meta['n_qubits']} qubits, cuts {b.meta['cuts']}, "
+                       f"subcircuits {b.meta['subcircuits']}, active 10-20"}
+    with Context(dev.index or 0) as ctx:
+        cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).to(dev) for p in ps])
+                for c, ps in zip(b.circuits, b.probs)]
+        qs = [ctx.set_qubit_roles(cids[ci], roles) for ci, roles in b.queries]
+        bins = sum(1 << na for _, na in qs)
+        outs = [torch.empty(1 << na, dtype=torch.float32, device=dev) for _, na in qs]
+        totals = torch.zeros(len(qs), dtype=torch.float64, device=dev)
+        sample = list(range(0, len(qs), len(qs) // 8))[:8]
+        refs = {}
+        for j in sample:
+            ci, roles = b.queries[j]
+            c = b.circuits[ci]
+            refs[j] = O.reconstruct(O.Graph.from_arrays(c.n_qubits, *c.graph_arrays()),
+                                    [p.astype(np.float64) for p in b.probs[ci]], roles)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize(dev)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                tot += e0.elapsed_time(e1)
+            return tot / reps
+
+        def err():
+            return max(float(np.abs(outs[j].double().cpu().numpy() - refs[j]).max()) for j in sample)
+
+        bid = ctx.batch_create([q for q, _ in qs], outs, totals)
+        graph = torch.cuda.CUDAGraph()
+        ctx.batch_run(bid)
+        with torch.cuda.graph(graph):
+            ctx.batch_run(bid)
+        ms = timed(graph.replay)
+        ctx.batch_status(bid)
+        res["batch_fp32"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "launches": 1, "max_abs_err_vs_fp64": err()}
+        for prec in ("fp32", "split_bf16"):
+            def plain():
+                for (q, _), o in zip(qs, outs):
+                    ctx.reconstruct(q, o, prec)
+            ms = timed(plain)
+            res[f"plain_{prec}"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "max_abs_err_vs_fp64": err()}
+        res["batch_vs_plain_fp32"] = res["plain_fp32"]["ms"] / res["batch_fp32"]["ms"]
+        res["bins"] = bins
+        ctx.batch_release(bid)
+    return res
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -466,6 +536,7 @@ def main():
         line["config"]["precision"] = prec
         if world == 1 and not args.no_extras:
             line["tensor_microbench"] = tensor_microbench(dev)
+            line["batched_level"] = batch_bench(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

@@ -365,7 +365,9 @@ cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s) {
   // TMEM lane can leave the operands
   if (a.Mp % kBM || a.Np % kBN || a.Kp % kBK || a.Kp <= 0 || a.M > a.Mp || a.N > a.Np || a.K > a.Kp)
     return cudaErrorInvalidValue;
-  if ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 1023) return cudaErrorInvalidValue;
+  // TMA wants 16-byte aligned global operands (the 1024-byte alignment the
+  // swizzle needs applies to the shared-memory stages only)
+  if ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 15) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, a.A, a.Mp, a.Kp) || !make_map(&mb, a.B, a.Np, a.Kp)) return cudaErrorInvalidValue;
   const int64_t tiles = (a.Mp / kBM) * (a.Np / kBN);
