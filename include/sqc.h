@@ -214,6 +214,50 @@ SQC_API sqc_status sqc_batch_run(sqc_ctx* ctx, sqc_batch_id b, void* stream);
 SQC_API sqc_status sqc_batch_status(sqc_ctx* ctx, sqc_batch_id b);
 SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b);
 
+/* Serving loop: continuous batching of zoom queries (one recursion level
+ * each) against circuits already loaded on the context.
+ *
+ * sqc_server_create starts one server thread that owns `ctx` from then on
+ * (do not call other functions on ctx until sqc_server_destroy returns).
+ * Clients call sqc_server_submit from any thread; the server admits waiting
+ * requests in arrival order while their plans and outputs fit the context's
+ * HBM budget (sqc_config.hbm_budget_bytes; a request that does not fit waits
+ * until launches retire), and launches each group of admitted requests as
+ * one persistent batch (plain = 1: one FP32 reconstruction per request) on
+ * one of n_streams non-blocking streams, so launches overlap; requests that
+ * arrive meanwhile go into the next free stream.  A request larger than the
+ * whole budget fails with SQC_EBUSY; requests still waiting when the server
+ * is destroyed are cancelled (state failed, SQC_EBUSY).  All allocations, uploads
+ * and frees are stream-ordered: the loop never synchronises the device.
+ * Results are FP32 bins, identical to sqc_reconstruct(SQC_PREC_FP32) of the
+ * same query run alone. */
+typedef struct sqc_server sqc_server;
+typedef struct {
+  int32_t max_batch;   /* most requests per launch (default 64)           */
+  int32_t n_streams;   /* launches in flight at once, 1..32 (default 4)   */
+  int32_t plain;       /* 1: one reconstruction per request (no batching) */
+  int32_t reserved[5];
+} sqc_server_config;
+
+SQC_API void sqc_server_default_config(sqc_server_config* cfg);
+SQC_API sqc_status sqc_server_create(sqc_ctx* ctx, const sqc_server_config* cfg, sqc_server** out);
+/* roles: [n_qubits] as in sqc_set_qubit_roles; *ticket identifies the request. */
+SQC_API sqc_status sqc_server_submit(sqc_server* srv, sqc_circuit_id circuit, const int8_t* roles, int32_t n_qubits,
+                                     int64_t* ticket);
+/* *state: 0 waiting, 1 running, 2 done, 3 failed (the call then returns the
+ * failure), 4 collected; *latency_us: submit-to-completion time once done. */
+SQC_API sqc_status sqc_server_poll(sqc_server* srv, int64_t ticket, int32_t* state, double* latency_us,
+                                   int32_t* n_active);
+/* Copy a done request's 2^{n_active} FP32 bins to host_out (capacity in
+ * values); the server moved them to host memory when the launch retired.
+ * SQC_EBUSY if not done yet. */
+SQC_API sqc_status sqc_server_result(sqc_server* srv, int64_t ticket, float* host_out, uint64_t capacity);
+/* Block until no request is waiting or running (SQC_ETIMEOUT after timeout_s). */
+SQC_API sqc_status sqc_server_drain(sqc_server* srv, double timeout_s);
+SQC_API sqc_status sqc_server_stats(sqc_server* srv, int64_t* launches, int64_t* admitted, int64_t* busy_refusals);
+/* Finish the requests in flight, free everything the server holds, stop the thread. */
+SQC_API void sqc_server_destroy(sqc_server* srv);
+
 /* Allocation-free bin selection.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory -- code
  * embedded in a host application that owns every device allocation, or a
@@ -235,6 +279,10 @@ SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b);
 SQC_API sqc_status sqc_top_bins_noalloc(int device, const void* probs, sqc_dtype dtype, uint64_t n, int32_t k,
                                         double threshold, uint64_t* bins_out, double* probs_out,
                                         int32_t* n_found, void* stream);
+
+/* Device memory the context holds now (resident circuits, plans, batches,
+ * workspaces) and its budget (0 = none); host values. */
+SQC_API sqc_status sqc_memory_info(const sqc_ctx* ctx, uint64_t* held_bytes, uint64_t* budget_bytes);
 
 /* Introspection of a planned query (host values, no device work):
  * n_steps contraction steps; flops = sum of 2*M*N*K over the steps;

@@ -72,6 +72,16 @@ _SIGS = {
     "sqc_batch_run": (_c.c_int32, [_P, _c.c_int64, _P]),
     "sqc_batch_status": (_c.c_int32, [_P, _c.c_int64]),
     "sqc_batch_release": (_c.c_int32, [_P, _c.c_int64]),
+    "sqc_server_default_config": (None, [_P]),
+    "sqc_server_create": (_c.c_int32, [_P, _P, _c.POINTER(_P)]),
+    "sqc_server_submit": (_c.c_int32, [_P, _c.c_int64, _P, _c.c_int32, _c.POINTER(_c.c_int64)]),
+    "sqc_server_poll": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_double),
+                                     _c.POINTER(_c.c_int32)]),
+    "sqc_server_result": (_c.c_int32, [_P, _c.c_int64, _P, _c.c_uint64]),
+    "sqc_server_drain": (_c.c_int32, [_P, _c.c_double]),
+    "sqc_server_stats": (_c.c_int32, [_P, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
+    "sqc_server_destroy": (None, [_P]),
+    "sqc_memory_info": (_c.c_int32, [_P, _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64)]),
     "sqc_profile_enable": (_c.c_int32, [_P, _c.c_int]),
     "sqc_profile_read": (_c.c_int32, [_P, _P, _P, _P]),
 }
@@ -236,6 +246,12 @@ class Context:
                                              ctypes.byref(wb)))
         return {"n_steps": ns.value, "flops": fl.value, "merge_bytes": mb.value, "work_bytes": wb.value}
 
+    def memory_info(self) -> dict:
+        """Device bytes the context holds and its HBM budget (0: none)."""
+        held, budget = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._lib.sqc_memory_info(self._h, ctypes.byref(held), ctypes.byref(budget)))
+        return {"held": held.value, "budget": budget.value}
+
     def query_steps(self, query: int) -> list[tuple[int, int, int]]:
         """(M, N, Kd) of every contraction step, in launch order."""
         out = []
@@ -342,6 +358,71 @@ def top_bins_noalloc(probs, k: int, threshold: float = -math.inf, bins_out=None,
     if st != 0:
         raise SQCError(st, lib.sqc_last_error(None).decode())
     return bins_out, probs_out, n_found
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("plain", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class Server:
+    """Continuous-batching serving loop over a context (sqc_server_*).  The
+    server thread owns the context until close()."""
+
+    def __init__(self, ctx: Context, max_batch: int = 64, n_streams: int = 4, plain: bool = False):
+        self._lib = ctx._lib
+        self._ctx = ctx
+        cfg = _ServerConfig()
+        self._lib.sqc_server_default_config(ctypes.byref(cfg))
+        cfg.max_batch, cfg.n_streams, cfg.plain = max_batch, n_streams, int(plain)
+        h = _P()
+        ctx._check(self._lib.sqc_server_create(ctx._h, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, circuit: int, roles) -> int:
+        r = np.ascontiguousarray(np.asarray(roles, dtype=np.int8))
+        t = ctypes.c_int64()
+        st = self._lib.sqc_server_submit(self._h, circuit, r.ctypes.data, r.size, ctypes.byref(t))
+        if st != 0:
+            raise SQCError(st, "submit failed")
+        return t.value
+
+    def poll(self, ticket: int):
+        """(state, latency_us, n_active); state 0 waiting, 1 running, 2 done, 3 failed, 4 collected."""
+        s, lat, na = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
+        st = self._lib.sqc_server_poll(self._h, ticket, ctypes.byref(s), ctypes.byref(lat), ctypes.byref(na))
+        if st != 0:
+            raise SQCError(st, "request failed")
+        return s.value, lat.value, na.value
+
+    def result(self, ticket: int) -> np.ndarray:
+        _, _, na = self.poll(ticket)
+        out = np.empty(1 << na, dtype=np.float32)
+        st = self._lib.sqc_server_result(self._h, ticket, out.ctypes.data, out.size)
+        if st != 0:
+            raise SQCError(st, "result not available")
+        return out
+
+    def drain(self, timeout_s: float = 60.0):
+        st = self._lib.sqc_server_drain(self._h, timeout_s)
+        if st != 0:
+            raise SQCError(st, "drain timed out")
+
+    def stats(self) -> dict:
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._lib.sqc_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return {"launches": a.value, "admitted": b.value, "busy_refusals": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sqc_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def declared_symbols() -> list[str]:

@@ -113,6 +113,11 @@ struct StageMark {
 
 struct sqc_ctx {
   int device = 0;
+  // stream-ordered allocation and uploads (the serving loop): when set, every
+  // device allocation, upload and free of the context is issued on this
+  // stream and nothing synchronises the device
+  cudaStream_t alloc_stream = nullptr;
+  bool async_alloc = false;
   bool prof = false;
   bool prof_keep = false;       // marks belong to a captured graph: keep them across reads
   std::vector<StageMark> marks;
@@ -204,7 +209,7 @@ sqc_status dev_alloc(sqc_ctx* ctx, void** p, size_t bytes, bool admit = true) {
   if (admit && ctx->cfg.hbm_budget_bytes && ctx->bytes + bytes > ctx->cfg.hbm_budget_bytes)
     return fail(ctx, SQC_EBUSY, "HBM budget exceeded: " + std::to_string(ctx->bytes + bytes) + " > " +
                                      std::to_string(ctx->cfg.hbm_budget_bytes) + " bytes");
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = ctx->async_alloc ? cudaMallocAsync(p, bytes, ctx->alloc_stream) : cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -218,8 +223,18 @@ void dev_free(sqc_ctx* ctx, void* p, size_t bytes) {
   if (!p) return;
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
-  cudaFree(p);
+  if (ctx->async_alloc) cudaFreeAsync(p, ctx->alloc_stream); else cudaFree(p);
   ctx->bytes = ctx->bytes >= bytes ? ctx->bytes - bytes : 0;
+}
+
+cudaError_t upload(sqc_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (ctx->async_alloc) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->alloc_stream);
+  return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+}
+
+cudaError_t zero(sqc_ctx* ctx, void* dst, size_t bytes) {
+  if (ctx->async_alloc) return cudaMemsetAsync(dst, 0, bytes, ctx->alloc_stream);
+  return cudaMemset(dst, 0, bytes);
 }
 
 inline int popc32(uint32_t x) { return __builtin_popcount(x); }
@@ -667,12 +682,11 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     blocks += (outs + per - 1) / per;
   }
   P->merge_blocks = blocks;
-  cudaError_t e = cudaMemcpy(maps_dev, maps.host.data(), sizeof(uint64_t) * maps.host.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && nC > 0)
-    e = cudaMemcpy(P->merge_dev, P->merge_host.data(), sizeof(MergeDesc) * nC, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(base + off_cnt, 0, 64);
+  cudaError_t e = upload(ctx, maps_dev, maps.host.data(), sizeof(uint64_t) * maps.host.size());
+  if (e == cudaSuccess && nC > 0) e = upload(ctx, P->merge_dev, P->merge_host.data(), sizeof(MergeDesc) * nC);
+  if (e == cudaSuccess) e = zero(ctx, base + off_cnt, 64);
   // BF16 operand padding (shared-index columns beyond K) must read as zero
-  if (e == cudaSuccess && zero_end > zero_begin) e = cudaMemset(base + zero_begin, 0, zero_end - zero_begin);
+  if (e == cudaSuccess && zero_end > zero_begin) e = zero(ctx, base + zero_begin, zero_end - zero_begin);
   if (e != cudaSuccess) {
     free_plan(ctx, P);
     return cuda_fail(ctx, e, "plan upload");
@@ -688,12 +702,25 @@ sqc_status ensure_select_work(sqc_ctx* ctx, Query* q) {
   sqc_status st = dev_alloc(ctx, &q->sel_mem, q->sel_bytes);
   if (st != SQC_OK) return st;
   select_work_carve(q->sel_mem, 0, sel_blocks, &q->sel);
-  cudaError_t e = cudaMemset(q->sel_mem, 0, q->sel_bytes);
+  cudaError_t e = zero(ctx, q->sel_mem, q->sel_bytes);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "selection workspace");
   return SQC_OK;
 }
 
 }  // namespace
+
+// Hooks for the serving loop (server.cu), which drives a context from its
+// own thread.
+namespace sqc {
+void ctx_set_alloc_stream(sqc_ctx* ctx, cudaStream_t s) {
+  ctx->alloc_stream = s;
+  ctx->async_alloc = s != nullptr;
+}
+int ctx_device(const sqc_ctx* ctx) { return ctx->device; }
+sqc_status ctx_alloc(sqc_ctx* ctx, void** p, size_t bytes) { return dev_alloc(ctx, p, bytes); }
+void ctx_free(sqc_ctx* ctx, void* p, size_t bytes) { dev_free(ctx, p, bytes); }
+sqc_status ctx_fail(sqc_ctx* ctx, sqc_status st, const char* msg) { return fail(ctx, st, msg); }
+}  // namespace sqc
 
 // ================================================================ C ABI =====
 
@@ -862,7 +889,6 @@ SQC_API sqc_status sqc_set_qubit_roles(sqc_ctx* ctx, sqc_circuit_id id, const in
   q->roles.assign(roles, roles + c.n_qubits);
   resolve_roles(c, q.get());
   sqc_status st = build_plan(ctx, c, q.get(), false, &q->plans[SQC_PREC_FP32]);
-  if (st == SQC_OK) st = ensure_select_work(ctx, q.get());
   if (st != SQC_OK) {
     free_query(ctx, q.get());
     return st;
@@ -879,7 +905,7 @@ SQC_API sqc_status sqc_release_query(sqc_ctx* ctx, sqc_query_id qid) {
   auto it = ctx->queries.find(qid);
   if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
   DeviceGuard g(ctx->device);
-  cudaDeviceSynchronize();
+  if (!ctx->async_alloc) cudaDeviceSynchronize();   // stream-ordered frees need no device sync
   free_query(ctx, it->second.get());
   ctx->queries.erase(it);
   return SQC_OK;
@@ -897,6 +923,13 @@ SQC_API sqc_status sqc_query_info(const sqc_ctx* cctx, sqc_query_id qid, int32_t
   if (flops) *flops = P.flops;
   if (merge_bytes) *merge_bytes = q.merge_bytes;
   if (work_bytes) *work_bytes = q.plans[0].work_bytes + q.plans[1].work_bytes + q.sel_bytes;
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_memory_info(const sqc_ctx* ctx, uint64_t* held_bytes, uint64_t* budget_bytes) {
+  if (!ctx) return SQC_EINVAL;
+  if (held_bytes) *held_bytes = ctx->bytes;
+  if (budget_bytes) *budget_bytes = ctx->cfg.hbm_budget_bytes;
   return SQC_OK;
 }
 
@@ -1036,6 +1069,11 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* prob
   auto it = ctx->queries.find(qid);
   if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
   DeviceGuard g(ctx->device);
+  {
+    // the first selection on a query allocates its workspace
+    sqc_status st = ensure_select_work(ctx, it->second.get());
+    if (st != SQC_OK) return st;
+  }
   StageScope scope(ctx, static_cast<cudaStream_t>(stream), SQC_STAGE_SELECT);
   ctx->launches += (dtype == SQC_F64 ? 8 : 4) + 4;
   CK(launch_select(it->second->sel, probs, dtype == SQC_F64, n, k, threshold,
@@ -1151,16 +1189,13 @@ SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id*
   }
   std::vector<BatchItem> flat(items.size());
   for (size_t k = 0; k < items.size(); ++k) flat[k] = items[k].it;
-  cudaError_t e = cudaMemcpy(base + o_items, flat.data(), sizeof(BatchItem) * flat.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !mdescs.empty())
-    e = cudaMemcpy(base + o_md, mdescs.data(), sizeof(MergeDesc) * mdescs.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(base + o_st, steps.data(), sizeof(BatchStep) * steps.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(base + o_exp, expected.data(), sizeof(unsigned) * expected.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(base + o_cnt, 0, sizeof(unsigned) * expected.size());
-  if (e == cudaSuccess) e = cudaMemset(base + o_pc, 0, sizeof(unsigned) * steps.size());
-  if (e == cudaSuccess) e = cudaMemset(base + o_ctl, 0, 64);
+  cudaError_t e = upload(ctx, base + o_items, flat.data(), sizeof(BatchItem) * flat.size());
+  if (e == cudaSuccess && !mdescs.empty()) e = upload(ctx, base + o_md, mdescs.data(), sizeof(MergeDesc) * mdescs.size());
+  if (e == cudaSuccess) e = upload(ctx, base + o_st, steps.data(), sizeof(BatchStep) * steps.size());
+  if (e == cudaSuccess) e = upload(ctx, base + o_exp, expected.data(), sizeof(unsigned) * expected.size());
+  if (e == cudaSuccess) e = zero(ctx, base + o_cnt, sizeof(unsigned) * expected.size());
+  if (e == cudaSuccess) e = zero(ctx, base + o_pc, sizeof(unsigned) * steps.size());
+  if (e == cudaSuccess) e = zero(ctx, base + o_ctl, 64);
   if (e != cudaSuccess) {
     dev_free(ctx, B->work, B->work_bytes);
     return cuda_fail(ctx, e, "batch upload");
@@ -1220,7 +1255,7 @@ SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b) {
   auto it = ctx->batches.find(b);
   if (it == ctx->batches.end()) return fail(ctx, SQC_ENOTFOUND, "unknown batch");
   DeviceGuard g(ctx->device);
-  cudaDeviceSynchronize();
+  if (!ctx->async_alloc) cudaDeviceSynchronize();
   dev_free(ctx, it->second->work, it->second->work_bytes);
   ctx->batches.erase(it);
   return SQC_OK;

@@ -190,3 +190,13 @@ cudaError_t select_configure();
 constexpr int kSelectMaxK = 4096;
 
 }  // namespace sqc
+
+// ---- serving-loop hooks into the context (defined with the C ABI) ----------
+struct sqc_ctx;
+namespace sqc {
+void ctx_set_alloc_stream(sqc_ctx* ctx, cudaStream_t s);   // nullptr: synchronous allocation again
+int ctx_device(const sqc_ctx* ctx);
+int32_t ctx_alloc(sqc_ctx* ctx, void** p, size_t bytes);    // budget-checked (SQC_EBUSY when over)
+void ctx_free(sqc_ctx* ctx, void* p, size_t bytes);
+int32_t ctx_fail(sqc_ctx* ctx, int32_t st, const char* msg);
+}  // namespace sqc

@@ -182,3 +182,102 @@ def batch_level(seed: int = 4, n_circuits: int = 4, n_queries: int = 256, a_rang
     return BatchWorkload(f"batch{n_queries}_s{seed}", circuits, probs, queries,
                          {"seed": seed, "n_qubits": [c.n_qubits for c in circuits],
                           "cuts": [c.n_edges for c in circuits], "subcircuits": [c.n_subcircuits for c in circuits]})
+
+
+def _merge_components(parts: list[CutCircuit]) -> CutCircuit:
+    """Place independent circuits side by side (disjoint qubits): a compute
+    graph made of several components, joined by outer products only."""
+    from .circuits import Block
+    blocks, off = [], 0
+    for c in parts:
+        for blk in c.blocks:
+            gates = []
+            for g in blk.gates:
+                if g[0] == "cz":
+                    gates.append(("cz", g[1] + off, g[2] + off))
+                elif g[0] == "rz":
+                    gates.append(("rz", g[1] + off, g[2]))
+                else:
+                    gates.append((g[0], g[1] + off))
+            blocks.append(Block([q + off for q in blk.qubits], gates))
+        off += c.n_qubits
+    return CutCircuit(off, blocks).finalize()
+
+
+def serving_set(seed: int = 6, n_circuits: int = 8, n_qubit_range=(200, 1000), n_sub_range=(16, 50),
+                K_range=(10, 40), max_width: int = 14, max_log_input: int = 18, n_queries: int = 512,
+                a_range=(12, 20), dtype=np.float32) -> BatchWorkload:
+    """Resident circuits for the serving loop: seeded random line circuits of
+    n_qubit_range qubits cut into n_sub_range subcircuits of at most
+    max_width qubits at K_range wires.  With fewer cuts than subcircuits - 1
+    the compute graph is a forest of chains.  Outputs are random numbers.
+    Each query fixes a random zoom prefix (the lowest 0-2 data qubits of a
+    few subcircuits) and asks for a_range active qubits spread over a few
+    subcircuits; everything else is merged."""
+    rng = np.random.default_rng(seed)
+    circuits, probs = [], []
+    while len(circuits) < n_circuits:
+        n_sub = int(rng.integers(n_sub_range[0], n_sub_range[1] + 1))
+        K = int(rng.integers(K_range[0], K_range[1] + 1))
+        n_comp = max(1, n_sub - K)
+        sizes = [n_sub // n_comp + (1 if i < n_sub % n_comp else 0) for i in range(n_comp)]
+        links = sum(s - 1 for s in sizes)
+        extra = K - links                     # cuts beyond one per link: spread as wider hand-offs
+        parts = []
+        ok = True
+        for ci, sz in enumerate(sizes):
+            h = [1] * (sz - 1)
+            for _ in range(max(0, extra) if ci == 0 else 0):
+                if not h:
+                    break
+                j = int(rng.integers(len(h)))
+                if h[j] < 3:
+                    h[j] += 1
+            widths = []
+            for b in range(sz):
+                hin = h[b - 1] if b > 0 else 0
+                hout = h[b] if b < sz - 1 else 0
+                wmax = min(max_width, max_log_input - 2 * (hin + hout))
+                wmin = hin + hout + 2
+                if wmax < wmin:
+                    ok = False
+                    break
+                widths.append(int(rng.integers(max(wmin, wmax - 3), wmax + 1)))
+            if not ok:
+                break
+            parts.append(chain_line_circuit(int(rng.integers(1 << 30)), widths, h, 2) if sz > 1 else
+                         chain_line_circuit(int(rng.integers(1 << 30)), widths, [], 2))
+        if not ok:
+            continue
+        c = _merge_components(parts)
+        if not (n_qubit_range[0] <= c.n_qubits <= n_qubit_range[1]):
+            continue
+        circuits.append(c)
+        probs.append([random_variant_probs(c, i, rng).astype(dtype) for i in range(c.n_subcircuits)])
+    queries = []
+    for _ in range(n_queries):
+        ci = int(rng.integers(n_circuits))
+        c = circuits[ci]
+        roles = np.full(c.n_qubits, MERGED, dtype=np.int8)
+        nsub = c.n_subcircuits
+        zoomed = rng.choice(nsub, size=min(nsub, int(rng.integers(1, 4))), replace=False)
+        zoom_n = np.zeros(nsub, dtype=int)
+        for i in zoomed:
+            zoom_n[i] = int(rng.integers(0, min(3, len(c.data_qubits[i])) + 1))
+        a_total = int(rng.integers(a_range[0], a_range[1] + 1))
+        hosts = rng.choice(nsub, size=min(nsub, int(rng.integers(2, 6))), replace=False)
+        act_n = np.zeros(nsub, dtype=int)
+        for _ in range(a_total):
+            cand = [i for i in hosts if zoom_n[i] + act_n[i] < len(c.data_qubits[i])]
+            if not cand:
+                cand = [i for i in range(nsub) if zoom_n[i] + act_n[i] < len(c.data_qubits[i])]
+            act_n[int(rng.choice(cand))] += 1
+        for i, dq in enumerate(c.data_qubits):
+            for q in dq[:zoom_n[i]]:
+                roles[q] = ZOOM1 if rng.integers(2) else ZOOM0
+            for q in dq[zoom_n[i]:zoom_n[i] + act_n[i]]:
+                roles[q] = ACTIVE
+        queries.append((ci, roles))
+    return BatchWorkload(f"serve{n_circuits}_s{seed}", circuits, probs, queries,
+                         {"seed": seed, "n_qubits": [c.n_qubits for c in circuits],
+                          "cuts": [c.n_edges for c in circuits], "subcircuits": [c.n_subcircuits for c in circuits]})
