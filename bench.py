@@ -302,6 +302,67 @@ def batch_bench(dev, reps: int = 10) -> dict:
     return res
 
 
+def serving_bench(dev, rates=(100, 300, 1000, 3000, 5000), seconds: float = 0.6, max_per_rate: int = 600) -> dict:
+    """Serving stream: zoom queries (random zoom prefix, 12-20 active qubits)
+    arrive by Poisson arrivals against 8 resident random-output circuits of
+    200-1000 qubits (16-50 subcircuits of <= 14 qubits, 10-40 cuts; forests
+    of chains where cuts < subcircuits - 1).  For every arrival rate the
+    continuous-batching server and the plain one-query-per-launch FP32
+    server are offered the same seeded arrival sequence; latency is submit
+    to completion on the server's clock, throughput = bins completed / wall
+    time from first submission to last completion."""
+    import torch
+    from paper_2207_00933_gb300 import Context, Server
+    from synthetic import workloads as W
+    b = W.serving_set(n_queries=4096)
+    rng = np.random.default_rng(12)
+    out = {"workload": f"8 circuits {b.meta['n_qubits']} qubits, cuts {b.meta['cuts']}, "
+                       f"subcircuits {b.meta['subcircuits']}; queries: zoom prefix + 12-20 active"}
+    for mode in ("batched", "plain"):
+        res = {}
+        ctx = Context(dev.index or 0)
+        cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(),
+                                            [torch.from_numpy(p).to(dev) for p in ps])
+                for c, ps in zip(b.circuits, b.probs)]
+        torch.cuda.synchronize(dev)
+        with Server(ctx, max_batch=64, n_streams=4, plain=(mode == "plain")) as srv:
+            # warm-up
+            for ci, roles in b.queries[:32]:
+                srv.submit(cids[ci], roles)
+            srv.drain(120.0)
+            qi = 32
+            for rate in rates:
+                n = int(min(max_per_rate, max(20, rate * seconds)))
+                gaps = np.random.default_rng(1000 + rate).exponential(1.0 / rate, n)
+                tickets = []
+                t0 = time.perf_counter()
+                t_next = t0
+                for k in range(n):
+                    t_next += gaps[k]
+                    while time.perf_counter() < t_next:
+                        pass
+                    ci, roles = b.queries[qi % len(b.queries)]
+                    qi += 1
+                    tickets.append(srv.submit(cids[ci], roles))
+                srv.drain(300.0)
+                wall_end = time.perf_counter()
+                lat, bins = [], 0
+                for t in tickets:
+                    state, us, na = srv.poll(t)
+                    lat.append(us)
+                    bins += 1 << na
+                    srv.result(t)
+                lat.sort()
+                res[str(rate)] = {"queries": n, "p50_ms": lat[len(lat) // 2] / 1e3,
+                                  "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] / 1e3,
+                                  "bins_per_s": bins / (wall_end - t0),
+                                  "offered_per_s": rate, "achieved_per_s": n / (wall_end - t0)}
+            res["server_stats"] = srv.stats()
+        ctx.close()
+        out[mode] = res
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -537,6 +598,7 @@ def main():
         if world == 1 and not args.no_extras:
             line["tensor_microbench"] = tensor_microbench(dev)
             line["batched_level"] = batch_bench(dev)
+            line["serving"] = serving_bench(dev)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
