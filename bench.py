@@ -538,7 +538,7 @@ def main():
     hbm, src = peaks()
     achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9
     kernel_of = {"attribute": "fold_kernel+mix_kernel", "merge": "merge_kernel", "contract": "gemm_simt_kernel",
-                 "final": "gemm_simt_kernel (last step)", "select": "radix_pass+compact+sort_emit"}
+                 "final": "gemm_simt_kernel (last step)", "select": "radix_pass+compact+rank_emit"}
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": src,
                 "stages": {k: {"us": 1e3 * stage_ms[k], "share": share[k],
