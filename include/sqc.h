@@ -297,6 +297,20 @@ SQC_API sqc_status sqc_query_info(const sqc_ctx* ctx, sqc_query_id q, int32_t* n
 SQC_API sqc_status sqc_query_step(const sqc_ctx* ctx, sqc_query_id q, int32_t step, int64_t* M, int64_t* N,
                                   int64_t* Kd);
 
+/* States assignment (Section 4, Algorithm 2, target-bin loop): while the
+ * product of the bin counts l'_i exceeds M, halve (rounding up) the largest,
+ * ties to the lowest subcircuit index.  l[n_subcircuits] in, l_out out.
+ * Host only: needs no context and no GPU. */
+SQC_API sqc_status sqc_assign_states(int32_t n_subcircuits, const uint64_t* l, uint64_t M, uint64_t* l_out);
+
+/* Qubit roles of one recursion (Algorithm 1 with Algorithm 2's
+ * assignment): zoom[n_qubits] marks the qubits earlier recursions fixed
+ * (SQC_ROLE_ZOOM0/ZOOM1; any other value = free).  Per subcircuit the free
+ * data qubits, in the graph's data_qubit order, enumerate its states j; with
+ * l'_i = 2^{a_i} bins, j % l'_i makes the first a_i of them active, the rest
+ * merged.  roles[n_qubits] out.  Host only. */
+SQC_API sqc_status sqc_recursion_roles(const sqc_graph* graph, const int8_t* zoom, uint64_t M, int8_t* roles);
+
 /* Stage timing (tracing).  When enabled, the library records a pair of CUDA
  * events on the caller's stream around each stage it launches and counts
  * its kernel launches.  Stages: */

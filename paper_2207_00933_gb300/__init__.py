@@ -82,6 +82,8 @@ _SIGS = {
     "sqc_server_stats": (_c.c_int32, [_P, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64)]),
     "sqc_server_destroy": (None, [_P]),
     "sqc_memory_info": (_c.c_int32, [_P, _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64)]),
+    "sqc_assign_states": (_c.c_int32, [_c.c_int32, _P, _c.c_uint64, _P]),
+    "sqc_recursion_roles": (_c.c_int32, [_P, _P, _c.c_uint64, _P]),
     "sqc_profile_enable": (_c.c_int32, [_P, _c.c_int]),
     "sqc_profile_read": (_c.c_int32, [_P, _P, _P, _P]),
 }
@@ -423,6 +425,34 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def assign_states(l, M: int) -> list[int]:
+    """Algorithm 2's target bin counts (sqc_assign_states); host only."""
+    lib = load_library()
+    a = np.ascontiguousarray(np.asarray(l, dtype=np.uint64))
+    out = np.empty_like(a)
+    st = lib.sqc_assign_states(a.size, a.ctypes.data, int(M), out.ctypes.data)
+    if st != 0:
+        raise SQCError(st, "assign_states")
+    return out.tolist()
+
+
+def recursion_roles(n_qubits: int, edge_up, edge_down, n_data, data_qubit, zoom, M: int) -> np.ndarray:
+    """Roles of one recursion (sqc_recursion_roles); zoom: per qubit
+    ROLE_ZOOM0/ROLE_ZOOM1 for fixed qubits, anything else free.  Host only."""
+    lib = load_library()
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.int32)) for a in (edge_up, edge_down, n_data, data_qubit)]
+    g = _Graph()
+    g.n_qubits, g.n_subcircuits, g.n_edges = n_qubits, len(arrs[2]), len(arrs[0])
+    ip = ctypes.POINTER(ctypes.c_int32)
+    g.edge_up, g.edge_down, g.n_data, g.data_qubit = (a.ctypes.data_as(ip) for a in arrs)
+    z = np.ascontiguousarray(np.asarray(zoom, dtype=np.int8))
+    roles = np.empty(n_qubits, dtype=np.int8)
+    st = lib.sqc_recursion_roles(ctypes.byref(g), z.ctypes.data, int(M), roles.ctypes.data)
+    if st != 0:
+        raise SQCError(st, "recursion_roles")
+    return roles
 
 
 def declared_symbols() -> list[str]:

@@ -98,9 +98,9 @@ struct Query {
   int n_active = 0;
   int64_t out_elems = 1;
   Plan plans[2];                 // [SQC_PREC_FP32], [SQC_PREC_SPLIT_BF16]
-  void* sel_mem = nullptr;
+  void* sel_mem = nullptr;       // cooperative selection workspace (+ error flag)
   size_t sel_bytes = 0;
-  SelectWork sel{};
+  int sel_grid = 0;
   double merge_bytes = 0.0;
 };
 
@@ -350,7 +350,8 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
       d.n = n;
       d.kin = kin;
       d.kout = kout;
-      int L2 = std::min(3, n / 2), L1 = std::min(3, n - L2);
+      // x tile: 8 consecutive low values (32-byte read runs) x 2 top-bit values
+      int L2 = std::min(1, n / 2), L1 = std::min(3, n - L2);
       const int64_t S = int64_t(1) << (2 * kin);
       while ((S << (L1 + L2)) > kAttrSmemMax / 4) {
         if (L1 >= L2 && L1 > 0) --L1;
@@ -697,11 +698,10 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
 
 sqc_status ensure_select_work(sqc_ctx* ctx, Query* q) {
   if (q->sel_mem) return SQC_OK;
-  const int sel_blocks = 1024;
-  q->sel_bytes = select_work_bytes(0, sel_blocks);
+  q->sel_grid = select_coop_grid();
+  q->sel_bytes = select_coop_bytes(q->sel_grid) + 64;
   sqc_status st = dev_alloc(ctx, &q->sel_mem, q->sel_bytes);
   if (st != SQC_OK) return st;
-  select_work_carve(q->sel_mem, 0, sel_blocks, &q->sel);
   cudaError_t e = zero(ctx, q->sel_mem, q->sel_bytes);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "selection workspace");
   return SQC_OK;
@@ -1075,10 +1075,12 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* prob
     if (st != SQC_OK) return st;
   }
   StageScope scope(ctx, static_cast<cudaStream_t>(stream), SQC_STAGE_SELECT);
-  ctx->launches += (dtype == SQC_F64 ? 8 : 4) + 4;
-  CK(launch_select(it->second->sel, probs, dtype == SQC_F64, n, k, threshold,
-                   reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found,
-                   static_cast<cudaStream_t>(stream)));
+  ctx->launches += 1;
+  Query& q = *it->second;
+  int* err = reinterpret_cast<int*>(static_cast<char*>(q.sel_mem) + q.sel_bytes - 64);
+  CK(launch_select_coop(q.sel_mem, q.sel_grid, probs, dtype == SQC_F64, n, k, threshold,
+                        reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found, err,
+                        static_cast<cudaStream_t>(stream)));
   return SQC_OK;
 }
 

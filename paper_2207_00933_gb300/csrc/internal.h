@@ -185,6 +185,15 @@ cudaError_t launch_select(const SelectWork& w, const void* x, int is_f64, uint64
 cudaError_t launch_select_static(int device, const void* x, int is_f64, uint64_t n, int k, double threshold,
                                  unsigned long long* bins_out, double* probs_out, int* n_found, cudaStream_t s);
 size_t select_static_bytes();
+// The same selection as ONE cooperative launch (grid barriers between the
+// phases); `work` holds select_coop_bytes(grid) zero-initialised bytes,
+// grid = select_coop_grid() (co-resident CTAs); err: device flag set when a
+// bounded barrier wait gave up.
+size_t select_coop_bytes(int grid);
+int select_coop_grid();
+cudaError_t launch_select_coop(void* work, int grid, const void* x, int is_f64, uint64_t n, int k, double threshold,
+                               unsigned long long* bins_out, double* probs_out, int* n_found, int* err,
+                               cudaStream_t s);
 // one-time per-device kernel attributes (large shared memory for the sort)
 cudaError_t select_configure();
 constexpr int kSelectMaxK = 4096;

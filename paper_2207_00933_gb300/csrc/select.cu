@@ -130,9 +130,10 @@ __device__ __forceinline__ void load_chunk(const void* x, int aligned, uint64_t 
   }
 }
 
-// Aggregate equal digits across a warp: one shared atomic per distinct
-// digit.  The common case (every active lane has the same digit, as in the
-// exponent bytes of probabilities) takes one ballot and one compare.
+// Add one digit per lane to a histogram in shared memory.  `sh` is this
+// warp's private copy (kRadix counters), so lanes of other warps never
+// contend; when every active lane has the same digit (the exponent bytes of
+// probabilities) one lane adds the whole count.
 __device__ __forceinline__ void warp_hist_add(unsigned* sh, bool ok, unsigned dig, int lane) {
   const unsigned active = __ballot_sync(0xffffffffu, ok);
   if (!active) return;
@@ -142,20 +143,18 @@ __device__ __forceinline__ void warp_hist_add(unsigned* sh, bool ok, unsigned di
     if (lane == leader) atomicAdd(&sh[d0], unsigned(__popc(active)));
     return;
   }
-  if (ok) {
-    const unsigned peers = __match_any_sync(active, dig);
-    if (__ffs(peers) - 1 == lane) atomicAdd(&sh[dig], unsigned(__popc(peers)));
-  }
+  if (ok) atomicAdd(&sh[dig], 1u);
 }
 
 template <bool is_f64>
 __global__ void __launch_bounds__(kSelThreads)
 radix_pass(const void* x, int aligned, uint64_t n, unsigned long long key_thr, int k, int pass,
            int last_pass, int cap, unsigned* hist_all, unsigned long long* st) {
-  __shared__ unsigned sh[kRadix];
+  __shared__ unsigned shw[kSelThreads / 32][kRadix];   // one histogram per warp
+  unsigned* sh = shw[0];
   __shared__ bool is_last;
   if (st[ST_DONE] != 0) return;
-  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) sh[d] = 0;
+  for (int d = threadIdx.x; d < kRadix * (kSelThreads / 32); d += blockDim.x) (&shw[0][0])[d] = 0;
   __syncthreads();
   const int shift = 64 - kRadixBits * (pass + 1);
   const unsigned long long prefix = st[ST_PREFIX];
@@ -177,13 +176,16 @@ radix_pass(const void* x, int aligned, uint64_t n, unsigned long long key_thr, i
         const unsigned long long key = c[h].key[q];
         const bool ok =
             c[h].ok[q] && (pass == 0 || (key >> (shift + kRadixBits)) == (prefix >> (shift + kRadixBits)));
-        warp_hist_add(sh, ok, unsigned((key >> shift) & (kRadix - 1)), lane);
+        warp_hist_add(shw[threadIdx.x >> 5], ok, unsigned((key >> shift) & (kRadix - 1)), lane);
       }
   }
   __syncthreads();
   unsigned* hist = hist_all + pass * kRadix;
-  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
-    if (sh[d]) atomicAdd(&hist[d], sh[d]);
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+    unsigned v = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) v += shw[w][d];
+    if (v) atomicAdd(&hist[d], v);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -508,6 +510,372 @@ cudaError_t launch_select(const SelectWork& w, const void* x, int is_f64, uint64
   rank_emit<<<kRankGrid, 32 * kRankWarps, 0, s>>>(x, is_f64, st, w.cand_key, w.cand_idx, bins_out, probs_out,
                                                  n_found);
   return cudaGetLastError();
+}
+
+namespace {
+
+// ---- one cooperative launch ----------------------------------------------------
+// The same selection as launch_select, as ONE cooperative kernel: the radix
+// passes, the compaction, the (rare) ordered tie pass and the ranking are
+// phases separated by grid barriers (bounded spins on a generation counter)
+// instead of kernel launches.  Every CTA reads the global histogram after a
+// barrier and derives the same radix state, so no CTA has to broadcast it.
+constexpr int kCoopThreads = 256;
+constexpr int kCoopWarps = kCoopThreads / 32;
+constexpr uint32_t kBarrierLimit = 1u << 26;   // ~seconds of polling
+constexpr int kCBits = 8;                      // radix digit width of the cooperative passes
+constexpr int kCRadix = 1 << kCBits;
+constexpr int kCPasses = 8;                    // 8 x 8 = 64 key bits
+constexpr int kCSmem = kCoopWarps * kCRadix * 4;  // per-warp histograms
+constexpr int kChunks = 4;                     // vector chunks in flight per thread
+constexpr int kCopies = 1;                     // global histogram copies
+
+struct CoopWork {
+  unsigned* hist;                 // [kCPasses][kCopies][kCRadix]
+  unsigned long long* ctl;        // [0] n_cand, [1] barrier count, [2] barrier generation, [3] abort
+  unsigned long long* cand_key;   // [kMaxSort]
+  unsigned long long* cand_idx;   // [kMaxSort]
+  unsigned* rank;                 // [kMaxSort]
+  unsigned* tie_count;            // [grid]
+};
+
+// Grid barrier: every CTA arrives on one counter, the last one bumps the
+// generation the others poll (acquire loads, no sleep: a sleeping poller
+// wakes late).  Measured on GB300: ~2.4 us per barrier for 152-304 CTAs, of
+// which the same-address arrival chain is a small part; a two-level variant
+// (16 group counters) measured ~4 us.  Bounded: gives up (abort flag) after
+// kBarrierLimit polls.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* ctl, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned long long gen = static_cast<volatile unsigned long long*>(ctl)[2];
+    __threadfence();
+    if (atomicAdd(&ctl[1], 1ull) == nblocks - 1) {
+      ctl[1] = 0ull;
+      __threadfence();
+      atomicAdd(&ctl[2], 1ull);
+    } else {
+      uint32_t i = 0;
+      for (;;) {
+        unsigned long long g;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(g) : "l"(ctl + 2) : "memory");
+        if (g != gen) break;
+        if (++i > kBarrierLimit || static_cast<volatile unsigned long long*>(ctl)[3]) {
+          atomicExch(&ctl[3], 1ull);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// bits [lo, hi) of the key form the digit of pass p
+__device__ __forceinline__ int pass_hi(int p) { return 64 - kCBits * p; }
+__device__ __forceinline__ int pass_lo(int p) { const int l = 64 - kCBits * (p + 1); return l > 0 ? l : 0; }
+
+template <bool is_f64>
+__global__ void __launch_bounds__(kCoopThreads)
+select_coop_kernel(const void* x, int aligned, uint64_t n, unsigned long long key_thr, int k, int cap,
+                   CoopWork w, unsigned long long* bins_out, double* probs_out, int* n_found, int* err) {
+  extern __shared__ unsigned shw[];               // [kCoopWarps][kCRadix]
+  __shared__ unsigned long long s_prefix, s_krem, s_take;
+  __shared__ int s_bits, s_done;
+  const unsigned nb = gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t gtid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const uint64_t gthreads = uint64_t(nb) * blockDim.x;
+  const int passes = is_f64 ? kCPasses : 4;       // FP32 keys hold 32 significant bits
+  const uint64_t span = uint64_t(blockDim.x) * kVec;
+  // (the histograms, ranks and candidate count start at zero: the previous
+  // call cleared them on its way out, and the workspace starts zeroed)
+  if (threadIdx.x == 0) {
+    s_prefix = 0ull;
+    s_krem = (unsigned long long)k;
+    s_bits = 0;
+    s_done = 0;
+    s_take = 0ull;
+  }
+  __syncthreads();
+  for (int pass = 0; pass < passes; ++pass) {
+    const int hi = pass_hi(pass), lo = pass_lo(pass);
+    const unsigned dmask = (1u << (hi - lo)) - 1u;
+    const unsigned long long prefix = s_prefix;
+    for (int d = threadIdx.x; d < kCoopWarps * kCRadix; d += blockDim.x) shw[d] = 0;
+    __syncthreads();
+    unsigned* mine = shw + warp * kCRadix;
+    for (uint64_t base = uint64_t(blockIdx.x) * span * kChunks; base < n; base += uint64_t(nb) * span * kChunks) {
+      Chunk c[kChunks];
+#pragma unroll
+      for (int h = 0; h < kChunks; ++h)
+        load_chunk<is_f64>(x, aligned, n, base + h * span + uint64_t(threadIdx.x) * kVec, key_thr, &c[h]);
+#pragma unroll
+      for (int h = 0; h < kChunks; ++h)
+#pragma unroll
+        for (int q = 0; q < kVec; ++q) {
+          const unsigned long long key = c[h].key[q];
+          const bool ok = c[h].ok[q] && (pass == 0 || (key >> hi) == (prefix >> hi));
+          warp_hist_add(mine, ok, unsigned(key >> lo) & dmask, lane);
+        }
+    }
+    __syncthreads();
+    unsigned* hist = w.hist + size_t(pass) * kCopies * kCRadix;
+    unsigned* my_copy = hist + (blockIdx.x % kCopies) * kCRadix;
+    for (int d = threadIdx.x; d < kCRadix; d += blockDim.x) {
+      unsigned v = 0;
+      for (int ww = 0; ww < kCoopWarps; ++ww) v += shw[ww * kCRadix + d];
+      if (v) atomicAdd(&my_copy[d], v);
+    }
+    if (!grid_barrier(w.ctl, nb)) goto fail;
+    __syncthreads();
+    for (int d = threadIdx.x; d < kCRadix; d += blockDim.x) {
+      unsigned v = 0;
+      for (int cpy = 0; cpy < kCopies; ++cpy) v += static_cast<volatile unsigned*>(hist)[cpy * kCRadix + d];
+      shw[d] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      constexpr int kPer = kCRadix / 32;
+      unsigned long long part = 0;
+      for (int q = 0; q < kPer; ++q) part += shw[lane * kPer + q];
+      unsigned long long suf = part;
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long t = __shfl_down_sync(0xffffffffu, suf, off);
+        if (lane + off < 32) suf += t;
+      }
+      const unsigned long long total = __shfl_sync(0xffffffffu, suf, 0);
+      const unsigned long long krem = s_krem;
+      bool refine = true;
+      if (pass == 0) {
+        if (lane == 0) s_take = total < (unsigned long long)k ? total : (unsigned long long)k;
+        if (total <= (unsigned long long)k) {
+          refine = false;
+          if (lane == 0) s_done = 2;
+        }
+      }
+      const unsigned reach = __ballot_sync(0xffffffffu, suf >= krem);
+      const int L = reach ? 31 - __clz(reach) : 0;
+      if (refine && lane == L) {
+        unsigned long long cum = suf - part;
+        int d = lane * kPer + kPer - 1;
+        for (; d > lane * kPer; --d) {
+          if (cum + shw[d] >= krem) break;
+          cum += shw[d];
+        }
+        s_prefix = prefix | ((unsigned long long)d << lo);
+        s_bits = 64 - lo;
+        s_krem = krem - cum;
+        if (shw[d] <= (unsigned)cap) s_done = 1;
+        else if (pass == passes - 1) s_done = 3;
+      }
+    }
+    __syncthreads();
+    if (s_done) break;
+  }
+  {
+    // compaction: values certainly selected, plus the bucket unless it is an
+    // oversized group of exact ties
+    const int done = s_done, bits = s_bits;
+    const unsigned long long pv = bits ? (s_prefix >> (64 - bits)) : 0ull;
+    for (uint64_t base = uint64_t(blockIdx.x) * span * kChunks; base < n; base += uint64_t(nb) * span * kChunks) {
+      Chunk c[kChunks];
+#pragma unroll
+      for (int h = 0; h < kChunks; ++h)
+        load_chunk<is_f64>(x, aligned, n, base + h * span + uint64_t(threadIdx.x) * kVec, key_thr, &c[h]);
+#pragma unroll
+      for (int h = 0; h < kChunks; ++h)
+#pragma unroll
+        for (int q = 0; q < kVec; ++q) {
+          bool take = false;
+          if (c[h].ok[q]) {
+            if (done == 2) {
+              take = true;
+            } else {
+              const unsigned long long hb = c[h].key[q] >> (64 - bits);
+              take = (done == 3) ? (hb > pv) : (hb >= pv);
+            }
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, take);
+          if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long slot = 0;
+            if (lane == leader) slot = atomicAdd(&w.ctl[0], (unsigned long long)__popc(m));
+            slot = __shfl_sync(0xffffffffu, slot, leader);
+            if (take) {
+              const unsigned long long r = slot + __popc(m & ((1u << lane) - 1u));
+              w.cand_key[r] = c[h].key[q];
+              w.cand_idx[r] = base + h * span + uint64_t(threadIdx.x) * kVec + q;
+            }
+          }
+        }
+    }
+    if (!grid_barrier(w.ctl, nb)) goto fail;
+    if (done == 3) {
+      // exact ties beyond capacity, taken in ascending bin order: count per
+      // contiguous range, barrier, then an ordered block scan per range
+      const unsigned long long tkey = s_prefix, need = s_krem;
+      const uint64_t range = (n + nb - 1) / nb;
+      const uint64_t b0 = uint64_t(blockIdx.x) * range;
+      const uint64_t e0 = (b0 + range < n) ? b0 + range : n;
+      __shared__ unsigned cnt;
+      __shared__ unsigned wsum[kCoopWarps];
+      if (threadIdx.x == 0) cnt = 0;
+      __syncthreads();
+      unsigned my = 0;
+      for (uint64_t i = b0 + threadIdx.x; i < e0; i += blockDim.x) {
+        double v;
+        const unsigned long long key = key_of(x, is_f64, i, &v);
+        if (key >= key_thr && !isnan(v) && key == tkey) ++my;
+      }
+      atomicAdd(&cnt, my);
+      __syncthreads();
+      if (threadIdx.x == 0) w.tie_count[blockIdx.x] = cnt;
+      const unsigned long long first = static_cast<volatile unsigned long long*>(w.ctl)[0];
+      if (!grid_barrier(w.ctl, nb)) goto fail;
+      __shared__ unsigned long long tbase;
+      if (threadIdx.x == 0) {
+        unsigned long long sacc = 0;
+        for (unsigned b = 0; b < blockIdx.x; ++b) sacc += static_cast<volatile unsigned*>(w.tie_count)[b];
+        tbase = sacc;
+      }
+      __syncthreads();
+      unsigned long long run = tbase;
+      for (uint64_t t0 = b0; t0 < e0 && run < need; t0 += blockDim.x) {
+        const uint64_t i = t0 + threadIdx.x;
+        bool tie = false;
+        if (i < e0) {
+          double v;
+          const unsigned long long key = key_of(x, is_f64, i, &v);
+          tie = (key >= key_thr && !isnan(v) && key == tkey);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, tie);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        unsigned before = 0, all = 0;
+        for (int ww = 0; ww < kCoopWarps; ++ww) {
+          if (ww < warp) before += wsum[ww];
+          all += wsum[ww];
+        }
+        const unsigned long long rank = run + before + __popc(bal & ((1u << lane) - 1u));
+        if (tie && rank < need) {
+          w.cand_key[first + rank] = tkey;
+          w.cand_idx[first + rank] = i;
+        }
+        run += all;
+        __syncthreads();
+      }
+      if (!grid_barrier(w.ctl, nb)) goto fail;
+    }
+  }
+  {
+    // ranking: every warp of the grid takes one (group of 32 candidates,
+    // slice of all candidates) pair and adds its count to the candidates'
+    // ranks; the order (key desc, index asc) is total, so ranks are distinct
+    unsigned long long nc = static_cast<volatile unsigned long long*>(w.ctl)[0];
+    if (s_done == 3) nc += s_krem;
+    if (nc > kMaxSort) nc = kMaxSort;
+    const unsigned long long groups = (nc + 31) / 32;
+    const uint64_t warps = gthreads / 32;
+    const uint64_t gw = gtid / 32;
+    const uint64_t slices = groups ? (warps / groups > 0 ? warps / groups : 1) : 1;
+    for (uint64_t task = gw; task < groups * slices; task += warps) {
+      const uint64_t g = task / slices, sl = task % slices;
+      const unsigned long long me = g * 32 + lane;
+      const bool have = me < nc;
+      const unsigned long long mk = have ? w.cand_key[me] : 0ull, mi = have ? w.cand_idx[me] : 0ull;
+      const unsigned long long per = (nc + slices - 1) / slices;
+      const unsigned long long j0 = per * sl, j1 = (j0 + per < nc) ? j0 + per : nc;
+      unsigned cntr = 0;
+      for (unsigned long long jb = j0; jb < j1; jb += 32) {
+        const unsigned long long j = jb + lane;
+        const bool ok = j < j1;
+        const unsigned long long kj = ok ? w.cand_key[j] : 0ull, ij = ok ? w.cand_idx[j] : 0ull;
+        const int m = int((j1 - jb) < 32 ? (j1 - jb) : 32);
+        for (int r = 0; r < m; ++r) {
+          const unsigned long long kr = __shfl_sync(0xffffffffu, kj, r);
+          const unsigned long long ir = __shfl_sync(0xffffffffu, ij, r);
+          cntr += (kr > mk) || (kr == mk && ir < mi);
+        }
+      }
+      if (have && cntr) atomicAdd(&w.rank[me], cntr);
+    }
+    if (!grid_barrier(w.ctl, nb)) goto fail;
+    const unsigned long long take = s_take;
+    for (uint64_t i = gtid; i < nc; i += gthreads) {
+      const unsigned r = w.rank[i];
+      w.rank[i] = 0u;                              // cleared for the next call
+      if (r < take) {
+        const unsigned long long b = w.cand_idx[i];
+        bins_out[r] = b;
+        probs_out[r] = is_f64 ? static_cast<const double*>(x)[b] : double(static_cast<const float*>(x)[b]);
+      }
+    }
+    if (gtid == 0) *n_found = int(take);
+  }
+  // every CTA has read the histograms and the candidate count by now (the
+  // ranking barrier); clear them for the next call
+  for (uint64_t i = gtid; i < uint64_t(kCPasses) * kCopies * kCRadix; i += gthreads) w.hist[i] = 0u;
+  if (gtid == 0) w.ctl[0] = 0ull;
+  return;
+fail:
+  if (threadIdx.x == 0 && err) atomicExch(err, 1);
+}
+
+}  // namespace
+
+size_t select_coop_bytes(int grid) {
+  return sizeof(unsigned) * kCPasses * kCopies * kCRadix + sizeof(unsigned long long) * 32 +
+         2 * sizeof(unsigned long long) * kMaxSort + sizeof(unsigned) * kMaxSort + sizeof(unsigned) * size_t(grid) +
+         256;
+}
+
+int select_coop_grid() {
+  static int g = 0;
+  if (!g) {
+    int dev = 0, sms = 152, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(select_coop_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCSmem);
+    cudaFuncSetAttribute(select_coop_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, select_coop_kernel<false>, kCoopThreads, kCSmem);
+    int per64 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per64, select_coop_kernel<true>, kCoopThreads, kCSmem);
+    per = per < per64 ? per : per64;
+    g = sms * (per >= 2 ? 2 : (per > 0 ? per : 1));
+  }
+  return g;
+}
+
+cudaError_t launch_select_coop(void* work, int grid, const void* x, int is_f64, uint64_t n, int k, double threshold,
+                               unsigned long long* bins_out, double* probs_out, int* n_found, int* err,
+                               cudaStream_t s) {
+  if (k < 1 || k > kSelectMaxK) return cudaErrorInvalidValue;
+  const int cap = (k > 512 ? k : 512) < kMaxSort - k ? (k > 512 ? k : 512) : kMaxSort - k;
+  char* p = static_cast<char*>(work);
+  CoopWork w;
+  w.ctl = reinterpret_cast<unsigned long long*>(p);
+  p += sizeof(unsigned long long) * 32;
+  w.cand_key = reinterpret_cast<unsigned long long*>(p);
+  p += sizeof(unsigned long long) * kMaxSort;
+  w.cand_idx = reinterpret_cast<unsigned long long*>(p);
+  p += sizeof(unsigned long long) * kMaxSort;
+  w.hist = reinterpret_cast<unsigned*>(p);
+  p += sizeof(unsigned) * kCPasses * kCopies * kCRadix;
+  w.rank = reinterpret_cast<unsigned*>(p);
+  p += sizeof(unsigned) * kMaxSort;
+  w.tie_count = reinterpret_cast<unsigned*>(p);
+  int aligned = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+  unsigned long long kt = threshold_key(is_f64, threshold);
+  void* args[] = {const_cast<void**>(&x), &aligned, &n, &kt, &k, const_cast<int*>(&cap), &w, &bins_out, &probs_out,
+                  &n_found, &err};
+  const void* fn = is_f64 ? reinterpret_cast<const void*>(select_coop_kernel<true>)
+                          : reinterpret_cast<const void*>(select_coop_kernel<false>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoopThreads), args, kCSmem, s);
 }
 
 // ---- allocation-free variant -------------------------------------------------

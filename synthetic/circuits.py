@@ -224,3 +224,38 @@ def random_block_circuit(seed: int, n_qubits: int, n_blocks: int, max_block: int
         last.qubits = sorted(last.qubits + fresh)
         last.gates += _line_layers(rng, last.qubits, 1)
     return CutCircuit(n_qubits, blocks).finalize()
+
+
+def bernstein_vazirani_chain(seed: int, widths: list[int], handoffs: list[int]) -> tuple[CutCircuit, list[int]]:
+    """Bernstein-Vazirani in phase-oracle form on a chain of blocks: H on
+    every qubit, Z (= T^4) on the qubits of the hidden string s, H again, so
+    the output is |s> with probability 1.  Each qubit's first H sits in the
+    first block that holds it and the rest in its last block, so the cut
+    wires carry |+>.  Returns (circuit, s)."""
+    rng = np.random.default_rng(seed)
+    start, ranges = 0, []
+    for b, w in enumerate(widths):
+        ranges.append(list(range(start, start + w)))
+        if b < len(handoffs):
+            start = start + w - handoffs[b]
+    n = start + widths[-1]
+    s = [int(v) for v in rng.integers(0, 2, n)]
+    first = {}
+    last = {}
+    for b, qs in enumerate(ranges):
+        for q in qs:
+            first.setdefault(q, b)
+            last[q] = b
+    blocks = []
+    for b, qs in enumerate(ranges):
+        gates = []
+        for q in qs:
+            if first[q] == b:
+                gates.append(("h", q))
+        for q in qs:
+            if last[q] == b:
+                if s[q]:
+                    gates += [("t", q)] * 4
+                gates.append(("h", q))
+        blocks.append(Block(qs, gates))
+    return CutCircuit(n, blocks).finalize(), s

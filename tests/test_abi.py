@@ -46,3 +46,35 @@ def test_null_arguments_are_rejected(lib):
     assert lib.sqc_create(None, 0, None) == 1
     assert lib.sqc_last_error(None)
     lib.sqc_destroy(None)                # ignored
+
+
+def test_assign_states_matches_algorithm_2_oracle(lib):
+    import numpy as np
+    import oracle as O
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        n = int(rng.integers(1, 7))
+        l = [1 << int(rng.integers(0, 12)) for _ in range(n)]
+        M = 1 << int(rng.integers(0, 30))
+        assert sqc.assign_states(l, M) == O.states_assignment(l, M)
+    assert sqc.assign_states([2 ** 7, 2 ** 8, 2 ** 7, 2 ** 8], 2 ** 20) == [32] * 4
+
+
+def test_recursion_roles_match_oracle(lib):
+    import numpy as np
+    import oracle as O
+    from synthetic import workloads as W
+    for w, M in ((W.merged_30q(), 2 ** 20), (W.grid_40q(), 2 ** 22)):
+        c = w.circuit
+        g = O.Graph.from_arrays(c.n_qubits, *c.graph_arrays())
+        rng = np.random.default_rng(1)
+        for trial in range(5):
+            zoom = {}
+            if trial:
+                for q in rng.choice(c.n_qubits, size=int(rng.integers(1, 12)), replace=False):
+                    zoom[int(q)] = int(rng.integers(2))
+            zarr = np.full(c.n_qubits, O.MERGED, dtype=np.int8)
+            for q, v in zoom.items():
+                zarr[q] = O.ZOOM1 if v else O.ZOOM0
+            got = sqc.recursion_roles(c.n_qubits, *c.graph_arrays(), zarr, M)
+            assert got.tolist() == list(O.roles_for_recursion(g, zoom, M))
