@@ -92,7 +92,13 @@ typedef struct {
   int32_t fp64_chunk_min_edges;
   /* FP32 terms summed per chunk before the FP64 addition (>= 16, power of 2). */
   int32_t chunk_terms;
-  int32_t reserved[5];
+  /* First-level index slicing (Section 6.3): number of cut edges to write
+   * out explicitly, chosen greedily as the edge whose slicing shrinks the
+   * total size of the subcircuit tensors most (ties: lowest edge id).  Each
+   * query then runs 4^slice_edges smaller contractions whose results are
+   * added into the output (in FP64 for FP64 outputs).  0 = no slicing. */
+  int32_t slice_edges;
+  int32_t reserved[4];
 } sqc_config;
 
 /* Compute graph (Section 5, Fig. 3d).  Vertices are subcircuits 0..n_C-1;
@@ -283,6 +289,11 @@ SQC_API sqc_status sqc_top_bins_noalloc(int device, const void* probs, sqc_dtype
 /* Device memory the context holds now (resident circuits, plans, batches,
  * workspaces) and its budget (0 = none); host values. */
 SQC_API sqc_status sqc_memory_info(const sqc_ctx* ctx, uint64_t* held_bytes, uint64_t* budget_bytes);
+
+/* The cut edges query q slices (Section 6.3), in the order the greedy rule
+ * chose them: *n_sliced values written to edges (capacity cap). */
+SQC_API sqc_status sqc_query_slices(const sqc_ctx* ctx, sqc_query_id q, int32_t* n_sliced, int32_t* edges,
+                                    int32_t cap);
 
 /* Introspection of a planned query (host values, no device work):
  * n_steps contraction steps; flops = sum of 2*M*N*K over the steps;

@@ -37,7 +37,7 @@ class SQCError(RuntimeError):
 class _Config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_active_qubits", ctypes.c_int32),
                 ("fp64_chunk_min_edges", ctypes.c_int32), ("chunk_terms", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("slice_edges", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class _Graph(ctypes.Structure):
@@ -83,6 +83,7 @@ _SIGS = {
     "sqc_server_destroy": (None, [_P]),
     "sqc_memory_info": (_c.c_int32, [_P, _c.POINTER(_c.c_uint64), _c.POINTER(_c.c_uint64)]),
     "sqc_assign_states": (_c.c_int32, [_c.c_int32, _P, _c.c_uint64, _P]),
+    "sqc_query_slices": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_c.c_int32), _P, _c.c_int32]),
     "sqc_recursion_roles": (_c.c_int32, [_P, _P, _c.c_uint64, _P]),
     "sqc_profile_enable": (_c.c_int32, [_P, _c.c_int]),
     "sqc_profile_read": (_c.c_int32, [_P, _P, _P, _P]),
@@ -145,7 +146,7 @@ class Context:
     """One library context on one GPU (C ABI: sqc_create / sqc_destroy)."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_active_qubits: int = 32,
-                 fp64_chunk_min_edges: int = 12, chunk_terms: int = 256):
+                 fp64_chunk_min_edges: int = 12, chunk_terms: int = 256, slice_edges: int = 0):
         self._lib = load_library()
         cfg = _Config()
         self._lib.sqc_default_config(ctypes.byref(cfg))
@@ -153,6 +154,7 @@ class Context:
         cfg.max_active_qubits = max_active_qubits
         cfg.fp64_chunk_min_edges = fp64_chunk_min_edges
         cfg.chunk_terms = chunk_terms
+        cfg.slice_edges = slice_edges
         h = _P()
         st = self._lib.sqc_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != 0:
@@ -247,6 +249,13 @@ class Context:
         self._check(self._lib.sqc_query_info(self._h, query, ctypes.byref(ns), ctypes.byref(fl), ctypes.byref(mb),
                                              ctypes.byref(wb)))
         return {"n_steps": ns.value, "flops": fl.value, "merge_bytes": mb.value, "work_bytes": wb.value}
+
+    def query_slices(self, query: int) -> list[int]:
+        """Cut edges the query slices (Section 6.3), in the greedy order."""
+        n = ctypes.c_int32()
+        buf = (ctypes.c_int32 * 64)()
+        self._check(self._lib.sqc_query_slices(self._h, query, ctypes.byref(n), buf, 64))
+        return list(buf[: n.value])
 
     def memory_info(self) -> dict:
         """Device bytes the context holds and its HBM budget (0: none)."""

@@ -82,6 +82,8 @@ struct Plan {
   unsigned* counter = nullptr;
   int* err = nullptr;            // set by bounded device waits that gave up
   double flops = 0.0;
+  std::vector<int> sliced;       // first-level sliced edges (Section 6.3), in greedy order
+  int64_t n_slices = 1;          // 4^{sliced edges}: merge descriptor sets, one per slice
 };
 
 struct Batch {
@@ -461,10 +463,44 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
   for (int qb = 0; qb < c.n_qubits; ++qb)
     if (q->roles[qb] == SQC_ROLE_ACTIVE) canon[qb] = na++;
 
+  // first-level slicing (Section 6.3): write out cfg.slice_edges cut edges,
+  // each time the one whose slicing shrinks sum_i 4^{k_i} 2^{a_i} most
+  // (ties: lowest edge id)
+  std::vector<int> a_of(nC, 0);
+  for (int i = 0; i < nC; ++i)
+    for (int t = 0; t < c.ndata[i]; ++t) a_of[i] += q->roles[c.dq[i][t]] == SQC_ROLE_ACTIVE;
+  std::set<int> sliced;
+  P->sliced.clear();
+  auto total_size = [&](const std::set<int>& sl) {
+    double tot = 0;
+    for (int i = 0; i < nC; ++i) {
+      int k = 0;
+      for (int e : c.inc[i]) k += !sl.count(e);
+      tot += std::ldexp(1.0, 2 * k + a_of[i]);
+    }
+    return tot;
+  };
+  for (int sidx = 0; sidx < ctx->cfg.slice_edges && int(sliced.size()) < c.K; ++sidx) {
+    int best = -1;
+    double best_size = 0;
+    for (int e = 0; e < c.K; ++e) {
+      if (sliced.count(e)) continue;
+      std::set<int> t = sliced;
+      t.insert(e);
+      const double sz = total_size(t);
+      if (best < 0 || sz < best_size) { best = e; best_size = sz; }
+    }
+    sliced.insert(best);
+    P->sliced.push_back(best);
+  }
+  P->n_slices = int64_t(1) << (2 * sliced.size());
+
   // subcircuit tensors T_i and the merge index codes
   P->split = split;
   P->tensors.assign(nC, Tensor{});
   std::vector<std::vector<int>> row_codes(nC), col_codes(nC);
+  std::vector<std::vector<uint64_t>> rowsel(nC);
+  std::vector<std::vector<std::pair<int, int>>> slice_pos(nC);   // (digit shift in A's row, sliced index)
   P->merge_host.assign(nC, MergeDesc{});
   double merge_bytes = 0.0;
   for (int i = 0; i < nC; ++i) {
@@ -483,13 +519,30 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     }
     Tensor& T = P->tensors[i];
     T.producer_sub = i;
-    // row index e: incident edge p's digit at bits 2(k-1-p) (lo) and 2(k-1-p)+1 (hi)
-    row_codes[i].assign(2 * k, 0);
-    for (int p = 0; p < k; ++p) {
+    // row index e of A_i: incident edge p's digit at bits 2(k-1-p) (lo) and
+    // 2(k-1-p)+1 (hi).  Sliced edges leave T_i: its rows run over the other
+    // edges (kept in A's digit order) and rowsel maps them back to A's rows.
+    std::vector<int> kept_shift;
+    for (int p = k - 1; p >= 0; --p) {           // least significant digit first
       const int eid = c.inc[i][p];
-      row_codes[i][2 * (k - 1 - p)] = 2 * eid;
-      row_codes[i][2 * (k - 1 - p) + 1] = 2 * eid + 1;
+      const int shift = 2 * (k - 1 - p);
+      if (sliced.count(eid)) {
+        const int sidx = int(std::find(P->sliced.begin(), P->sliced.end(), eid) - P->sliced.begin());
+        slice_pos[i].push_back({shift, sidx});
+        continue;
+      }
+      row_codes[i].push_back(2 * eid);
+      row_codes[i].push_back(2 * eid + 1);
+      kept_shift.push_back(shift);
       T.edges.insert(eid);
+    }
+    if (!slice_pos[i].empty()) {
+      rowsel[i].assign(size_t(1) << (2 * kept_shift.size()), 0);
+      for (size_t r = 0; r < rowsel[i].size(); ++r) {
+        uint64_t e = 0;
+        for (size_t t = 0; t < kept_shift.size(); ++t) e |= uint64_t((r >> (2 * t)) & 3) << kept_shift[t];
+        rowsel[i][r] = e;
+      }
     }
     // column index b: u-th lowest active storage bit
     for (int sp = 0; sp < n; ++sp)
@@ -498,7 +551,7 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     T.bits.insert(T.bits.end(), col_codes[i].begin(), col_codes[i].end());
     MergeDesc& d = P->merge_host[i];
     d.A = c.A[i];
-    d.rows = c.V[i];
+    d.rows = int64_t(1) << row_codes[i].size();
     d.n = n;
     d.act_mask = act;
     d.mer_mask = mer;
@@ -603,7 +656,8 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     // tensor cores for the big steps: M, N >= 128 (one UMMA tile), and a
     // shared index short enough to be one FP32 chunk
     st.tc = tc_ok && st.M >= gemm_tc_min_rows() && st.N >= gemm_tc_min_rows() &&
-            (st.Kd <= ctx->cfg.chunk_terms || c.K < ctx->cfg.fp64_chunk_min_edges);
+            (st.Kd <= ctx->cfg.chunk_terms || c.K < ctx->cfg.fp64_chunk_min_edges) &&
+            !(P->n_slices > 1 && s == int(P->steps.size()) - 1);   // slices accumulate on the SIMT path
     st.Kp = st.tc ? std::max<int64_t>(st.Kd, gemm_tc_k_align()) : st.Kd;
     std::vector<int> lay = sh;
     for (int p = ilog2(st.Kd); p < ilog2(st.Kp); ++p) lay.push_back(kPad);
@@ -625,15 +679,17 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     P->flops += 2.0 * double(st.M) * double(st.N) * double(st.Kd);
   }
   std::vector<std::pair<size_t, size_t>> merge_map_off(nC);
+  std::vector<size_t> rowsel_off(nC, 0);
   for (int i = 0; i < nC; ++i) {
     const std::map<int, int> tpos = positions(P->tensors[i].layout);
     merge_map_off[i] = {maps.add(make_map(row_codes[i], tpos)), maps.add(make_map(col_codes[i], tpos))};
+    if (!rowsel[i].empty()) rowsel_off[i] = maps.add(rowsel[i]);
   }
 
   // workspace: descriptors | maps | tensors | partials + counter + error flag
   auto align = [](size_t x) { return (x + 1023) & ~size_t(1023); };
   size_t off = 0;
-  const size_t off_desc = off; off = align(off + sizeof(MergeDesc) * nC);
+  const size_t off_desc = off; off = align(off + sizeof(MergeDesc) * nC * size_t(P->n_slices));
   const size_t off_maps = off; off = align(off + sizeof(uint64_t) * maps.host.size());
   std::vector<size_t> off_tensor(P->tensors.size(), 0);
   size_t zero_begin = 0, zero_end = 0;
@@ -677,6 +733,8 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     d.dst = P->tensors[i].buf;          // null for the result (set per call)
     d.kind = P->tensors[i].kind;
     d.plane_stride = P->tensors[i].plane_stride;
+    d.rowsel = rowsel[i].empty() ? nullptr : maps_dev + rowsel_off[i];
+    d.row_add = 0;
     d.block_begin = blocks;
     const int64_t outs = d.rows << d.a;
     const int64_t per = 256 / d.lanes;
@@ -684,7 +742,18 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
   }
   P->merge_blocks = blocks;
   cudaError_t e = upload(ctx, maps_dev, maps.host.data(), sizeof(uint64_t) * maps.host.size());
-  if (e == cudaSuccess && nC > 0) e = upload(ctx, P->merge_dev, P->merge_host.data(), sizeof(MergeDesc) * nC);
+  if (e == cudaSuccess && nC > 0) {
+    // one descriptor set per slice: slice sigma fixes sliced edge j's digit
+    // to (sigma >> 2j) & 3 in every A row it reads
+    std::vector<MergeDesc> sets(size_t(nC) * size_t(P->n_slices));
+    for (int64_t sg = 0; sg < P->n_slices; ++sg)
+      for (int i = 0; i < nC; ++i) {
+        MergeDesc d = P->merge_host[i];
+        for (const auto& sp : slice_pos[i]) d.row_add += int64_t((sg >> (2 * sp.second)) & 3) << sp.first;
+        sets[size_t(sg) * nC + i] = d;
+      }
+    e = upload(ctx, P->merge_dev, sets.data(), sizeof(MergeDesc) * sets.size());
+  }
   if (e == cudaSuccess) e = zero(ctx, base + off_cnt, 64);
   // BF16 operand padding (shared-index columns beyond K) must read as zero
   if (e == cudaSuccess && zero_end > zero_begin) e = zero(ctx, base + zero_begin, zero_end - zero_begin);
@@ -761,6 +830,8 @@ SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg) 
     return fail(nullptr, SQC_EINVAL, "max_active_qubits must be in [0, 40]");
   if (ctx->cfg.chunk_terms < 16 || (ctx->cfg.chunk_terms & (ctx->cfg.chunk_terms - 1)))
     return fail(nullptr, SQC_EINVAL, "chunk_terms must be a power of two >= 16");
+  if (ctx->cfg.slice_edges < 0 || ctx->cfg.slice_edges > 8)
+    return fail(nullptr, SQC_EINVAL, "slice_edges must be in [0, 8]");
   DeviceGuard g(device);
   e = select_configure();
   if (e == cudaSuccess) e = attr_configure();
@@ -926,6 +997,18 @@ SQC_API sqc_status sqc_query_info(const sqc_ctx* cctx, sqc_query_id qid, int32_t
   return SQC_OK;
 }
 
+SQC_API sqc_status sqc_query_slices(const sqc_ctx* cctx, sqc_query_id qid, int32_t* n_sliced, int32_t* edges,
+                                    int32_t cap) {
+  sqc_ctx* ctx = const_cast<sqc_ctx*>(cctx);
+  if (!ctx || !n_sliced) return SQC_EINVAL;
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  const Plan& P = it->second->plans[SQC_PREC_FP32];
+  *n_sliced = int32_t(P.sliced.size());
+  for (size_t j = 0; j < P.sliced.size() && edges && int32_t(j) < cap; ++j) edges[j] = P.sliced[j];
+  return SQC_OK;
+}
+
 SQC_API sqc_status sqc_memory_info(const sqc_ctx* ctx, uint64_t* held_bytes, uint64_t* budget_bytes) {
   if (!ctx) return SQC_EINVAL;
   if (held_bytes) *held_bytes = ctx->bytes;
@@ -992,67 +1075,79 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
     }
     return SQC_OK;
   }
-  {
-    StageScope scope(ctx, s, SQC_STAGE_MERGE);
-    CK(launch_merge_blocks(P.merge_dev, int(P.merge_host.size()), P.merge_blocks, s));
-    ctx->launches += 1;
-  }
-  for (size_t si = 0; si < P.steps.size(); ++si) {
-    const Step& st = P.steps[si];
-    const bool last = int(si) == int(P.steps.size()) - 1;
-    const Tensor& Z = P.tensors[st.z];
-    void* C = last ? out_bins : Z.buf;
-    const int kind = last ? out_kind : Z.kind;
-    StageScope scope(ctx, s, last ? SQC_STAGE_FINAL : SQC_STAGE_CONTRACT);
-    if (st.tc) {
-      GemmTcArgs a{};
-      a.A = P.tensors[st.x].buf;
-      a.B = P.tensors[st.y].buf;
-      a.M = st.M;
-      a.N = st.N;
-      a.K = st.Kd;
-      a.Mp = st.M;
-      a.Np = st.N;
-      a.Kp = st.Kp;
-      a.rowmap = st.rowmap;
-      a.colmap = st.colmap;
-      a.C = C;
-      a.kind = kind;
-      a.plane_stride = last ? 0 : Z.plane_stride;
-      a.alpha = last ? alpha : 1.0;
-      a.chunk = 0;
-      a.partials = (last && total_prob) ? P.partials : nullptr;
-      a.counter = P.counter;
-      a.total = total_prob;
-      a.err = P.err;
-      CK(launch_gemm_tc(a, s));
-    } else {
-      GemmArgs a{};
-      a.A = static_cast<const float*>(P.tensors[st.x].buf);
-      a.B = static_cast<const float*>(P.tensors[st.y].buf);
-      a.M = st.M;
-      a.N = st.N;
-      a.K = st.Kd;
-      a.rowmap = st.rowmap;
-      a.colmap = st.colmap;
-      a.vec4 = st.vec4;
-      a.C = C;
-      a.kind = kind;
-      a.plane_stride = last ? 0 : Z.plane_stride;
-      if (last) {
-        a.alpha = alpha;
-        a.chunk = (out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
-                      ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
-                      : 0;
-        a.partials = total_prob ? P.partials : nullptr;
+  // first-level slices (Section 6.3): every slice runs the whole merge and
+  // contraction over the unsliced edges and adds its bins into the output
+  const int nCm = int(P.merge_host.size());
+  for (int64_t sg = 0; sg < P.n_slices; ++sg) {
+    {
+      StageScope scope(ctx, s, SQC_STAGE_MERGE);
+      CK(launch_merge_blocks(P.merge_dev + sg * nCm, nCm, P.merge_blocks, s));
+      ctx->launches += 1;
+    }
+    for (size_t si = 0; si < P.steps.size(); ++si) {
+      const Step& st = P.steps[si];
+      const bool last = int(si) == int(P.steps.size()) - 1;
+      const Tensor& Z = P.tensors[st.z];
+      void* C = last ? out_bins : Z.buf;
+      const int kind = last ? out_kind : Z.kind;
+      const bool sums_here = last && total_prob && P.n_slices == 1;
+      StageScope scope(ctx, s, last ? SQC_STAGE_FINAL : SQC_STAGE_CONTRACT);
+      if (st.tc) {
+        GemmTcArgs a{};
+        a.A = P.tensors[st.x].buf;
+        a.B = P.tensors[st.y].buf;
+        a.M = st.M;
+        a.N = st.N;
+        a.K = st.Kd;
+        a.Mp = st.M;
+        a.Np = st.N;
+        a.Kp = st.Kp;
+        a.rowmap = st.rowmap;
+        a.colmap = st.colmap;
+        a.C = C;
+        a.kind = kind;
+        a.plane_stride = last ? 0 : Z.plane_stride;
+        a.alpha = last ? alpha : 1.0;
+        a.chunk = 0;
+        a.partials = sums_here ? P.partials : nullptr;
         a.counter = P.counter;
         a.total = total_prob;
+        a.err = P.err;
+        CK(launch_gemm_tc(a, s));
       } else {
-        a.alpha = 1.0;
-        a.chunk = 0;
+        GemmArgs a{};
+        a.A = static_cast<const float*>(P.tensors[st.x].buf);
+        a.B = static_cast<const float*>(P.tensors[st.y].buf);
+        a.M = st.M;
+        a.N = st.N;
+        a.K = st.Kd;
+        a.rowmap = st.rowmap;
+        a.colmap = st.colmap;
+        a.vec4 = st.vec4;
+        a.C = C;
+        a.kind = kind;
+        a.plane_stride = last ? 0 : Z.plane_stride;
+        if (last) {
+          a.alpha = alpha;
+          a.chunk = (out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
+                        ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
+                        : 0;
+          a.accumulate = sg > 0;
+          a.partials = sums_here ? P.partials : nullptr;
+          a.counter = P.counter;
+          a.total = total_prob;
+        } else {
+          a.alpha = 1.0;
+          a.chunk = 0;
+        }
+        CK(launch_gemm_simt(a, s));
       }
-      CK(launch_gemm_simt(a, s));
+      ctx->launches += 1;
     }
+  }
+  if (total_prob && P.n_slices > 1) {
+    StageScope scope(ctx, s, SQC_STAGE_FINAL);
+    CK(launch_sum(out_bins, out_dtype == SQC_F64, uint64_t(q.out_elems), P.partials, P.counter, total_prob, s));
     ctx->launches += 1;
   }
   return SQC_OK;
@@ -1106,6 +1201,7 @@ SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id*
     const Circuit& c = *cit->second;
     Plan& P = q.plans[SQC_PREC_FP32];
     if (P.steps.empty()) return fail(ctx, SQC_EINVAL, "batch: every query needs at least two subcircuits");
+    if (P.n_slices > 1) return fail(ctx, SQC_EINVAL, "batch: sliced queries (cfg.slice_edges > 0) run one at a time");
     if (!outs[j]) return fail(ctx, SQC_EINVAL, "batch: null output");
     // tensor slots of this query
     std::vector<int> slot(P.tensors.size(), -1), level(P.tensors.size(), 0);

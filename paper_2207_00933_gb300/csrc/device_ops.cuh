@@ -20,7 +20,8 @@ __device__ __forceinline__ void merge_block(const MergeDesc& d, int64_t blk) {
   if (valid) {
     const int64_t e = o >> d.a;
     const uint32_t b = uint32_t(o & ((int64_t(1) << d.a) - 1));
-    const float* row = d.A + (e << d.n);
+    const int64_t er = d.rowsel ? int64_t(d.rowsel[e]) + d.row_add : e;
+    const float* row = d.A + (er << d.n);
     const uint32_t run = 1u << d.m;
     if (d.fast) {
       const float* src = row + (d.zoom_val | (b << d.m));
@@ -142,7 +143,12 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
           q.x = acc[i][j] * alpha_f; q.y = acc[i][j + 1] * alpha_f;
           q.z = acc[i][j + 2] * alpha_f; q.w = acc[i][j + 3] * alpha_f;
           sum_f += (q.x + q.y) + (q.z + q.w);
-          *reinterpret_cast<float4*>(static_cast<float*>(a.C) + rbase + a.colmap[c0 + j]) = q;
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(a.C) + rbase + a.colmap[c0 + j]);
+          if (a.accumulate) {
+            const float4 o = *dst;
+            q.x += o.x; q.y += o.y; q.z += o.z; q.w += o.w;
+          }
+          *dst = q;
         }
       } else {
 #pragma unroll
@@ -151,7 +157,8 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
           if (col >= a.N) continue;
           const float v = acc[i][j] * alpha_f;
           sum_f += v;
-          static_cast<float*>(a.C)[rbase + a.colmap[col]] = v;
+          float* dst = static_cast<float*>(a.C) + rbase + a.colmap[col];
+          *dst = a.accumulate ? *dst + v : v;
         }
       }
     } else {
@@ -162,7 +169,15 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
         double v;
         if constexpr (CHUNKED) v = acc64[i][j]; else v = double(acc[i][j] * alpha_f);
         if (a.kind == OUT_F64) sum_d += v; else sum_f += float(v);
-        store_out(a.C, a.kind, a.plane_stride, rbase + a.colmap[col], v);
+        if (a.accumulate && a.kind == OUT_F64) {
+          double* dst = static_cast<double*>(a.C) + rbase + a.colmap[col];
+          *dst += v;                          // slices add up in FP64
+        } else if (a.accumulate && a.kind == OUT_F32) {
+          float* dst = static_cast<float*>(a.C) + rbase + a.colmap[col];
+          *dst += float(v);
+        } else {
+          store_out(a.C, a.kind, a.plane_stride, rbase + a.colmap[col], v);
+        }
       }
     }
   }

@@ -77,6 +77,10 @@ struct MergeDesc {
   int64_t plane_stride;                   // OUT_BF16X3: elements between planes
   double alpha;
   int64_t block_begin;                    // first CTA of this descriptor
+  // first-level slicing: the merge reads row rowsel[e] + row_add of A (the
+  // sliced edges' digits fixed); rowsel == nullptr: row e
+  const uint64_t* rowsel;
+  int64_t row_add;
 };
 constexpr int kMaxMerge = 64;
 // descs: device array of n descriptors; total_blocks = CTAs over all of them
@@ -95,6 +99,7 @@ struct GemmArgs {
   double alpha;
   int64_t chunk;            // FP32 terms per chunk before the FP64 add (0 = plain FP32)
   int vec4;                 // colmap[4j..4j+3] contiguous and 4-aligned for all j
+  int accumulate;           // add into C instead of overwriting (later slices, FP32/FP64 outputs)
   double* partials;         // per-CTA sums of the written values (nullable)
   unsigned* counter;        // zero-initialised; last CTA writes *total and resets it
   double* total;
