@@ -59,7 +59,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
-    ap.add_argument("--no-extras", action="store_true", help="skip the split-BF16 variant and the tensor microbench")
+    ap.add_argument("--no-extras", action="store_true", help="skip the microbenchmarks, batch and serving runs")
+    ap.add_argument("--extra", choices=["tensor", "hbm", "batch", "serving"],
+                    help="run only this microbenchmark and print its JSON line")
     return ap.parse_args()
 
 
@@ -131,6 +133,55 @@ def tensor_microbench(dev, reps: int = 20) -> dict:
             out[prec] = d
         ctx.unload(cid)
     return {"shape": {"M": M, "N": N, "K": K}, "workload": "randline32_K4_a24 (two subcircuits, 4 shared cuts)", **out}
+
+
+def hbm_microbench(dev, reps: int = 10) -> dict:
+    """HBM-bound stages at a size where they stream: two line subcircuits of
+    20 and 22 qubits sharing 2 cut edges, with random outputs (4^2 variants
+    each, 320 MiB of FP32 input, 272 MiB of attributed tensors), 10 + 14
+    active qubits.  Times, with stage events and the inputs resident in HBM
+    (all buffers larger than L2), the attribution (reads every variant
+    output once, writes A) and the merge (reads A once); achieved bandwidth
+    is the algorithmic bytes over the stage time.  The result is checked
+    against the FP64 oracle."""
+    import torch
+    import oracle as O
+    from paper_2207_00933_gb300 import Context
+    from synthetic import workloads as W
+    w = W.random_line_chain(12, [20, 22], [2], 1, [10, 14])
+    c = w.circuit
+    hbm, src = peaks()
+    out = {"workload": "randline40_K2_a24 (subcircuits of 20 and 22 measured qubits, 2 cuts, 10+14 active)",
+           "peak_gbs": hbm, "peak_source": src}
+    with Context(dev.index or 0) as ctx:
+        probs_dev = [torch.from_numpy(p).to(dev) for p in w.probs]
+        cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), probs_dev)
+        qid, na = ctx.set_qubit_roles(cid, w.roles)
+        res = torch.empty(1 << na, dtype=torch.float32, device=dev)
+        steps = ctx.query_steps(qid)
+
+        def step():
+            ctx.update_subcircuit_outputs(cid, probs_dev)
+            ctx.reconstruct(qid, res, "fp32")
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize(dev)
+        ctx.profile_enable(True)
+        for _ in range(reps):
+            step()
+        pr = ctx.profile_read()
+        ctx.profile_enable(False)
+        algo = algorithmic_bytes(w, steps, 4)
+        for k in ("attribute", "merge"):
+            ms = pr["ms"][k] / max(1, pr["calls"][k])
+            gbs = algo[k] / (ms * 1e-3) / 1e9
+            out[k] = {"us": 1e3 * ms, "bytes": algo[k], "GBps": gbs, "frac": gbs / hbm}
+        g = O.Graph.from_arrays(c.n_qubits, *c.graph_arrays())
+        ref = O.reconstruct(g, [p.astype(np.float64) for p in w.probs], w.roles)
+        out["max_abs_err_vs_fp64"] = float(np.abs(res.double().cpu().numpy() - ref).max())
+        ctx.unload(cid)
+    return out
 
 
 # ---- clocks during the timed region ---------------------------------------------
@@ -423,6 +474,14 @@ def main():
     import torch
     import torch.distributed as dist
 
+    if args.extra:
+        import __graft_entry__
+        __graft_entry__.build()
+        dev = torch.device("cuda", 0)
+        fn = {"tensor": tensor_microbench, "hbm": hbm_microbench, "batch": batch_bench, "serving": serving_bench}
+        print(json.dumps({"extra": args.extra, **fn[args.extra](dev)}), flush=True)
+        return
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -537,8 +596,8 @@ def main():
     dom = max(stage_ms, key=lambda k: prof["ms"][k])
     hbm, src = peaks()
     achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9
-    kernel_of = {"attribute": "fold_kernel+mix_kernel", "merge": "merge_kernel", "contract": "gemm_simt_kernel",
-                 "final": "gemm_simt_kernel (last step)", "select": "radix_pass+compact+rank_emit"}
+    kernel_of = {"attribute": "attr_fused_kernel", "merge": "merge_kernel", "contract": "gemm_simt_kernel",
+                 "final": "gemm_simt_kernel (last step)", "select": "select_coop_kernel"}
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": src,
                 "stages": {k: {"us": 1e3 * stage_ms[k], "share": share[k],
@@ -597,6 +656,7 @@ def main():
         line["config"]["precision"] = prec
         if world == 1 and not args.no_extras:
             line["tensor_microbench"] = tensor_microbench(dev)
+            line["hbm_microbench"] = hbm_microbench(dev)
             line["batched_level"] = batch_bench(dev)
             line["serving"] = serving_bench(dev)
         if world == 1 and not args.no_cpu_baseline:

@@ -352,12 +352,25 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
       d.n = n;
       d.kin = kin;
       d.kout = kout;
-      // x tile: 8 consecutive low values (32-byte read runs) x 2 top-bit values
+      // x tile: 2^L1 consecutive low values (read runs) x 2^L2 top-bit
+      // values (write runs of the bit-reversed A).  Start at 8 x 2; grow
+      // toward 32 x 8 (128-byte reads, whole 32-byte write sectors) while
+      // the subcircuit still has kAttrTileTarget tiles, so that small
+      // subcircuits keep enough CTAs and large ones amortise each tile's
+      // shared-memory passes over more data.
       int L2 = std::min(1, n / 2), L1 = std::min(3, n - L2);
       const int64_t S = int64_t(1) << (2 * kin);
       while ((S << (L1 + L2)) > kAttrSmemMax / 4) {
         if (L1 >= L2 && L1 > 0) --L1;
         else if (L2 > 0) --L2;
+        else break;
+      }
+      constexpr int64_t kAttrTileTarget = 4096;
+      for (;;) {
+        const int64_t tiles_next = ((int64_t(1) << (n - L1 - L2)) << (2 * kout)) >> 1;
+        if (L1 + L2 >= n || tiles_next < kAttrTileTarget || (S << (L1 + L2 + 1)) > kAttrSmemMax / 4) break;
+        if (L2 < 3) ++L2;
+        else if (L1 < 5) ++L1;
         else break;
       }
       d.L1 = L1;

@@ -90,44 +90,62 @@ __global__ void __launch_bounds__(256) mix_kernel(MixArgs a) {
   }
 }
 
-__device__ __forceinline__ int64_t variant_of(const AttrDesc& d, int64_t vbase, int s) {
-  int64_t v = vbase;
-  for (int q = 0; q < d.kin; ++q) v |= int64_t((s >> (2 * q)) & 3) << d.inshift[q];
-  return v;
+// ---- fused attribution -------------------------------------------------------
+// For subcircuits with at most kMaxFusedIn incoming cut edges.  A CTA owns
+// one tile: 2^L1 consecutive low values of the data state x times 2^L2
+// values of its top bits (so that the reads of p run over 2^L1 consecutive
+// x and the bit-reversed writes of A over 2^L2 consecutive storage
+// addresses), for one combination o of outgoing-edge bases and all 4^kin
+// prepared-state combinations s:
+//   1. fold the outcomes c of the outgoing wires into shared memory,
+//   2. expand the incoming edges one at a time in place:
+//      (|0>,|1>,|+>,|+i>) -> (I, X, Y, Z) = (a+b, 2c-(a+b), 2d-(a+b), a-b),
+//   3. write the 4^kin labelled rows to A (data index bit-reversed).
+// Every variant output is read once.
+//
+// A tile holds TX = 2^(L1+L2) <= 256 states, so with 256 threads every
+// thread keeps the same state slot j in all three phases and only steps
+// through the rows s; the per-element work is a table lookup, an OR and a
+// shift.  The slot's shared-memory position is XOR-swizzled so that phase
+// 3, which reads the slots in storage order (top bits fastest), hits 32
+// distinct banks.
+struct AttrTileCtx {
+  uint64_t vlo[256];   // variant-index contribution of the low 4 in-edge digits of s
+  uint64_t vhi[64];    // ... of the digits above them
+};
+
+__device__ __forceinline__ uint64_t in_digits(const AttrTileCtx& t, int s) {
+  return t.vlo[s & 255] | t.vhi[s >> 8];
 }
 
-__device__ __forceinline__ int64_t x_in_tile(const AttrDesc& d, int64_t xm, int j) {
-  const int64_t jl = j & ((1 << d.L1) - 1);
-  const int64_t jh = j >> d.L1;
-  return jl | (xm << d.L1) | (jh << (d.n - d.L2));
+// shared-memory position of slot j = jl | jh << L1 within a row
+__device__ __forceinline__ int slot_pos(int j, int L1, int L2) {
+  if (L1 + L2 <= 5) return j;
+  const int jh = j >> L1;
+  const int m = L1 >= 5 ? jh : (jh >> (5 - L1));
+  return j ^ ((m << (5 - L2)) & ((1 << L1) - 1));
 }
 
-// Phase 1 of the fused attribution: fold the outcomes of the outgoing wires
-// for every (s, x) of the tile into shared memory.  NC = outcomes handled per
-// round (all of them when 2^kout <= 8); kU entries per thread per round, so
-// that NC x kU independent loads are in flight.
 template <int NC, bool F64>
-__device__ __forceinline__ void fold_phase(const AttrDesc& d, float* val, int S, int lt, int64_t vbase,
-                                           uint32_t signed_mask) {
+__device__ __forceinline__ void fold_phase(const AttrDesc& d, const AttrTileCtx& t, float* val, int S, int lt,
+                                           uint64_t x, int pos, uint64_t vbase, uint32_t signed_mask) {
   constexpr int kU = NC >= 8 ? 2 : (NC >= 4 ? 4 : 8);
-  // tiles are (x middle bits) x (4^kout outgoing bases): shifts, no division
-  const int64_t xm = (int64_t(blockIdx.x) - d.block_begin) >> (2 * d.kout);
   const int n = d.n;
-  const int64_t row_len = (int64_t(1) << n) << d.kout;
+  const int row_shift = n + d.kout;
   const int nc = 1 << d.kout;
-  const int total = S << lt;
+  const int TX = 1 << lt;
+  const int step = int(blockDim.x) >> lt;
   const float* p32 = static_cast<const float*>(d.p);
   const double* p64 = static_cast<const double*>(d.p);
-  for (int b0 = 0; b0 < total; b0 += int(blockDim.x) * kU) {
-    int64_t base[kU];
+  for (int s0 = int(threadIdx.x) >> lt; s0 < S; s0 += step * kU) {
+    uint64_t base[kU];
     float acc[kU];
     bool ok[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
-      const int idx = b0 + u * int(blockDim.x) + int(threadIdx.x);
-      ok[u] = idx < total;
-      const int s = ok[u] ? idx >> lt : 0, j = ok[u] ? idx & ((1 << lt) - 1) : 0;
-      base[u] = variant_of(d, vbase, s) * row_len + x_in_tile(d, xm, j);
+      const int s = s0 + u * step;
+      ok[u] = s < S;
+      base[u] = ((in_digits(t, ok[u] ? s : 0) | vbase) << row_shift) + x;
       acc[u] = 0.f;
     }
     for (int c0 = 0; c0 < nc; c0 += NC) {
@@ -136,7 +154,7 @@ __device__ __forceinline__ void fold_phase(const AttrDesc& d, float* val, int S,
       for (int cc = 0; cc < NC; ++cc)
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-          const int64_t a = base[u] + (int64_t(c0 + cc) << n);
+          const uint64_t a = base[u] + (uint64_t(c0 + cc) << n);
           // the input type is a template parameter: FP64 conversions (a
           // narrow pipe on this GPU) exist only in the FP64-input variant
           if constexpr (F64)
@@ -153,88 +171,123 @@ __device__ __forceinline__ void fold_phase(const AttrDesc& d, float* val, int S,
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u)
-      if (ok[u]) val[b0 + u * int(blockDim.x) + int(threadIdx.x)] = acc[u];
+      if (ok[u]) val[(s0 + u * step) * TX + pos] = acc[u];
   }
 }
 
-// Fused attribution for subcircuits with at most kMaxFusedIn incoming cut
-// edges.  A CTA owns one tile of data states x (2^L1 consecutive low values
-// times 2^L2 values of the top bits, so that both the reads of p and the
-// bit-reversed writes of A touch whole 32-byte sectors) for one combination
-// o of outgoing-edge bases and all 4^kin prepared-state combinations s:
-//   1. load and fold the outcomes c of the outgoing wires into shared memory,
-//   2. apply the incoming-edge expansion one edge at a time in place:
-//      (|0>,|1>,|+>,|+i>) -> (I, X, Y, Z) = (a+b, 2c-(a+b), 2d-(a+b), a-b),
-//   3. write the 4^kin labelled rows to A (data index bit-reversed).
-// Every variant output is read once.
-__global__ void __launch_bounds__(256) attr_fused_kernel(AttrLaunch L) {
-  extern __shared__ float val[];
-  // the descriptor of this CTA, copied with constant parameter offsets only
-  // (a dynamic index into the parameter block would copy all of it to local
-  // memory in every thread)
-  __shared__ AttrDesc d;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int i = 0; i < kAttrPerLaunch; ++i)
-      if (i < L.n && L.d[i].block_begin <= int64_t(blockIdx.x)) d = L.d[i];
-  }
-  __syncthreads();
-  const int64_t t = int64_t(blockIdx.x) - d.block_begin;
-  const int64_t o = t & ((int64_t(1) << (2 * d.kout)) - 1);
-  const int64_t xm = t >> (2 * d.kout);
+// One tile (index t relative to the descriptor's first tile).
+__device__ __forceinline__ void attr_tile(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
+  // tiles are (x middle bits) x (4^kout outgoing bases): shifts, no division
+  const uint64_t o = uint64_t(t) & ((uint64_t(1) << (2 * d.kout)) - 1);
+  const uint64_t xm = uint64_t(t) >> (2 * d.kout);
   const int S = 1 << (2 * d.kin);
-  const int TX = 1 << (d.L1 + d.L2);
+  const int L1 = d.L1, L2 = d.L2, lt = L1 + L2;
+  const int TX = 1 << lt;
   const int n = d.n;
-  const int64_t X = int64_t(1) << n;
-  // base variant index: the outgoing edges' bases from o
-  int64_t vbase = 0;
+  const int step = int(blockDim.x) >> lt;
+  // the outgoing edges' bases from o
+  uint64_t vbase = 0;
   uint32_t signed_mask = 0;
   for (int u = 0; u < d.kout; ++u) {
-    const int64_t dig = (o >> (2 * u)) & 3;
+    const uint64_t dig = (o >> (2 * u)) & 3;
     vbase |= dig << d.outshift[u];
     if (dig) signed_mask |= 1u << u;
   }
-  // phase 1, specialised on the number of outcomes so that no load slot is
-  // predicated away
-  const int lt = d.L1 + d.L2;
+  // this thread's slot in phases 1-2: j = low bits of the thread index
+  const int j = int(threadIdx.x) & (TX - 1);
+  auto x_of = [&](int jj) -> uint64_t {
+    const uint64_t jl = uint64_t(jj & ((1 << L1) - 1)), jh = uint64_t(jj >> L1);
+    return jl | (xm << L1) | (jh << (n - L2));
+  };
+  const int pos = slot_pos(j, L1, L2);
   if (d.in_f64) {
     switch (d.kout) {
-      case 0: fold_phase<1, true>(d, val, S, lt, vbase, signed_mask); break;
-      case 1: fold_phase<2, true>(d, val, S, lt, vbase, signed_mask); break;
-      case 2: fold_phase<4, true>(d, val, S, lt, vbase, signed_mask); break;
-      default: fold_phase<8, true>(d, val, S, lt, vbase, signed_mask); break;
+      case 0: fold_phase<1, true>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
+      case 1: fold_phase<2, true>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
+      case 2: fold_phase<4, true>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
+      default: fold_phase<8, true>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
     }
   } else {
     switch (d.kout) {
-      case 0: fold_phase<1, false>(d, val, S, lt, vbase, signed_mask); break;
-      case 1: fold_phase<2, false>(d, val, S, lt, vbase, signed_mask); break;
-      case 2: fold_phase<4, false>(d, val, S, lt, vbase, signed_mask); break;
-      default: fold_phase<8, false>(d, val, S, lt, vbase, signed_mask); break;
+      case 0: fold_phase<1, false>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
+      case 1: fold_phase<2, false>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
+      case 2: fold_phase<4, false>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
+      default: fold_phase<8, false>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
     }
   }
   __syncthreads();
   for (int q = 0; q < d.kin; ++q) {
     const int lowmask = (1 << (2 * q)) - 1;
-    for (int idx = threadIdx.x; idx < (S / 4) * TX; idx += blockDim.x) {
-      const int g = idx >> lt, j = idx & (TX - 1);
+    const int st = TX << (2 * q);
+    for (int g = int(threadIdx.x) >> lt; g < (S >> 2); g += step) {
       const int s0 = ((g & ~lowmask) << 2) | (g & lowmask);
-      const int st = 1 << (2 * q);
-      float* a = val + s0 * TX + j;
-      const float v0 = a[0], v1 = a[st * TX], v2 = a[2 * st * TX], v3 = a[3 * st * TX];
+      float* a = val + s0 * TX + pos;
+      const float v0 = a[0], v1 = a[st], v2 = a[2 * st], v3 = a[3 * st];
       const float sum = v0 + v1;
-      a[0] = sum;                       // I
-      a[st * TX] = 2.f * v2 - sum;      // X
-      a[2 * st * TX] = 2.f * v3 - sum;  // Y
-      a[3 * st * TX] = v0 - v1;         // Z
+      a[0] = sum;                 // I
+      a[st] = 2.f * v2 - sum;     // X
+      a[2 * st] = 2.f * v3 - sum; // Y
+      a[3 * st] = v0 - v1;        // Z
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < S * TX; idx += blockDim.x) {
-    const int s = idx >> lt, jr = idx & (TX - 1);
-    const int jh = jr & ((1 << d.L2) - 1), jl = jr >> d.L2;
-    const int j = jl | (jh << d.L1);
-    const int64_t e = variant_of(d, vbase, s);
-    d.A[e * X + rev_bits(uint32_t(x_in_tile(d, xm, j)), n)] = val[s * TX + j];
+  // phase 3: slot order with the top bits fastest, so that consecutive
+  // threads write consecutive (bit-reversed) storage addresses
+  const int jh = j & ((1 << L2) - 1), jl = j >> L2;
+  const int jw = jl | (jh << L1);
+  const int posw = slot_pos(jw, L1, L2);
+  const uint64_t xw = rev_bits(uint32_t(x_of(jw)), n);
+  for (int s = int(threadIdx.x) >> lt; s < S; s += step)
+    d.A[((in_digits(tc, s) | vbase) << n) + xw] = val[s * TX + posw];
+}
+
+__device__ void fill_tile_ctx(const AttrDesc& d, AttrTileCtx& t) {
+  for (int i = threadIdx.x; i < 256 + 64; i += blockDim.x) {
+    const int s = i < 256 ? i : ((i - 256) << 8);
+    uint64_t v = 0;
+    for (int q = 0; q < d.kin; ++q) v |= uint64_t((s >> (2 * q)) & 3) << d.inshift[q];
+    if (i < 256) t.vlo[i] = v;
+    else t.vhi[i - 256] = v;
+  }
+}
+
+// Persistent: CTAs walk the tiles of all descriptors; a CTA copies a
+// descriptor into shared memory only when it crosses into it (constant
+// parameter offsets only: a dynamic index into the parameter block would copy
+// all of it to local memory in every thread).
+__global__ void __launch_bounds__(256) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
+  extern __shared__ float val[];
+  __shared__ AttrDesc d;
+  __shared__ AttrTileCtx tc;
+  __shared__ int cur, changed;
+  if (threadIdx.x == 0) cur = -1;
+  __syncthreads();
+  for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int di = 0;
+#pragma unroll
+      for (int i = 1; i < kAttrPerLaunch; ++i)
+        if (i < L.n && L.d[i].block_begin <= tile) di = i;
+      changed = di != cur;
+      if (changed) {
+        switch (di) {
+#define SQC_ATTR_CASE(k) case k: d = L.d[k]; break;
+          SQC_ATTR_CASE(0) SQC_ATTR_CASE(1) SQC_ATTR_CASE(2) SQC_ATTR_CASE(3) SQC_ATTR_CASE(4) SQC_ATTR_CASE(5)
+          SQC_ATTR_CASE(6) SQC_ATTR_CASE(7) SQC_ATTR_CASE(8) SQC_ATTR_CASE(9) SQC_ATTR_CASE(10) SQC_ATTR_CASE(11)
+          SQC_ATTR_CASE(12) SQC_ATTR_CASE(13) SQC_ATTR_CASE(14) SQC_ATTR_CASE(15)
+#undef SQC_ATTR_CASE
+          default: break;
+        }
+        cur = di;
+      }
+    }
+    __syncthreads();
+    if (changed) {
+      fill_tile_ctx(d, tc);
+      __syncthreads();
+    }
+    attr_tile(d, tc, tile - d.block_begin, val);
+    __syncthreads();
   }
 }
 
@@ -257,7 +310,12 @@ cudaError_t launch_fold(const FoldArgs& a, cudaStream_t s) {
 
 cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s) {
   if (L.n <= 0 || blocks <= 0) return cudaSuccess;
-  attr_fused_kernel<<<unsigned(blocks), 256, smem_bytes, s>>>(L);
+  // persistent grid: as many CTAs as fit on the 152 SMs at once (256
+  // threads each, at most 8 per SM; shared memory 227 KB per SM)
+  const int64_t per_sm_smem = (227 * 1024) / (smem_bytes + 4096);
+  const int64_t per_sm = per_sm_smem < 8 ? (per_sm_smem < 1 ? 1 : per_sm_smem) : 8;
+  const int64_t grid = blocks < 152 * per_sm ? blocks : 152 * per_sm;
+  attr_fused_kernel<<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
   return cudaGetLastError();
 }
 
