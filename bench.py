@@ -11,8 +11,10 @@ workload is the 30-qubit line circuit cut at K=8 into 4 subcircuits with
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA
 events on the launching stream; the inputs fit in L2, so a 256 MiB buffer
-is written between steps (outside the events) to flush it.  One JSON line
-on rank 0.  --impl reference times the FP64 CPU oracle on the same
+is written between steps (outside the events) to flush it.  The per-stage
+times behind the roofline come from a second, separate run of K steps with
+stage events inside the step (they are not in the timed region).  One JSON
+line on rank 0.  --impl reference times the FP64 CPU oracle on the same
 workload instead.
 """
 from __future__ import annotations
@@ -533,25 +535,29 @@ def main():
     info = ctx.query_info(qid)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     use_graph = not args.no_graph
-    if use_graph:
+
+    def capture(profiled):
         # the whole step (attribution, merge, contraction steps, selection)
-        # captured once and replayed; stage events become graph nodes
-        ctx.profile_enable(2)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
+        # captured once and replayed; with profiling the stage events
+        # become graph nodes
+        ctx.profile_enable(2 if profiled else False)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
             step()
         torch.cuda.synchronize(dev)
-        run = graph.replay
         for _ in range(max(3, args.warmup)):
-            run()
+            g.replay()
         torch.cuda.synchronize(dev)
-        ctx.profile_read()
+        if profiled:
+            ctx.profile_read()
+        return g
+
+    # timed region: the step alone, no stage events inside
+    if use_graph:
+        run = capture(False).replay
     else:
-        ctx.profile_enable(True)
+        ctx.profile_enable(False)
         run = step
-    stage_total = {k: 0.0 for k in ("attribute", "merge", "contract", "final", "select")}
-    stage_calls = {k: 0 for k in stage_total}
-    launches = 0
     sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
@@ -564,20 +570,27 @@ def main():
         ev[i][0].record(stream)
         run()
         ev[i][1].record(stream)
-        if use_graph:
-            # stage events of this replay are read before the next one
-            torch.cuda.synchronize(dev)
-            pr = ctx.profile_read()
-            for k in stage_total:
-                stage_total[k] += pr["ms"][k]
-                stage_calls[k] += pr["calls"][k]
-            launches += pr["launches"]
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
+
+    # stage breakdown (roofline, launch count): the same step with stage
+    # events, run separately after the timed region
+    stage_total = {k: 0.0 for k in ("attribute", "merge", "contract", "final", "select")}
+    stage_calls = {k: 0 for k in stage_total}
+    launches = 0
+    prun = capture(True).replay if use_graph else step
     if not use_graph:
+        ctx.profile_enable(True)
+    for i in range(args.steps):
+        flush.zero_()
+        prun()
+        torch.cuda.synchronize(dev)
         pr = ctx.profile_read()
-        stage_total, stage_calls, launches = dict(pr["ms"]), dict(pr["calls"]), pr["launches"]
+        for k in stage_total:
+            stage_total[k] += pr["ms"][k]
+            stage_calls[k] += pr["calls"][k]
+        launches += pr["launches"]
     ctx.profile_enable(False)
     prof = {"ms": stage_total, "calls": stage_calls, "launches": launches}
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -597,7 +610,8 @@ def main():
     hbm, src = peaks()
     achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9
     kernel_of = {"attribute": "attr_fused_kernel", "merge": "merge_kernel", "contract": "gemm_simt_kernel",
-                 "final": "gemm_simt_kernel (last step)", "select": "select_coop_kernel"}
+                 "final": "gemm_simt_kernel (last step)",
+                 "select": "select_resident_kernel" if (1 << na) * out_b <= (24 << 20) else "select_coop_kernel"}
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": src,
                 "stages": {k: {"us": 1e3 * stage_ms[k], "share": share[k],

@@ -815,6 +815,7 @@ SQC_API void sqc_default_config(sqc_config* cfg) {
   cfg->max_active_qubits = 32;
   cfg->fp64_chunk_min_edges = 12;
   cfg->chunk_terms = 256;
+  cfg->select_resident = 1;
 }
 
 SQC_API const char* sqc_last_error(const sqc_ctx* ctx) {
@@ -845,6 +846,8 @@ SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg) 
     return fail(nullptr, SQC_EINVAL, "chunk_terms must be a power of two >= 16");
   if (ctx->cfg.slice_edges < 0 || ctx->cfg.slice_edges > 8)
     return fail(nullptr, SQC_EINVAL, "slice_edges must be in [0, 8]");
+  if (ctx->cfg.select_resident != 0 && ctx->cfg.select_resident != 1)
+    return fail(nullptr, SQC_EINVAL, "select_resident must be 0 or 1");
   DeviceGuard g(device);
   e = select_configure();
   if (e == cudaSuccess) e = attr_configure();
@@ -1186,9 +1189,15 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* prob
   ctx->launches += 1;
   Query& q = *it->second;
   int* err = reinterpret_cast<int*>(static_cast<char*>(q.sel_mem) + q.sel_bytes - 64);
-  CK(launch_select_coop(q.sel_mem, q.sel_grid, probs, dtype == SQC_F64, n, k, threshold,
-                        reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found, err,
-                        static_cast<cudaStream_t>(stream)));
+  const int rgrid = ctx->cfg.select_resident ? select_resident_grid() : 0;
+  if (rgrid > 0 && select_resident_smem(n, dtype == SQC_F64, rgrid, nullptr))
+    CK(launch_select_resident(q.sel_mem, rgrid, probs, dtype == SQC_F64, n, k, threshold,
+                              reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found, err,
+                              static_cast<cudaStream_t>(stream)));
+  else
+    CK(launch_select_coop(q.sel_mem, q.sel_grid, probs, dtype == SQC_F64, n, k, threshold,
+                          reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found, err,
+                          static_cast<cudaStream_t>(stream)));
   return SQC_OK;
 }
 

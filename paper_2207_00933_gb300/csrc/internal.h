@@ -199,6 +199,15 @@ int select_coop_grid();
 cudaError_t launch_select_coop(void* work, int grid, const void* x, int is_f64, uint64_t n, int k, double threshold,
                                unsigned long long* bins_out, double* probs_out, int* n_found, int* err,
                                cudaStream_t s);
+// The same selection with every CTA's slice of the input held in shared
+// memory (one 1024-thread CTA per SM): one read of the input, 12-bit digits.
+// Uses the same workspace as launch_select_coop.  select_resident_smem()
+// returns 0 when n values do not fit; grid = select_resident_grid().
+int select_resident_grid();
+size_t select_resident_smem(uint64_t n, int is_f64, int grid, uint64_t* per);
+cudaError_t launch_select_resident(void* work, int grid, const void* x, int is_f64, uint64_t n, int k,
+                                   double threshold, unsigned long long* bins_out, double* probs_out, int* n_found,
+                                   int* err, cudaStream_t s);
 // one-time per-device kernel attributes (large shared memory for the sort)
 cudaError_t select_configure();
 constexpr int kSelectMaxK = 4096;

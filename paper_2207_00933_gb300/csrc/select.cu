@@ -826,12 +826,417 @@ fail:
   if (threadIdx.x == 0 && err) atomicExch(err, 1);
 }
 
+
+// ---- shared-memory-resident cooperative selection --------------------------------
+// For inputs that fit in the shared memory of one CTA per SM (the usual
+// recursion level: 2^20 FP32 bins are 27 KB per SM).  Every CTA loads its
+// contiguous slice ONCE, as keys, into shared memory and builds the first
+// 12-bit histogram on the way; the refinement passes, the compaction and
+// the tie scan then read shared memory only.  Grid barriers are a
+// monotonic arrival counter (one release-add per CTA, acquire polling, no
+// last-arriver step).  The ranking needs no barrier: every warp owns whole
+// candidates and counts the candidates ahead of each over shared-memory
+// tiles, then writes it at its rank.  Control flow is uniform across CTAs
+// (every CTA derives the same decisions from the same global histograms),
+// so every CTA meets every barrier.
+constexpr int kRThreads = 1024;
+constexpr int kRWarps = kRThreads / 32;
+constexpr int kRBits = 12;
+constexpr int kRRadix = 1 << kRBits;
+constexpr int kRMaxPasses = 6;                      // 64-bit keys: 5 x 12 + 4 bits
+constexpr int kRTile = 2048;                        // candidates per ranking tile
+constexpr int kRHistBytes = kRRadix * 4;
+constexpr int kRRegionMin = kRTile * 16;            // the ranking tile reuses the key region
+constexpr int kRSmemMax = 200 * 1024;               // dynamic shared memory per CTA at most
+constexpr size_t kRCtlOffset = 128;                 // byte offset of this kernel's control words
+constexpr uint32_t kRBarrierLimit = 1u << 21;       // polls (~1-2 s) before a barrier gives up
+
+struct ResWork {
+  unsigned* ctl;                  // [0] candidates, [1] barrier arrivals, [2] exits, [3] abort
+  unsigned* hist;                 // [kRMaxPasses][kRRadix]
+  unsigned long long* cand_key;   // [kMaxSort]
+  unsigned long long* cand_idx;   // [kMaxSort]
+  unsigned* tie_count;            // [grid]
+};
+
+template <bool F64> struct ResKey;
+template <> struct ResKey<false> {
+  using T = unsigned;
+  static constexpr int kBits = 32;
+};
+template <> struct ResKey<true> {
+  using T = unsigned long long;
+  static constexpr int kBits = 64;
+};
+
+__device__ __forceinline__ bool res_barrier(unsigned* ctl, unsigned target) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctl + 1) : "memory");
+    uint32_t i = 0;
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctl + 1) : "memory");
+      if (v >= target) break;
+      if (++i > kRBarrierLimit || static_cast<volatile unsigned*>(ctl)[3]) {
+        atomicExch(ctl + 3, 1u);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Decision after a pass: over the pass's global histogram, the digit holding the krem-th largest in-scope key is found
+// with a block-wide suffix scan (4 bins per thread).  Writes the shared
+// decision words; identical in every CTA.
+struct ResState {
+  unsigned long long prefix;  // determined key bits (as a 64-bit value)
+  unsigned long long krem;    // how many to take from the current bucket
+  unsigned long long take;    // min(k, values >= threshold)
+  int lo;                     // bits below lo are undetermined
+  int done;                   // 0 refine, 1 bucket fits, 2 take every value, 3 exact ties > cap
+};
+
+__device__ __forceinline__ void res_decide(const unsigned* ghist, int pass, int lo, bool last_pass,
+                                           int k, int cap, ResState* st, unsigned long long* wtot) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  unsigned v[4];
+  unsigned long long s = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[q] = __ldcg(ghist + 4 * t + q);
+    s += v[q];
+  }
+  // suffix sums over threads: inclusive within the warp from the top lane
+  unsigned long long inc = s;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, inc, off);
+    if (lane + off < 32) inc += o;
+  }
+  if (lane == 0) wtot[warp] = inc;                  // warp total
+  __syncthreads();
+  unsigned long long above_w = 0, total = 0;
+  for (int w = 0; w < kRWarps; ++w) {
+    const unsigned long long x = wtot[w];
+    total += x;
+    if (w > warp) above_w += x;
+  }
+  const unsigned long long above = above_w + inc - s;   // keys in bins above this thread's four
+  const unsigned long long krem = pass == 0 ? (unsigned long long)k : st->krem;
+  __syncthreads();
+  if (pass == 0 && t == 0) {
+    st->take = total < (unsigned long long)k ? total : (unsigned long long)k;
+    if (total <= (unsigned long long)k) st->done = 2;
+  }
+  if (!(pass == 0 && total <= (unsigned long long)k) && above < krem && above + s >= krem) {
+    unsigned long long cum = above;
+    int d = 4 * t + 3;
+    for (; d > 4 * t; --d) {
+      if (cum + v[d - 4 * t] >= krem) break;
+      cum += v[d - 4 * t];
+    }
+    st->prefix |= (unsigned long long)d << lo;
+    st->krem = krem - cum;
+    st->lo = lo;
+    if (v[d - 4 * t] <= unsigned(cap)) st->done = 1;
+    else if (last_pass) st->done = 3;
+  }
+  __syncthreads();
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(kRThreads, 1)
+select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, unsigned long long key_thr64, int k,
+                       int cap, ResWork w, unsigned long long* bins_out, double* probs_out, int* n_found, int* err) {
+  using KeyT = typename ResKey<F64>::T;
+  constexpr int KB = ResKey<F64>::kBits;
+  constexpr int V = F64 ? 2 : 4;                    // values per 16-byte vector
+  extern __shared__ __align__(16) unsigned char rsm[];
+  unsigned* sh = reinterpret_cast<unsigned*>(rsm);                 // [kRRadix]
+  KeyT* keys = reinterpret_cast<KeyT*>(rsm + kRHistBytes);         // [per], later the ranking tile
+  __shared__ ResState st;
+  __shared__ unsigned long long wtot[kRWarps];
+  __shared__ unsigned wcnt[kRWarps];
+  const unsigned nb = gridDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const KeyT key_thr = F64 ? KeyT(key_thr64) : KeyT(key_thr64 >> 32);
+  const uint64_t start = uint64_t(blockIdx.x) * per;
+  const int cnt = int(start < n ? ((n - start) < per ? (n - start) : per) : 0);
+  unsigned bar = 0;                                 // barriers met so far
+  bool ok = true;
+  if (tid == 0) {
+    st.prefix = 0ull;
+    st.krem = (unsigned long long)k;
+    st.take = 0ull;
+    st.lo = KB;
+    st.done = 0;
+  }
+  for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
+  __syncthreads();
+  // pass 0 with the load: keys of excluded values (NaN or below the
+  // threshold) are stored as 0, which no included value has
+  {
+    const int lo0 = KB - kRBits;
+    // the loop bound is the same for the whole CTA: warp_hist_add needs
+    // every lane of the warp
+    for (int b0 = 0; b0 < cnt; b0 += kRThreads * V) {
+      const int i0 = b0 + tid * V;
+      KeyT kv[V];
+      if constexpr (F64) {
+        const double* p = static_cast<const double*>(x) + start + i0;
+        double a[2];
+        if (aligned && i0 + 2 <= cnt) {
+          const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+          a[0] = q.x; a[1] = q.y;
+        } else {
+          a[0] = i0 < cnt ? p[0] : __longlong_as_double(0x7ff8000000000000ll);
+          a[1] = i0 + 1 < cnt ? p[1] : __longlong_as_double(0x7ff8000000000000ll);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const unsigned long long u = __double_as_longlong(a[q]);
+          const bool nan = (u & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
+          const unsigned long long kk = key_f64(a[q]);
+          kv[q] = (!nan && kk >= key_thr) ? kk : 0ull;
+        }
+      } else {
+        const float* p = static_cast<const float*>(x) + start + i0;
+        float a[4];
+        if (aligned && i0 + 4 <= cnt) {
+          const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+          a[0] = q.x; a[1] = q.y; a[2] = q.z; a[3] = q.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) a[q] = i0 + q < cnt ? p[q] : __uint_as_float(0x7fc00000u);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const unsigned u = __float_as_uint(a[q]);
+          const bool nan = (u & 0x7fffffffu) > 0x7f800000u;
+          const unsigned kk = unsigned(key_f32(a[q]) >> 32);
+          kv[q] = (!nan && kk >= key_thr) ? kk : 0u;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        if (i0 + q < cnt) keys[i0 + q] = kv[q];
+        warp_hist_add(sh, kv[q] != 0, unsigned(kv[q] >> lo0), lane);
+      }
+    }
+  }
+  // the refinement loop: flush, barrier, decide; then the next digit from
+  // shared memory
+  for (int pass = 0; pass < (KB + kRBits - 1) / kRBits; ++pass) {
+    const int hi = KB - kRBits * pass;
+    const int lo = hi - kRBits > 0 ? hi - kRBits : 0;
+    if (pass > 0) {
+      const KeyT pfx = KeyT(st.prefix);
+      const unsigned dmask = (1u << (hi - lo)) - 1u;
+      for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
+      __syncthreads();
+      for (int i0 = 0; i0 < cnt; i0 += kRThreads) {
+        const int i = i0 + tid;
+        const KeyT kk = i < cnt ? keys[i] : KeyT(0);
+        const bool in = kk != 0 && (kk >> hi) == (pfx >> hi);
+        warp_hist_add(sh, in, unsigned(kk >> lo) & dmask, lane);
+      }
+    }
+    __syncthreads();
+    unsigned* gh = w.hist + size_t(pass) * kRRadix;
+    for (int d = tid; d < kRRadix; d += kRThreads) {
+      const unsigned v = sh[d];
+      if (v) atomicAdd(gh + d, v);
+    }
+    if (!(ok = res_barrier(w.ctl, nb * ++bar))) break;
+    res_decide(gh, pass, lo, lo == 0, k, cap, &st, wtot);
+    if (st.done) break;
+  }
+  if (ok) {
+    // every CTA has read every histogram it will read: clear them for the
+    // next call (after the next barrier nobody reads them)
+    const int done = st.done, lo = st.lo;
+    const KeyT pv = KeyT(done == 2 ? 0ull : (st.prefix >> lo));
+    // compaction: values above the bucket, and the bucket itself unless it
+    // is an oversized group of exact ties
+    for (int i0 = 0; i0 < cnt; i0 += kRThreads) {
+      const int i = i0 + tid;
+      const KeyT kk = i < cnt ? keys[i] : KeyT(0);
+      bool take = false;
+      if (kk != 0) {
+        if (done == 2) take = true;
+        else {
+          const KeyT hb = lo >= KB ? KeyT(0) : KeyT(kk >> lo);
+          take = done == 3 ? hb > pv : hb >= pv;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, take);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned slot = 0;
+        if (lane == leader) slot = atomicAdd(w.ctl, unsigned(__popc(m)));
+        slot = __shfl_sync(0xffffffffu, slot, leader);
+        if (take) {
+          const unsigned r = slot + __popc(m & ((1u << lane) - 1u));
+          w.cand_key[r] = (unsigned long long)kk;
+          w.cand_idx[r] = start + i;
+        }
+      }
+    }
+    if (done == 3) {
+      // exact ties of the k-th key beyond capacity: ascending bin order,
+      // via per-CTA counts and an ordered scan of each slice
+      const KeyT tkey = KeyT(st.prefix);
+      unsigned my = 0;
+      for (int i = tid; i < cnt; i += kRThreads) my += keys[i] == tkey;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(0xffffffffu, my, off);
+      if (lane == 0) wcnt[warp] = my;
+      __syncthreads();
+      if (tid == 0) {
+        unsigned c = 0;
+        for (int ww = 0; ww < kRWarps; ++ww) c += wcnt[ww];
+        w.tie_count[blockIdx.x] = c;
+      }
+      ok = res_barrier(w.ctl, nb * ++bar);
+      if (ok) {
+        __shared__ unsigned long long tbase;
+        if (tid == 0) {
+          unsigned long long b = 0;
+          for (unsigned r = 0; r < blockIdx.x; ++r) b += __ldcg(w.tie_count + r);
+          tbase = b;
+        }
+        __syncthreads();
+        const unsigned long long need = st.krem, first = st.take - st.krem;
+        unsigned long long run = tbase;
+        for (int i0 = 0; i0 < cnt && run < need; i0 += kRThreads) {
+          const int i = i0 + tid;
+          const bool tie = i < cnt && keys[i] == tkey;
+          const unsigned bal = __ballot_sync(0xffffffffu, tie);
+          if (lane == 0) wcnt[warp] = __popc(bal);
+          __syncthreads();
+          unsigned before = 0, all = 0;
+          for (int ww = 0; ww < kRWarps; ++ww) {
+            if (ww < warp) before += wcnt[ww];
+            all += wcnt[ww];
+          }
+          const unsigned long long rank = run + before + __popc(bal & ((1u << lane) - 1u));
+          if (tie && rank < need) {
+            w.cand_key[first + rank] = (unsigned long long)tkey;
+            w.cand_idx[first + rank] = start + i;
+          }
+          run += all;
+          __syncthreads();
+        }
+      }
+    }
+    if (ok) ok = res_barrier(w.ctl, nb * ++bar);
+  }
+  if (ok) {
+    // the histograms are no longer read by anyone
+    for (uint64_t i = uint64_t(blockIdx.x) * kRThreads + tid; i < uint64_t(kRMaxPasses) * kRRadix;
+         i += uint64_t(nb) * kRThreads)
+      w.hist[i] = 0u;
+    // ranking: warp v of CTA r owns candidates r*32 + v + j*nb*32
+    const unsigned long long take = st.take;
+    unsigned long long nc = __ldcg(w.ctl);
+    if (st.done == 3) nc += st.krem;
+    if (nc > (unsigned long long)kMaxSort) nc = kMaxSort;
+    unsigned long long* tk = reinterpret_cast<unsigned long long*>(rsm + kRHistBytes);
+    unsigned long long* ti = tk + kRTile;
+    const unsigned long long stride = uint64_t(nb) * kRWarps;
+    // the loop bounds depend on the CTA only, so every thread meets the
+    // tile barriers
+    for (unsigned long long cb = uint64_t(blockIdx.x) * kRWarps; cb < nc; cb += 2 * stride) {
+      const unsigned long long c0 = cb + warp, c1 = c0 + stride;
+      const bool h0 = c0 < nc, h1 = c1 < nc;
+      const unsigned long long mk0 = h0 ? __ldcg(w.cand_key + c0) : 0ull, mi0 = h0 ? __ldcg(w.cand_idx + c0) : 0ull;
+      const unsigned long long mk1 = h1 ? __ldcg(w.cand_key + c1) : 0ull, mi1 = h1 ? __ldcg(w.cand_idx + c1) : 0ull;
+      unsigned r0 = 0, r1 = 0;
+      for (unsigned long long t0 = 0; t0 < nc; t0 += kRTile) {
+        const int len = int(nc - t0 < kRTile ? nc - t0 : kRTile);
+        __syncthreads();
+        for (int e = tid; e < len; e += kRThreads) {
+          tk[e] = __ldcg(w.cand_key + t0 + e);
+          ti[e] = __ldcg(w.cand_idx + t0 + e);
+        }
+        __syncthreads();
+        if (h0)
+          for (int e = lane; e < len; e += 32) {
+            const unsigned long long a = tk[e], b = ti[e];
+            r0 += (a > mk0) || (a == mk0 && b < mi0);
+            r1 += h1 && ((a > mk1) || (a == mk1 && b < mi1));
+          }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        r0 += __shfl_down_sync(0xffffffffu, r0, off);
+        r1 += __shfl_down_sync(0xffffffffu, r1, off);
+      }
+      if (lane == 0) {
+        if (h0 && r0 < take) {
+          bins_out[r0] = mi0;
+          probs_out[r0] = F64 ? static_cast<const double*>(x)[mi0] : double(static_cast<const float*>(x)[mi0]);
+        }
+        if (h1 && r1 < take) {
+          bins_out[r1] = mi1;
+          probs_out[r1] = F64 ? static_cast<const double*>(x)[mi1] : double(static_cast<const float*>(x)[mi1]);
+        }
+      }
+    }
+    if (blockIdx.x == 0 && tid == 0) *n_found = int(take);
+  } else if (tid == 0 && err) {
+    atomicExch(err, 1);
+  }
+  // the last CTA out re-arms the control words (every CTA has read the
+  // candidate count and passed its last barrier by now); after an abort it
+  // also clears the histograms, which some CTAs may have left dirty
+  __shared__ int last;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(w.ctl + 2, 1u) == nb - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    if (__ldcg(w.ctl + 3))
+      for (int i = tid; i < kRMaxPasses * kRRadix; i += kRThreads) w.hist[i] = 0u;
+    __syncthreads();
+    if (tid == 0) {
+      w.ctl[0] = 0u;
+      w.ctl[1] = 0u;
+      w.ctl[3] = 0u;
+      __threadfence();
+      w.ctl[2] = 0u;
+    }
+  }
+}
+
 }  // namespace
 
-size_t select_coop_bytes(int grid) {
+namespace {
+// bytes of the streaming kernel's part of the workspace
+size_t coop_part_bytes(int grid) {
   return sizeof(unsigned) * kCPasses * kCopies * kCRadix + sizeof(unsigned long long) * 32 +
          2 * sizeof(unsigned long long) * kMaxSort + sizeof(unsigned) * kMaxSort + sizeof(unsigned) * size_t(grid) +
          256;
+}
+}  // namespace
+
+// One workspace serves both cooperative kernels: the resident kernel's
+// control words sit in unused words of the streaming kernel's control
+// block, its histograms after the streaming kernel's part, and both kernels
+// leave everything they need zeroed as they found it.
+size_t select_coop_bytes(int grid) {
+  return coop_part_bytes(grid) + sizeof(unsigned) * kRMaxPasses * kRRadix + 256;
 }
 
 int select_coop_grid() {
@@ -849,6 +1254,63 @@ int select_coop_grid() {
     g = sms * (per >= 2 ? 2 : (per > 0 ? per : 1));
   }
   return g;
+}
+
+// The resident kernel runs one 1024-thread CTA per SM (0 if it cannot be
+// made co-resident with its largest shared-memory size).
+int select_resident_grid() {
+  static int g = -1;
+  if (g < 0) {
+    int dev = 0, sms = 152, p32 = 0, p64 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(select_resident_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmemMax);
+    cudaFuncSetAttribute(select_resident_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmemMax);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, select_resident_kernel<false>, kRThreads, kRSmemMax);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, select_resident_kernel<true>, kRThreads, kRSmemMax);
+    g = (p32 >= 1 && p64 >= 1) ? sms : 0;
+    if (g > select_coop_grid()) g = select_coop_grid();   // tie counts live in the streaming part
+  }
+  return g;
+}
+
+// Shared memory the resident kernel needs for n values on `grid` CTAs (0:
+// does not fit); *per = values per CTA (a multiple of 4, so every slice
+// starts 16-byte aligned).
+size_t select_resident_smem(uint64_t n, int is_f64, int grid, uint64_t* per) {
+  if (grid <= 0) return 0;
+  uint64_t p = (n + uint64_t(grid) - 1) / uint64_t(grid);
+  p = (p + 3) & ~uint64_t(3);
+  const uint64_t region = p * (is_f64 ? 8 : 4);
+  const uint64_t need = uint64_t(kRHistBytes) + (region > uint64_t(kRRegionMin) ? region : uint64_t(kRRegionMin));
+  if (per) *per = p;
+  return need <= uint64_t(kRSmemMax) ? size_t(need) : 0;
+}
+
+cudaError_t launch_select_resident(void* work, int grid, const void* x, int is_f64, uint64_t n, int k,
+                                   double threshold, unsigned long long* bins_out, double* probs_out, int* n_found,
+                                   int* err, cudaStream_t s) {
+  if (k < 1 || k > kSelectMaxK) return cudaErrorInvalidValue;
+  uint64_t per = 0;
+  const size_t smem = select_resident_smem(n, is_f64, grid, &per);
+  if (!smem) return cudaErrorInvalidValue;
+  const int cap = (k > 512 ? k : 512) < kMaxSort - k ? (k > 512 ? k : 512) : kMaxSort - k;
+  char* p = static_cast<char*>(work);
+  ResWork w;
+  w.ctl = reinterpret_cast<unsigned*>(p + kRCtlOffset);
+  w.cand_key = reinterpret_cast<unsigned long long*>(p + sizeof(unsigned long long) * 32);
+  w.cand_idx = w.cand_key + kMaxSort;
+  // the streaming kernel's tie counts (layout of launch_select_coop)
+  w.tie_count = reinterpret_cast<unsigned*>(p + sizeof(unsigned long long) * 32 + 2 * sizeof(unsigned long long) * kMaxSort +
+                                            sizeof(unsigned) * kCPasses * kCopies * kCRadix + sizeof(unsigned) * kMaxSort);
+  w.hist = reinterpret_cast<unsigned*>(p + ((coop_part_bytes(select_coop_grid()) + 255) & ~size_t(255)));
+  int aligned = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+  unsigned long long kt = threshold_key(is_f64, threshold);
+  void* args[] = {const_cast<void**>(&x), &aligned, &n, &per, &kt, &k, const_cast<int*>(&cap), &w, &bins_out,
+                  &probs_out, &n_found, &err};
+  const void* fn = is_f64 ? reinterpret_cast<const void*>(select_resident_kernel<true>)
+                          : reinterpret_cast<const void*>(select_resident_kernel<false>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kRThreads), args, smem, s);
 }
 
 cudaError_t launch_select_coop(void* work, int grid, const void* x, int is_f64, uint64_t n, int k, double threshold,
