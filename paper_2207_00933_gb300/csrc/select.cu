@@ -844,7 +844,8 @@ constexpr int kRWarps = kRThreads / 32;
 constexpr int kRBits = 12;
 constexpr int kRRadix = 1 << kRBits;
 constexpr int kRMaxPasses = 6;                      // 64-bit keys: 5 x 12 + 4 bits
-constexpr int kRTile = 2048;                        // candidates per ranking tile
+constexpr int kRRankMax = 128;                      // candidates one CTA ranks at most (kMaxSort / grid + 1)
+constexpr int kRTile = 1024;                        // candidates per ranking tile
 constexpr int kRHistBytes = kRRadix * 4;
 constexpr int kRRegionMin = kRTile * 16;            // the ranking tile reuses the key region
 constexpr int kRSmemMax = 200 * 1024;               // dynamic shared memory per CTA at most
@@ -852,7 +853,9 @@ constexpr size_t kRCtlOffset = 128;                 // byte offset of this kerne
 constexpr uint32_t kRBarrierLimit = 1u << 21;       // polls (~1-2 s) before a barrier gives up
 
 struct ResWork {
-  unsigned* ctl;                  // [0] candidates, [1] barrier arrivals, [2] exits, [3] abort
+  // [0] barrier word: arrivals (high 32 bits) and candidates (low 32 bits,
+  // added at the compaction barrier); [1] exits; [2] abort; [3] slots
+  unsigned long long* ctl;
   unsigned* hist;                 // [kRMaxPasses][kRRadix]
   unsigned long long* cand_key;   // [kMaxSort]
   unsigned long long* cand_idx;   // [kMaxSort]
@@ -869,33 +872,39 @@ template <> struct ResKey<true> {
   static constexpr int kBits = 64;
 };
 
-__device__ __forceinline__ bool res_barrier(unsigned* ctl, unsigned target) {
-  __shared__ int ok;
+// Arrive with `add` (1 << 32 plus any count for the low word) and wait
+// until `arrivals` CTAs have arrived; returns the barrier word seen (0 after
+// an abort).  The release-add publishes the CTA's writes (ordered before it
+// by the CTA barrier), the acquire poll makes the others' visible.
+__device__ __forceinline__ unsigned long long res_barrier(unsigned long long* ctl, unsigned long long add,
+                                                          unsigned arrivals) {
+  __shared__ unsigned long long seen;
   __syncthreads();
   if (threadIdx.x == 0) {
-    ok = 1;
-    __threadfence();
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctl + 1) : "memory");
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(ctl), "l"(add) : "memory");
     uint32_t i = 0;
     for (;;) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctl + 1) : "memory");
-      if (v >= target) break;
-      if (++i > kRBarrierLimit || static_cast<volatile unsigned*>(ctl)[3]) {
-        atomicExch(ctl + 3, 1u);
-        ok = 0;
+      unsigned long long v;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctl) : "memory");
+      if ((v >> 32) >= arrivals) {
+        seen = v;
+        break;
+      }
+      if (++i > kRBarrierLimit || static_cast<volatile unsigned long long*>(ctl)[2]) {
+        atomicExch(ctl + 2, 1ull);
+        seen = 0ull;
         break;
       }
     }
-    __threadfence();
   }
   __syncthreads();
-  return ok != 0;
+  return seen;
 }
 
-// Decision after a pass: over the pass's global histogram, the digit holding the krem-th largest in-scope key is found
-// with a block-wide suffix scan (4 bins per thread).  Writes the shared
-// decision words; identical in every CTA.
+// Decision after a pass: over the pass's global histogram, the digit
+// holding the krem-th largest in-scope key is found with a block-wide
+// suffix scan (4 bins per thread, one 16-byte load each).  Writes the
+// shared decision words; identical in every CTA.
 struct ResState {
   unsigned long long prefix;  // determined key bits (as a 64-bit value)
   unsigned long long krem;    // how many to take from the current bucket
@@ -907,49 +916,65 @@ struct ResState {
 __device__ __forceinline__ void res_decide(const unsigned* ghist, int pass, int lo, bool last_pass,
                                            int k, int cap, ResState* st, unsigned long long* wtot) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  unsigned v[4];
-  unsigned long long s = 0;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    v[q] = __ldcg(ghist + 4 * t + q);
-    s += v[q];
-  }
-  // suffix sums over threads: inclusive within the warp from the top lane
+  const uint4 q4 = __ldcg(reinterpret_cast<const uint4*>(ghist) + t);
+  const unsigned v[4] = {q4.x, q4.y, q4.z, q4.w};
+  const unsigned long long s = (unsigned long long)v[0] + v[1] + v[2] + v[3];
+  // suffix sums over threads: inclusive within the warp from the top lane,
+  // then over the warp totals by warp 0
   unsigned long long inc = s;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
     const unsigned long long o = __shfl_down_sync(0xffffffffu, inc, off);
     if (lane + off < 32) inc += o;
   }
-  if (lane == 0) wtot[warp] = inc;                  // warp total
-  __syncthreads();
-  unsigned long long above_w = 0, total = 0;
-  for (int w = 0; w < kRWarps; ++w) {
-    const unsigned long long x = wtot[w];
-    total += x;
-    if (w > warp) above_w += x;
-  }
-  const unsigned long long above = above_w + inc - s;   // keys in bins above this thread's four
+  if (lane == 0) wtot[warp] = inc;
   const unsigned long long krem = pass == 0 ? (unsigned long long)k : st->krem;
   __syncthreads();
+  if (warp == 0) {
+    const unsigned long long mine = wtot[lane];
+    unsigned long long suf = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned long long o = __shfl_down_sync(0xffffffffu, suf, off);
+      if (lane + off < 32) suf += o;
+    }
+    wtot[32 + lane] = suf - mine;                   // keys in the warps above
+    if (lane == 0) wtot[64] = suf;                  // all keys in scope
+  }
+  __syncthreads();
+  const unsigned long long total = wtot[64];
+  const unsigned long long above = wtot[32 + warp] + inc - s;   // keys in bins above this thread's four
   if (pass == 0 && t == 0) {
     st->take = total < (unsigned long long)k ? total : (unsigned long long)k;
     if (total <= (unsigned long long)k) st->done = 2;
   }
   if (!(pass == 0 && total <= (unsigned long long)k) && above < krem && above + s >= krem) {
     unsigned long long cum = above;
-    int d = 4 * t + 3;
-    for (; d > 4 * t; --d) {
-      if (cum + v[d - 4 * t] >= krem) break;
-      cum += v[d - 4 * t];
+    int j = 3;
+    for (; j > 0; --j) {
+      if (cum + v[j] >= krem) break;
+      cum += v[j];
     }
-    st->prefix |= (unsigned long long)d << lo;
+    st->prefix |= (unsigned long long)(4 * t + j) << lo;
     st->krem = krem - cum;
     st->lo = lo;
-    if (v[d - 4 * t] <= unsigned(cap)) st->done = 1;
+    if (v[j] <= unsigned(cap)) st->done = 1;
     else if (last_pass) st->done = 3;
   }
   __syncthreads();
+}
+
+// The value a key was made from (the key transform is a bijection).
+template <bool F64>
+__device__ __forceinline__ double value_of_key(unsigned long long key) {
+  if constexpr (F64) {
+    const unsigned long long u = (key >> 63) ? (key & 0x7fffffffffffffffull) : ~key;
+    return __longlong_as_double((long long)u);
+  } else {
+    const unsigned k32 = unsigned(key);
+    const unsigned u = (k32 >> 31) ? (k32 & 0x7fffffffu) : ~k32;
+    return double(__uint_as_float(u));
+  }
 }
 
 template <bool F64>
@@ -963,7 +988,7 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
   unsigned* sh = reinterpret_cast<unsigned*>(rsm);                 // [kRRadix]
   KeyT* keys = reinterpret_cast<KeyT*>(rsm + kRHistBytes);         // [per], later the ranking tile
   __shared__ ResState st;
-  __shared__ unsigned long long wtot[kRWarps];
+  __shared__ unsigned long long wtot[2 * kRWarps + 1];
   __shared__ unsigned wcnt[kRWarps];
   const unsigned nb = gridDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1055,41 +1080,64 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
       const unsigned v = sh[d];
       if (v) atomicAdd(gh + d, v);
     }
-    if (!(ok = res_barrier(w.ctl, nb * ++bar))) break;
+    if (!(ok = res_barrier(w.ctl, 1ull << 32, nb * ++bar) != 0ull)) break;
     res_decide(gh, pass, lo, lo == 0, k, cap, &st, wtot);
     if (st.done) break;
   }
+  unsigned long long nc = 0;
   if (ok) {
-    // every CTA has read every histogram it will read: clear them for the
-    // next call (after the next barrier nobody reads them)
     const int done = st.done, lo = st.lo;
     const KeyT pv = KeyT(done == 2 ? 0ull : (st.prefix >> lo));
     // compaction: values above the bucket, and the bucket itself unless it
-    // is an oversized group of exact ties
-    for (int i0 = 0; i0 < cnt; i0 += kRThreads) {
-      const int i = i0 + tid;
-      const KeyT kk = i < cnt ? keys[i] : KeyT(0);
-      bool take = false;
-      if (kk != 0) {
-        if (done == 2) take = true;
-        else {
-          const KeyT hb = lo >= KB ? KeyT(0) : KeyT(kk >> lo);
-          take = done == 3 ? hb > pv : hb >= pv;
-        }
+    // is an oversized group of exact ties.  Counted first (one slot
+    // reservation per CTA), then written, each thread its own elements in
+    // order.
+    auto takes = [&](KeyT kk) -> bool {
+      if (kk == 0) return false;
+      if (done == 2) return true;
+      const KeyT hb = lo >= KB ? KeyT(0) : KeyT(kk >> lo);
+      return done == 3 ? hb > pv : hb >= pv;
+    };
+    unsigned mine = 0;
+    for (int i = tid; i < cnt; i += kRThreads) mine += takes(keys[i]);
+    // exclusive prefix of `mine` over the CTA
+    unsigned incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    if (lane == 31) wcnt[warp] = incl;
+    __syncthreads();
+    __shared__ unsigned cta_taken;
+    __shared__ unsigned long long cta_base;
+    if (warp == 0) {
+      const unsigned wv = wcnt[lane];
+      unsigned wi = wv;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, wi, off);
+        if (lane >= off) wi += o;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, take);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        unsigned slot = 0;
-        if (lane == leader) slot = atomicAdd(w.ctl, unsigned(__popc(m)));
-        slot = __shfl_sync(0xffffffffu, slot, leader);
-        if (take) {
-          const unsigned r = slot + __popc(m & ((1u << lane) - 1u));
+      wcnt[lane] = wi - wv;                          // warps before this one
+      if (lane == 31) {
+        cta_taken = wi;
+        cta_base = wi ? atomicAdd(w.ctl + 3, (unsigned long long)wi) : 0ull;
+      }
+    }
+    __syncthreads();
+    {
+      unsigned long long r = cta_base + wcnt[warp] + (incl - mine);
+      for (int i = tid; i < cnt; i += kRThreads) {
+        const KeyT kk = keys[i];
+        if (takes(kk)) {
           w.cand_key[r] = (unsigned long long)kk;
           w.cand_idx[r] = start + i;
+          ++r;
         }
       }
     }
+    __syncthreads();
     if (done == 3) {
       // exact ties of the k-th key beyond capacity: ascending bin order,
       // via per-CTA counts and an ordered scan of each slice
@@ -1105,7 +1153,7 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
         for (int ww = 0; ww < kRWarps; ++ww) c += wcnt[ww];
         w.tie_count[blockIdx.x] = c;
       }
-      ok = res_barrier(w.ctl, nb * ++bar);
+      ok = res_barrier(w.ctl, 1ull << 32, nb * ++bar) != 0ull;
       if (ok) {
         __shared__ unsigned long long tbase;
         if (tid == 0) {
@@ -1137,57 +1185,77 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
         }
       }
     }
-    if (ok) ok = res_barrier(w.ctl, nb * ++bar);
+    // the last barrier also sums the candidate counts into the low word
+    if (ok) {
+      const unsigned long long word = res_barrier(w.ctl, (1ull << 32) | cta_taken, nb * ++bar);
+      ok = word != 0ull;
+      nc = word & 0xffffffffull;
+    }
   }
   if (ok) {
     // the histograms are no longer read by anyone
     for (uint64_t i = uint64_t(blockIdx.x) * kRThreads + tid; i < uint64_t(kRMaxPasses) * kRRadix;
          i += uint64_t(nb) * kRThreads)
       w.hist[i] = 0u;
-    // ranking: warp v of CTA r owns candidates r*32 + v + j*nb*32
+    // ranking: CTA r owns a contiguous block of candidates; warp v of it
+    // counts, for owned candidates v, v + 32, ..., the candidates ahead in
+    // the final order over shared-memory tiles of the whole list.  For FP32
+    // keys that order (key descending, bin ascending) is one 64-bit compare
+    // of key << 32 | (2^32 - 1 - bin).
     const unsigned long long take = st.take;
-    unsigned long long nc = __ldcg(w.ctl);
     if (st.done == 3) nc += st.krem;
     if (nc > (unsigned long long)kMaxSort) nc = kMaxSort;
-    unsigned long long* tk = reinterpret_cast<unsigned long long*>(rsm + kRHistBytes);
-    unsigned long long* ti = tk + kRTile;
-    const unsigned long long stride = uint64_t(nb) * kRWarps;
-    // the loop bounds depend on the CTA only, so every thread meets the
-    // tile barriers
-    for (unsigned long long cb = uint64_t(blockIdx.x) * kRWarps; cb < nc; cb += 2 * stride) {
-      const unsigned long long c0 = cb + warp, c1 = c0 + stride;
-      const bool h0 = c0 < nc, h1 = c1 < nc;
-      const unsigned long long mk0 = h0 ? __ldcg(w.cand_key + c0) : 0ull, mi0 = h0 ? __ldcg(w.cand_idx + c0) : 0ull;
-      const unsigned long long mk1 = h1 ? __ldcg(w.cand_key + c1) : 0ull, mi1 = h1 ? __ldcg(w.cand_idx + c1) : 0ull;
-      unsigned r0 = 0, r1 = 0;
+    const unsigned long long per_cta = (nc + nb - 1) / nb;
+    const unsigned long long cb0 = uint64_t(blockIdx.x) * per_cta;
+    const unsigned long long cb1 = cb0 + per_cta < nc ? cb0 + per_cta : nc;
+    if (cb0 < nc) {
+      const int m = int(cb1 - cb0);                   // <= kMaxSort / nb + 1 <= kRRankMax
+      unsigned long long* tk = reinterpret_cast<unsigned long long*>(rsm + kRHistBytes);   // [kRTile]
+      unsigned long long* ti = tk + kRTile;                                                // [kRTile] (FP64)
+      auto packed = [](unsigned long long kk, unsigned long long ii) {
+        return F64 ? kk : ((kk << 32) | (0xffffffffull - ii));
+      };
+      unsigned long long mk[kRRankMax / kRWarps], mi[kRRankMax / kRWarps];
+      unsigned cnt_ahead[kRRankMax / kRWarps];
+#pragma unroll
+      for (int j = 0; j < kRRankMax / kRWarps; ++j) {
+        const int c = warp + j * kRWarps;
+        const bool have = c < m;
+        const unsigned long long kk = have ? __ldcg(w.cand_key + cb0 + c) : 0ull;
+        mi[j] = have ? __ldcg(w.cand_idx + cb0 + c) : 0ull;
+        mk[j] = packed(kk, mi[j]);
+        cnt_ahead[j] = 0u;
+      }
       for (unsigned long long t0 = 0; t0 < nc; t0 += kRTile) {
         const int len = int(nc - t0 < kRTile ? nc - t0 : kRTile);
         __syncthreads();
         for (int e = tid; e < len; e += kRThreads) {
-          tk[e] = __ldcg(w.cand_key + t0 + e);
-          ti[e] = __ldcg(w.cand_idx + t0 + e);
+          const unsigned long long kk = __ldcg(w.cand_key + t0 + e), ii = __ldcg(w.cand_idx + t0 + e);
+          tk[e] = packed(kk, ii);
+          if (F64) ti[e] = ii;
         }
         __syncthreads();
-        if (h0)
+#pragma unroll
+        for (int j = 0; j < kRRankMax / kRWarps; ++j) {
+          if (warp + j * kRWarps >= m) break;
+          unsigned c = 0;
           for (int e = lane; e < len; e += 32) {
-            const unsigned long long a = tk[e], b = ti[e];
-            r0 += (a > mk0) || (a == mk0 && b < mi0);
-            r1 += h1 && ((a > mk1) || (a == mk1 && b < mi1));
+            if constexpr (F64)
+              c += (tk[e] > mk[j]) || (tk[e] == mk[j] && ti[e] < mi[j]);
+            else
+              c += tk[e] > mk[j];
           }
+          cnt_ahead[j] += c;
+        }
       }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        r0 += __shfl_down_sync(0xffffffffu, r0, off);
-        r1 += __shfl_down_sync(0xffffffffu, r1, off);
-      }
-      if (lane == 0) {
-        if (h0 && r0 < take) {
-          bins_out[r0] = mi0;
-          probs_out[r0] = F64 ? static_cast<const double*>(x)[mi0] : double(static_cast<const float*>(x)[mi0]);
-        }
-        if (h1 && r1 < take) {
-          bins_out[r1] = mi1;
-          probs_out[r1] = F64 ? static_cast<const double*>(x)[mi1] : double(static_cast<const float*>(x)[mi1]);
+      for (int j = 0; j < kRRankMax / kRWarps; ++j) {
+        unsigned c = cnt_ahead[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+        if (lane == 0 && warp + j * kRWarps < m && c < take) {
+          bins_out[c] = mi[j];
+          probs_out[c] = value_of_key<F64>(F64 ? mk[j] : (mk[j] >> 32));
         }
       }
     }
@@ -1200,22 +1268,17 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
   // also clears the histograms, which some CTAs may have left dirty
   __shared__ int last;
   __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    last = atomicAdd(w.ctl + 2, 1u) == nb - 1;
-  }
+  // (no fences: the next launch on the stream starts after this one ends)
+  if (tid == 0) last = atomicAdd(w.ctl + 1, 1ull) == nb - 1;
   __syncthreads();
   if (last) {
-    __threadfence();
-    if (__ldcg(w.ctl + 3))
+    if (__ldcg(w.ctl + 2))
       for (int i = tid; i < kRMaxPasses * kRRadix; i += kRThreads) w.hist[i] = 0u;
-    __syncthreads();
     if (tid == 0) {
-      w.ctl[0] = 0u;
-      w.ctl[1] = 0u;
-      w.ctl[3] = 0u;
-      __threadfence();
-      w.ctl[2] = 0u;
+      w.ctl[0] = 0ull;
+      w.ctl[1] = 0ull;
+      w.ctl[2] = 0ull;
+      w.ctl[3] = 0ull;
     }
   }
 }
@@ -1270,6 +1333,7 @@ int select_resident_grid() {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, select_resident_kernel<true>, kRThreads, kRSmemMax);
     g = (p32 >= 1 && p64 >= 1) ? sms : 0;
     if (g > select_coop_grid()) g = select_coop_grid();   // tie counts live in the streaming part
+    if (g * kRRankMax < kMaxSort) g = 0;                   // each CTA ranks at most kRRankMax candidates
   }
   return g;
 }
@@ -1297,7 +1361,7 @@ cudaError_t launch_select_resident(void* work, int grid, const void* x, int is_f
   const int cap = (k > 512 ? k : 512) < kMaxSort - k ? (k > 512 ? k : 512) : kMaxSort - k;
   char* p = static_cast<char*>(work);
   ResWork w;
-  w.ctl = reinterpret_cast<unsigned*>(p + kRCtlOffset);
+  w.ctl = reinterpret_cast<unsigned long long*>(p + kRCtlOffset);
   w.cand_key = reinterpret_cast<unsigned long long*>(p + sizeof(unsigned long long) * 32);
   w.cand_idx = w.cand_key + kMaxSort;
   // the streaming kernel's tie counts (layout of launch_select_coop)
