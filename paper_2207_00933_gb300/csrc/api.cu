@@ -375,6 +375,7 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
       }
       d.L1 = L1;
       d.L2 = L2;
+      d.vec = L1 == 5 && L2 == 3 && dtype != SQC_F64 && (reinterpret_cast<uintptr_t>(src[i]) % 16) == 0;
       for (int t = 0; t < kin; ++t) d.inshift[t] = digit_shift(*c, i, c->ins[i][t]);
       for (int u = 0; u < kout; ++u) d.outshift[u] = digit_shift(*c, i, c->outs[i][u]);
       d.block_begin = blocks;

@@ -241,6 +241,116 @@ __device__ __forceinline__ void attr_tile(const AttrDesc& d, const AttrTileCtx& 
     d.A[((in_digits(tc, s) | vbase) << n) + xw] = val[s * TX + posw];
 }
 
+
+// The same tile for the largest tile shape (32 x 8 states, TX = 256) with
+// FP32 input: every thread handles 4 consecutive states (one 16-byte load
+// per row and outcome, 16-byte shared-memory and global accesses).  64
+// threads cover a row, so 4 rows are in flight per pass.  In phase 3 a
+// thread writes 4 consecutive storage addresses of A: the same low state
+// bits with the top bits jh = rev3(r), r = r0 .. r0+3 (the top 3 state
+// bits are the low 3 storage bits, reversed).
+template <int NC>
+__device__ __forceinline__ void fold_phase_v4(const AttrDesc& d, const AttrTileCtx& t, float* val, int S,
+                                              uint64_t x0, int pos, uint64_t vbase, uint32_t signed_mask) {
+  constexpr int kU = NC >= 4 ? 1 : (NC >= 2 ? 2 : 4);   // rows per thread per round
+  const int n = d.n;
+  const int row_shift = n + d.kout;
+  const int nc = 1 << d.kout;
+  const float* p = static_cast<const float*>(d.p);
+  for (int s0 = int(threadIdx.x) >> 6; s0 < S; s0 += 4 * kU) {
+    uint64_t base[kU];
+    float4 acc[kU];
+    bool ok[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int s = s0 + 4 * u;
+      ok[u] = s < S;
+      base[u] = ((in_digits(t, ok[u] ? s : 0) | vbase) << row_shift) + x0;
+      acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int c0 = 0; c0 < nc; c0 += NC) {
+      float4 w[NC][kU];
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          w[cc][u] = ok[u] ? __ldg(reinterpret_cast<const float4*>(p + base[u] + (uint64_t(c0 + cc) << n)))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) {
+        const float sg = (__popc(uint32_t(c0 + cc) & signed_mask) & 1) ? -1.f : 1.f;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          acc[u].x = fmaf(sg, w[cc][u].x, acc[u].x);
+          acc[u].y = fmaf(sg, w[cc][u].y, acc[u].y);
+          acc[u].z = fmaf(sg, w[cc][u].z, acc[u].z);
+          acc[u].w = fmaf(sg, w[cc][u].w, acc[u].w);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (ok[u]) *reinterpret_cast<float4*>(val + (s0 + 4 * u) * 256 + pos) = acc[u];
+  }
+}
+
+__device__ __forceinline__ void attr_tile_v4(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
+  const uint64_t o = uint64_t(t) & ((uint64_t(1) << (2 * d.kout)) - 1);
+  const uint64_t xm = uint64_t(t) >> (2 * d.kout);
+  const int S = 1 << (2 * d.kin);
+  const int n = d.n;
+  uint64_t vbase = 0;
+  uint32_t signed_mask = 0;
+  for (int u = 0; u < d.kout; ++u) {
+    const uint64_t dig = (o >> (2 * u)) & 3;
+    vbase |= dig << d.outshift[u];
+    if (dig) signed_mask |= 1u << u;
+  }
+  const int g = int(threadIdx.x) & 63;
+  const int j0 = 4 * g;                              // 4 consecutive low bits, one jh
+  const uint64_t x0 = uint64_t(j0 & 31) | (xm << 5) | (uint64_t(j0 >> 5) << (n - 3));
+  const int pos = slot_pos(j0, 5, 3);                // a multiple of 4
+  switch (d.kout) {
+    case 0: fold_phase_v4<1>(d, tc, val, S, x0, pos, vbase, signed_mask); break;
+    case 1: fold_phase_v4<2>(d, tc, val, S, x0, pos, vbase, signed_mask); break;
+    case 2: fold_phase_v4<4>(d, tc, val, S, x0, pos, vbase, signed_mask); break;
+    default: fold_phase_v4<8>(d, tc, val, S, x0, pos, vbase, signed_mask); break;
+  }
+  __syncthreads();
+  for (int q = 0; q < d.kin; ++q) {
+    const int lowmask = (1 << (2 * q)) - 1;
+    const int st = 256 << (2 * q);
+    for (int gg = int(threadIdx.x) >> 6; gg < (S >> 2); gg += 4) {
+      const int s0 = ((gg & ~lowmask) << 2) | (gg & lowmask);
+      float* a = val + s0 * 256 + pos;
+      const float4 v0 = *reinterpret_cast<const float4*>(a);
+      const float4 v1 = *reinterpret_cast<const float4*>(a + st);
+      const float4 v2 = *reinterpret_cast<const float4*>(a + 2 * st);
+      const float4 v3 = *reinterpret_cast<const float4*>(a + 3 * st);
+      const float4 sm = make_float4(v0.x + v1.x, v0.y + v1.y, v0.z + v1.z, v0.w + v1.w);
+      *reinterpret_cast<float4*>(a) = sm;                                                     // I
+      *reinterpret_cast<float4*>(a + st) =
+          make_float4(2.f * v2.x - sm.x, 2.f * v2.y - sm.y, 2.f * v2.z - sm.z, 2.f * v2.w - sm.w);   // X
+      *reinterpret_cast<float4*>(a + 2 * st) =
+          make_float4(2.f * v3.x - sm.x, 2.f * v3.y - sm.y, 2.f * v3.z - sm.z, 2.f * v3.w - sm.w);   // Y
+      *reinterpret_cast<float4*>(a + 3 * st) =
+          make_float4(v0.x - v1.x, v0.y - v1.y, v0.z - v1.z, v0.w - v1.w);                   // Z
+    }
+    __syncthreads();
+  }
+  // phase 3: thread g writes storage offsets r0 .. r0+3 of low state bits jl
+  const int jl = g >> 1, r0 = (g & 1) * 4;
+  int pw[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) pw[q] = slot_pos(jl | (int(__brev(uint32_t(r0 + q)) >> 29) << 5), 5, 3);
+  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << 5)), n) + uint64_t(r0);
+  for (int s = int(threadIdx.x) >> 6; s < S; s += 4) {
+    const float* v = val + s * 256;
+    *reinterpret_cast<float4*>(d.A + ((in_digits(tc, s) | vbase) << n) + xw) =
+        make_float4(v[pw[0]], v[pw[1]], v[pw[2]], v[pw[3]]);
+  }
+}
+
 __device__ void fill_tile_ctx(const AttrDesc& d, AttrTileCtx& t) {
   for (int i = threadIdx.x; i < 256 + 64; i += blockDim.x) {
     const int s = i < 256 ? i : ((i - 256) << 8);
@@ -286,7 +396,10 @@ __global__ void __launch_bounds__(256) attr_fused_kernel(AttrLaunch L, int64_t t
       fill_tile_ctx(d, tc);
       __syncthreads();
     }
-    attr_tile(d, tc, tile - d.block_begin, val);
+    if (d.vec)
+      attr_tile_v4(d, tc, tile - d.block_begin, val);
+    else
+      attr_tile(d, tc, tile - d.block_begin, val);
     __syncthreads();
   }
 }

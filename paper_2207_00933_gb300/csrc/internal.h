@@ -48,6 +48,7 @@ struct AttrDesc {
   int in_f64;
   int n, kin, kout;
   int L1, L2;                 // x tile: 2^L1 low values x 2^L2 top-bit values
+  int vec;                    // 32 x 8 tile, FP32 input, 16-byte aligned: 4 states per thread
   int inshift[kMaxFusedIn];
   int outshift[16];
   int64_t block_begin;

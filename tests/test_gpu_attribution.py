@@ -1,0 +1,72 @@
+"""GPU parity of the attribution (Eq. 1 with the I/X/Y/Z expansion of
+every cut wire) on large subcircuits, where the kernel switches to 32 x 8
+state tiles: the 4-states-per-thread form for 16-byte aligned FP32 inputs,
+the one-state-per-thread form for FP64 inputs and for FP32 inputs that are
+not 16-byte aligned.  Each case covers a different number of outgoing cut
+edges (1, 2, 3) and of incoming ones (0, 2, 3), and is checked through the
+whole reconstruction against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synthetic import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ABS_TOL = 1e-6
+REL_TOL = 1e-5
+
+# (widths, hand-offs, active qubits per subcircuit)
+CASES = {
+    "kout1": ([20, 6], [1], [8, 4]),        # 19 data qubits, 1 outgoing edge
+    "kout3": ([18, 6], [3], [8, 4]),        # 15 data qubits, 3 outgoing edges
+    "kout2_kin2": ([20, 22], [2], [10, 10]),  # 18 + 22 data qubits, 2 cuts
+}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2207_00933_gb300 import Context, _build
+    _build.build()
+    c = Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _device_input(p, form):
+    import torch
+    if form == "fp64":
+        return torch.from_numpy(p.astype(np.float64)).cuda()
+    t = torch.from_numpy(p).cuda()
+    if form == "fp32_aligned":
+        assert t.data_ptr() % 16 == 0
+        return t
+    # the same values one element into a larger buffer: 4-byte aligned only
+    buf = torch.empty(p.size + 1, dtype=torch.float32, device="cuda")
+    view = buf[1:].view(p.shape)
+    view.copy_(t)
+    assert view.data_ptr() % 16 == 4
+    return view
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_large_tiles_match_oracle(ctx, case):
+    import torch
+    widths, handoffs, active = CASES[case]
+    w = W.random_line_chain(21, widths, handoffs, 1, active)
+    c = w.circuit
+    ref = O.reconstruct(O.Graph.from_arrays(c.n_qubits, *c.graph_arrays()),
+                        [p.astype(np.float64) for p in w.probs], w.roles)
+    scale = np.abs(ref).max()
+    for form in ("fp32_aligned", "fp32_unaligned", "fp64"):
+        probs = [_device_input(p, form) for p in w.probs]
+        cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), probs)
+        qid, na = ctx.set_qubit_roles(cid, w.roles)
+        out = torch.empty(1 << na, dtype=torch.float32, device="cuda")
+        ctx.reconstruct(qid, out)
+        torch.cuda.synchronize()
+        err = np.abs(out.double().cpu().numpy() - ref).max()
+        assert err <= ABS_TOL and err <= REL_TOL * scale + 1e-12, (case, form, err)
+        ctx.unload(cid)
