@@ -63,6 +63,7 @@ struct Step {
   uint64_t* rowmap = nullptr;    // device
   uint64_t* colmap = nullptr;
   int vec4 = 0;
+  int contig16 = 0;           // colmap runs of 16 consecutive, 4-aligned offsets; rowmap 4-aligned
 };
 
 // Everything one precision needs to run a query: contraction order, layouts,
@@ -689,6 +690,12 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     for (size_t i = 0; v4 && i < rm.size(); ++i)
       if (rm[i] & 3) v4 = false;
     st.vec4 = v4;
+    bool c16 = st.N % 16 == 0;
+    for (size_t j = 0; c16 && j < cm.size(); ++j)
+      if (cm[j] != cm[j & ~size_t(15)] + (j & 15) || (cm[j & ~size_t(15)] & 3)) c16 = false;
+    for (size_t i = 0; c16 && i < rm.size(); ++i)
+      if (rm[i] & 3) c16 = false;
+    st.contig16 = c16;
     step_map_off[s] = {maps.add(rm), maps.add(cm)};
     P->flops += 2.0 * double(st.M) * double(st.N) * double(st.Kd);
   }
@@ -1130,6 +1137,7 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
         a.counter = P.counter;
         a.total = total_prob;
         a.err = P.err;
+        a.contig16 = st.contig16;
         CK(launch_gemm_tc(a, s));
       } else {
         GemmArgs a{};

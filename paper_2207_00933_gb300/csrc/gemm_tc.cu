@@ -33,16 +33,31 @@ namespace sqc {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kBN = 128;
-constexpr int kBK = 64;            // 64 BF16 = 128 bytes: one 128-byte swizzle row
-constexpr int kStages = 2;
-constexpr int kTileA = kBM * kBK * 2;
-constexpr int kTileB = kBN * kBK * 2;
-constexpr int kStageBytes = 3 * kTileA + 3 * kTileB;
-constexpr int kThreads = 192;
-constexpr int kTmemCols = 128;
+constexpr int kKAlign = 64;        // the shared index is padded to a multiple of this
+constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, each half of the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kSpinLimit = 1u << 24;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+
+// Tile configurations: BN output columns per tile, BK shared-index columns
+// per stage (BK BF16 = one swizzle row: 64 -> 128-byte swizzle, 32 ->
+// 64-byte swizzle), STAGES pipeline stages.
+//   128 x 128, BK 64, 2 stages of 96 KB (narrow steps)
+//   128 x 256, BK 32, 3 stages of 72 KB: 25% less operand traffic per flop
+template <int BN_, int BK_, int STAGES_>
+struct TcCfg {
+  static constexpr int BN = BN_, BK = BK_, STAGES = STAGES_;
+  static constexpr int kTileA = kBM * BK * 2;
+  static constexpr int kTileB = BN * BK * 2;
+  static constexpr int kStageBytes = 3 * kTileA + 3 * kTileB;
+  static constexpr int kTmemCols = BN;          // one FP32 accumulator buffer
+  static constexpr int kSmemBytes = STAGES * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int kSwizzleBytes = BK * 2;
+  // instruction descriptor: D = FP32, A = B = BF16, both K-major, M x N
+  static constexpr uint32_t kIdesc =
+      (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
+};
+using CfgNarrow = TcCfg<128, 64, 2>;
+using CfgWide = TcCfg<256, 32, 3>;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -88,30 +103,29 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major tile of 8-row x 128-byte swizzle
-// atoms (128-byte swizzle), atoms 1024 bytes apart.
+// Shared-memory matrix descriptor: K-major tile of 8-row swizzle atoms
+// (rows of SW bytes: 128-byte or 64-byte swizzle), atoms 8 x SW bytes apart.
+template <int SW>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  static_assert(SW == 128 || SW == 64, "swizzle");
   uint64_t d = 0;
   d |= uint64_t((addr & 0x3FFFFu) >> 4);   // start address
   d |= uint64_t(1) << 16;                  // leading byte offset (unused for swizzled K-major)
-  d |= uint64_t(1024 >> 4) << 32;          // stride byte offset: next 8-row group
+  d |= uint64_t((8 * SW) >> 4) << 32;      // stride byte offset: next 8-row group
   d |= uint64_t(1) << 46;                  // descriptor version
-  d |= uint64_t(2) << 61;                  // 128-byte swizzle
+  d |= uint64_t(SW == 128 ? 2 : 4) << 61;  // swizzle mode
   return d;
 }
 
-// Instruction descriptor: D = FP32, A = B = BF16, both K-major, M x N.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kBN >> 3) << 17) |
-                            (uint32_t(kBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n"
       " .reg .pred p;\n"
       " setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
       "}\n" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
@@ -120,17 +134,21 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 32 consecutive accumulator columns of this thread's TMEM lane (one
+// load, one wait).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Store 16 consecutive columns of one output row.  `contig`: the columns'
@@ -157,10 +175,14 @@ __device__ __forceinline__ void store16(const GemmTcArgs& a, uint64_t off, bool 
 }
 
 // Persistent: grid = min(tiles, SMs); CTA b takes tiles b, b + grid, ...
-// The accumulator is double-buffered in TMEM (2 x 128 columns) so that the
+// The accumulator is double-buffered in TMEM (2 x BN columns) so that the
 // epilogue of one tile overlaps the loads and MMAs of the next.
+template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmTcArgs a) {
+  constexpr int kBN = Cfg::BN, kBK = Cfg::BK, kStages = Cfg::STAGES;
+  constexpr int kTileA = Cfg::kTileA, kTileB = Cfg::kTileB, kStageBytes = Cfg::kStageBytes;
+  constexpr int kTmemCols = Cfg::kTmemCols, kSW = Cfg::kSwizzleBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
@@ -185,7 +207,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);            // one arrival per epilogue warp
+      mbar_init(&acc_empty[b], kEpiWarps);    // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
@@ -202,7 +224,6 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  float sum_f = 0.f;
   double sum_d = 0.0;
 
   if (warp == 0 && lane == 0) {
@@ -254,11 +275,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const uint32_t base = smem_u32(smem + s * kStageBytes);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-          const uint64_t da = smem_desc(base + pa[q] * kTileA);
-          const uint64_t db = smem_desc(base + 3 * kTileA + pb[q] * kTileB);
+          const uint64_t da = smem_desc<kSW>(base + pa[q] * kTileA);
+          const uint64_t db = smem_desc<kSW>(base + 3 * kTileA + pb[q] * kTileB);
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk)   // K = 16 per instruction: +32 bytes = +2 in the address field
-            mma_bf16(dacc, da + 2 * kk, db + 2 * kk, (kb | q | kk) != 0);
+            mma_bf16(dacc, da + 2 * kk, db + 2 * kk, Cfg::kIdesc, (kb | q | kk) != 0);
         }
         mma_commit(&empty[s]);
       }
@@ -266,8 +287,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       if (!ok) break;
     }
   } else if (warp >= 2) {
-    // ---- epilogue
+    // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (its rows) and
+    // half (w-2)/4 of the tile's columns, 32 columns per TMEM load
     const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
     const float alpha_f = float(a.alpha);
     int64_t t = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
@@ -282,23 +305,27 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const int64_t row = m0 + quad * 32 + lane;
       const bool row_ok = row < a.M;
       const uint64_t rbase = row_ok ? a.rowmap[row] : 0;
-      for (int c0 = 0; c0 < kBN; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + uint32_t(buf * kTmemCols) + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
-        const int64_t col0 = n0 + c0;
-        const int ncols = int(a.N - col0 < 16 ? (a.N - col0 > 0 ? a.N - col0 : 0) : 16);
-        if (!row_ok || ncols == 0) continue;
+      for (int c0 = half * (kBN / 2); c0 < (half + 1) * (kBN / 2); c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + uint32_t(buf * kTmemCols) + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
+        if (!row_ok) continue;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          v[j] *= alpha_f;
-          if (j < ncols) {
-            if (a.kind == OUT_F64) sum_d += double(v[j]); else sum_f += v[j];
+        for (int h = 0; h < 2; ++h) {
+          const int64_t col0 = n0 + c0 + 16 * h;
+          const int ncols = int(a.N - col0 < 16 ? (a.N - col0 > 0 ? a.N - col0 : 0) : 16);
+          if (ncols == 0) continue;
+          float* f = v + 16 * h;
+          // probability check: the 16 values summed in FP32, the chunks in FP64
+          float cs = 0.f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            f[j] *= alpha_f;
+            if (j < ncols) cs += f[j];
           }
+          sum_d += double(cs);
+          const uint64_t c_first = a.colmap[col0];
+          store16(a, rbase + c_first, a.contig16 && ncols == 16, f, a.colmap, col0, rbase, ncols);
         }
-        const uint64_t c_first = a.colmap[col0];
-        const bool contig = ncols == 16 && a.colmap[col0 + 15] == c_first + 15 &&
-                            ((rbase + c_first) & (a.kind == OUT_F64 ? 1 : 3)) == 0;
-        store16(a, rbase + c_first, contig, v, a.colmap, col0, rbase, ncols);
       }
       // hand the accumulator back to the MMA warp
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -313,7 +340,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
   }
   if (failed && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
-  if (a.partials) finish_total(sum_d + double(sum_f), a.partials, a.counter, a.total, red);
+  if (a.partials) finish_total(sum_d, a.partials, a.counter, a.total, red);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -335,17 +362,29 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D map over BF16 planes [3][rows][Kp], box 64 x 128 x 1, 128-byte swizzle.
-bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t Kp) {
+// 3-D map over BF16 planes [3][rows][Kp], box bk x box_rows x 1, with the
+// swizzle of a bk-wide row (128 or 64 bytes).
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t Kp, int bk, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[3] = {cuuint64_t(Kp), cuuint64_t(rows), 3};
   const cuuint64_t strides[2] = {cuuint64_t(Kp) * 2, cuuint64_t(rows) * cuuint64_t(Kp) * 2};
-  const cuuint32_t box[3] = {kBK, kBM, 1};
+  const cuuint32_t box[3] = {cuuint32_t(bk), cuuint32_t(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class Cfg>
+cudaError_t launch_cfg(const GemmTcArgs& a, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a.A, a.Mp, a.Kp, Cfg::BK, kBM) || !make_map(&mb, a.B, a.Np, a.Kp, Cfg::BK, Cfg::BN))
+    return cudaErrorInvalidValue;
+  const int64_t tiles = (a.Mp / kBM) * (a.Np / Cfg::BN);
+  const int64_t grid = tiles < 152 ? tiles : 152;    // persistent: at most one CTA per SM
+  gemm_tc_kernel<Cfg><<<unsigned(grid), kThreads, Cfg::kSmemBytes, s>>>(ma, mb, a);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -353,27 +392,29 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t Kp) {
 bool gemm_tc_available() { return encode_fn() != nullptr; }
 
 int gemm_tc_min_rows() { return kBM; }
-int gemm_tc_k_align() { return kBK; }
+int gemm_tc_k_align() { return kKAlign; }
 
 cudaError_t gemm_tc_configure() {
-  return cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<CfgNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       CfgNarrow::kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_tc_kernel<CfgWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             CfgWide::kSmemBytes);
+  return e;
 }
 
 cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s) {
   // shape contract: Mp, Np multiples of 128 (they are the powers of two M, N
   // >= 128), Kp a multiple of 64; checked here so that no TMA coordinate or
   // TMEM lane can leave the operands
-  if (a.Mp % kBM || a.Np % kBN || a.Kp % kBK || a.Kp <= 0 || a.M > a.Mp || a.N > a.Np || a.K > a.Kp)
+  if (a.Mp % kBM || a.Np % 128 || a.Kp % kKAlign || a.Kp <= 0 || a.M > a.Mp || a.N > a.Np || a.K > a.Kp)
     return cudaErrorInvalidValue;
   // TMA wants 16-byte aligned global operands (the 1024-byte alignment the
   // swizzle needs applies to the shared-memory stages only)
   if ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 15) return cudaErrorInvalidValue;
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, a.A, a.Mp, a.Kp) || !make_map(&mb, a.B, a.Np, a.Kp)) return cudaErrorInvalidValue;
-  const int64_t tiles = (a.Mp / kBM) * (a.Np / kBN);
-  const int64_t grid = tiles < 152 ? tiles : 152;    // persistent: at most one CTA per SM
-  gemm_tc_kernel<<<unsigned(grid), kThreads, kSmemBytes, s>>>(ma, mb, a);
-  return cudaGetLastError();
+  // 256-wide tiles when they still fill every SM at least once
+  if (a.Np % 256 == 0 && (a.Mp / kBM) * (a.Np / 256) >= 152) return launch_cfg<CfgWide>(a, s);
+  return launch_cfg<CfgNarrow>(a, s);
 }
 
 }  // namespace sqc

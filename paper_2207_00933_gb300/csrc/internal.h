@@ -124,6 +124,7 @@ struct GemmTcArgs {
   unsigned* counter;
   double* total;
   int* err;                 // device error flag (bounded waits)
+  int contig16;             // colmap: runs of 16 consecutive 4-aligned offsets, rowmap 4-aligned
 };
 cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s);
 bool gemm_tc_available();          // the driver's tensor-map encoder is reachable

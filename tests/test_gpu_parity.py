@@ -139,6 +139,25 @@ def test_split_bf16_contraction_bound_step(ctx):
         check(P, ref)
 
 
+@pytest.mark.parametrize("active,out", [((12, 12), "float32"), ((12, 12), "float64"), ((11, 12), "float32")])
+def test_split_bf16_wide_tiles(ctx, active, out):
+    # 4096 x 4096 x 256 (and 2048 x 4096): enough 128 x 256 tiles to fill
+    # every SM, so the tensor-core step runs the 256-wide, 32-deep,
+    # three-stage configuration (64-byte swizzle)
+    w = W.random_line_chain(11, [16, 16], [4], 1, list(active))
+    ref = oracle_run(w)
+    P, tot = gpu_run(ctx, w, out_dtype=out, precision="split_bf16")
+    check(P, ref)
+    # the FP64 check sums exactly the bins that were written
+    assert abs(tot - O.total_probability(P)) < 1e-9
+    # and drifts from the oracle's total only by the tensor cores' FP32
+    # accumulation, which may drop up to one unit in the last place (2^-23
+    # relative) per accumulation step, always toward zero: the step adds
+    # 6 products x Kp/16 MMAs into one accumulator, so the drift of a total
+    # near 1 is at most 6 * (256 / 16) * 2^-23 = 1.1e-5
+    assert abs(tot - O.total_probability(ref)) <= 6 * (256 // 16) * 2.0 ** -23
+
+
 def test_zoomed_children_sum_to_parent(ctx):
     w = W.merged_30q()
     q = w.circuit.data_qubits[2][6]
