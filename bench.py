@@ -611,7 +611,7 @@ def main():
     achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9
     kernel_of = {"attribute": "attr_fused_kernel", "merge": "merge_kernel", "contract": "gemm_simt_kernel",
                  "final": "gemm_simt_kernel (last step)",
-                 "select": "select_resident_kernel" if (1 << na) * out_b <= (24 << 20) else "select_coop_kernel"}
+                 "select": "select_resident_kernel" if (1 << na) <= 7_000_000 else "select_coop_kernel"}
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": src,
                 "stages": {k: {"us": 1e3 * stage_ms[k], "share": share[k],

@@ -98,9 +98,10 @@ typedef struct {
    * query then runs 4^slice_edges smaller contractions whose results are
    * added into the output (in FP64 for FP64 outputs).  0 = no slicing. */
   int32_t slice_edges;
-  /* Selection (sqc_top_bins): 1 = hold the values in shared memory, one
-   * slice per SM, when they fit (up to ~28 MB of FP32 or FP64 values on
-   * 152 SMs; one read of the input); 0 = always the streaming kernel. */
+  /* Selection (sqc_top_bins): 1 = hold one 32-bit key word per value in
+   * shared memory, one slice per SM, when they fit (up to ~7 million FP32
+   * or FP64 values on 152 SMs; one read of the input); 0 = always the
+   * streaming kernel. */
   int32_t select_resident;
   int32_t reserved[3];
 } sqc_config;

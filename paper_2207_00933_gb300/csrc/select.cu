@@ -862,16 +862,6 @@ struct ResWork {
   unsigned* tie_count;            // [grid]
 };
 
-template <bool F64> struct ResKey;
-template <> struct ResKey<false> {
-  using T = unsigned;
-  static constexpr int kBits = 32;
-};
-template <> struct ResKey<true> {
-  using T = unsigned long long;
-  static constexpr int kBits = 64;
-};
-
 // Arrive with `add` (1 << 32 plus any count for the low word) and wait
 // until `arrivals` CTAs have arrived; returns the barrier word seen (0 after
 // an abort).  The release-add publishes the CTA's writes (ordered before it
@@ -981,20 +971,32 @@ template <bool F64>
 __global__ void __launch_bounds__(kRThreads, 1)
 select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, unsigned long long key_thr64, int k,
                        int cap, ResWork w, unsigned long long* bins_out, double* probs_out, int* n_found, int* err) {
-  using KeyT = typename ResKey<F64>::T;
-  constexpr int KB = ResKey<F64>::kBits;
+  // Shared memory holds one 32-bit word per value: the whole key of an FP32
+  // value, the high word of the 64-bit key of an FP64 value (its low word
+  // is read back from the input only for values whose high word equals the
+  // determined prefix).  Digits: 12, 12 and 8 bits per word.
+  constexpr int KB = F64 ? 64 : 32;
+  constexpr int kPasses = F64 ? 6 : 3;
   constexpr int V = F64 ? 2 : 4;                    // values per 16-byte vector
   extern __shared__ __align__(16) unsigned char rsm[];
   unsigned* sh = reinterpret_cast<unsigned*>(rsm);                 // [kRRadix]
-  KeyT* keys = reinterpret_cast<KeyT*>(rsm + kRHistBytes);         // [per], later the ranking tile
+  unsigned* keys = reinterpret_cast<unsigned*>(rsm + kRHistBytes); // [per], later the ranking tile
   __shared__ ResState st;
   __shared__ unsigned long long wtot[2 * kRWarps + 1];
   __shared__ unsigned wcnt[kRWarps];
   const unsigned nb = gridDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const KeyT key_thr = F64 ? KeyT(key_thr64) : KeyT(key_thr64 >> 32);
+  const unsigned long long key_thr = F64 ? key_thr64 : (key_thr64 >> 32);
   const uint64_t start = uint64_t(blockIdx.x) * per;
   const int cnt = int(start < n ? ((n - start) < per ? (n - start) : per) : 0);
+  // low word of the 64-bit key of value i of the slice (FP64 only)
+  auto low_word = [&](int i) -> unsigned {
+    return unsigned(key_f64(static_cast<const double*>(x)[start + i]));
+  };
+  auto full_key = [&](int i, unsigned kk) -> unsigned long long {
+    if constexpr (F64) return ((unsigned long long)kk << 32) | low_word(i);
+    else return (unsigned long long)kk;
+  };
   unsigned bar = 0;                                 // barriers met so far
   bool ok = true;
   if (tid == 0) {
@@ -1007,14 +1009,14 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
   for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
   __syncthreads();
   // pass 0 with the load: keys of excluded values (NaN or below the
-  // threshold) are stored as 0, which no included value has
+  // threshold) are stored as 0, which no included value has (the smallest
+  // included key word is 0x007fffff for FP32, 0x000fffff for FP64)
   {
-    const int lo0 = KB - kRBits;
     // the loop bound is the same for the whole CTA: warp_hist_add needs
     // every lane of the warp
     for (int b0 = 0; b0 < cnt; b0 += kRThreads * V) {
       const int i0 = b0 + tid * V;
-      KeyT kv[V];
+      unsigned kv[V];
       if constexpr (F64) {
         const double* p = static_cast<const double*>(x) + start + i0;
         double a[2];
@@ -1030,7 +1032,7 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
           const unsigned long long u = __double_as_longlong(a[q]);
           const bool nan = (u & 0x7fffffffffffffffull) > 0x7ff0000000000000ull;
           const unsigned long long kk = key_f64(a[q]);
-          kv[q] = (!nan && kk >= key_thr) ? kk : 0ull;
+          kv[q] = (!nan && kk >= key_thr) ? unsigned(kk >> 32) : 0u;
         }
       } else {
         const float* p = static_cast<const float*>(x) + start + i0;
@@ -1047,31 +1049,46 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
           const unsigned u = __float_as_uint(a[q]);
           const bool nan = (u & 0x7fffffffu) > 0x7f800000u;
           const unsigned kk = unsigned(key_f32(a[q]) >> 32);
-          kv[q] = (!nan && kk >= key_thr) ? kk : 0u;
+          kv[q] = (!nan && kk >= unsigned(key_thr)) ? kk : 0u;
         }
       }
 #pragma unroll
       for (int q = 0; q < V; ++q) {
         if (i0 + q < cnt) keys[i0 + q] = kv[q];
-        warp_hist_add(sh, kv[q] != 0, unsigned(kv[q] >> lo0), lane);
+        warp_hist_add(sh, kv[q] != 0, kv[q] >> (32 - kRBits), lane);
       }
     }
   }
   // the refinement loop: flush, barrier, decide; then the next digit from
-  // shared memory
-  for (int pass = 0; pass < (KB + kRBits - 1) / kRBits; ++pass) {
-    const int hi = KB - kRBits * pass;
-    const int lo = hi - kRBits > 0 ? hi - kRBits : 0;
+  // shared memory (and, for the low word of FP64 keys, from the input)
+  for (int pass = 0; pass < kPasses; ++pass) {
+    const int word = pass / 3;                      // 0: the (high) word in shared memory, 1: the low word
+    const int hi_w = 32 - kRBits * (pass % 3);      // digit bits [lo_w, hi_w) of the word: 32-20, 20-8, 8-0
+    const int lo_w = pass % 3 == 2 ? 0 : hi_w - kRBits;
+    const int lo = ((F64 && word == 0) ? 32 : 0) + lo_w;   // bit position in the whole key
     if (pass > 0) {
-      const KeyT pfx = KeyT(st.prefix);
-      const unsigned dmask = (1u << (hi - lo)) - 1u;
+      const unsigned long long pfx = st.prefix;
+      const unsigned pfx_hi = F64 ? unsigned(pfx >> 32) : unsigned(pfx);
+      const unsigned pfx_lo = unsigned(pfx);
+      const unsigned dmask = (1u << (hi_w - lo_w)) - 1u;
       for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
       __syncthreads();
       for (int i0 = 0; i0 < cnt; i0 += kRThreads) {
         const int i = i0 + tid;
-        const KeyT kk = i < cnt ? keys[i] : KeyT(0);
-        const bool in = kk != 0 && (kk >> hi) == (pfx >> hi);
-        warp_hist_add(sh, in, unsigned(kk >> lo) & dmask, lane);
+        const unsigned kk = i < cnt ? keys[i] : 0u;
+        bool in = false;
+        unsigned dig = 0;
+        if (kk != 0) {
+          if (word == 0) {
+            in = hi_w >= 32 || (kk >> hi_w) == (pfx_hi >> hi_w);
+            dig = (kk >> lo_w) & dmask;
+          } else if (kk == pfx_hi) {
+            const unsigned lw = low_word(i);
+            in = hi_w >= 32 || (lw >> hi_w) == (pfx_lo >> hi_w);
+            dig = (lw >> lo_w) & dmask;
+          }
+        }
+        warp_hist_add(sh, in, dig, lane);
       }
     }
     __syncthreads();
@@ -1087,19 +1104,29 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
   unsigned long long nc = 0;
   if (ok) {
     const int done = st.done, lo = st.lo;
-    const KeyT pv = KeyT(done == 2 ? 0ull : (st.prefix >> lo));
+    const unsigned long long pfx = st.prefix;
     // compaction: values above the bucket, and the bucket itself unless it
     // is an oversized group of exact ties.  Counted first (one slot
     // reservation per CTA), then written, each thread its own elements in
     // order.
-    auto takes = [&](KeyT kk) -> bool {
+    auto takes = [&](int i, unsigned kk) -> bool {
       if (kk == 0) return false;
       if (done == 2) return true;
-      const KeyT hb = lo >= KB ? KeyT(0) : KeyT(kk >> lo);
+      if (!F64 || lo >= 32) {
+        // the bucket is decided within the word in shared memory
+        const int l = F64 ? lo - 32 : lo;
+        const unsigned pw = F64 ? unsigned(pfx >> 32) : unsigned(pfx);
+        const unsigned hb = kk >> l, pv = pw >> l;
+        return done == 3 ? hb > pv : hb >= pv;
+      }
+      // FP64 with the bucket in the low word: every high bit is decided
+      const unsigned ph = unsigned(pfx >> 32);
+      if (kk != ph) return kk > ph;
+      const unsigned hb = low_word(i) >> lo, pv = unsigned(pfx) >> lo;
       return done == 3 ? hb > pv : hb >= pv;
     };
     unsigned mine = 0;
-    for (int i = tid; i < cnt; i += kRThreads) mine += takes(keys[i]);
+    for (int i = tid; i < cnt; i += kRThreads) mine += takes(i, keys[i]);
     // exclusive prefix of `mine` over the CTA
     unsigned incl = mine;
 #pragma unroll
@@ -1129,9 +1156,9 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
     {
       unsigned long long r = cta_base + wcnt[warp] + (incl - mine);
       for (int i = tid; i < cnt; i += kRThreads) {
-        const KeyT kk = keys[i];
-        if (takes(kk)) {
-          w.cand_key[r] = (unsigned long long)kk;
+        const unsigned kk = keys[i];
+        if (takes(i, kk)) {
+          w.cand_key[r] = full_key(i, kk);
           w.cand_idx[r] = start + i;
           ++r;
         }
@@ -1141,9 +1168,15 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
     if (done == 3) {
       // exact ties of the k-th key beyond capacity: ascending bin order,
       // via per-CTA counts and an ordered scan of each slice
-      const KeyT tkey = KeyT(st.prefix);
+      const unsigned long long tkey = st.prefix;
+      const unsigned tk_hi = F64 ? unsigned(tkey >> 32) : unsigned(tkey);
+      auto is_tie = [&](int i, unsigned kk) -> bool {
+        if (kk != tk_hi) return false;
+        if constexpr (F64) return low_word(i) == unsigned(tkey);
+        else return true;
+      };
       unsigned my = 0;
-      for (int i = tid; i < cnt; i += kRThreads) my += keys[i] == tkey;
+      for (int i = tid; i < cnt; i += kRThreads) my += is_tie(i, keys[i]);
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(0xffffffffu, my, off);
       if (lane == 0) wcnt[warp] = my;
@@ -1166,7 +1199,7 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
         unsigned long long run = tbase;
         for (int i0 = 0; i0 < cnt && run < need; i0 += kRThreads) {
           const int i = i0 + tid;
-          const bool tie = i < cnt && keys[i] == tkey;
+          const bool tie = i < cnt && is_tie(i, keys[i]);
           const unsigned bal = __ballot_sync(0xffffffffu, tie);
           if (lane == 0) wcnt[warp] = __popc(bal);
           __syncthreads();
@@ -1177,7 +1210,7 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
           }
           const unsigned long long rank = run + before + __popc(bal & ((1u << lane) - 1u));
           if (tie && rank < need) {
-            w.cand_key[first + rank] = (unsigned long long)tkey;
+            w.cand_key[first + rank] = tkey;
             w.cand_idx[first + rank] = start + i;
           }
           run += all;
@@ -1345,7 +1378,7 @@ size_t select_resident_smem(uint64_t n, int is_f64, int grid, uint64_t* per) {
   if (grid <= 0) return 0;
   uint64_t p = (n + uint64_t(grid) - 1) / uint64_t(grid);
   p = (p + 3) & ~uint64_t(3);
-  const uint64_t region = p * (is_f64 ? 8 : 4);
+  const uint64_t region = p * 4;                   // one 32-bit key word per value
   const uint64_t need = uint64_t(kRHistBytes) + (region > uint64_t(kRRegionMin) ? region : uint64_t(kRRegionMin));
   if (per) *per = p;
   return need <= uint64_t(kRSmemMax) ? size_t(need) : 0;

@@ -1,6 +1,6 @@
 """GPU parity of the bin selection (Algorithm 1: keep the largest bins, then
 the probability check) for both cooperative kernels: the shared-memory
-resident one (default for inputs up to ~28 MB) and the streaming one
+resident one (default for up to ~7 million values) and the streaming one
 (select_resident=False, and every larger input).  Results are compared
 exactly with the oracle's top_bins on the same values: bins ordered by
 value descending, ties by bin index ascending, values >= threshold."""
@@ -116,10 +116,10 @@ def test_selection_size_limits_and_shared_workspace(ctxs):
     the workspace as the other expects it."""
     ctx, qid = ctxs[True]
     rng = np.random.default_rng(11)
-    big32 = _values("narrow", 7_500_000, "float32", rng)      # > 200 KB per SM
+    big32 = _values("narrow", 7_500_000, "float32", rng)      # > 200 KB of key words per SM
     small = _values("porter_thomas", 1 << 20, "float32", rng)
-    big64 = _values("porter_thomas", (1 << 22) + 3, "float64", rng)
-    mid64 = _values("ties", 1 << 21, "float64", rng)           # resident
+    big64 = _values("porter_thomas", 7_400_000, "float64", rng)
+    mid64 = _values("ties", (1 << 22) + 3, "float64", rng)     # resident (32-bit key words)
     fulls = {id(x): _full_order(x) for x in (big32, small, big64, mid64)}
     for x in (big32, small, big64, mid64, small, big32):
         _check(ctx, qid, x, 1024, -math.inf, fulls[id(x)])
