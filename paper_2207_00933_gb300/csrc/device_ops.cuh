@@ -26,8 +26,17 @@ __device__ __forceinline__ void merge_block(const MergeDesc& d, int64_t blk) {
     if (d.fast) {
       const float* src = row + (d.zoom_val | (b << d.m));
       if (run >= 4u * lanes) {
+        // four independent 16-byte loads in flight per lane and round
         const float4* s4 = reinterpret_cast<const float4*>(src);
-        for (uint32_t r = lane; r < run / 4; r += lanes) {
+        const uint32_t nv = run / 4;
+        uint32_t r = lane;
+        for (; r + 3u * lanes < nv; r += 4u * lanes) {
+          const float4 q0 = __ldg(s4 + r), q1 = __ldg(s4 + r + lanes);
+          const float4 q2 = __ldg(s4 + r + 2u * lanes), q3 = __ldg(s4 + r + 3u * lanes);
+          acc += (((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w))) +
+                 (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
+        }
+        for (; r < nv; r += lanes) {
           const float4 q = __ldg(s4 + r);
           acc += (q.x + q.y) + (q.z + q.w);
         }

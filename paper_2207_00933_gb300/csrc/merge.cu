@@ -16,23 +16,40 @@ namespace sqc {
 
 namespace {
 
-__global__ void __launch_bounds__(256) merge_kernel(const MergeDesc* __restrict__ descs, int n) {
+// Persistent: CTAs walk the blocks of all descriptors in order; a CTA
+// reads a descriptor (and where the next one starts) only when it crosses
+// into it.
+__global__ void __launch_bounds__(256) merge_kernel(const MergeDesc* __restrict__ descs, int n,
+                                                    int64_t total_blocks) {
   __shared__ MergeDesc d;
+  __shared__ int cur;
+  __shared__ int64_t next_begin;
   if (threadIdx.x == 0) {
-    int lo = 0;
-    for (int i = 1; i < n; ++i)
-      if (descs[i].block_begin <= int64_t(blockIdx.x)) lo = i;
-    d = descs[lo];
+    cur = -1;
+    next_begin = 0;
   }
   __syncthreads();
-  merge_block(d, int64_t(blockIdx.x) - d.block_begin);
+  for (int64_t blk = blockIdx.x; blk < total_blocks; blk += gridDim.x) {
+    if (threadIdx.x == 0 && blk >= next_begin) {
+      int i = cur < 0 ? 0 : cur;
+      while (i + 1 < n && descs[i + 1].block_begin <= blk) ++i;
+      d = descs[i];
+      cur = i;
+      next_begin = i + 1 < n ? descs[i + 1].block_begin : total_blocks;
+    }
+    __syncthreads();
+    merge_block(d, blk - d.block_begin);
+    __syncthreads();
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_merge_blocks(const MergeDesc* d_descs, int n, int64_t total_blocks, cudaStream_t s) {
   if (n <= 0 || total_blocks <= 0) return cudaSuccess;
-  merge_kernel<<<unsigned(total_blocks), 256, 0, s>>>(d_descs, n);
+  // 8 CTAs of 256 threads per SM
+  const int64_t grid = total_blocks < 152 * 8 ? total_blocks : 152 * 8;
+  merge_kernel<<<unsigned(grid), 256, 0, s>>>(d_descs, n, total_blocks);
   return cudaGetLastError();
 }
 
