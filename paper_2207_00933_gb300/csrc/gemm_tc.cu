@@ -58,6 +58,9 @@ struct TcCfg {
 };
 using CfgNarrow = TcCfg<128, 64, 2>;
 using CfgWide = TcCfg<256, 32, 3>;
+//   the same in 2-CTA pairs sharing B (a 16-deep, 6-stage, 32-byte-swizzle
+//   variant measured 19% slower)
+using CfgPair = CfgWide;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -103,17 +106,32 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// The same load delivered to every CTA of the cluster in `mask`, at the same
+// shared-memory offset, completing on the barrier at the same offset in each.
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, "
+      "{%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major tile of 8-row swizzle atoms
 // (rows of SW bytes: 128-byte or 64-byte swizzle), atoms 8 x SW bytes apart.
 template <int SW>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  static_assert(SW == 128 || SW == 64, "swizzle");
+  static_assert(SW == 128 || SW == 64 || SW == 32, "swizzle");
   uint64_t d = 0;
   d |= uint64_t((addr & 0x3FFFFu) >> 4);   // start address
   d |= uint64_t(1) << 16;                  // leading byte offset (unused for swizzled K-major)
   d |= uint64_t((8 * SW) >> 4) << 32;      // stride byte offset: next 8-row group
   d |= uint64_t(1) << 46;                  // descriptor version
-  d |= uint64_t(SW == 128 ? 2 : 4) << 61;  // swizzle mode
+  d |= uint64_t(SW == 128 ? 2 : (SW == 64 ? 4 : 6)) << 61;  // swizzle mode
   return d;
 }
 
@@ -132,6 +150,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+// Commit arriving on the barrier at the same offset in every CTA of `mask`.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 
 // 32 consecutive accumulator columns of this thread's TMEM lane (one
@@ -177,7 +204,12 @@ __device__ __forceinline__ void store16(const GemmTcArgs& a, uint64_t off, bool 
 // Persistent: grid = min(tiles, SMs); CTA b takes tiles b, b + grid, ...
 // The accumulator is double-buffered in TMEM (2 x BN columns) so that the
 // epilogue of one tile overlaps the loads and MMAs of the next.
-template <class Cfg>
+// PAIR: clusters of two CTAs on vertically adjacent tiles (same columns)
+// share every B tile: each CTA loads half of its rows and multicasts them to
+// both, so B is read from L2 once per pair.  A stage of either CTA is then
+// refilled only after both CTAs' MMAs have consumed it (the MMA commits
+// arrive on both CTAs' `empty` barriers).
+template <class Cfg, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmTcArgs a) {
   constexpr int kBN = Cfg::BN, kBK = Cfg::BK, kStages = Cfg::STAGES;
@@ -198,12 +230,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int tn_shift = __ffsll(tiles_n) - 1;
   const int64_t ntiles = (a.Mp / kBM) * tiles_n;
   const int nk = int(a.Kp / kBK);
+  // work units: tiles, or (PAIR) pairs of vertically adjacent tiles, this
+  // CTA taking the one of its cluster rank
+  uint32_t rank = 0;
+  if constexpr (PAIR) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const int64_t unit0 = PAIR ? int64_t(blockIdx.x >> 1) : int64_t(blockIdx.x);
+  const int64_t unit_step = PAIR ? int64_t(gridDim.x >> 1) : int64_t(gridDim.x);
+  const int64_t nunits = PAIR ? ntiles / 2 : ntiles;
+  auto tile_m0 = [&](int64_t u) -> int64_t { return ((u >> tn_shift) * (PAIR ? 2 : 1) + rank) * kBM; };
 
   if (threadIdx.x == 0) {
     failed = 0;
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], PAIR ? 2 : 1);     // PAIR: both CTAs' MMAs
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -221,6 +261,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // the partner's multicasts and commits target this CTA's barriers: both
+  // CTAs' barriers are initialised before either starts
+  if constexpr (PAIR) cluster_sync();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
@@ -229,9 +272,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: one continuous ring of stages across all tiles
     int64_t it = 0, issued = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-      const int m0 = int((tile >> tn_shift) * kBM);
-      const int n0 = int((tile & (tiles_n - 1)) * kBN);
+    for (int64_t u = unit0; u < nunits && !failed; u += unit_step) {
+      const int m0 = int(tile_m0(u));
+      const int n0 = int((u & (tiles_n - 1)) * kBN);
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = int(it % kStages);
         const int64_t use = it / kStages;
@@ -242,7 +285,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         uint8_t* st = smem + s * kStageBytes;
         mbar_expect_tx(&full[s], kStageBytes);
         for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
-        for (int p = 0; p < 3; ++p) tma_load_3d(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
+        if constexpr (PAIR) {
+          // this CTA's half of the B rows, to both CTAs
+          for (int p = 0; p < 3; ++p)
+            tma_load_3d_mc(st + 3 * kTileA + p * kTileB + int(rank) * (kTileB / 2), &tmB, kb * kBK,
+                           n0 + int(rank) * (kBN / 2), p, &full[s], uint16_t(0x3));
+        } else {
+          for (int p = 0; p < 3; ++p) tma_load_3d(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
+        }
         issued = it + 1;
       }
     }
@@ -254,7 +304,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
     constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
     int64_t it = 0, t = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++t) {
+    for (int64_t u = unit0; u < nunits && !failed; u += unit_step, ++t) {
       const int buf = int(t & 1);
       const int64_t use = t >> 1;
       if (use > 0 && !mbar_wait(&acc_empty[buf], uint32_t((use - 1) & 1))) {
@@ -281,7 +331,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           for (int kk = 0; kk < kBK / 16; ++kk)   // K = 16 per instruction: +32 bytes = +2 in the address field
             mma_bf16(dacc, da + 2 * kk, db + 2 * kk, Cfg::kIdesc, (kb | q | kk) != 0);
         }
-        mma_commit(&empty[s]);
+        if constexpr (PAIR) mma_commit_mc(&empty[s], uint16_t(0x3));
+        else mma_commit(&empty[s]);
       }
       mma_commit(&acc_full[buf]);
       if (!ok) break;
@@ -293,15 +344,15 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     const int half = (warp - 2) >> 2;
     const float alpha_f = float(a.alpha);
     int64_t t = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+    for (int64_t u = unit0; u < nunits; u += unit_step, ++t) {
       const int buf = int(t & 1);
       if (!mbar_wait(&acc_full[buf], uint32_t((t >> 1) & 1)) || failed) {
         atomicExch(&failed, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t m0 = (tile >> tn_shift) * kBM;
-      const int64_t n0 = (tile & (tiles_n - 1)) * kBN;
+      const int64_t m0 = tile_m0(u);
+      const int64_t n0 = (u & (tiles_n - 1)) * kBN;
       const int64_t row = m0 + quad * 32 + lane;
       const bool row_ok = row < a.M;
       const uint64_t rbase = row_ok ? a.rowmap[row] : 0;
@@ -335,6 +386,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  // neither CTA leaves while the partner may still signal its barriers
+  if constexpr (PAIR) cluster_sync();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
@@ -372,7 +425,8 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t Kp, int bk
   const cuuint32_t box[3] = {cuuint32_t(bk), cuuint32_t(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE,
+            bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B),
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -383,8 +437,56 @@ cudaError_t launch_cfg(const GemmTcArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
   const int64_t tiles = (a.Mp / kBM) * (a.Np / Cfg::BN);
   const int64_t grid = tiles < 152 ? tiles : 152;    // persistent: at most one CTA per SM
-  gemm_tc_kernel<Cfg><<<unsigned(grid), kThreads, Cfg::kSmemBytes, s>>>(ma, mb, a);
+  gemm_tc_kernel<Cfg, false><<<unsigned(grid), kThreads, Cfg::kSmemBytes, s>>>(ma, mb, a);
   return cudaGetLastError();
+}
+
+// Co-resident 2-CTA clusters of the pair kernel (0: none), once per process.
+int pair_clusters() {
+  static int n = -1;
+  if (n < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(152, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = CfgPair::kSmemBytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, gemm_tc_kernel<CfgPair, true>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      c = 0;
+    }
+    n = c < 76 ? c : 76;
+  }
+  return n;
+}
+
+cudaError_t launch_pair(const GemmTcArgs& a, int clusters, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  // B is loaded in halves (BN / 2 rows) by the two CTAs of a pair
+  if (!make_map(&ma, a.A, a.Mp, a.Kp, CfgPair::BK, kBM) ||
+      !make_map(&mb, a.B, a.Np, a.Kp, CfgPair::BK, CfgPair::BN / 2))
+    return cudaErrorInvalidValue;
+  const int64_t units = (a.Mp / (2 * kBM)) * (a.Np / CfgPair::BN);
+  const int64_t nc = units < clusters ? units : clusters;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(unsigned(2 * nc), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = CfgPair::kSmemBytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<CfgPair, true>, ma, mb, a);
 }
 
 }  // namespace
@@ -395,11 +497,14 @@ int gemm_tc_min_rows() { return kBM; }
 int gemm_tc_k_align() { return kKAlign; }
 
 cudaError_t gemm_tc_configure() {
-  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<CfgNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       CfgNarrow::kSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<CfgNarrow, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, CfgNarrow::kSmemBytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gemm_tc_kernel<CfgWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(gemm_tc_kernel<CfgWide, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              CfgWide::kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(gemm_tc_kernel<CfgPair, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             CfgPair::kSmemBytes);
   return e;
 }
 
@@ -412,8 +517,14 @@ cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s) {
   // TMA wants 16-byte aligned global operands (the 1024-byte alignment the
   // swizzle needs applies to the shared-memory stages only)
   if ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 15) return cudaErrorInvalidValue;
-  // 256-wide tiles when they still fill every SM at least once
-  if (a.Np % 256 == 0 && (a.Mp / kBM) * (a.Np / 256) >= 152) return launch_cfg<CfgWide>(a, s);
+  // 256-wide tiles when they still fill every SM at least once; in pairs
+  // sharing B when the row tiles pair up and the pairs fill the clusters
+  if (a.Np % 256 == 0 && (a.Mp / kBM) * (a.Np / 256) >= 152) {
+    const int clusters = pair_clusters();
+    if (a.Mp % (2 * kBM) == 0 && clusters > 0 && (a.Mp / (2 * kBM)) * (a.Np / 256) >= clusters)
+      return launch_pair(a, clusters, s);
+    return launch_cfg<CfgWide>(a, s);
+  }
   return launch_cfg<CfgNarrow>(a, s);
 }
 
