@@ -145,7 +145,10 @@ SQC_API const char* sqc_last_error(const sqc_ctx* ctx);
  *   probs[i]: subcircuit i's outputs, [4^{k_i}][2^{w_i}] row-major,
  *             w_i = n_data[i] + #outgoing edges of i, in `dtype`;
  *             host pointers if probs_on_device == 0 (copied, then
- *             synchronised), else device pointers (read on `stream`).
+ *             synchronised; while `stream` is being captured into a CUDA
+ *             graph there is no synchronisation, and the buffers must be
+ *             pinned and stay valid for every replay), else device
+ *             pointers (read on `stream`).
  * On success *out_id names the circuit until sqc_unload. */
 SQC_API sqc_status sqc_load_subcircuit_outputs(sqc_ctx* ctx, const sqc_graph* graph,
                                                const void* const* probs, sqc_dtype dtype,

@@ -410,7 +410,14 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
   }
   sqc_status st = flush();
   if (st != SQC_OK) return st;
-  if (!on_device) CK(cudaStreamSynchronize(s));
+  if (!on_device) {
+    // host inputs: the caller may reuse its buffers on return, except while
+    // the stream is captured into a graph (no synchronisation is allowed
+    // there; the graph's copies then read the pinned buffers at every replay)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) CK(cudaStreamSynchronize(s));
+  }
   return SQC_OK;
 }
 
