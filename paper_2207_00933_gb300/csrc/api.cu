@@ -377,11 +377,16 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
       d.L1 = L1;
       d.L2 = L2;
       d.vec = L1 == 5 && L2 == 3 && dtype != SQC_F64 && (reinterpret_cast<uintptr_t>(src[i]) % 16) == 0;
+      d.async2 = d.vec && kout == 0 && kin >= 1 && S <= 32;
       for (int t = 0; t < kin; ++t) d.inshift[t] = digit_shift(*c, i, c->ins[i][t]);
       for (int u = 0; u < kout; ++u) d.outshift[u] = digit_shift(*c, i, c->outs[i][u]);
       d.block_begin = blocks;
-      blocks += (int64_t(1) << (n - L1 - L2)) << (2 * kout);
-      smem = std::max(smem, int(S << (L1 + L2)) * 4);
+      // a 4-state-per-thread CTA takes 4 tiles at once when there is a
+      // single prepared-state row (no incoming edges): one per 64 threads
+      const int64_t tiles_i = (int64_t(1) << (n - L1 - L2)) << (2 * kout);
+      blocks += (d.vec && kin == 0) ? tiles_i / 4 : tiles_i;
+      d.block_end = blocks;
+      smem = std::max(smem, int((d.vec && kin == 0 ? 4 : (d.async2 ? 2 * S : S)) << (L1 + L2)) * 4);
       if (++L.n == kAttrPerLaunch) {
         sqc_status st = flush();
         if (st != SQC_OK) return st;

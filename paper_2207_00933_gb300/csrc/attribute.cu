@@ -351,6 +351,118 @@ __device__ __forceinline__ void attr_tile_v4(const AttrDesc& d, const AttrTileCt
   }
 }
 
+// No incoming edges (a single prepared-state row): work unit t is the four
+// tiles 4t .. 4t+3, one per 64-thread group, each group folding the
+// outcomes of its 256 states (4 per thread) and writing them through its
+// own 256-float region of shared memory.
+__device__ __forceinline__ void attr_tiles_v4_kin0(const AttrDesc& d, int64_t t, float* val) {
+  const int g4 = int(threadIdx.x) >> 6;
+  const uint64_t tt = uint64_t(t) * 4 + uint64_t(g4);
+  const uint64_t o = tt & ((uint64_t(1) << (2 * d.kout)) - 1);
+  const uint64_t xm = tt >> (2 * d.kout);
+  const int n = d.n;
+  uint64_t vbase = 0;
+  uint32_t signed_mask = 0;
+  for (int u = 0; u < d.kout; ++u) {
+    const uint64_t dig = (o >> (2 * u)) & 3;
+    vbase |= dig << d.outshift[u];
+    if (dig) signed_mask |= 1u << u;
+  }
+  const int g = int(threadIdx.x) & 63;
+  const int j0 = 4 * g;
+  const uint64_t x0 = uint64_t(j0 & 31) | (xm << 5) | (uint64_t(j0 >> 5) << (n - 3));
+  const int pos = slot_pos(j0, 5, 3);
+  float* mine = val + g4 * 256;
+  const float* p = static_cast<const float*>(d.p) + (vbase << (n + d.kout)) + x0;
+  const int nc = 1 << d.kout;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c0 = 0; c0 < nc; c0 += 4) {
+    float4 w[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc)
+      w[cc] = c0 + cc < nc ? __ldg(reinterpret_cast<const float4*>(p + (uint64_t(c0 + cc) << n)))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const float sg = (__popc(uint32_t(c0 + cc) & signed_mask) & 1) ? -1.f : 1.f;
+      acc.x = fmaf(sg, w[cc].x, acc.x);
+      acc.y = fmaf(sg, w[cc].y, acc.y);
+      acc.z = fmaf(sg, w[cc].z, acc.z);
+      acc.w = fmaf(sg, w[cc].w, acc.w);
+    }
+  }
+  *reinterpret_cast<float4*>(mine + pos) = acc;
+  __syncthreads();
+  const int jl = g >> 1, r0 = (g & 1) * 4;
+  float o4[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o4[q] = mine[slot_pos(jl | (int(__brev(uint32_t(r0 + q)) >> 29) << 5), 5, 3)];
+  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << 5)), n) + uint64_t(r0);
+  *reinterpret_cast<float4*>(d.A + (vbase << n) + xw) = make_float4(o4[0], o4[1], o4[2], o4[3]);
+}
+
+// ---- double-buffered form (no outgoing edges, 4^kin <= 32): the rows of
+// the next tile are copied into the other half of shared memory by
+// cp.async while this tile is expanded and written
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(uint32_t(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// the 4^kin rows of tile t into buf (states in the swizzled slots)
+__device__ __forceinline__ void v4_issue(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* buf) {
+  const uint64_t xm = uint64_t(t);                  // no outgoing edges: tile = x middle bits
+  const int S = 1 << (2 * d.kin), n = d.n;
+  const int j0 = 4 * (int(threadIdx.x) & 63);
+  const uint64_t x0 = uint64_t(j0 & 31) | (xm << 5) | (uint64_t(j0 >> 5) << (n - 3));
+  const int pos = slot_pos(j0, 5, 3);
+  const float* p = static_cast<const float*>(d.p);
+  for (int s = int(threadIdx.x) >> 6; s < S; s += 4) cp_async16(buf + s * 256 + pos, p + (in_digits(tc, s) << n) + x0);
+}
+
+// expansion of the incoming edges and the bit-reversed write of tile t
+__device__ __forceinline__ void v4_finish(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
+  const uint64_t xm = uint64_t(t);
+  const int S = 1 << (2 * d.kin), n = d.n;
+  const int g = int(threadIdx.x) & 63;
+  const int pos = slot_pos(4 * g, 5, 3);
+  for (int q = 0; q < d.kin; ++q) {
+    const int lowmask = (1 << (2 * q)) - 1;
+    const int st = 256 << (2 * q);
+    for (int gg = int(threadIdx.x) >> 6; gg < (S >> 2); gg += 4) {
+      const int s0 = ((gg & ~lowmask) << 2) | (gg & lowmask);
+      float* a = val + s0 * 256 + pos;
+      const float4 v0 = *reinterpret_cast<const float4*>(a);
+      const float4 v1 = *reinterpret_cast<const float4*>(a + st);
+      const float4 v2 = *reinterpret_cast<const float4*>(a + 2 * st);
+      const float4 v3 = *reinterpret_cast<const float4*>(a + 3 * st);
+      const float4 sm = make_float4(v0.x + v1.x, v0.y + v1.y, v0.z + v1.z, v0.w + v1.w);
+      *reinterpret_cast<float4*>(a) = sm;
+      *reinterpret_cast<float4*>(a + st) =
+          make_float4(2.f * v2.x - sm.x, 2.f * v2.y - sm.y, 2.f * v2.z - sm.z, 2.f * v2.w - sm.w);
+      *reinterpret_cast<float4*>(a + 2 * st) =
+          make_float4(2.f * v3.x - sm.x, 2.f * v3.y - sm.y, 2.f * v3.z - sm.z, 2.f * v3.w - sm.w);
+      *reinterpret_cast<float4*>(a + 3 * st) = make_float4(v0.x - v1.x, v0.y - v1.y, v0.z - v1.z, v0.w - v1.w);
+    }
+    __syncthreads();
+  }
+  const int jl = g >> 1, r0 = (g & 1) * 4;
+  int pw[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) pw[q] = slot_pos(jl | (int(__brev(uint32_t(r0 + q)) >> 29) << 5), 5, 3);
+  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << 5)), n) + uint64_t(r0);
+  for (int s = int(threadIdx.x) >> 6; s < S; s += 4) {
+    const float* v = val + s * 256;
+    *reinterpret_cast<float4*>(d.A + (in_digits(tc, s) << n) + xw) = make_float4(v[pw[0]], v[pw[1]], v[pw[2]], v[pw[3]]);
+  }
+}
+
 __device__ void fill_tile_ctx(const AttrDesc& d, AttrTileCtx& t) {
   for (int i = threadIdx.x; i < 256 + 64; i += blockDim.x) {
     const int s = i < 256 ? i : ((i - 256) << 8);
@@ -365,13 +477,15 @@ __device__ void fill_tile_ctx(const AttrDesc& d, AttrTileCtx& t) {
 // descriptor into shared memory only when it crosses into it (constant
 // parameter offsets only: a dynamic index into the parameter block would copy
 // all of it to local memory in every thread).
-__global__ void __launch_bounds__(256) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
+__global__ void __launch_bounds__(256, 4) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
   extern __shared__ float val[];
   __shared__ AttrDesc d;
   __shared__ AttrTileCtx tc;
   __shared__ int cur, changed;
   if (threadIdx.x == 0) cur = -1;
   __syncthreads();
+  bool have_next = false;                 // the double-buffered form copied this tile already
+  int half = 0;                           // its current half of shared memory
   for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     if (threadIdx.x == 0) {
       int di = 0;
@@ -396,7 +510,30 @@ __global__ void __launch_bounds__(256) attr_fused_kernel(AttrLaunch L, int64_t t
       fill_tile_ctx(d, tc);
       __syncthreads();
     }
-    if (d.vec)
+    if (d.async2) {
+      const int64_t t = tile - d.block_begin;
+      const int rows = (1 << (2 * d.kin)) * 256;
+      float* cur_buf = val + half * rows;
+      if (!have_next) {
+        v4_issue(d, tc, t, cur_buf);
+        cp_async_commit();
+      }
+      // this CTA's next tile, when it is of the same subcircuit
+      const bool next = tile + gridDim.x < d.block_end;
+      if (next) {
+        v4_issue(d, tc, t + gridDim.x, val + (half ^ 1) * rows);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      v4_finish(d, tc, t, cur_buf);
+      have_next = next;
+      if (next) half ^= 1;
+    } else if (d.vec && d.kin == 0)
+      attr_tiles_v4_kin0(d, tile - d.block_begin, val);
+    else if (d.vec)
       attr_tile_v4(d, tc, tile - d.block_begin, val);
     else
       attr_tile(d, tc, tile - d.block_begin, val);
@@ -423,11 +560,20 @@ cudaError_t launch_fold(const FoldArgs& a, cudaStream_t s) {
 
 cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s) {
   if (L.n <= 0 || blocks <= 0) return cudaSuccess;
-  // persistent grid: as many CTAs as fit on the 152 SMs at once (256
-  // threads each, at most 8 per SM; shared memory 227 KB per SM)
-  const int64_t per_sm_smem = (227 * 1024) / (smem_bytes + 4096);
-  const int64_t per_sm = per_sm_smem < 8 ? (per_sm_smem < 1 ? 1 : per_sm_smem) : 8;
-  const int64_t grid = blocks < 152 * per_sm ? blocks : 152 * per_sm;
+  // persistent grid: exactly as many CTAs as are resident at once (limited
+  // by registers and shared memory), so that no CTA's tile list starts
+  // after the others have finished theirs
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, attr_fused_kernel, 256, smem_bytes) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t grid = blocks < int64_t(sms) * per_sm ? blocks : int64_t(sms) * per_sm;
   attr_fused_kernel<<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
   return cudaGetLastError();
 }

@@ -49,9 +49,11 @@ struct AttrDesc {
   int n, kin, kout;
   int L1, L2;                 // x tile: 2^L1 low values x 2^L2 top-bit values
   int vec;                    // 32 x 8 tile, FP32 input, 16-byte aligned: 4 states per thread
+  int async2;                 // vec, no outgoing edges, 4^kin <= 32: loads double-buffered by cp.async
   int inshift[kMaxFusedIn];
   int outshift[16];
   int64_t block_begin;
+  int64_t block_end;           // first block of the next descriptor
 };
 struct AttrLaunch {
   AttrDesc d[kAttrPerLaunch];
