@@ -49,6 +49,11 @@ METRIC = "recon bins/s"
 UNIT = "bins/s"
 TOPK = 1024
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of
+# `bench.py --steps 3 --warmup 3 --no-extras --no-cpu-baseline` on this
+# workload; to be re-taken (or dropped) whenever that kernel changes
+NCU_TRAFFIC = {("line30_K8_a20", "fp32", "select_resident_kernel"): 4292608 + 256}
 
 
 def parse():
@@ -612,8 +617,10 @@ def main():
     kernel_of = {"attribute": "attr_fused_kernel", "merge": "merge_kernel", "contract": "gemm_simt_kernel",
                  "final": "gemm_simt_kernel (last step)",
                  "select": "select_resident_kernel" if (1 << na) <= 7_000_000 else "select_coop_kernel"}
+    traffic = NCU_TRAFFIC.get((args.workload, prec, kernel_of[dom]))
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                "algorithmic_bytes": algo[dom],
                 "stages": {k: {"us": 1e3 * stage_ms[k], "share": share[k],
                                "GBps": algo[k] / (stage_ms[k] * 1e-3) / 1e9} for k in stage_ms}}
 
