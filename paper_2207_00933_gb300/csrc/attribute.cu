@@ -477,7 +477,10 @@ __device__ void fill_tile_ctx(const AttrDesc& d, AttrTileCtx& t) {
 // descriptor into shared memory only when it crosses into it (constant
 // parameter offsets only: a dynamic index into the parameter block would copy
 // all of it to local memory in every thread).
-__global__ void __launch_bounds__(256, 4) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
+// VEC: every descriptor of the launch takes a 4-state-per-thread form, so
+// the one-state paths (and their registers) are left out.
+template <bool VEC>
+__global__ void __launch_bounds__(256, VEC ? 6 : 4) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
   extern __shared__ float val[];
   __shared__ AttrDesc d;
   __shared__ AttrTileCtx tc;
@@ -531,12 +534,13 @@ __global__ void __launch_bounds__(256, 4) attr_fused_kernel(AttrLaunch L, int64_
       v4_finish(d, tc, t, cur_buf);
       have_next = next;
       if (next) half ^= 1;
-    } else if (d.vec && d.kin == 0)
+    } else if (d.vec && d.kin == 0) {
       attr_tiles_v4_kin0(d, tile - d.block_begin, val);
-    else if (d.vec)
+    } else if (VEC || d.vec) {
       attr_tile_v4(d, tc, tile - d.block_begin, val);
-    else
+    } else {
       attr_tile(d, tc, tile - d.block_begin, val);
+    }
     __syncthreads();
   }
 }
@@ -569,17 +573,27 @@ cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_byte
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
   }
+  bool all_vec = true;
+  for (int i = 0; i < L.n; ++i) all_vec = all_vec && L.d[i].vec;
+  const void* fn = all_vec ? reinterpret_cast<const void*>(attr_fused_kernel<true>)
+                           : reinterpret_cast<const void*>(attr_fused_kernel<false>);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, attr_fused_kernel, 256, smem_bytes) != cudaSuccess ||
-      per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem_bytes) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int64_t grid = blocks < int64_t(sms) * per_sm ? blocks : int64_t(sms) * per_sm;
-  attr_fused_kernel<<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
+  if (all_vec)
+    attr_fused_kernel<true><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
+  else
+    attr_fused_kernel<false><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
   return cudaGetLastError();
 }
 
 cudaError_t attr_configure() {
-  return cudaFuncSetAttribute(attr_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
+  cudaError_t e = cudaFuncSetAttribute(attr_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kAttrSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(attr_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
+  return e;
 }
 
 cudaError_t launch_mix(const MixArgs& a, cudaStream_t s) {
