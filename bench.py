@@ -357,6 +357,22 @@ def batch_bench(dev, reps: int = 10) -> dict:
         res["batch_vs_plain_fp32"] = res["plain_fp32"]["ms"] / res["batch_fp32"]["ms"]
         res["bins"] = bins
         ctx.batch_release(bid)
+    # the same batch with the merge pyramid (merges read the level that
+    # holds the sums over each subcircuit's merged qubits)
+    with Context(dev.index or 0, merge_pyramid=True) as ctx:
+        cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).to(dev) for p in ps])
+                for c, ps in zip(b.circuits, b.probs)]
+        qs = [ctx.set_qubit_roles(cids[ci], roles) for ci, roles in b.queries]
+        bid = ctx.batch_create([q for q, _ in qs], outs, totals)
+        graph = torch.cuda.CUDAGraph()
+        ctx.batch_run(bid)
+        with torch.cuda.graph(graph):
+            ctx.batch_run(bid)
+        ms = timed(graph.replay)
+        ctx.batch_status(bid)
+        res["batch_fp32_pyramid"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "launches": 1,
+                                     "max_abs_err_vs_fp64": err()}
+        ctx.batch_release(bid)
     return res
 
 

@@ -103,7 +103,16 @@ typedef struct {
    * or FP64 values on 152 SMs; one read of the input); 0 = always the
    * streaming kernel. */
   int32_t select_resident;
-  int32_t reserved[3];
+  /* Merge pyramid (1 = on, default 0): after every attribution, also keep
+   * the partial marginals of each A_i over its 1, 2, ..., n_i lowest
+   * storage bits (pairwise sums; about as much memory again as A_i, counted
+   * in the HBM budget).  A query whose merged qubits of a subcircuit are
+   * exactly its highest data qubits (the recursion's roles) then reads
+   * 4^{k_i} 2^{a_i} values instead of 4^{k_i} 2^{a_i + m_i}.  Worth it when
+   * many queries share one load; it adds a pass over A_i to every load and
+   * update. */
+  int32_t merge_pyramid;
+  int32_t reserved[2];
 } sqc_config;
 
 /* Compute graph (Section 5, Fig. 3d).  Vertices are subcircuits 0..n_C-1;

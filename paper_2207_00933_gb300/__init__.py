@@ -38,7 +38,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_active_qubits", ctypes.c_int32),
                 ("fp64_chunk_min_edges", ctypes.c_int32), ("chunk_terms", ctypes.c_int32),
                 ("slice_edges", ctypes.c_int32), ("select_resident", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("merge_pyramid", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Graph(ctypes.Structure):
@@ -148,7 +148,7 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_active_qubits: int = 32,
                  fp64_chunk_min_edges: int = 12, chunk_terms: int = 256, slice_edges: int = 0,
-                 select_resident: bool = True):
+                 select_resident: bool = True, merge_pyramid: bool = False):
         self._lib = load_library()
         cfg = _Config()
         self._lib.sqc_default_config(ctypes.byref(cfg))
@@ -158,6 +158,7 @@ class Context:
         cfg.chunk_terms = chunk_terms
         cfg.slice_edges = slice_edges
         cfg.select_resident = int(bool(select_resident))
+        cfg.merge_pyramid = int(bool(merge_pyramid))
         h = _P()
         st = self._lib.sqc_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != 0:

@@ -33,6 +33,10 @@ struct Circuit {
   std::vector<int64_t> V;        // 4^k_i
   std::vector<int> w;            // n_i + kout_i
   std::vector<float*> A;         // [V_i][2^n_i], data index bit-reversed
+  // merge pyramid (cfg.merge_pyramid): level m = 1..n_i of subcircuit i at
+  // pyr[i] + V_i (2^n_i - 2^(n_i-m+1)), [V_i][2^(n_i-m)], the sums of A_i
+  // over its m lowest storage bits
+  std::vector<float*> pyr;
   void* staging = nullptr;       // device copy of one subcircuit's host input
   size_t staging_bytes = 0;
   float* scratch = nullptr;      // fold output for subcircuits with incoming edges
@@ -415,6 +419,11 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
   }
   sqc_status st = flush();
   if (st != SQC_OK) return st;
+  for (size_t i = 0; i < c->pyr.size(); ++i)
+    if (c->pyr[i]) {
+      CK(launch_pyramid(c->A[i], c->pyr[i], c->V[i], c->ndata[i], s));
+      ctx->launches += (c->ndata[i] + kPyramidLevelsPerPass - 1) / kPyramidLevelsPerPass;
+    }
   if (!on_device) {
     // host inputs: the caller may reuse its buffers on return, except while
     // the stream is captured into a graph (no synchronisation is allowed
@@ -440,6 +449,8 @@ void free_query(sqc_ctx* ctx, Query* q) {
 void free_circuit(sqc_ctx* ctx, Circuit* c) {
   for (int i = 0; i < c->nC; ++i)
     if (c->A[i]) dev_free(ctx, c->A[i], size_t(c->V[i]) * (size_t(1) << c->ndata[i]) * 4);
+  for (size_t i = 0; i < c->pyr.size(); ++i)
+    if (c->pyr[i]) dev_free(ctx, c->pyr[i], size_t(c->V[i]) * (size_t(1) << c->ndata[i]) * 4);
   dev_free(ctx, c->staging, c->staging_bytes);
   dev_free(ctx, c->scratch, c->scratch_floats * 4);
 }
@@ -586,6 +597,16 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     d.a = popc32(act);
     d.m = popc32(mer);
     d.fast = (mer == ((1u << d.m) - 1u)) && (act == (((1u << d.a) - 1u) << d.m));
+    if (d.fast && d.m > 0 && i < int(c.pyr.size()) && c.pyr[i]) {
+      // read the pyramid level holding the sums over the m merged bits
+      const int m = d.m;
+      d.A = c.pyr[i] + size_t(c.V[i]) * ((size_t(1) << n) - (size_t(1) << (n - m + 1)));
+      d.n = n - m;
+      d.act_mask = act >> m;
+      d.mer_mask = 0;
+      d.zoom_val = zval >> m;
+      d.m = 0;
+    }
     const uint32_t run = 1u << d.m;
     int lanes = d.fast ? int(run / 16) : int(run / 4);
     d.lanes = std::max(1, std::min(32, lanes));
@@ -868,6 +889,8 @@ SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg) 
     return fail(nullptr, SQC_EINVAL, "slice_edges must be in [0, 8]");
   if (ctx->cfg.select_resident != 0 && ctx->cfg.select_resident != 1)
     return fail(nullptr, SQC_EINVAL, "select_resident must be 0 or 1");
+  if (ctx->cfg.merge_pyramid != 0 && ctx->cfg.merge_pyramid != 1)
+    return fail(nullptr, SQC_EINVAL, "merge_pyramid must be 0 or 1");
   DeviceGuard g(device);
   e = select_configure();
   if (e == cudaSuccess) e = attr_configure();
@@ -919,6 +942,16 @@ SQC_API sqc_status sqc_load_subcircuit_outputs(sqc_ctx* ctx, const sqc_graph* gr
     st = dev_alloc(ctx, &p, size_t(c->V[i]) * (size_t(1) << c->ndata[i]) * 4);
     if (st != SQC_OK) return cleanup(st);
     c->A[i] = static_cast<float*>(p);
+  }
+  if (ctx->cfg.merge_pyramid) {
+    c->pyr.assign(c->nC, nullptr);
+    for (int i = 0; i < c->nC; ++i) {
+      if (c->ndata[i] == 0) continue;
+      void* p = nullptr;
+      st = dev_alloc(ctx, &p, size_t(c->V[i]) * (size_t(1) << c->ndata[i]) * 4);
+      if (st != SQC_OK) return cleanup(st);
+      c->pyr[i] = static_cast<float*>(p);
+    }
   }
   if (!probs_on_device) {
     c->staging_bytes = stage;

@@ -88,6 +88,11 @@ struct MergeDesc {
 constexpr int kMaxMerge = 64;
 // descs: device array of n descriptors; total_blocks = CTAs over all of them
 cudaError_t launch_merge_blocks(const MergeDesc* descs, int n, int64_t total_blocks, cudaStream_t s);
+// Merge pyramid of one subcircuit (A: [V][2^n]): level m = 1..n at
+// pyr + V (2^n - 2^(n-m+1)), [V][2^(n-m)], level m = pairwise sums of level
+// m-1 (level 0 = A).  One launch per kPyramidLevelsPerPass levels.
+constexpr int kPyramidLevelsPerPass = 10;
+cudaError_t launch_pyramid(const float* A, float* pyr, int64_t V, int n, cudaStream_t s);
 
 // ---- contraction step, FP32 SIMT (Section 6.1: C = A B over the shared index)
 struct GemmArgs {

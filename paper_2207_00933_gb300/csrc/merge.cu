@@ -43,7 +43,60 @@ __global__ void __launch_bounds__(256) merge_kernel(const MergeDesc* __restrict_
   }
 }
 
+// Levels s+1 .. s+c of the merge pyramid from level s: a CTA takes chunks
+// of 2^c consecutive values of one row, halves them c times in shared
+// memory (pairwise sums) and writes every level's share.
+__global__ void __launch_bounds__(256) pyramid_kernel(const float* __restrict__ src, float* pyr, int64_t V, int n,
+                                                      int s, int c) {
+  __shared__ float buf[1 << kPyramidLevelsPerPass];
+  const int C = 1 << c;
+  const int row_shift = n - s - c;                   // chunks per row = 2^row_shift
+  const int64_t total = V << row_shift;
+  for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int64_t e = b >> row_shift;
+    const int64_t ch = b & ((int64_t(1) << row_shift) - 1);
+    const float* in = src + (e << (n - s)) + (ch << c);
+    for (int i = threadIdx.x; i < C; i += blockDim.x) buf[i] = in[i];
+    __syncthreads();
+    for (int l = 1; l <= c; ++l) {
+      const int half = C >> l;
+      const int m = s + l;
+      float* out = pyr + V * ((int64_t(1) << n) - (int64_t(1) << (n - m + 1))) + (e << (n - m)) + (ch << (c - l));
+      float t[(1 << kPyramidLevelsPerPass) / 2 / 256];
+#pragma unroll
+      for (int k = 0; k < int(sizeof(t) / sizeof(float)); ++k) {
+        const int i = int(threadIdx.x) + k * 256;
+        t[k] = i < half ? buf[2 * i] + buf[2 * i + 1] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < int(sizeof(t) / sizeof(float)); ++k) {
+        const int i = int(threadIdx.x) + k * 256;
+        if (i < half) {
+          buf[i] = t[k];
+          out[i] = t[k];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pyramid(const float* A, float* pyr, int64_t V, int n, cudaStream_t s) {
+  for (int lev = 0; lev < n;) {
+    const int c = n - lev < kPyramidLevelsPerPass ? n - lev : kPyramidLevelsPerPass;
+    const float* src = lev == 0 ? A : pyr + V * ((int64_t(1) << n) - (int64_t(1) << (n - lev + 1)));
+    const int64_t total = V << (n - lev - c);
+    const int64_t grid = total < 152 * 8 ? total : 152 * 8;
+    pyramid_kernel<<<unsigned(grid), 256, 0, s>>>(src, pyr, V, n, lev, c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    lev += c;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_merge_blocks(const MergeDesc* d_descs, int n, int64_t total_blocks, cudaStream_t s) {
   if (n <= 0 || total_blocks <= 0) return cudaSuccess;
