@@ -384,7 +384,8 @@ def serving_bench(dev, rates=(100, 300, 1000, 3000, 5000), seconds: float = 0.6,
     continuous-batching server and the plain one-query-per-launch FP32
     server are offered the same seeded arrival sequence; latency is submit
     to completion on the server's clock, throughput = bins completed / wall
-    time from first submission to last completion."""
+    time from first submission to last completion.  `batched_pyramid` is
+    the batching server on a context with the merge pyramid."""
     import torch
     from paper_2207_00933_gb300 import Context, Server
     from synthetic import workloads as W
@@ -392,9 +393,9 @@ def serving_bench(dev, rates=(100, 300, 1000, 3000, 5000), seconds: float = 0.6,
     rng = np.random.default_rng(12)
     out = {"workload": f"8 circuits {b.meta['n_qubits']} qubits, cuts {b.meta['cuts']}, "
                        f"subcircuits {b.meta['subcircuits']}; queries: zoom prefix + 12-20 active"}
-    for mode in ("batched", "plain"):
+    for mode in ("batched", "plain", "batched_pyramid"):
         res = {}
-        ctx = Context(dev.index or 0)
+        ctx = Context(dev.index or 0, merge_pyramid=(mode == "batched_pyramid"))
         cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(),
                                             [torch.from_numpy(p).to(dev) for p in ps])
                 for c, ps in zip(b.circuits, b.probs)]
