@@ -112,6 +112,17 @@ typedef struct {
    * many queries share one load; it adds a pass over A_i to every load and
    * update. */
   int32_t merge_pyramid;
+  /* Budget-driven index slicing (Section 6.3), applied after slice_edges:
+   * first level -- keep writing out the cut edge that shrinks
+   * sum_i 4^{k_i} 2^{a_i} (the merged subcircuit tensors, in floats) most
+   * until that sum is <= 2^slice_input_log2; second level -- then keep
+   * writing out the edge that shrinks the largest intermediate tensor of
+   * the contraction most (ties: smaller input sum, then lower edge id)
+   * until every intermediate is <= 2^slice_intermediate_log2 floats.
+   * 0 = off.  At most 8 edges are sliced in all; a query whose budgets
+   * would need more fails with SQC_ESHAPE. */
+  int32_t slice_input_log2;
+  int32_t slice_intermediate_log2;
   int32_t reserved[2];
 } sqc_config;
 

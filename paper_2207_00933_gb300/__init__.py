@@ -38,7 +38,8 @@ class _Config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_active_qubits", ctypes.c_int32),
                 ("fp64_chunk_min_edges", ctypes.c_int32), ("chunk_terms", ctypes.c_int32),
                 ("slice_edges", ctypes.c_int32), ("select_resident", ctypes.c_int32),
-                ("merge_pyramid", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("merge_pyramid", ctypes.c_int32), ("slice_input_log2", ctypes.c_int32),
+                ("slice_intermediate_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Graph(ctypes.Structure):
@@ -148,7 +149,8 @@ class Context:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_active_qubits: int = 32,
                  fp64_chunk_min_edges: int = 12, chunk_terms: int = 256, slice_edges: int = 0,
-                 select_resident: bool = True, merge_pyramid: bool = False):
+                 select_resident: bool = True, merge_pyramid: bool = False, slice_input_log2: int = 0,
+                 slice_intermediate_log2: int = 0):
         self._lib = load_library()
         cfg = _Config()
         self._lib.sqc_default_config(ctypes.byref(cfg))
@@ -159,6 +161,8 @@ class Context:
         cfg.slice_edges = slice_edges
         cfg.select_resident = int(bool(select_resident))
         cfg.merge_pyramid = int(bool(merge_pyramid))
+        cfg.slice_input_log2 = slice_input_log2
+        cfg.slice_intermediate_log2 = slice_intermediate_log2
         h = _P()
         st = self._lib.sqc_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != 0:

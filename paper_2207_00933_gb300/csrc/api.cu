@@ -518,7 +518,7 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     }
     return tot;
   };
-  for (int sidx = 0; sidx < ctx->cfg.slice_edges && int(sliced.size()) < c.K; ++sidx) {
+  auto slice_one = [&]() {
     int best = -1;
     double best_size = 0;
     for (int e = 0; e < c.K; ++e) {
@@ -530,6 +530,75 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     }
     sliced.insert(best);
     P->sliced.push_back(best);
+  };
+  for (int sidx = 0; sidx < ctx->cfg.slice_edges && int(sliced.size()) < c.K; ++sidx) slice_one();
+  constexpr int kMaxSliced = 8;
+  // first level by budget: the paper's rule (slice until the inputs fit)
+  if (ctx->cfg.slice_input_log2 > 0) {
+    const double budget = std::ldexp(1.0, ctx->cfg.slice_input_log2);
+    while (total_size(sliced) > budget) {
+      if (int(sliced.size()) >= std::min(c.K, kMaxSliced))
+        return fail(ctx, SQC_ESHAPE, "slicing: the input budget needs more than 8 sliced edges");
+      slice_one();
+    }
+  }
+  // second level: the largest intermediate of the greedy contraction order
+  // (the same rule as below, on tensor summaries: open edges, bins)
+  auto max_intermediate = [&](const std::set<int>& sl) {
+    struct Sum { std::set<int> edges; int bins; };
+    std::vector<Sum> alive_t;
+    for (int i = 0; i < nC; ++i) {
+      Sum s{{}, a_of[i]};
+      for (int e : c.inc[i]) if (!sl.count(e)) s.edges.insert(e);
+      alive_t.push_back(s);
+    }
+    double worst = 0;
+    while (alive_t.size() > 1) {
+      int bx = -1, by = -1;
+      double best = 0, best_out = 0;
+      bool best_conn = false;
+      for (size_t x = 0; x < alive_t.size(); ++x)
+        for (size_t y = x + 1; y < alive_t.size(); ++y) {
+          int sh = 0;
+          for (int e : alive_t[x].edges) sh += int(alive_t[y].edges.count(e));
+          const bool conn = sh > 0;
+          const double fx = 2.0 * double(alive_t[x].edges.size()) + alive_t[x].bins - 2.0 * sh;
+          const double fy = 2.0 * double(alive_t[y].edges.size()) + alive_t[y].bins - 2.0 * sh;
+          const double out = std::ldexp(1.0, int(fx + fy));
+          const double cost = std::ldexp(1.0, int(fx + fy + 2 * sh));
+          bool better;
+          if (bx < 0) better = true;
+          else if (conn != best_conn) better = conn;
+          else better = cost < best || (cost == best && out < best_out);
+          if (better) { bx = int(x); by = int(y); best = cost; best_out = out; best_conn = conn; }
+        }
+      Sum z{{}, alive_t[bx].bins + alive_t[by].bins};
+      for (int e : alive_t[bx].edges) if (!alive_t[by].edges.count(e)) z.edges.insert(e);
+      for (int e : alive_t[by].edges) if (!alive_t[bx].edges.count(e)) z.edges.insert(e);
+      alive_t.erase(alive_t.begin() + by);
+      alive_t.erase(alive_t.begin() + bx);
+      if (!alive_t.empty()) worst = std::max(worst, std::ldexp(1.0, 2 * int(z.edges.size()) + z.bins));
+      alive_t.push_back(z);
+    }
+    return worst;
+  };
+  if (ctx->cfg.slice_intermediate_log2 > 0) {
+    const double budget = std::ldexp(1.0, ctx->cfg.slice_intermediate_log2);
+    while (max_intermediate(sliced) > budget) {
+      if (int(sliced.size()) >= std::min(c.K, kMaxSliced))
+        return fail(ctx, SQC_ESHAPE, "slicing: the intermediate budget needs more than 8 sliced edges");
+      int best = -1;
+      double best_mi = 0, best_in = 0;
+      for (int e = 0; e < c.K; ++e) {
+        if (sliced.count(e)) continue;
+        std::set<int> t = sliced;
+        t.insert(e);
+        const double mi = max_intermediate(t), in = total_size(t);
+        if (best < 0 || mi < best_mi || (mi == best_mi && in < best_in)) { best = e; best_mi = mi; best_in = in; }
+      }
+      sliced.insert(best);
+      P->sliced.push_back(best);
+    }
   }
   P->n_slices = int64_t(1) << (2 * sliced.size());
 
@@ -891,6 +960,9 @@ SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg) 
     return fail(nullptr, SQC_EINVAL, "select_resident must be 0 or 1");
   if (ctx->cfg.merge_pyramid != 0 && ctx->cfg.merge_pyramid != 1)
     return fail(nullptr, SQC_EINVAL, "merge_pyramid must be 0 or 1");
+  if (ctx->cfg.slice_input_log2 < 0 || ctx->cfg.slice_input_log2 > 62 || ctx->cfg.slice_intermediate_log2 < 0 ||
+      ctx->cfg.slice_intermediate_log2 > 62)
+    return fail(nullptr, SQC_EINVAL, "slice_input_log2 and slice_intermediate_log2 must be in [0, 62]");
   DeviceGuard g(device);
   e = select_configure();
   if (e == cudaSuccess) e = attr_configure();
