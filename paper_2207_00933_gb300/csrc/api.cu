@@ -382,6 +382,15 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
       d.L2 = L2;
       d.vec = L1 == 5 && L2 == 3 && dtype != SQC_F64 && (reinterpret_cast<uintptr_t>(src[i]) % 16) == 0;
       d.async2 = d.vec && kout == 0 && kin >= 1 && S <= 32;
+      // without outgoing edges A_i is as large as p_i, and the 32 x 8
+      // split's 32-byte bit-reversed write runs leave much of the DRAM
+      // bandwidth unused: the double-buffered form takes the 16 x 16 split
+      // (64-byte read and write runs).  With outgoing edges the reads
+      // dominate and the 128-byte read runs of 32 x 8 measured faster.
+      if (d.async2) {
+        d.L1 = 4;
+        d.L2 = 4;
+      }
       for (int t = 0; t < kin; ++t) d.inshift[t] = digit_shift(*c, i, c->ins[i][t]);
       for (int u = 0; u < kout; ++u) d.outshift[u] = digit_shift(*c, i, c->outs[i][u]);
       d.block_begin = blocks;

@@ -126,6 +126,16 @@ __device__ __forceinline__ int slot_pos(int j, int L1, int L2) {
   return j ^ ((m << (5 - L2)) & ((1 << L1) - 1));
 }
 
+// Shared-memory slot of state j in the 4-states-per-thread forms: the 5/3
+// tile shape (128-byte reads, 32-byte write runs) swizzles as slot_pos
+// does; the 4/4 shape (64-byte reads and write runs) needs no swizzle
+// (phase 3 then reads with at most 2-way bank conflicts).
+template <int L1>
+__device__ __forceinline__ int v4_pos(int j) {
+  if constexpr (L1 == 5) return slot_pos(j, 5, 3);
+  else return j;
+}
+
 template <int NC, bool F64>
 __device__ __forceinline__ void fold_phase(const AttrDesc& d, const AttrTileCtx& t, float* val, int S, int lt,
                                            uint64_t x, int pos, uint64_t vbase, uint32_t signed_mask) {
@@ -294,7 +304,9 @@ __device__ __forceinline__ void fold_phase_v4(const AttrDesc& d, const AttrTileC
   }
 }
 
+template <int L1>
 __device__ __forceinline__ void attr_tile_v4(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
+  constexpr int L2 = 8 - L1;
   const uint64_t o = uint64_t(t) & ((uint64_t(1) << (2 * d.kout)) - 1);
   const uint64_t xm = uint64_t(t) >> (2 * d.kout);
   const int S = 1 << (2 * d.kin);
@@ -308,8 +320,8 @@ __device__ __forceinline__ void attr_tile_v4(const AttrDesc& d, const AttrTileCt
   }
   const int g = int(threadIdx.x) & 63;
   const int j0 = 4 * g;                              // 4 consecutive low bits, one jh
-  const uint64_t x0 = uint64_t(j0 & 31) | (xm << 5) | (uint64_t(j0 >> 5) << (n - 3));
-  const int pos = slot_pos(j0, 5, 3);                // a multiple of 4
+  const uint64_t x0 = uint64_t(j0 & ((1 << L1) - 1)) | (xm << L1) | (uint64_t(j0 >> L1) << (n - L2));
+  const int pos = v4_pos<L1>(j0);                    // a multiple of 4
   switch (d.kout) {
     case 0: fold_phase_v4<1>(d, tc, val, S, x0, pos, vbase, signed_mask); break;
     case 1: fold_phase_v4<2>(d, tc, val, S, x0, pos, vbase, signed_mask); break;
@@ -338,12 +350,14 @@ __device__ __forceinline__ void attr_tile_v4(const AttrDesc& d, const AttrTileCt
     }
     __syncthreads();
   }
-  // phase 3: thread g writes storage offsets r0 .. r0+3 of low state bits jl
-  const int jl = g >> 1, r0 = (g & 1) * 4;
+  // phase 3: thread g writes storage offsets r0 .. r0+3 of low state bits
+  // jl (top state bits jh = the L2-bit reversal of the offset)
+  constexpr int kPerJl = (1 << L2) / 4;
+  const int jl = g / kPerJl, r0 = (g % kPerJl) * 4;
   int pw[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) pw[q] = slot_pos(jl | (int(__brev(uint32_t(r0 + q)) >> 29) << 5), 5, 3);
-  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << 5)), n) + uint64_t(r0);
+  for (int q = 0; q < 4; ++q) pw[q] = v4_pos<L1>(jl | (int(__brev(uint32_t(r0 + q)) >> (32 - L2)) << L1));
+  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << L1)), n) + uint64_t(r0);
   for (int s = int(threadIdx.x) >> 6; s < S; s += 4) {
     const float* v = val + s * 256;
     *reinterpret_cast<float4*>(d.A + ((in_digits(tc, s) | vbase) << n) + xw) =
@@ -355,7 +369,9 @@ __device__ __forceinline__ void attr_tile_v4(const AttrDesc& d, const AttrTileCt
 // tiles 4t .. 4t+3, one per 64-thread group, each group folding the
 // outcomes of its 256 states (4 per thread) and writing them through its
 // own 256-float region of shared memory.
+template <int L1>
 __device__ __forceinline__ void attr_tiles_v4_kin0(const AttrDesc& d, int64_t t, float* val) {
+  constexpr int L2 = 8 - L1;
   const int g4 = int(threadIdx.x) >> 6;
   const uint64_t tt = uint64_t(t) * 4 + uint64_t(g4);
   const uint64_t o = tt & ((uint64_t(1) << (2 * d.kout)) - 1);
@@ -370,8 +386,8 @@ __device__ __forceinline__ void attr_tiles_v4_kin0(const AttrDesc& d, int64_t t,
   }
   const int g = int(threadIdx.x) & 63;
   const int j0 = 4 * g;
-  const uint64_t x0 = uint64_t(j0 & 31) | (xm << 5) | (uint64_t(j0 >> 5) << (n - 3));
-  const int pos = slot_pos(j0, 5, 3);
+  const uint64_t x0 = uint64_t(j0 & ((1 << L1) - 1)) | (xm << L1) | (uint64_t(j0 >> L1) << (n - L2));
+  const int pos = v4_pos<L1>(j0);
   float* mine = val + g4 * 256;
   const float* p = static_cast<const float*>(d.p) + (vbase << (n + d.kout)) + x0;
   const int nc = 1 << d.kout;
@@ -393,11 +409,12 @@ __device__ __forceinline__ void attr_tiles_v4_kin0(const AttrDesc& d, int64_t t,
   }
   *reinterpret_cast<float4*>(mine + pos) = acc;
   __syncthreads();
-  const int jl = g >> 1, r0 = (g & 1) * 4;
+  constexpr int kPerJl = (1 << L2) / 4;
+  const int jl = g / kPerJl, r0 = (g % kPerJl) * 4;
   float o4[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) o4[q] = mine[slot_pos(jl | (int(__brev(uint32_t(r0 + q)) >> 29) << 5), 5, 3)];
-  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << 5)), n) + uint64_t(r0);
+  for (int q = 0; q < 4; ++q) o4[q] = mine[v4_pos<L1>(jl | (int(__brev(uint32_t(r0 + q)) >> (32 - L2)) << L1))];
+  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << L1)), n) + uint64_t(r0);
   *reinterpret_cast<float4*>(d.A + (vbase << n) + xw) = make_float4(o4[0], o4[1], o4[2], o4[3]);
 }
 
@@ -415,23 +432,27 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// the 4^kin rows of tile t into buf (states in the swizzled slots)
+// the 4^kin rows of tile t into buf (states in the slots of v4_pos)
+template <int L1>
 __device__ __forceinline__ void v4_issue(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* buf) {
+  constexpr int L2 = 8 - L1;
   const uint64_t xm = uint64_t(t);                  // no outgoing edges: tile = x middle bits
   const int S = 1 << (2 * d.kin), n = d.n;
   const int j0 = 4 * (int(threadIdx.x) & 63);
-  const uint64_t x0 = uint64_t(j0 & 31) | (xm << 5) | (uint64_t(j0 >> 5) << (n - 3));
-  const int pos = slot_pos(j0, 5, 3);
+  const uint64_t x0 = uint64_t(j0 & ((1 << L1) - 1)) | (xm << L1) | (uint64_t(j0 >> L1) << (n - L2));
+  const int pos = v4_pos<L1>(j0);
   const float* p = static_cast<const float*>(d.p);
   for (int s = int(threadIdx.x) >> 6; s < S; s += 4) cp_async16(buf + s * 256 + pos, p + (in_digits(tc, s) << n) + x0);
 }
 
 // expansion of the incoming edges and the bit-reversed write of tile t
+template <int L1>
 __device__ __forceinline__ void v4_finish(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
+  constexpr int L2 = 8 - L1;
   const uint64_t xm = uint64_t(t);
   const int S = 1 << (2 * d.kin), n = d.n;
   const int g = int(threadIdx.x) & 63;
-  const int pos = slot_pos(4 * g, 5, 3);
+  const int pos = v4_pos<L1>(4 * g);
   for (int q = 0; q < d.kin; ++q) {
     const int lowmask = (1 << (2 * q)) - 1;
     const int st = 256 << (2 * q);
@@ -452,11 +473,14 @@ __device__ __forceinline__ void v4_finish(const AttrDesc& d, const AttrTileCtx& 
     }
     __syncthreads();
   }
-  const int jl = g >> 1, r0 = (g & 1) * 4;
+  // thread g writes storage offsets r0 .. r0+3 (top state bits jh = the
+  // L2-bit reversal of the offset) of the low state bits jl
+  constexpr int kPerJl = (1 << L2) / 4;             // threads per low-bit value
+  const int jl = g / kPerJl, r0 = (g % kPerJl) * 4;
   int pw[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) pw[q] = slot_pos(jl | (int(__brev(uint32_t(r0 + q)) >> 29) << 5), 5, 3);
-  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << 5)), n) + uint64_t(r0);
+  for (int q = 0; q < 4; ++q) pw[q] = v4_pos<L1>(jl | (int(__brev(uint32_t(r0 + q)) >> (32 - L2)) << L1));
+  const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << L1)), n) + uint64_t(r0);
   for (int s = int(threadIdx.x) >> 6; s < S; s += 4) {
     const float* v = val + s * 256;
     *reinterpret_cast<float4*>(d.A + (in_digits(tc, s) << n) + xw) = make_float4(v[pw[0]], v[pw[1]], v[pw[2]], v[pw[3]]);
@@ -517,27 +541,31 @@ __global__ void __launch_bounds__(256, VEC ? 6 : 4) attr_fused_kernel(AttrLaunch
       const int64_t t = tile - d.block_begin;
       const int rows = (1 << (2 * d.kin)) * 256;
       float* cur_buf = val + half * rows;
+      const bool sq = d.L1 == 4;                     // 4/4 tile shape
       if (!have_next) {
-        v4_issue(d, tc, t, cur_buf);
+        if (sq) v4_issue<4>(d, tc, t, cur_buf); else v4_issue<5>(d, tc, t, cur_buf);
         cp_async_commit();
       }
       // this CTA's next tile, when it is of the same subcircuit
       const bool next = tile + gridDim.x < d.block_end;
       if (next) {
-        v4_issue(d, tc, t + gridDim.x, val + (half ^ 1) * rows);
+        float* nb = val + (half ^ 1) * rows;
+        if (sq) v4_issue<4>(d, tc, t + gridDim.x, nb); else v4_issue<5>(d, tc, t + gridDim.x, nb);
         cp_async_commit();
         cp_async_wait<1>();
       } else {
         cp_async_wait<0>();
       }
       __syncthreads();
-      v4_finish(d, tc, t, cur_buf);
+      if (sq) v4_finish<4>(d, tc, t, cur_buf); else v4_finish<5>(d, tc, t, cur_buf);
       have_next = next;
       if (next) half ^= 1;
     } else if (d.vec && d.kin == 0) {
-      attr_tiles_v4_kin0(d, tile - d.block_begin, val);
+      if (d.L1 == 4) attr_tiles_v4_kin0<4>(d, tile - d.block_begin, val);
+      else attr_tiles_v4_kin0<5>(d, tile - d.block_begin, val);
     } else if (VEC || d.vec) {
-      attr_tile_v4(d, tc, tile - d.block_begin, val);
+      if (d.L1 == 4) attr_tile_v4<4>(d, tc, tile - d.block_begin, val);
+      else attr_tile_v4<5>(d, tc, tile - d.block_begin, val);
     } else {
       attr_tile(d, tc, tile - d.block_begin, val);
     }

@@ -2,9 +2,10 @@
 every cut wire) on large subcircuits, where the kernel switches to 32 x 8
 state tiles: the 4-states-per-thread form for 16-byte aligned FP32 inputs,
 the one-state-per-thread form for FP64 inputs and for FP32 inputs that are
-not 16-byte aligned.  Each case covers a different number of outgoing cut
-edges (1, 2, 3) and of incoming ones (0, 2, 3), and is checked through the
-whole reconstruction against the FP64 oracle."""
+not 16-byte aligned.  The cases cover subcircuits with 1, 2 or 3 outgoing
+cut edges and none, with incoming edges and without (every form of the
+kernel), each checked through the whole reconstruction against the FP64
+oracle."""
 import numpy as np
 import pytest
 
@@ -21,6 +22,7 @@ CASES = {
     "kout1": ([20, 6], [1], [8, 4]),        # 19 data qubits, 1 outgoing edge
     "kout3": ([18, 6], [3], [8, 4]),        # 15 data qubits, 3 outgoing edges
     "kout2_kin2": ([20, 22], [2], [10, 10]),  # 18 + 22 data qubits, 2 cuts
+    "kin1_kout1": ([6, 21, 6], [1, 1], [3, 8, 3]),  # a middle subcircuit of 20 data qubits
 }
 
 
