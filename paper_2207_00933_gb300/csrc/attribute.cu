@@ -561,11 +561,10 @@ __global__ void __launch_bounds__(256, VEC ? 6 : 4) attr_fused_kernel(AttrLaunch
       have_next = next;
       if (next) half ^= 1;
     } else if (d.vec && d.kin == 0) {
-      if (d.L1 == 4) attr_tiles_v4_kin0<4>(d, tile - d.block_begin, val);
-      else attr_tiles_v4_kin0<5>(d, tile - d.block_begin, val);
+      // (the host gives the 16 x 16 split to the double-buffered form only)
+      attr_tiles_v4_kin0<5>(d, tile - d.block_begin, val);
     } else if (VEC || d.vec) {
-      if (d.L1 == 4) attr_tile_v4<4>(d, tc, tile - d.block_begin, val);
-      else attr_tile_v4<5>(d, tc, tile - d.block_begin, val);
+      attr_tile_v4<5>(d, tc, tile - d.block_begin, val);
     } else {
       attr_tile(d, tc, tile - d.block_begin, val);
     }
