@@ -693,9 +693,20 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
   }
   q->merge_bytes = merge_bytes;
 
-  // greedy contraction order on the Section 6.2 cost (multiplications)
+  // greedy contraction order on the Section 6.2 cost (multiplications);
+  // open edges as 64-bit masks (K <= 60) so that a pair's shared edges are
+  // one popcount
   std::vector<int> alive;
-  for (int i = 0; i < nC; ++i) alive.push_back(i);
+  std::vector<uint64_t> emask;
+  auto mask_of = [](const std::set<int>& edges) {
+    uint64_t m = 0;
+    for (int e : edges) m |= uint64_t(1) << e;
+    return m;
+  };
+  for (int i = 0; i < nC; ++i) {
+    alive.push_back(i);
+    emask.push_back(mask_of(P->tensors[i].edges));
+  }
   while (alive.size() > 1) {
     int bx = -1, by = -1;
     double best = 0, best_out = 0;
@@ -704,8 +715,7 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
       for (size_t b = a + 1; b < alive.size(); ++b) {
         const Tensor& X = P->tensors[alive[a]];
         const Tensor& Y = P->tensors[alive[b]];
-        int sh = 0;
-        for (int e : X.edges) sh += int(Y.edges.count(e));
+        const int sh = __builtin_popcountll(emask[alive[a]] & emask[alive[b]]);
         const bool conn = sh > 0;
         const double fx = double(X.bits.size()) - 2.0 * sh, fy = double(Y.bits.size()) - 2.0 * sh;
         const double out = std::ldexp(1.0, int(fx + fy));
@@ -734,6 +744,7 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     for (int e : Y.edges) if (!X.edges.count(e)) Z.edges.insert(e);
     Z.producer_step = int(P->steps.size());
     st.z = int(P->tensors.size());
+    emask.push_back(mask_of(Z.edges));
     P->tensors.push_back(Z);
     P->steps.push_back(st);
     alive.erase(std::find(alive.begin(), alive.end(), bx));
