@@ -594,12 +594,13 @@ cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_byte
   // persistent grid: exactly as many CTAs as are resident at once (limited
   // by registers and shared memory), so that no CTA's tile list starts
   // after the others have finished theirs
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  // (function-local statics: initialised once, thread-safe)
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-  }
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    return n;
+  }();
   bool all_vec = true;
   for (int i = 0; i < L.n; ++i) all_vec = all_vec && L.d[i].vec;
   const void* fn = all_vec ? reinterpret_cast<const void*>(attr_fused_kernel<true>)

@@ -401,17 +401,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // looked up once per process (thread-safe initialisation)
+  static const EncodeTiledFn fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q{};
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return EncodeTiledFn(nullptr);
+  }();
   return fn;
 }
 
@@ -443,8 +442,7 @@ cudaError_t launch_cfg(const GemmTcArgs& a, cudaStream_t s) {
 
 // Co-resident 2-CTA clusters of the pair kernel (0: none), once per process.
 int pair_clusters() {
-  static int n = -1;
-  if (n < 0) {
+  static const int n = [] {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -461,8 +459,8 @@ int pair_clusters() {
       cudaGetLastError();
       c = 0;
     }
-    n = c < 76 ? c : 76;
-  }
+    return c < 76 ? c : 76;
+  }();
   return n;
 }
 

@@ -1336,8 +1336,8 @@ size_t select_coop_bytes(int grid) {
 }
 
 int select_coop_grid() {
-  static int g = 0;
-  if (!g) {
+  // computed once per process (thread-safe initialisation)
+  static const int g = [] {
     int dev = 0, sms = 152, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1347,16 +1347,15 @@ int select_coop_grid() {
     int per64 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per64, select_coop_kernel<true>, kCoopThreads, kCSmem);
     per = per < per64 ? per : per64;
-    g = sms * (per >= 2 ? 2 : (per > 0 ? per : 1));
-  }
+    return sms * (per >= 2 ? 2 : (per > 0 ? per : 1));
+  }();
   return g;
 }
 
 // The resident kernel runs one 1024-thread CTA per SM (0 if it cannot be
 // made co-resident with its largest shared-memory size).
 int select_resident_grid() {
-  static int g = -1;
-  if (g < 0) {
+  static const int g = [] {
     int dev = 0, sms = 152, p32 = 0, p64 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1364,10 +1363,11 @@ int select_resident_grid() {
     cudaFuncSetAttribute(select_resident_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmemMax);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, select_resident_kernel<false>, kRThreads, kRSmemMax);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, select_resident_kernel<true>, kRThreads, kRSmemMax);
-    g = (p32 >= 1 && p64 >= 1) ? sms : 0;
-    if (g > select_coop_grid()) g = select_coop_grid();   // tie counts live in the streaming part
-    if (g * kRRankMax < kMaxSort) g = 0;                   // each CTA ranks at most kRRankMax candidates
-  }
+    int r = (p32 >= 1 && p64 >= 1) ? sms : 0;
+    if (r > select_coop_grid()) r = select_coop_grid();   // tie counts live in the streaming part
+    if (r * kRRankMax < kMaxSort) r = 0;                   // each CTA ranks at most kRRankMax candidates
+    return r;
+  }();
   return g;
 }
 
