@@ -72,8 +72,21 @@ struct Step {
 
 // Everything one precision needs to run a query: contraction order, layouts,
 // maps, buffers.  Built on first use of that precision.
+// What a plan's device part (workspace allocation, uploads) needs from its
+// host part; kept between the two when they run on different threads.
+struct PlanDraft {
+  size_t off_desc = 0, off_maps = 0, off_part = 0, off_cnt = 0, zero_begin = 0, zero_end = 0;
+  std::vector<size_t> off_tensor;
+  std::vector<uint64_t> maps;
+  std::vector<std::pair<size_t, size_t>> step_map_off, merge_map_off;
+  std::vector<size_t> rowsel_off;
+  std::vector<char> has_rowsel;
+  std::vector<std::vector<std::pair<int, int>>> slice_pos;
+};
+
 struct Plan {
   bool built = false;
+  std::unique_ptr<PlanDraft> draft;   // host part done, device part pending
   bool split = false;
   std::vector<Tensor> tensors;
   std::vector<Step> steps;
@@ -153,8 +166,14 @@ struct DeviceGuard {
   }
 };
 
+// Host-only planning on a worker thread reports into its own string
+// instead of the context's (which another thread may be using).
+thread_local std::string* t_err_sink = nullptr;
+
 sqc_status fail(sqc_ctx* ctx, sqc_status st, const std::string& msg) {
-  if (ctx) ctx->err = msg; else g_create_error = msg;
+  if (t_err_sink) *t_err_sink = msg;
+  else if (ctx) ctx->err = msg;
+  else g_create_error = msg;
   return st;
 }
 
@@ -503,7 +522,11 @@ void resolve_roles(const Circuit& c, Query* q) {
   q->out_elems = int64_t(1) << na;
 }
 
-sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan* P) {
+sqc_status finalize_plan(sqc_ctx* ctx, Plan* P);
+
+// Host part of a plan; with defer the device part (finalize_plan) is left
+// for the caller.
+sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan* P, bool defer = false) {
   const int nC = c.nC;
   std::vector<int> canon(c.n_qubits, -1);
   int na = 0;
@@ -853,30 +876,56 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
   const size_t off_part = off; off = align(off + sizeof(double) * size_t(max_tiles));
   const size_t off_cnt = off; off = align(off + 64);
   P->work_bytes = off;
-  sqc_status st = dev_alloc(ctx, &P->work, off);
+  auto D = std::make_unique<PlanDraft>();
+  D->off_desc = off_desc;
+  D->off_maps = off_maps;
+  D->off_part = off_part;
+  D->off_cnt = off_cnt;
+  D->zero_begin = zero_begin;
+  D->zero_end = zero_end;
+  D->off_tensor = std::move(off_tensor);
+  D->maps = std::move(maps.host);
+  D->step_map_off = std::move(step_map_off);
+  D->merge_map_off = std::move(merge_map_off);
+  D->rowsel_off = std::move(rowsel_off);
+  D->has_rowsel.resize(nC);
+  for (int i = 0; i < nC; ++i) D->has_rowsel[i] = !rowsel[i].empty();
+  D->slice_pos = std::move(slice_pos);
+  P->draft = std::move(D);
+  return defer ? SQC_OK : finalize_plan(ctx, P);
+}
+
+// Device part of a plan: allocate the workspace, point the steps and merge
+// descriptors into it, upload maps and descriptors, zero what must start
+// at zero.
+sqc_status finalize_plan(sqc_ctx* ctx, Plan* P) {
+  if (!P->draft) return fail(ctx, SQC_EINVAL, "plan: nothing to finalize");
+  const PlanDraft& D = *P->draft;
+  const int nC = int(P->merge_host.size());
+  sqc_status st = dev_alloc(ctx, &P->work, P->work_bytes);
   if (st != SQC_OK) return st;
   char* base = static_cast<char*>(P->work);
-  P->merge_dev = reinterpret_cast<MergeDesc*>(base + off_desc);
-  uint64_t* maps_dev = reinterpret_cast<uint64_t*>(base + off_maps);
+  P->merge_dev = reinterpret_cast<MergeDesc*>(base + D.off_desc);
+  uint64_t* maps_dev = reinterpret_cast<uint64_t*>(base + D.off_maps);
   for (size_t t = 0; t < P->tensors.size(); ++t)
-    if (int(t) != P->final_tensor) P->tensors[t].buf = base + off_tensor[t];
-  P->partials = reinterpret_cast<double*>(base + off_part);
-  P->counter = reinterpret_cast<unsigned*>(base + off_cnt);
-  P->err = reinterpret_cast<int*>(base + off_cnt + 16);
+    if (int(t) != P->final_tensor) P->tensors[t].buf = base + D.off_tensor[t];
+  P->partials = reinterpret_cast<double*>(base + D.off_part);
+  P->counter = reinterpret_cast<unsigned*>(base + D.off_cnt);
+  P->err = reinterpret_cast<int*>(base + D.off_cnt + 16);
 
   for (size_t s = 0; s < P->steps.size(); ++s) {
-    P->steps[s].rowmap = maps_dev + step_map_off[s].first;
-    P->steps[s].colmap = maps_dev + step_map_off[s].second;
+    P->steps[s].rowmap = maps_dev + D.step_map_off[s].first;
+    P->steps[s].colmap = maps_dev + D.step_map_off[s].second;
   }
   int64_t blocks = 0;
   for (int i = 0; i < nC; ++i) {
     MergeDesc& d = P->merge_host[i];
-    d.rowmap = maps_dev + merge_map_off[i].first;
-    d.colmap = maps_dev + merge_map_off[i].second;
+    d.rowmap = maps_dev + D.merge_map_off[i].first;
+    d.colmap = maps_dev + D.merge_map_off[i].second;
     d.dst = P->tensors[i].buf;          // null for the result (set per call)
     d.kind = P->tensors[i].kind;
     d.plane_stride = P->tensors[i].plane_stride;
-    d.rowsel = rowsel[i].empty() ? nullptr : maps_dev + rowsel_off[i];
+    d.rowsel = D.has_rowsel[i] ? maps_dev + D.rowsel_off[i] : nullptr;
     d.row_add = 0;
     d.block_begin = blocks;
     const int64_t outs = d.rows << d.a;
@@ -884,7 +933,7 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     blocks += (outs + per - 1) / per;
   }
   P->merge_blocks = blocks;
-  cudaError_t e = upload(ctx, maps_dev, maps.host.data(), sizeof(uint64_t) * maps.host.size());
+  cudaError_t e = upload(ctx, maps_dev, D.maps.data(), sizeof(uint64_t) * D.maps.size());
   if (e == cudaSuccess && nC > 0) {
     // one descriptor set per slice: slice sigma fixes sliced edge j's digit
     // to (sigma >> 2j) & 3 in every A row it reads
@@ -892,18 +941,19 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     for (int64_t sg = 0; sg < P->n_slices; ++sg)
       for (int i = 0; i < nC; ++i) {
         MergeDesc d = P->merge_host[i];
-        for (const auto& sp : slice_pos[i]) d.row_add += int64_t((sg >> (2 * sp.second)) & 3) << sp.first;
+        for (const auto& sp : D.slice_pos[i]) d.row_add += int64_t((sg >> (2 * sp.second)) & 3) << sp.first;
         sets[size_t(sg) * nC + i] = d;
       }
     e = upload(ctx, P->merge_dev, sets.data(), sizeof(MergeDesc) * sets.size());
   }
-  if (e == cudaSuccess) e = zero(ctx, base + off_cnt, 64);
+  if (e == cudaSuccess) e = zero(ctx, base + D.off_cnt, 64);
   // BF16 operand padding (shared-index columns beyond K) must read as zero
-  if (e == cudaSuccess && zero_end > zero_begin) e = zero(ctx, base + zero_begin, zero_end - zero_begin);
+  if (e == cudaSuccess && D.zero_end > D.zero_begin) e = zero(ctx, base + D.zero_begin, D.zero_end - D.zero_begin);
   if (e != cudaSuccess) {
     free_plan(ctx, P);
     return cuda_fail(ctx, e, "plan upload");
   }
+  P->draft.reset();
   P->built = true;
   return SQC_OK;
 }
@@ -924,6 +974,62 @@ sqc_status ensure_select_work(sqc_ctx* ctx, Query* q) {
 // Hooks for the serving loop (server.cu), which drives a context from its
 // own thread.
 namespace sqc {
+struct QueryDraft {
+  int64_t circuit_id = 0;
+  std::unique_ptr<Query> q;
+};
+
+const void* ctx_circuit(sqc_ctx* ctx, int64_t circuit) {
+  auto it = ctx->circuits.find(circuit);
+  return it == ctx->circuits.end() ? nullptr : it->second.get();
+}
+
+int32_t query_draft(const sqc_ctx* cctx, int64_t circuit_id, const void* circuit, const int8_t* roles,
+                    QueryDraft** out, std::string* err) {
+  sqc_ctx* ctx = const_cast<sqc_ctx*>(cctx);      // read only: configuration (errors go to *err)
+  t_err_sink = err;
+  *out = nullptr;
+  const Circuit& c = *static_cast<const Circuit*>(circuit);
+  sqc_status st = SQC_OK;
+  int na = 0;
+  for (int qb = 0; qb < c.n_qubits && st == SQC_OK; ++qb) {
+    if (roles[qb] < SQC_ROLE_ACTIVE || roles[qb] > SQC_ROLE_ZOOM1) st = fail(ctx, SQC_EINVAL, "role out of range");
+    na += roles[qb] == SQC_ROLE_ACTIVE;
+  }
+  if (st == SQC_OK && na > ctx->cfg.max_active_qubits)
+    st = fail(ctx, SQC_ESHAPE, "active qubits " + std::to_string(na) + " > max_active_qubits");
+  auto d = std::make_unique<QueryDraft>();
+  if (st == SQC_OK) {
+    d->circuit_id = circuit_id;
+    d->q = std::make_unique<Query>();
+    d->q->circuit = circuit_id;
+    d->q->roles.assign(roles, roles + c.n_qubits);
+    resolve_roles(c, d->q.get());
+    st = build_plan(ctx, c, d->q.get(), false, &d->q->plans[SQC_PREC_FP32], true);
+  }
+  t_err_sink = nullptr;
+  if (st == SQC_OK) *out = d.release();
+  return st;
+}
+
+int32_t query_commit(sqc_ctx* ctx, QueryDraft* d, int64_t* query, int32_t* n_active) {
+  std::unique_ptr<QueryDraft> own(d);
+  if (!ctx->circuits.count(d->circuit_id)) return fail(ctx, SQC_ENOTFOUND, "circuit of a drafted query was unloaded");
+  DeviceGuard g(ctx->device);
+  sqc_status st = finalize_plan(ctx, &d->q->plans[SQC_PREC_FP32]);
+  if (st != SQC_OK) {
+    free_query(ctx, d->q.get());
+    return st;
+  }
+  const int64_t qid = ctx->next_id++;
+  if (n_active) *n_active = d->q->n_active;
+  ctx->queries[qid] = std::move(d->q);
+  *query = qid;
+  return SQC_OK;
+}
+
+void query_draft_free(QueryDraft* d) { delete d; }
+
 void ctx_set_alloc_stream(sqc_ctx* ctx, cudaStream_t s) {
   ctx->alloc_stream = s;
   ctx->async_alloc = s != nullptr;
@@ -1107,29 +1213,14 @@ SQC_API sqc_status sqc_set_qubit_roles(sqc_ctx* ctx, sqc_circuit_id id, const in
   if (!ctx || !roles || !out_q) return fail(ctx, SQC_EINVAL, "null argument");
   auto it = ctx->circuits.find(id);
   if (it == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "unknown circuit");
-  const Circuit& c = *it->second;
-  int na = 0;
-  for (int qb = 0; qb < c.n_qubits; ++qb) {
-    if (roles[qb] < SQC_ROLE_ACTIVE || roles[qb] > SQC_ROLE_ZOOM1) return fail(ctx, SQC_EINVAL, "role out of range");
-    na += roles[qb] == SQC_ROLE_ACTIVE;
-  }
-  if (na > ctx->cfg.max_active_qubits)
-    return fail(ctx, SQC_ESHAPE, "active qubits " + std::to_string(na) + " > max_active_qubits");
-  DeviceGuard g(ctx->device);
-  auto q = std::make_unique<Query>();
-  q->circuit = id;
-  q->roles.assign(roles, roles + c.n_qubits);
-  resolve_roles(c, q.get());
-  sqc_status st = build_plan(ctx, c, q.get(), false, &q->plans[SQC_PREC_FP32]);
-  if (st != SQC_OK) {
-    free_query(ctx, q.get());
-    return st;
-  }
-  const int64_t qid = ctx->next_id++;
-  if (n_active) *n_active = q->n_active;
-  ctx->queries[qid] = std::move(q);
-  *out_q = qid;
-  return SQC_OK;
+  sqc::QueryDraft* d = nullptr;
+  std::string err;
+  sqc_status st = sqc::query_draft(ctx, id, it->second.get(), roles, &d, &err);
+  if (st != SQC_OK) return fail(ctx, st, err);
+  int64_t q = 0;
+  st = sqc::query_commit(ctx, d, &q, n_active);
+  if (st == SQC_OK) *out_q = q;
+  return st;
 }
 
 SQC_API sqc_status sqc_release_query(sqc_ctx* ctx, sqc_query_id qid) {

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace sqc {
 
 enum OutKind : int { OUT_F32 = 0, OUT_F64 = 1, OUT_BF16X3 = 2 };
@@ -231,4 +233,16 @@ int ctx_device(const sqc_ctx* ctx);
 int32_t ctx_alloc(sqc_ctx* ctx, void** p, size_t bytes);    // budget-checked (SQC_EBUSY when over)
 void ctx_free(sqc_ctx* ctx, void* p, size_t bytes);
 int32_t ctx_fail(sqc_ctx* ctx, int32_t st, const char* msg);
+// sqc_set_qubit_roles in two parts.  query_draft is the host part (roles,
+// slicing, contraction order, layouts, maps); it reads only the context's
+// configuration and the circuit, so several drafts may run at once on other
+// threads while the circuit stays loaded.  query_commit is the device part
+// (workspace, uploads) and registers the query; it runs on the thread that
+// owns the context and consumes the draft either way.
+struct QueryDraft;
+const void* ctx_circuit(sqc_ctx* ctx, int64_t circuit);     // nullptr: unknown
+int32_t query_draft(const sqc_ctx* ctx, int64_t circuit_id, const void* circuit, const int8_t* roles,
+                    QueryDraft** out, std::string* err);
+int32_t query_commit(sqc_ctx* ctx, QueryDraft* d, int64_t* query, int32_t* n_active);
+void query_draft_free(QueryDraft* d);
 }  // namespace sqc

@@ -19,6 +19,7 @@
 // synchronises the device.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -79,6 +80,7 @@ struct sqc_server {
   std::vector<Slot> slots;         // server thread only
   std::deque<int64_t> waiting;     // server thread only
   int64_t launches = 0, admitted = 0, busy_refusals = 0;
+  size_t planner_threads = 1;      // host planning threads per dispatch
   std::string err;
 
   void loop();
@@ -130,20 +132,54 @@ bool sqc_server::dispatch(Slot& sl, int idx) {
   std::vector<void*> outs;
   std::vector<int32_t> nas;
   const int limit = cfg.max_batch > 0 ? cfg.max_batch : 256;
-  while (!waiting.empty() && int(taken.size()) < limit) {
-    const int64_t tk = waiting.front();
-    Request* r;
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      r = &reqs[tk];
+  // the host part of the next waiting requests' plans, on planner threads
+  // (it reads only the configuration and the circuits); the device part
+  // and the admission below stay on this thread, in arrival order
+  const size_t nd = std::min(waiting.size(), size_t(limit));
+  std::vector<int64_t> cand(waiting.begin(), waiting.begin() + std::ptrdiff_t(nd));
+  std::vector<Request*> rp(nd);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (size_t j = 0; j < nd; ++j) rp[j] = &reqs[cand[j]];
+  }
+  std::vector<const void*> circ(nd);
+  for (size_t j = 0; j < nd; ++j) circ[j] = sqc::ctx_circuit(ctx, rp[j]->circuit);
+  std::vector<sqc::QueryDraft*> drafts(nd, nullptr);
+  std::vector<sqc_status> dst(nd, SQC_OK);
+  std::vector<std::string> derr(nd);
+  auto draft = [&](size_t j0, size_t step) {
+    for (size_t j = j0; j < nd; j += step) {
+      if (!circ[j]) {
+        dst[j] = SQC_ENOTFOUND;
+        continue;
+      }
+      dst[j] = sqc::query_draft(ctx, rp[j]->circuit, circ[j], rp[j]->roles.data(), &drafts[j], &derr[j]);
     }
+  };
+  const size_t nt = nd >= 4 ? std::min<size_t>(nd / 2, planner_threads) : 1;
+  if (nt <= 1) {
+    draft(0, 1);
+  } else {
+    std::vector<std::thread> ts;
+    for (size_t t = 1; t < nt; ++t) ts.emplace_back(draft, t, nt);
+    draft(0, nt);
+    for (std::thread& t : ts) t.join();
+  }
+  size_t j = 0;
+  for (; j < nd && int(taken.size()) < limit; ++j) {
+    const int64_t tk = cand[j];
+    Request* r = rp[j];
     sqc_query_id q = 0;
     int32_t na = 0;
     // nothing else holds request memory: a request that does not fit now
     // never will
     bool alone = taken.empty();
     for (const Slot& o : slots) alone = alone && !o.busy;
-    sqc_status st = sqc_set_qubit_roles(ctx, r->circuit, r->roles.data(), &q, &na);
+    sqc_status st = dst[j];
+    if (st == SQC_OK) {
+      st = sqc::query_commit(ctx, drafts[j], &q, &na);   // consumes the draft
+      drafts[j] = nullptr;
+    }
     void* out = nullptr;
     const size_t ob = size_t(4) << na;
     if (st == SQC_OK) {
@@ -171,6 +207,9 @@ bool sqc_server::dispatch(Slot& sl, int idx) {
     outs.push_back(out);
     nas.push_back(na);
   }
+  // drafts of requests left waiting are dropped (planned again later)
+  for (; j < nd; ++j)
+    if (drafts[j]) sqc::query_draft_free(drafts[j]);
   if (taken.empty()) return false;
   const double t = now_us();
   sqc_status st = SQC_OK;
@@ -307,6 +346,10 @@ SQC_API sqc_status sqc_server_create(sqc_ctx* ctx, const sqc_server_config* cfg,
     }
   }
   cudaSetDevice(prev);
+  {
+    const unsigned hc = std::thread::hardware_concurrency();
+    srv->planner_threads = hc >= 4 ? std::min<size_t>(8, hc / 2) : 1;
+  }
   srv->th = std::thread([srv] { srv->loop(); });
   *out = srv;
   return SQC_OK;
