@@ -263,6 +263,10 @@ SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b);
  * whole budget fails with SQC_EBUSY; requests still waiting when the server
  * is destroyed are cancelled (state failed, SQC_EBUSY).  All allocations, uploads
  * and frees are stream-ordered: the loop never synchronises the device.
+ * The host part of the waiting requests' plans (contraction order, layouts,
+ * maps) runs on up to 8 short-lived planner threads (half the host's
+ * hardware threads) per admission round; the rest stays on the server
+ * thread. 
  * Results are FP32 bins, identical to sqc_reconstruct(SQC_PREC_FP32) of the
  * same query run alone. */
 typedef struct sqc_server sqc_server;
