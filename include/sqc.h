@@ -247,6 +247,19 @@ SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id*
 SQC_API sqc_status sqc_batch_run(sqc_ctx* ctx, sqc_batch_id b, void* stream);
 SQC_API sqc_status sqc_batch_status(sqc_ctx* ctx, sqc_batch_id b);
 SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b);
+/* Project-written autotuner of the batched launch (the paper has no
+ * counterpart): builds the batch of sqc_batch_create(n, qs, outs, out_dtype,
+ * totals) under each tile policy -- 0 by occupancy, 1 small 32 x 32 tiles,
+ * 2 large 64 x 64 / 128 x 64 tiles -- times `reps` launches of each on the
+ * default stream (CUDA events, after one warm-up launch), releases them, and
+ * makes the fastest policy the context's choice for later batches (also
+ * the serving loop's).  ms[3] (may be NULL) receives the mean time per
+ * launch of each policy.  The bins do not depend on the policy (each bin is
+ * summed in the same order); the outputs are overwritten.  Synchronises the
+ * device. */
+SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
+                                      sqc_dtype out_dtype, double* totals, int32_t reps, int32_t* best_policy,
+                                      float* ms);
 
 /* Serving loop: continuous batching of zoom queries (one recursion level
  * each) against circuits already loaded on the context.

@@ -74,6 +74,8 @@ _SIGS = {
     "sqc_batch_run": (_c.c_int32, [_P, _c.c_int64, _P]),
     "sqc_batch_status": (_c.c_int32, [_P, _c.c_int64]),
     "sqc_batch_release": (_c.c_int32, [_P, _c.c_int64]),
+    "sqc_batch_autotune": (_c.c_int32, [_P, _c.c_int32, _P, _P, _c.c_int, _P, _c.c_int32,
+                                        _c.POINTER(_c.c_int32), _P]),
     "sqc_server_default_config": (None, [_P]),
     "sqc_server_create": (_c.c_int32, [_P, _P, _c.POINTER(_P)]),
     "sqc_server_submit": (_c.c_int32, [_P, _c.c_int64, _P, _c.c_int32, _c.POINTER(_c.c_int64)]),
@@ -315,6 +317,21 @@ class Context:
 
     def batch_release(self, batch: int):
         self._check(self._lib.sqc_batch_release(self._h, batch))
+
+    def batch_autotune(self, queries: list[int], outs: list, totals=None, reps: int = 5):
+        """Time the batched launch of `queries` under each tile policy
+        (sqc_batch_autotune) and keep the fastest for later batches.
+        Returns (best policy, mean ms per launch of each policy)."""
+        n = len(queries)
+        qa = (ctypes.c_int64 * n)(*queries)
+        oa = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        dt = _dtype_code(outs[0])
+        if any(_dtype_code(o) != dt for o in outs):
+            raise ValueError("batch outputs must share one dtype")
+        best = ctypes.c_int32()
+        ms = (ctypes.c_float * 3)()
+        self._check(self._lib.sqc_batch_autotune(self._h, n, qa, oa, dt, _ptr(totals), reps, ctypes.byref(best), ms))
+        return best.value, list(ms)
 
     def top_bins(self, query: int, probs, k: int, threshold: float = -math.inf, bins_out=None, probs_out=None,
                  n_found=None, stream=None):

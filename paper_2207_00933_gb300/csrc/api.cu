@@ -147,6 +147,7 @@ struct sqc_ctx {
   std::string err;
   size_t bytes = 0;
   int64_t next_id = 1;
+  int batch_policy = 0;          // tile policy of new batches (sqc_batch_autotune)
   std::map<int64_t, std::unique_ptr<Circuit>> circuits;
   std::map<int64_t, std::unique_ptr<Query>> queries;
   std::map<int64_t, std::unique_ptr<Batch>> batches;
@@ -1499,7 +1500,7 @@ SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id*
                     ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
                     : 0;
       int64_t bm = 0, bn = 0;
-      bs.cfg = batch_tile_cfg(a.M, a.N, a.K, a.chunk > 0, a.chunk, &bm, &bn);
+      bs.cfg = batch_tile_cfg(a.M, a.N, a.K, a.chunk > 0, a.chunk, &bm, &bn, ctx->batch_policy);
       bs.ntiles = ((a.M + bm - 1) / bm) * ((a.N + bn - 1) / bn);
       if (last && totals) {
         part_off.push_back(n_parts);
@@ -1616,6 +1617,47 @@ SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b) {
   dev_free(ctx, it->second->work, it->second->work_bytes);
   ctx->batches.erase(it);
   return SQC_OK;
+}
+
+SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
+                                      sqc_dtype out_dtype, double* totals, int32_t reps, int32_t* best_policy,
+                                      float* ms) {
+  if (!ctx || !best_policy || reps < 1) return fail(ctx, SQC_EINVAL, "batch autotune: null argument or reps < 1");
+  DeviceGuard g(ctx->device);
+  const int saved = ctx->batch_policy;
+  int best = -1;
+  float best_ms = 0.f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  sqc_status st = SQC_OK;
+  for (int p = 0; p < kBatchPolicies && st == SQC_OK; ++p) {
+    ctx->batch_policy = p;
+    sqc_batch_id b = 0;
+    st = sqc_batch_create(ctx, n, qs, outs, out_dtype, totals, &b);
+    if (st != SQC_OK) break;
+    st = sqc_batch_run(ctx, b, nullptr);                       // warm-up
+    cudaError_t e = cudaSuccess;
+    if (st == SQC_OK) e = cudaEventRecord(e0, nullptr);
+    for (int r = 0; r < reps && st == SQC_OK && e == cudaSuccess; ++r) st = sqc_batch_run(ctx, b, nullptr);
+    if (st == SQC_OK && e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+    if (st == SQC_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (st == SQC_OK && e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (st == SQC_OK) st = sqc_batch_status(ctx, b);
+    const sqc_status rs = sqc_batch_release(ctx, b);
+    if (st == SQC_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "batch autotune timing");
+    if (st == SQC_OK) st = rs;
+    if (st != SQC_OK) break;
+    t /= float(reps);
+    if (ms) ms[p] = t;
+    if (best < 0 || t < best_ms) { best = p; best_ms = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->batch_policy = st == SQC_OK ? best : saved;
+  if (st == SQC_OK) *best_policy = best;
+  return st;
 }
 
 SQC_API sqc_status sqc_top_bins_noalloc(int device, const void* probs, sqc_dtype dtype, uint64_t n, int32_t k,

@@ -152,19 +152,40 @@ cudaError_t launch_batch(const BatchLaunch& L, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Tile configuration ids of the batch kernel and the per-step kernel.
-int batch_tile_cfg(int64_t M, int64_t N, int64_t K, bool chunked, int64_t chunk, int64_t* bm, int64_t* bn) {
+// Tile configuration ids of the batch kernel for one step, under a tile
+// policy: 0 = by occupancy (the default), 1 = small tiles (32 x 32: the
+// most work items, best balance for many uneven queries), 2 = large tiles
+// (64 x 64 or 128 x 64 wherever a step has enough of them: fewer operand
+// reloads).  Every configuration sums each bin in the same order, so the
+// bins do not depend on the policy.
+int batch_tile_cfg(int64_t M, int64_t N, int64_t K, bool chunked, int64_t chunk, int64_t* bm, int64_t* bn,
+                   int policy) {
   auto tiles = [&](int64_t a, int64_t b) { return ((M + a - 1) / a) * ((N + b - 1) / b); };
+  (void)chunk;
+  const bool deep = K >= 64;
+  if (policy == 1) {
+    *bm = 32; *bn = 32;
+    return chunked ? 5 : (deep ? 3 : 0);
+  }
+  if (policy == 2) {
+    if (chunked) {
+      if (tiles(64, 64) >= 4) { *bm = 64; *bn = 64; return 6; }
+      *bm = 32; *bn = 32;
+      return 5;
+    }
+    if (!deep && tiles(128, 64) >= 16) { *bm = 128; *bn = 64; return 2; }
+    if (tiles(64, 64) >= 4) { *bm = 64; *bn = 64; return deep ? 4 : 1; }
+    *bm = 32; *bn = 32;
+    return deep ? 3 : 0;
+  }
   if (chunked) {
     if (tiles(64, 64) >= 64) { *bm = 64; *bn = 64; return 6; }
     *bm = 32; *bn = 32;
     return 5;
   }
-  const bool deep = K >= 64;
   if (tiles(128, 64) >= 152 && !deep) { *bm = 128; *bn = 64; return 2; }
   if (tiles(64, 64) >= 64) { *bm = 64; *bn = 64; return deep ? 4 : 1; }
   *bm = 32; *bn = 32;
-  (void)chunk;
   return deep ? 3 : 0;
 }
 

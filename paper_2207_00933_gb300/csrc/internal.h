@@ -175,7 +175,9 @@ cudaError_t launch_batch(const BatchLaunch& L, int grid, cudaStream_t s);
 cudaError_t batch_configure();
 int batch_smem_bytes();
 // tile configuration for a step of the batch kernel; *bm, *bn its tile
-int batch_tile_cfg(int64_t M, int64_t N, int64_t K, bool chunked, int64_t chunk, int64_t* bm, int64_t* bn);
+int batch_tile_cfg(int64_t M, int64_t N, int64_t K, bool chunked, int64_t chunk, int64_t* bm, int64_t* bn,
+                   int policy);
+constexpr int kBatchPolicies = 3;
 
 // ---- probability check: FP64 sum of n values ---------------------------------
 cudaError_t launch_sum(const void* x, int is_f64, uint64_t n, double* partials, unsigned* counter,

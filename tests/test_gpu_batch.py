@@ -76,3 +76,40 @@ def test_batch_replays_from_a_cuda_graph(setup):
     for o, f in zip(outs, first):
         assert torch.equal(o, f)
     ctx.batch_release(bid)
+
+
+def test_autotune_policies_give_the_same_bins(setup):
+    """sqc_batch_autotune times the three tile policies; every policy sums
+    each bin in the same order, so the bins equal the one-at-a-time runs bit
+    for bit whichever policy wins, and the chosen policy is then used."""
+    import torch
+    ctx, b, qs = setup
+    outs = [torch.full((1 << na,), -1.0, dtype=torch.float32, device="cuda") for _, na in qs]
+    totals = torch.zeros(len(qs), dtype=torch.float64, device="cuda")
+    best, ms = ctx.batch_autotune([q for q, _ in qs], outs, totals, reps=3)
+    assert best in (0, 1, 2)
+    assert all(t > 0 for t in ms) and ms[best] == min(ms)
+    after_tune = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(-1.0)
+    bid = ctx.batch_create([q for q, _ in qs], outs, totals)     # built under the chosen policy
+    ctx.batch_run(bid)
+    ctx.batch_status(bid)
+    for j, (q, na) in enumerate(qs):
+        single = torch.empty_like(outs[j])
+        tot1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx.reconstruct(q, single, "fp32", tot1)
+        torch.cuda.synchronize()
+        assert torch.equal(single, outs[j]), j
+        assert torch.equal(single, after_tune[j]), j
+        assert abs(tot1.item() - totals[j].item()) <= 1e-12 * max(1.0, abs(tot1.item())) + 1e-15
+    ctx.batch_release(bid)
+
+
+def test_autotune_rejects_bad_arguments(setup):
+    import torch
+    from paper_2207_00933_gb300 import SQCError
+    ctx, b, qs = setup
+    outs = [torch.zeros((1 << na,), dtype=torch.float32, device="cuda") for _, na in qs]
+    with pytest.raises(SQCError):
+        ctx.batch_autotune([q for q, _ in qs], outs, reps=0)
