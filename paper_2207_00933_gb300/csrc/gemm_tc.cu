@@ -55,6 +55,9 @@ struct TcCfg {
   // instruction descriptor: D = FP32, A = B = BF16, both K-major, M x N
   static constexpr uint32_t kIdesc =
       (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
+  // the same with N = BN / 2 (half-width tail units of the pair kernel)
+  static constexpr uint32_t kIdescHalf =
+      (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 4) << 17) | (uint32_t(kBM >> 4) << 24);
 };
 using CfgNarrow = TcCfg<128, 64, 2>;
 using CfgWide = TcCfg<256, 32, 3>;
@@ -208,7 +211,10 @@ __device__ __forceinline__ void store16(const GemmTcArgs& a, uint64_t off, bool 
 // share every B tile: each CTA loads half of its rows and multicasts them to
 // both, so B is read from L2 once per pair.  A stage of either CTA is then
 // refilled only after both CTAs' MMAs have consumed it (the MMA commits
-// arrive on both CTAs' `empty` barriers).
+// arrive on both CTAs' `empty` barriers).  When the pair units leave a last
+// wave at most half full, its units are split into two half-width units
+// (N = BN / 2, B loaded by rank 0 alone and multicast), so that the tail
+// takes about half a unit's time instead of a whole one.
 template <class Cfg, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmTcArgs a) {
@@ -236,8 +242,22 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if constexpr (PAIR) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
   const int64_t unit0 = PAIR ? int64_t(blockIdx.x >> 1) : int64_t(blockIdx.x);
   const int64_t unit_step = PAIR ? int64_t(gridDim.x >> 1) : int64_t(gridDim.x);
-  const int64_t nunits = PAIR ? ntiles / 2 : ntiles;
-  auto tile_m0 = [&](int64_t u) -> int64_t { return ((u >> tn_shift) * (PAIR ? 2 : 1) + rank) * kBM; };
+  const int64_t nwide = PAIR ? ntiles / 2 : ntiles;
+  const int64_t tail = nwide % unit_step;
+  const bool split = PAIR && tail > 0 && 2 * tail <= unit_step;
+  const int64_t wide_end = split ? nwide - tail : nwide;        // units [wide_end, nunits) are half-width
+  const int64_t nunits = split ? wide_end + 2 * tail : nwide;
+  // unit u -> (tile row origin, column origin, half width)
+  auto unit_of = [&](int64_t u, int64_t* m0, int64_t* n0, bool* half) {
+    int64_t wu = u, noff = 0;
+    *half = u >= wide_end;
+    if (*half) {
+      wu = wide_end + ((u - wide_end) >> 1);
+      noff = ((u - wide_end) & 1) * (kBN / 2);
+    }
+    *m0 = ((wu >> tn_shift) * (PAIR ? 2 : 1) + rank) * kBM;
+    *n0 = (wu & (tiles_n - 1)) * kBN + noff;
+  };
 
   if (threadIdx.x == 0) {
     failed = 0;
@@ -273,8 +293,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // ---- TMA producer: one continuous ring of stages across all tiles
     int64_t it = 0, issued = 0;
     for (int64_t u = unit0; u < nunits && !failed; u += unit_step) {
-      const int m0 = int(tile_m0(u));
-      const int n0 = int((u & (tiles_n - 1)) * kBN);
+      int64_t um0, un0;
+      bool half;
+      unit_of(u, &um0, &un0, &half);
+      const int m0 = int(um0), n0 = int(un0);
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = int(it % kStages);
         const int64_t use = it / kStages;
@@ -283,13 +305,23 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           break;
         }
         uint8_t* st = smem + s * kStageBytes;
-        mbar_expect_tx(&full[s], kStageBytes);
+        // a half-width unit's stage holds the A planes and the first BN / 2
+        // rows of each B plane
+        mbar_expect_tx(&full[s], half ? 3 * kTileA + 3 * (kTileB / 2) : kStageBytes);
         for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
         if constexpr (PAIR) {
-          // this CTA's half of the B rows, to both CTAs
-          for (int p = 0; p < 3; ++p)
-            tma_load_3d_mc(st + 3 * kTileA + p * kTileB + int(rank) * (kTileB / 2), &tmB, kb * kBK,
-                           n0 + int(rank) * (kBN / 2), p, &full[s], uint16_t(0x3));
+          if (half) {
+            // the unit's BN / 2 B rows (one box of the map), loaded by rank
+            // 0 alone, to both CTAs
+            if (rank == 0)
+              for (int p = 0; p < 3; ++p)
+                tma_load_3d_mc(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s], uint16_t(0x3));
+          } else {
+            // this CTA's half of the B rows, to both CTAs
+            for (int p = 0; p < 3; ++p)
+              tma_load_3d_mc(st + 3 * kTileA + p * kTileB + int(rank) * (kTileB / 2), &tmB, kb * kBK,
+                             n0 + int(rank) * (kBN / 2), p, &full[s], uint16_t(0x3));
+          }
         } else {
           for (int p = 0; p < 3; ++p) tma_load_3d(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
         }
@@ -305,6 +337,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
     int64_t it = 0, t = 0;
     for (int64_t u = unit0; u < nunits && !failed; u += unit_step, ++t) {
+      const uint32_t idesc = u >= wide_end ? Cfg::kIdescHalf : Cfg::kIdesc;
       const int buf = int(t & 1);
       const int64_t use = t >> 1;
       if (use > 0 && !mbar_wait(&acc_empty[buf], uint32_t((use - 1) & 1))) {
@@ -329,7 +362,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
           const uint64_t db = smem_desc<kSW>(base + 3 * kTileA + pb[q] * kTileB);
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk)   // K = 16 per instruction: +32 bytes = +2 in the address field
-            mma_bf16(dacc, da + 2 * kk, db + 2 * kk, Cfg::kIdesc, (kb | q | kk) != 0);
+            mma_bf16(dacc, da + 2 * kk, db + 2 * kk, idesc, (kb | q | kk) != 0);
         }
         if constexpr (PAIR) mma_commit_mc(&empty[s], uint16_t(0x3));
         else mma_commit(&empty[s]);
@@ -351,12 +384,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t m0 = tile_m0(u);
-      const int64_t n0 = (u & (tiles_n - 1)) * kBN;
+      int64_t m0, n0;
+      bool half_unit;
+      unit_of(u, &m0, &n0, &half_unit);
+      const int width = half_unit ? kBN / 2 : kBN;
       const int64_t row = m0 + quad * 32 + lane;
       const bool row_ok = row < a.M;
       const uint64_t rbase = row_ok ? a.rowmap[row] : 0;
-      for (int c0 = half * (kBN / 2); c0 < (half + 1) * (kBN / 2); c0 += 32) {
+      for (int c0 = half * (width / 2); c0 < (half + 1) * (width / 2); c0 += 32) {
         float v[32];
         tmem_ld32(tmem + uint32_t(buf * kTmemCols) + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
         if (!row_ok) continue;

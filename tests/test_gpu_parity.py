@@ -143,7 +143,10 @@ def test_split_bf16_contraction_bound_step(ctx):
 def test_split_bf16_wide_tiles(ctx, active, out):
     # 4096 x 4096 x 256 (and 2048 x 4096): enough 128 x 256 tiles to fill
     # every SM, so the tensor-core step runs the 256-wide, 32-deep,
-    # three-stage configuration (64-byte swizzle)
+    # three-stage configuration (64-byte swizzle) in 2-CTA pairs.  At 4096 x
+    # 4096 the 256 pair units leave a last wave of 28 on 76 clusters, which
+    # runs as 56 half-width units; at 2048 x 4096 (128 units, a tail of 52)
+    # every unit is full width
     w = W.random_line_chain(11, [16, 16], [4], 1, list(active))
     ref = oracle_run(w)
     P, tot = gpu_run(ctx, w, out_dtype=out, precision="split_bf16")
