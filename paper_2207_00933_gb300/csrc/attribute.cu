@@ -185,7 +185,9 @@ __device__ __forceinline__ void fold_phase(const AttrDesc& d, const AttrTileCtx&
   }
 }
 
-// One tile (index t relative to the descriptor's first tile).
+// One tile (index t relative to the descriptor's first tile).  F64: the
+// FP64-input folds are compiled in.
+template <bool F64>
 __device__ __forceinline__ void attr_tile(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
   // tiles are (x middle bits) x (4^kout outgoing bases): shifts, no division
   const uint64_t o = uint64_t(t) & ((uint64_t(1) << (2 * d.kout)) - 1);
@@ -210,7 +212,7 @@ __device__ __forceinline__ void attr_tile(const AttrDesc& d, const AttrTileCtx& 
     return jl | (xm << L1) | (jh << (n - L2));
   };
   const int pos = slot_pos(j, L1, L2);
-  if (d.in_f64) {
+  if (F64 && d.in_f64) {
     switch (d.kout) {
       case 0: fold_phase<1, true>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
       case 1: fold_phase<2, true>(d, tc, val, S, lt, x_of(j), pos, vbase, signed_mask); break;
@@ -501,10 +503,15 @@ __device__ void fill_tile_ctx(const AttrDesc& d, AttrTileCtx& t) {
 // descriptor into shared memory only when it crosses into it (constant
 // parameter offsets only: a dynamic index into the parameter block would copy
 // all of it to local memory in every thread).
-// VEC: every descriptor of the launch takes a 4-state-per-thread form, so
-// the one-state paths (and their registers) are left out.
-template <bool VEC>
-__global__ void __launch_bounds__(256, VEC ? 6 : 4) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
+// MODE selects the forms compiled in, so that a launch runs the smallest
+// kernel that covers its descriptors (fewer registers, and for small
+// subcircuits fewer instruction-cache misses):
+//   kAttrAll  -- every form;
+//   kAttrVec  -- every descriptor takes a 4-state-per-thread form;
+//   kAttrOne  -- every descriptor takes the one-state form with FP32 input.
+enum : int { kAttrAll = 0, kAttrVec = 1, kAttrOne = 2 };
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
   extern __shared__ float val[];
   __shared__ AttrDesc d;
   __shared__ AttrTileCtx tc;
@@ -537,7 +544,9 @@ __global__ void __launch_bounds__(256, VEC ? 6 : 4) attr_fused_kernel(AttrLaunch
       fill_tile_ctx(d, tc);
       __syncthreads();
     }
-    if (d.async2) {
+    if (MODE == kAttrOne) {
+      attr_tile<false>(d, tc, tile - d.block_begin, val);
+    } else if (d.async2) {
       const int64_t t = tile - d.block_begin;
       const int rows = (1 << (2 * d.kin)) * 256;
       float* cur_buf = val + half * rows;
@@ -563,10 +572,10 @@ __global__ void __launch_bounds__(256, VEC ? 6 : 4) attr_fused_kernel(AttrLaunch
     } else if (d.vec && d.kin == 0) {
       // (the host gives the 16 x 16 split to the double-buffered form only)
       attr_tiles_v4_kin0<5>(d, tile - d.block_begin, val);
-    } else if (VEC || d.vec) {
+    } else if (MODE == kAttrVec || d.vec) {
       attr_tile_v4<5>(d, tc, tile - d.block_begin, val);
     } else {
-      attr_tile(d, tc, tile - d.block_begin, val);
+      attr_tile<true>(d, tc, tile - d.block_begin, val);
     }
     __syncthreads();
   }
@@ -601,26 +610,34 @@ cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_byte
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
     return n;
   }();
-  bool all_vec = true;
-  for (int i = 0; i < L.n; ++i) all_vec = all_vec && L.d[i].vec;
-  const void* fn = all_vec ? reinterpret_cast<const void*>(attr_fused_kernel<true>)
-                           : reinterpret_cast<const void*>(attr_fused_kernel<false>);
+  bool all_vec = true, all_one = true;
+  for (int i = 0; i < L.n; ++i) {
+    all_vec = all_vec && L.d[i].vec;
+    all_one = all_one && !L.d[i].vec && !L.d[i].async2 && !L.d[i].in_f64;
+  }
+  const void* fn = all_vec   ? reinterpret_cast<const void*>(attr_fused_kernel<kAttrVec>)
+                   : all_one ? reinterpret_cast<const void*>(attr_fused_kernel<kAttrOne>)
+                             : reinterpret_cast<const void*>(attr_fused_kernel<kAttrAll>);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem_bytes) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int64_t grid = blocks < int64_t(sms) * per_sm ? blocks : int64_t(sms) * per_sm;
   if (all_vec)
-    attr_fused_kernel<true><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
+    attr_fused_kernel<kAttrVec><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
+  else if (all_one)
+    attr_fused_kernel<kAttrOne><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
   else
-    attr_fused_kernel<false><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
+    attr_fused_kernel<kAttrAll><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
   return cudaGetLastError();
 }
 
 cudaError_t attr_configure() {
-  cudaError_t e = cudaFuncSetAttribute(attr_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(attr_fused_kernel<kAttrAll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kAttrSmemMax);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(attr_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
+    e = cudaFuncSetAttribute(attr_fused_kernel<kAttrVec>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(attr_fused_kernel<kAttrOne>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
   return e;
 }
 
