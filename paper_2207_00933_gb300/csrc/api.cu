@@ -1629,7 +1629,11 @@ SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_i
   float best_ms = 0.f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  const cudaError_t ee = cudaEventCreate(&e1);
+  if (ee != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ctx, ee, "batch autotune events");
+  }
   sqc_status st = SQC_OK;
   for (int p = 0; p < kBatchPolicies && st == SQC_OK; ++p) {
     ctx->batch_policy = p;
