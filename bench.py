@@ -386,6 +386,19 @@ def batch_bench(dev, reps: int = 10) -> dict:
         res["batch_fp32_pyramid"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "launches": 1,
                                      "max_abs_err_vs_fp64": err()}
         ctx.batch_release(bid)
+        # pyramid and the autotuned tile policy together
+        best, pol_ms = ctx.batch_autotune([q for q, _ in qs], outs, totals, reps=5)
+        bid = ctx.batch_create([q for q, _ in qs], outs, totals)
+        graph = torch.cuda.CUDAGraph()
+        ctx.batch_run(bid)
+        with torch.cuda.graph(graph):
+            ctx.batch_run(bid)
+        ms = timed(graph.replay)
+        ctx.batch_status(bid)
+        res["batch_fp32_pyramid_autotuned"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "launches": 1,
+                                               "policy": best, "policy_ms_unflushed": pol_ms,
+                                               "max_abs_err_vs_fp64": err()}
+        ctx.batch_release(bid)
     return res
 
 
