@@ -367,6 +367,32 @@ SQC_API sqc_status sqc_assign_states(int32_t n_subcircuits, const uint64_t* l, u
  * merged.  roles[n_qubits] out.  Host only. */
 SQC_API sqc_status sqc_recursion_roles(const sqc_graph* graph, const int8_t* zoom, uint64_t M, int8_t* roles);
 
+/* Host-only preview of the FP32 plan that sqc_set_qubit_roles builds for
+ * `roles` on a circuit of this graph under configuration `cfg` (NULL:
+ * defaults): first-level slicing (Section 6.3; by `slice_edges` or by the
+ * budgets `slice_input_log2` / `slice_intermediate_log2`) and the greedy
+ * pairwise contraction order on the Section 6.2 cost (connected pairs
+ * first, then fewest multiplications, then the smaller result).  Needs no
+ * GPU and allocates no device memory.
+ *   n_steps (out): contraction steps (n_subcircuits - 1);
+ *   steps: nullable host array [cap_steps][3] of (M, N, K) per step in
+ *          execution order -- C[M x N] = A[M x K] B[N x K]^T, K = 4^{shared
+ *          cut edges}; the last step's M x N is 2^{n_active};
+ *   n_sliced (out), sliced: nullable [cap_sliced] sliced edge ids in the
+ *          order they were chosen;
+ *   flops: nullable, 2 M N K summed over the steps of one slice;
+ *   work_bytes: nullable, the device workspace sqc_set_qubit_roles would
+ *          allocate for the query's FP32 plan;
+ *   err: nullable buffer of err_len bytes receiving the reason of a
+ *          failure (NUL-terminated, truncated).
+ * Errors as sqc_set_qubit_roles (SQC_EINVAL for a bad graph, role or
+ * configuration, SQC_ESHAPE for an unreachable slicing budget or too many
+ * active qubits). */
+SQC_API sqc_status sqc_plan_preview(const sqc_graph* graph, const int8_t* roles, const sqc_config* cfg,
+                                    int32_t* n_steps, int64_t* steps, int32_t cap_steps, int32_t* n_sliced,
+                                    int32_t* sliced, int32_t cap_sliced, double* flops, uint64_t* work_bytes,
+                                    char* err, int32_t err_len);
+
 /* Stage timing (tracing).  When enabled, the library records a pair of CUDA
  * events on the caller's stream around each stage it launches and counts
  * its kernel launches.  Stages: */

@@ -74,6 +74,8 @@ _SIGS = {
     "sqc_batch_run": (_c.c_int32, [_P, _c.c_int64, _P]),
     "sqc_batch_status": (_c.c_int32, [_P, _c.c_int64]),
     "sqc_batch_release": (_c.c_int32, [_P, _c.c_int64]),
+    "sqc_plan_preview": (_c.c_int32, [_P, _P, _P, _c.POINTER(_c.c_int32), _P, _c.c_int32,
+                                      _c.POINTER(_c.c_int32), _P, _c.c_int32, _P, _P, _c.c_char_p, _c.c_int32]),
     "sqc_batch_autotune": (_c.c_int32, [_P, _c.c_int32, _P, _P, _c.c_int, _P, _c.c_int32,
                                         _c.POINTER(_c.c_int32), _P]),
     "sqc_server_default_config": (None, [_P]),
@@ -472,21 +474,57 @@ def assign_states(l, M: int) -> list[int]:
     return out.tolist()
 
 
-def recursion_roles(n_qubits: int, edge_up, edge_down, n_data, data_qubit, zoom, M: int) -> np.ndarray:
-    """Roles of one recursion (sqc_recursion_roles); zoom: per qubit
-    ROLE_ZOOM0/ROLE_ZOOM1 for fixed qubits, anything else free.  Host only."""
-    lib = load_library()
+def _graph_struct(n_qubits: int, edge_up, edge_down, n_data, data_qubit):
+    """(sqc_graph, the int32 arrays it points into -- keep them alive)."""
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.int32)) for a in (edge_up, edge_down, n_data, data_qubit)]
     g = _Graph()
     g.n_qubits, g.n_subcircuits, g.n_edges = n_qubits, len(arrs[2]), len(arrs[0])
     ip = ctypes.POINTER(ctypes.c_int32)
     g.edge_up, g.edge_down, g.n_data, g.data_qubit = (a.ctypes.data_as(ip) for a in arrs)
+    return g, arrs
+
+
+def recursion_roles(n_qubits: int, edge_up, edge_down, n_data, data_qubit, zoom, M: int) -> np.ndarray:
+    """Roles of one recursion (sqc_recursion_roles); zoom: per qubit
+    ROLE_ZOOM0/ROLE_ZOOM1 for fixed qubits, anything else free.  Host only."""
+    lib = load_library()
+    g, arrs = _graph_struct(n_qubits, edge_up, edge_down, n_data, data_qubit)
     z = np.ascontiguousarray(np.asarray(zoom, dtype=np.int8))
     roles = np.empty(n_qubits, dtype=np.int8)
     st = lib.sqc_recursion_roles(ctypes.byref(g), z.ctypes.data, int(M), roles.ctypes.data)
     if st != 0:
         raise SQCError(st, "recursion_roles")
     return roles
+
+
+def plan_preview(n_qubits: int, edge_up, edge_down, n_data, data_qubit, roles, **config) -> dict:
+    """The FP32 plan sqc_set_qubit_roles would build (sqc_plan_preview):
+    host only, no GPU.  config: the Context keyword arguments that shape a
+    plan (max_active_qubits, slice_edges, slice_input_log2,
+    slice_intermediate_log2, ...).  Returns {"steps": [(M, N, K), ...],
+    "sliced": [edge ids], "flops": 2 sum MNK, "work_bytes": ...}."""
+    lib = load_library()
+    g, arrs = _graph_struct(n_qubits, edge_up, edge_down, n_data, data_qubit)
+    r = np.ascontiguousarray(np.asarray(roles, dtype=np.int8))
+    cfg = _Config()
+    lib.sqc_default_config(ctypes.byref(cfg))
+    for k, v in config.items():
+        if not hasattr(cfg, k):
+            raise TypeError(f"unknown configuration field {k}")
+        setattr(cfg, k, int(v))
+    cap = max(1, len(arrs[2]))
+    steps = np.zeros((cap, 3), dtype=np.int64)
+    sliced = np.zeros(max(1, len(arrs[0])), dtype=np.int32)
+    n_steps, n_sliced = ctypes.c_int32(), ctypes.c_int32()
+    flops, work = ctypes.c_double(), ctypes.c_uint64()
+    err = ctypes.create_string_buffer(256)
+    st = lib.sqc_plan_preview(ctypes.byref(g), r.ctypes.data, ctypes.byref(cfg), ctypes.byref(n_steps),
+                              steps.ctypes.data, cap, ctypes.byref(n_sliced), sliced.ctypes.data, sliced.size,
+                              ctypes.byref(flops), ctypes.byref(work), err, len(err))
+    if st != 0:
+        raise SQCError(st, err.value.decode())
+    return {"steps": [tuple(int(x) for x in s) for s in steps[:n_steps.value]],
+            "sliced": sliced[:n_sliced.value].tolist(), "flops": flops.value, "work_bytes": work.value}
 
 
 def declared_symbols() -> list[str]:

@@ -1041,6 +1041,21 @@ void ctx_free(sqc_ctx* ctx, void* p, size_t bytes) { dev_free(ctx, p, bytes); }
 sqc_status ctx_fail(sqc_ctx* ctx, sqc_status st, const char* msg) { return fail(ctx, st, msg); }
 }  // namespace sqc
 
+namespace {
+// Why a configuration is invalid (empty: it is valid).
+std::string config_error(const sqc_config& c) {
+  if (c.max_active_qubits < 0 || c.max_active_qubits > 40) return "max_active_qubits must be in [0, 40]";
+  if (c.chunk_terms < 16 || (c.chunk_terms & (c.chunk_terms - 1))) return "chunk_terms must be a power of two >= 16";
+  if (c.slice_edges < 0 || c.slice_edges > 8) return "slice_edges must be in [0, 8]";
+  if (c.select_resident != 0 && c.select_resident != 1) return "select_resident must be 0 or 1";
+  if (c.merge_pyramid != 0 && c.merge_pyramid != 1) return "merge_pyramid must be 0 or 1";
+  if (c.slice_input_log2 < 0 || c.slice_input_log2 > 62 || c.slice_intermediate_log2 < 0 ||
+      c.slice_intermediate_log2 > 62)
+    return "slice_input_log2 and slice_intermediate_log2 must be in [0, 62]";
+  return {};
+}
+}  // namespace
+
 // ================================================================ C ABI =====
 
 extern "C" {
@@ -1077,19 +1092,8 @@ SQC_API sqc_status sqc_create(sqc_ctx** out, int device, const sqc_config* cfg) 
   ctx->device = device;
   sqc_default_config(&ctx->cfg);
   if (cfg) ctx->cfg = *cfg;
-  if (ctx->cfg.max_active_qubits < 0 || ctx->cfg.max_active_qubits > 40)
-    return fail(nullptr, SQC_EINVAL, "max_active_qubits must be in [0, 40]");
-  if (ctx->cfg.chunk_terms < 16 || (ctx->cfg.chunk_terms & (ctx->cfg.chunk_terms - 1)))
-    return fail(nullptr, SQC_EINVAL, "chunk_terms must be a power of two >= 16");
-  if (ctx->cfg.slice_edges < 0 || ctx->cfg.slice_edges > 8)
-    return fail(nullptr, SQC_EINVAL, "slice_edges must be in [0, 8]");
-  if (ctx->cfg.select_resident != 0 && ctx->cfg.select_resident != 1)
-    return fail(nullptr, SQC_EINVAL, "select_resident must be 0 or 1");
-  if (ctx->cfg.merge_pyramid != 0 && ctx->cfg.merge_pyramid != 1)
-    return fail(nullptr, SQC_EINVAL, "merge_pyramid must be 0 or 1");
-  if (ctx->cfg.slice_input_log2 < 0 || ctx->cfg.slice_input_log2 > 62 || ctx->cfg.slice_intermediate_log2 < 0 ||
-      ctx->cfg.slice_intermediate_log2 > 62)
-    return fail(nullptr, SQC_EINVAL, "slice_input_log2 and slice_intermediate_log2 must be in [0, 62]");
+  const std::string ce = config_error(ctx->cfg);
+  if (!ce.empty()) return fail(nullptr, SQC_EINVAL, ce);
   DeviceGuard g(device);
   e = select_configure();
   if (e == cudaSuccess) e = attr_configure();
@@ -1661,6 +1665,53 @@ SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_i
   cudaEventDestroy(e1);
   ctx->batch_policy = st == SQC_OK ? best : saved;
   if (st == SQC_OK) *best_policy = best;
+  return st;
+}
+
+SQC_API sqc_status sqc_plan_preview(const sqc_graph* graph, const int8_t* roles, const sqc_config* cfg,
+                                    int32_t* n_steps, int64_t* steps, int32_t cap_steps, int32_t* n_sliced,
+                                    int32_t* sliced, int32_t cap_sliced, double* flops, uint64_t* work_bytes,
+                                    char* err, int32_t err_len) {
+  std::string msg;
+  sqc_status st = SQC_OK;
+  {
+    // a context holding only the configuration: planning is host work and
+    // nothing here touches a device
+    sqc_ctx ctx;
+    sqc_default_config(&ctx.cfg);
+    if (cfg) ctx.cfg = *cfg;
+    t_err_sink = &msg;
+    if (!graph || !roles || !n_steps || !n_sliced) st = fail(nullptr, SQC_EINVAL, "null argument");
+    if (st == SQC_OK) {
+      const std::string ce = config_error(ctx.cfg);
+      if (!ce.empty()) st = fail(nullptr, SQC_EINVAL, ce);
+    }
+    Circuit c;
+    if (st == SQC_OK) st = build_circuit(&ctx, graph, &c);
+    c.A.assign(c.nC, nullptr);          // no resident tensors: the plan only records their addresses
+    t_err_sink = nullptr;
+    sqc::QueryDraft* d = nullptr;
+    if (st == SQC_OK) st = sqc::query_draft(&ctx, 0, &c, roles, &d, &msg);
+    if (st == SQC_OK) {
+      const Plan& P = d->q->plans[SQC_PREC_FP32];
+      *n_steps = int32_t(P.steps.size());
+      for (size_t s = 0; steps && s < P.steps.size() && int32_t(s) < cap_steps; ++s) {
+        steps[3 * s] = P.steps[s].M;
+        steps[3 * s + 1] = P.steps[s].N;
+        steps[3 * s + 2] = P.steps[s].Kd;
+      }
+      *n_sliced = int32_t(P.sliced.size());
+      for (size_t j = 0; sliced && j < P.sliced.size() && int32_t(j) < cap_sliced; ++j) sliced[j] = P.sliced[j];
+      if (flops) *flops = P.flops;
+      if (work_bytes) *work_bytes = P.work_bytes;
+    }
+    sqc::query_draft_free(d);
+  }
+  if (err && err_len > 0) {
+    const size_t n = std::min(msg.size(), size_t(err_len - 1));
+    std::memcpy(err, msg.data(), n);
+    err[n] = '\0';
+  }
   return st;
 }
 
