@@ -128,6 +128,15 @@ def test_wire_cut_twice_matches_statevector():
     assert np.abs(P - full_circuit_probs(c)).max() < 1e-13
 
 
+def test_subcircuit_without_data_qubits_matches_statevector():
+    # the middle block hands every one of its wires on (2 in, 3 out, no
+    # data qubit), as subcircuit 2 of the paper's Fig. 5 graph (2^0 bins)
+    c = chain_line_circuit(7, [4, 3, 4], [2, 3], 3)
+    assert [len(d) for d in c.data_qubits] == [2, 0, 4] and c.n_edges == 5
+    P = O.reconstruct(graph_of(c), exact_probs(c), np.zeros(c.n_qubits, dtype=int))
+    assert np.abs(P - full_circuit_probs(c)).max() < 1e-13
+
+
 def test_zero_cut_identity():
     c = CutCircuit(5, [Block(list(range(5)), [("h", 0), ("cz", 0, 1), ("sx", 3), ("t", 1), ("sy", 4)])]).finalize()
     p = exact_probs(c)
