@@ -123,7 +123,24 @@ typedef struct {
    * would need more fails with SQC_ESHAPE. */
   int32_t slice_input_log2;
   int32_t slice_intermediate_log2;
-  int32_t reserved[2];
+  /* Split-BF16 steps large enough to fill every SM with 256 x 256 output
+   * units (1 = on): run them on 2-SM pairs (tcgen05.mma.cta_group::2,
+   * M = 256; each SM of a pair loads its own half of both operands, so a
+   * pair reads every operand tile from L2 once).  0 = one SM per unit. */
+  int32_t tc_pairs;
+  /* Limit, in milliseconds, of every bounded device wait (the batched
+   * launch's dependency waits, the tensor-core pipeline's barrier waits);
+   * a wait that runs out records SQC_ETIMEOUT and the kernel drains and
+   * returns.  0 = the default, 2000 ms. */
+  int32_t wait_limit_ms;
+  /* FP32 reconstructions (1 = on, the default): the merge and every
+   * contraction step of a query run as ONE persistent launch whose merge
+   * blocks and step tiles wait (bounded) only for the tensors they read,
+   * instead of one launch per stage; the bins are the same bit for bit.
+   * The first FP32 reconstruct of a query into each output format builds
+   * that launch's work list (allocates).  Sliced queries and split-BF16
+   * keep one launch per stage. */
+  int32_t fused_query;
 } sqc_config;
 
 /* Compute graph (Section 5, Fig. 3d).  Vertices are subcircuits 0..n_C-1;
@@ -143,7 +160,8 @@ typedef struct {
 } sqc_graph;
 
 /* Fill `cfg` with the defaults (no budget, 32 active qubits, FP64 chunking
- * from 12 edges, 256 terms per chunk). */
+ * from 12 edges, 256 terms per chunk, resident selection, single-launch
+ * FP32 queries; everything else off). */
 SQC_API void sqc_default_config(sqc_config* cfg);
 
 /* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
@@ -214,7 +232,7 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id q, sqc_precision p
 
 /* Select bins (Algorithm 1: keep the largest bins): among the n values at
  * device pointer `probs` (dtype), those >= threshold, ordered by value
- * descending then bin index ascending, at most k (1 <= k <= 16384).
+ * descending then bin index ascending, at most k (1 <= k <= 4096).
  * Outputs are device pointers: bins_out[k] (uint64), probs_out[k] (double),
  * n_found[1] (int32).  Uses query q's workspace; calls on the same query
  * must not overlap on the GPU.  Asynchronous on `stream`. */
@@ -247,6 +265,15 @@ SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id*
 SQC_API sqc_status sqc_batch_run(sqc_ctx* ctx, sqc_batch_id b, void* stream);
 SQC_API sqc_status sqc_batch_status(sqc_ctx* ctx, sqc_batch_id b);
 SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b);
+/* Failure-detection hook (the paper has no counterpart), host side only:
+ * with on = 1, raises by one the completion count that the batch's last
+ * intermediate tensor must reach, so that the items reading it can never
+ * start; the next sqc_batch_run then ends by the bounded wait running out
+ * (after cfg.wait_limit_ms), every CTA drains and returns, and
+ * sqc_batch_status reports SQC_ETIMEOUT.  on = 0 restores the batch.
+ * Synchronous (uploads the counts); the batch must not be running.  Fails
+ * with SQC_EINVAL for a batch without intermediate tensors. */
+SQC_API sqc_status sqc_batch_inject_stall(sqc_ctx* ctx, sqc_batch_id b, int32_t on);
 /* Project-written autotuner of the batched launch (the paper has no
  * counterpart): builds the batch of sqc_batch_create(n, qs, outs, out_dtype,
  * totals) under each tile policy -- 0 by occupancy, 1 small 32 x 32 tiles,
@@ -270,7 +297,8 @@ SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_i
  * requests in arrival order while their plans and outputs fit the context's
  * HBM budget (sqc_config.hbm_budget_bytes; a request that does not fit waits
  * until launches retire), and launches each group of admitted requests as
- * one persistent batch (plain = 1: one FP32 reconstruction per request) on
+ * one persistent batch (plain = 1: one FP32 reconstruction per request,
+ * one launch per stage -- the server turns cfg.fused_query off) on
  * one of n_streams non-blocking streams, so launches overlap; requests that
  * arrive meanwhile go into the next free stream.  A request larger than the
  * whole budget fails with SQC_EBUSY; requests still waiting when the server
@@ -319,9 +347,12 @@ SQC_API void sqc_server_destroy(sqc_server* srv);
  * library (held on every GPU that loads the library until the process
  * exits).
  *   device: the GPU that holds `probs` and the outputs (made current for
- *           the call).  The first call on a device looks up the array's
- *           device address and sets kernel attributes; make that first call
- *           before any stream capture.
+ *           the call).  The first call on a device only looks up the
+ *           array's device address (cudaGetSymbolAddress) and keeps it for
+ *           later calls; make that first call before any stream capture.
+ *           The kept address belongs to the device's primary context: after
+ *           a cudaDeviceReset the library must be reloaded before this entry
+ *           point is used again on that device.
  *   k must be in [1, 4096] (the scratch's capacity); larger k fails with
  *   SQC_ESHAPE.  Other arguments as in sqc_top_bins.
  * Every call shares the one array: calls whose GPU work may overlap (other
@@ -346,6 +377,12 @@ SQC_API sqc_status sqc_query_slices(const sqc_ctx* ctx, sqc_query_id q, int32_t*
  * workspace held. */
 SQC_API sqc_status sqc_query_info(const sqc_ctx* ctx, sqc_query_id q, int32_t* n_steps, double* flops,
                                   double* merge_bytes, uint64_t* work_bytes);
+
+/* Split-BF16 plan of query q (built by its first SPLIT_BF16 reconstruct;
+ * 0 and 0 before that): *n_tc of its *n_steps contraction steps run on the
+ * tcgen05 tensor cores, the others (M or N below 128) in FP32 on the SIMT
+ * cores.  Host values, no device work.  n_steps may be NULL. */
+SQC_API sqc_status sqc_query_tc_steps(const sqc_ctx* ctx, sqc_query_id q, int32_t* n_tc, int32_t* n_steps);
 
 /* Shape of contraction step `step` (0-based, in launch order) of query q:
  * the step computes C[M][N] = sum over Kd of A[M][Kd] * B[N][Kd]

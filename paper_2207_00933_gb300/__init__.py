@@ -39,7 +39,8 @@ class _Config(ctypes.Structure):
                 ("fp64_chunk_min_edges", ctypes.c_int32), ("chunk_terms", ctypes.c_int32),
                 ("slice_edges", ctypes.c_int32), ("select_resident", ctypes.c_int32),
                 ("merge_pyramid", ctypes.c_int32), ("slice_input_log2", ctypes.c_int32),
-                ("slice_intermediate_log2", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("slice_intermediate_log2", ctypes.c_int32), ("tc_pairs", ctypes.c_int32),
+                ("wait_limit_ms", ctypes.c_int32), ("fused_query", ctypes.c_int32)]
 
 
 class _Graph(ctypes.Structure):
@@ -68,12 +69,14 @@ _SIGS = {
                                     _c.POINTER(_c.c_double), _c.POINTER(_c.c_uint64)]),
     "sqc_query_step": (_c.c_int32, [_P, _c.c_int64, _c.c_int32, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64),
                                     _c.POINTER(_c.c_int64)]),
+    "sqc_query_tc_steps": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32)]),
     "sqc_top_bins_noalloc": (_c.c_int32, [_c.c_int, _P, _c.c_int, _c.c_uint64, _c.c_int32, _c.c_double, _P, _P,
                                           _P, _P]),
     "sqc_batch_create": (_c.c_int32, [_P, _c.c_int32, _P, _P, _c.c_int, _P, _c.POINTER(_c.c_int64)]),
     "sqc_batch_run": (_c.c_int32, [_P, _c.c_int64, _P]),
     "sqc_batch_status": (_c.c_int32, [_P, _c.c_int64]),
     "sqc_batch_release": (_c.c_int32, [_P, _c.c_int64]),
+    "sqc_batch_inject_stall": (_c.c_int32, [_P, _c.c_int64, _c.c_int32]),
     "sqc_plan_preview": (_c.c_int32, [_P, _P, _P, _c.POINTER(_c.c_int32), _P, _c.c_int32,
                                       _c.POINTER(_c.c_int32), _P, _c.c_int32, _P, _P, _c.c_char_p, _c.c_int32]),
     "sqc_batch_autotune": (_c.c_int32, [_P, _c.c_int32, _P, _P, _c.c_int, _P, _c.c_int32,
@@ -154,7 +157,8 @@ class Context:
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_active_qubits: int = 32,
                  fp64_chunk_min_edges: int = 12, chunk_terms: int = 256, slice_edges: int = 0,
                  select_resident: bool = True, merge_pyramid: bool = False, slice_input_log2: int = 0,
-                 slice_intermediate_log2: int = 0):
+                 slice_intermediate_log2: int = 0, tc_pairs: bool | None = None, wait_limit_ms: int = 0,
+                 fused_query: bool = True):
         self._lib = load_library()
         cfg = _Config()
         self._lib.sqc_default_config(ctypes.byref(cfg))
@@ -167,6 +171,10 @@ class Context:
         cfg.merge_pyramid = int(bool(merge_pyramid))
         cfg.slice_input_log2 = slice_input_log2
         cfg.slice_intermediate_log2 = slice_intermediate_log2
+        if tc_pairs is not None:
+            cfg.tc_pairs = int(bool(tc_pairs))
+        cfg.wait_limit_ms = wait_limit_ms
+        cfg.fused_query = int(bool(fused_query))
         h = _P()
         st = self._lib.sqc_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != 0:
@@ -284,6 +292,12 @@ class Context:
             out.append((m.value, n.value, k.value))
         return out
 
+    def query_tc_steps(self, query: int) -> tuple[int, int]:
+        """(steps on the tensor cores, steps) of the query's split-BF16 plan."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.sqc_query_tc_steps(self._h, query, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def reconstruct(self, query: int, out, precision: str = "fp32", total_prob=None, stream=None):
         """Bins of `query` into the device tensor `out` (float32/float64,
         2^n_active elements); total_prob: optional device float64 tensor of
@@ -319,6 +333,9 @@ class Context:
 
     def batch_release(self, batch: int):
         self._check(self._lib.sqc_batch_release(self._h, batch))
+
+    def batch_inject_stall(self, batch: int, on: bool = True):
+        self._check(self._lib.sqc_batch_inject_stall(self._h, batch, int(bool(on))))
 
     def batch_autotune(self, queries: list[int], outs: list, totals=None, reps: int = 5):
         """Time the batched launch of `queries` under each tile policy

@@ -110,6 +110,7 @@ struct Batch {
   BatchLaunch L{};
   int grid = 0;
   std::vector<sqc_query_id> queries;
+  std::vector<unsigned> expected;    // host copy of the completion targets
 };
 
 struct Query {
@@ -122,6 +123,10 @@ struct Query {
   size_t sel_bytes = 0;
   int sel_grid = 0;
   double merge_bytes = 0.0;
+  // single-launch FP32 reconstruction (merge and every step in one
+  // persistent launch), one per output format [OUT_F32], [OUT_F64]; built
+  // by the first FP32 reconstruct into that format
+  std::unique_ptr<Batch> solo[2];
 };
 
 }  // namespace
@@ -265,6 +270,12 @@ cudaError_t zero(sqc_ctx* ctx, void* dst, size_t bytes) {
 }
 
 inline int popc32(uint32_t x) { return __builtin_popcount(x); }
+
+// Limit of every bounded device wait, from the configuration.
+uint64_t wait_ns(const sqc_ctx* ctx) {
+  const int ms = ctx->cfg.wait_limit_ms > 0 ? ctx->cfg.wait_limit_ms : 2000;
+  return uint64_t(ms) * 1000000ull;
+}
 
 // ---- graph validation ---------------------------------------------------------
 
@@ -470,6 +481,11 @@ void free_plan(sqc_ctx* ctx, Plan* p) {
 }
 
 void free_query(sqc_ctx* ctx, Query* q) {
+  for (auto& b : q->solo)
+    if (b) {
+      dev_free(ctx, b->work, b->work_bytes);
+      b.reset();
+    }
   for (Plan& p : q->plans) free_plan(ctx, &p);
   dev_free(ctx, q->sel_mem, q->sel_bytes);
   q->sel_mem = nullptr;
@@ -814,11 +830,10 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     st.Kd = int64_t(1) << sh.size();
     st.M = int64_t(1) << fx.size();
     st.N = int64_t(1) << fy.size();
-    // tensor cores for the big steps: M, N >= 128 (one UMMA tile), and a
-    // shared index short enough to be one FP32 chunk
-    st.tc = tc_ok && st.M >= gemm_tc_min_rows() && st.N >= gemm_tc_min_rows() &&
-            (st.Kd <= ctx->cfg.chunk_terms || c.K < ctx->cfg.fp64_chunk_min_edges) &&
-            !(P->n_slices > 1 && s == int(P->steps.size()) - 1);   // slices accumulate on the SIMT path
+    // tensor cores for the big steps: M, N >= 128 (one UMMA tile); the
+    // kernel sums a long shared index in FP32 passes added in FP64 and adds
+    // later slices into the output itself
+    st.tc = tc_ok && st.M >= gemm_tc_min_rows() && st.N >= gemm_tc_min_rows();
     st.Kp = st.tc ? std::max<int64_t>(st.Kd, gemm_tc_k_align()) : st.Kd;
     std::vector<int> lay = sh;
     for (int p = ilog2(st.Kd); p < ilog2(st.Kp); ++p) lay.push_back(kPad);
@@ -970,6 +985,146 @@ sqc_status ensure_select_work(sqc_ctx* ctx, Query* q) {
   return SQC_OK;
 }
 
+// Work list of one persistent launch over the FP32 plans of n queries
+// (shared by sqc_batch_create and the single-query launch of
+// sqc_reconstruct).  solo: one query whose output and probability sum are
+// named per launch (BatchLaunch::out / total) instead of being baked in.
+sqc_status build_batch(sqc_ctx* ctx, int32_t n, Query* const* qv, void* const* outs, int out_kind, double* totals,
+                       bool solo, std::unique_ptr<Batch>* out_b) {
+  std::vector<MergeDesc> mdescs;
+  std::vector<BatchStep> steps;
+  std::vector<unsigned> expected;
+  struct Pending { BatchItem it; int level; };
+  std::vector<Pending> items;
+  std::vector<int64_t> part_off;     // per batch step with a probability sum: offset into partials
+  int64_t n_parts = 0;
+  for (int j = 0; j < n; ++j) {
+    Query& q = *qv[j];
+    auto cit = ctx->circuits.find(q.circuit);
+    if (cit == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "batch: circuit of a query was unloaded");
+    const Circuit& c = *cit->second;
+    Plan& P = q.plans[SQC_PREC_FP32];
+    if (P.steps.empty()) return fail(ctx, SQC_EINVAL, "batch: every query needs at least two subcircuits");
+    if (P.n_slices > 1) return fail(ctx, SQC_EINVAL, "batch: sliced queries (cfg.slice_edges > 0) run one at a time");
+    if (!solo && !outs[j]) return fail(ctx, SQC_EINVAL, "batch: null output");
+    // tensor slots of this query
+    std::vector<int> slot(P.tensors.size(), -1), level(P.tensors.size(), 0);
+    for (size_t t = 0; t < P.tensors.size(); ++t) {
+      if (int(t) == P.final_tensor) continue;
+      slot[t] = int(expected.size());
+      expected.push_back(0);
+    }
+    for (int i = 0; i < c.nC; ++i) {
+      const int di = int(mdescs.size());
+      mdescs.push_back(P.merge_host[i]);
+      const MergeDesc& d = P.merge_host[i];
+      const int64_t per = 256 / d.lanes;
+      const int64_t nblk = ((d.rows << d.a) + per - 1) / per;
+      for (int64_t b = 0; b < nblk; ++b) items.push_back({{kItemMerge, di, b, -1, -1, slot[i]}, 0});
+      expected[slot[i]] = unsigned(nblk);
+    }
+    const double alpha = std::ldexp(1.0, -c.K);
+    for (size_t si = 0; si < P.steps.size(); ++si) {
+      const Step& st = P.steps[si];
+      const bool last = si + 1 == P.steps.size();
+      BatchStep bs{};
+      GemmArgs& a = bs.a;
+      a.A = static_cast<const float*>(P.tensors[st.x].buf);
+      a.B = static_cast<const float*>(P.tensors[st.y].buf);
+      a.M = st.M;
+      a.N = st.N;
+      a.K = st.Kd;
+      a.rowmap = st.rowmap;
+      a.colmap = st.colmap;
+      a.vec4 = st.vec4;
+      a.C = last ? (solo ? nullptr : outs[j]) : P.tensors[st.z].buf;
+      a.kind = last ? out_kind : OUT_F32;
+      a.alpha = last ? alpha : 1.0;
+      a.chunk = (last && out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
+                    ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
+                    : 0;
+      bs.from_launch = last && solo;
+      int64_t bm = 0, bn = 0;
+      bs.cfg = batch_tile_cfg(a.M, a.N, a.K, a.chunk > 0, a.chunk, &bm, &bn, ctx->batch_policy);
+      bs.ntiles = ((a.M + bm - 1) / bm) * ((a.N + bn - 1) / bn);
+      if (last && (totals || solo)) {
+        part_off.push_back(n_parts);
+        bs.total = solo ? nullptr : totals + j;
+        n_parts += bs.ntiles;
+      } else {
+        part_off.push_back(-1);
+      }
+      const int lvl = 1 + std::max(level[st.x], level[st.y]);
+      level[st.z] = lvl;
+      const int si_b = int(steps.size());
+      steps.push_back(bs);
+      for (int64_t t = 0; t < bs.ntiles; ++t)
+        items.push_back({{kItemGemm, si_b, t, slot[st.x], slot[st.y], last ? -1 : slot[st.z]}, lvl});
+      if (!last) expected[slot[st.z]] = unsigned(bs.ntiles);
+    }
+  }
+  // dependency order: merges, then steps level by level (stable)
+  std::stable_sort(items.begin(), items.end(), [](const Pending& a, const Pending& b) { return a.level < b.level; });
+
+  auto B = std::make_unique<Batch>();
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t o_items = off; off = align(off + sizeof(BatchItem) * items.size());
+  const size_t o_md = off; off = align(off + sizeof(MergeDesc) * mdescs.size());
+  const size_t o_st = off; off = align(off + sizeof(BatchStep) * steps.size());
+  const size_t o_cnt = off; off = align(off + sizeof(unsigned) * expected.size());
+  const size_t o_exp = off; off = align(off + sizeof(unsigned) * expected.size());
+  const size_t o_part = off; off = align(off + sizeof(double) * size_t(std::max<int64_t>(n_parts, 1)));
+  const size_t o_pc = off; off = align(off + sizeof(unsigned) * steps.size());
+  const size_t o_ctl = off; off = align(off + 64);
+  B->work_bytes = off;
+  sqc_status st = dev_alloc(ctx, &B->work, off);
+  if (st != SQC_OK) return st;
+  char* base = static_cast<char*>(B->work);
+  for (size_t k = 0; k < steps.size(); ++k) {
+    steps[k].counter = reinterpret_cast<unsigned*>(base + o_pc) + k;
+    if (part_off[k] >= 0) {
+      steps[k].partials = reinterpret_cast<double*>(base + o_part) + part_off[k];
+      steps[k].a.partials = steps[k].partials;     // marks the query's last step
+      steps[k].a.counter = steps[k].counter;
+      steps[k].a.total = steps[k].total;
+    }
+  }
+  std::vector<BatchItem> flat(items.size());
+  for (size_t k = 0; k < items.size(); ++k) flat[k] = items[k].it;
+  cudaError_t e = upload(ctx, base + o_items, flat.data(), sizeof(BatchItem) * flat.size());
+  if (e == cudaSuccess && !mdescs.empty()) e = upload(ctx, base + o_md, mdescs.data(), sizeof(MergeDesc) * mdescs.size());
+  if (e == cudaSuccess) e = upload(ctx, base + o_st, steps.data(), sizeof(BatchStep) * steps.size());
+  if (e == cudaSuccess) e = upload(ctx, base + o_exp, expected.data(), sizeof(unsigned) * expected.size());
+  if (e == cudaSuccess) e = zero(ctx, base + o_cnt, sizeof(unsigned) * expected.size());
+  if (e == cudaSuccess) e = zero(ctx, base + o_pc, sizeof(unsigned) * steps.size());
+  if (e == cudaSuccess) e = zero(ctx, base + o_ctl, 64);
+  if (e != cudaSuccess) {
+    dev_free(ctx, B->work, B->work_bytes);
+    return cuda_fail(ctx, e, "batch upload");
+  }
+  BatchLaunch& L = B->L;
+  L.items = reinterpret_cast<const BatchItem*>(base + o_items);
+  L.n_items = int64_t(flat.size());
+  L.mdescs = reinterpret_cast<const MergeDesc*>(base + o_md);
+  L.steps = reinterpret_cast<const BatchStep*>(base + o_st);
+  L.counts = reinterpret_cast<unsigned*>(base + o_cnt);
+  L.expected = reinterpret_cast<const unsigned*>(base + o_exp);
+  L.n_slots = int64_t(expected.size());
+  L.head = reinterpret_cast<unsigned long long*>(base + o_ctl);
+  L.done = reinterpret_cast<unsigned*>(base + o_ctl + 8);
+  L.abort = reinterpret_cast<int*>(base + o_ctl + 16);
+  L.err = reinterpret_cast<int*>(base + o_ctl + 20);
+  L.wait_ns = wait_ns(ctx);
+  int sms = 152, per = 2;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  B->grid = int(std::min<int64_t>(int64_t(sms) * per, L.n_items));
+  B->expected = std::move(expected);
+  *out_b = std::move(B);
+  return SQC_OK;
+}
+
+
 }  // namespace
 
 // Hooks for the serving loop (server.cu), which drives a context from its
@@ -1036,6 +1191,7 @@ void ctx_set_alloc_stream(sqc_ctx* ctx, cudaStream_t s) {
   ctx->async_alloc = s != nullptr;
 }
 int ctx_device(const sqc_ctx* ctx) { return ctx->device; }
+void ctx_set_fused(sqc_ctx* ctx, bool on) { ctx->cfg.fused_query = on ? 1 : 0; }
 sqc_status ctx_alloc(sqc_ctx* ctx, void** p, size_t bytes) { return dev_alloc(ctx, p, bytes); }
 void ctx_free(sqc_ctx* ctx, void* p, size_t bytes) { dev_free(ctx, p, bytes); }
 sqc_status ctx_fail(sqc_ctx* ctx, sqc_status st, const char* msg) { return fail(ctx, st, msg); }
@@ -1049,6 +1205,9 @@ std::string config_error(const sqc_config& c) {
   if (c.slice_edges < 0 || c.slice_edges > 8) return "slice_edges must be in [0, 8]";
   if (c.select_resident != 0 && c.select_resident != 1) return "select_resident must be 0 or 1";
   if (c.merge_pyramid != 0 && c.merge_pyramid != 1) return "merge_pyramid must be 0 or 1";
+  if (c.tc_pairs != 0 && c.tc_pairs != 1) return "tc_pairs must be 0 or 1";
+  if (c.wait_limit_ms < 0 || c.wait_limit_ms > 600000) return "wait_limit_ms must be in [0, 600000]";
+  if (c.fused_query != 0 && c.fused_query != 1) return "fused_query must be 0 or 1";
   if (c.slice_input_log2 < 0 || c.slice_input_log2 > 62 || c.slice_intermediate_log2 < 0 ||
       c.slice_intermediate_log2 > 62)
     return "slice_input_log2 and slice_intermediate_log2 must be in [0, 62]";
@@ -1068,6 +1227,7 @@ SQC_API void sqc_default_config(sqc_config* cfg) {
   cfg->fp64_chunk_min_edges = 12;
   cfg->chunk_terms = 256;
   cfg->select_resident = 1;
+  cfg->fused_query = 1;
 }
 
 SQC_API const char* sqc_last_error(const sqc_ctx* ctx) {
@@ -1287,6 +1447,19 @@ SQC_API sqc_status sqc_query_step(const sqc_ctx* cctx, sqc_query_id qid, int32_t
   return SQC_OK;
 }
 
+SQC_API sqc_status sqc_query_tc_steps(const sqc_ctx* cctx, sqc_query_id qid, int32_t* n_tc, int32_t* n_steps) {
+  sqc_ctx* ctx = const_cast<sqc_ctx*>(cctx);
+  if (!ctx || !n_tc) return SQC_EINVAL;
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  const Plan& P = it->second->plans[SQC_PREC_SPLIT_BF16];
+  int32_t k = 0;
+  for (const Step& st : P.steps) k += st.tc ? 1 : 0;
+  *n_tc = k;
+  if (n_steps) *n_steps = P.built ? int32_t(P.steps.size()) : 0;
+  return SQC_OK;
+}
+
 SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
                                    sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream) {
   if (!ctx || !out_bins) return fail(ctx, SQC_EINVAL, "null argument");
@@ -1312,6 +1485,26 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int out_kind = out_dtype == SQC_F64 ? OUT_F64 : OUT_F32;
   const double alpha = std::ldexp(1.0, -c.K);
+
+  if (precision == SQC_PREC_FP32 && ctx->cfg.fused_query && P.n_slices == 1 && !P.steps.empty()) {
+    // the merge and every contraction step in ONE persistent launch: merge
+    // blocks and step tiles form a dependency-ordered work list, each item
+    // waiting only for the tensors it reads (the batched level's kernel
+    // with one query); the same bins as the per-step launches below
+    std::unique_ptr<Batch>& sb = q.solo[out_kind];
+    if (!sb) {
+      Query* qp = &q;
+      sqc_status st = build_batch(ctx, 1, &qp, nullptr, out_kind, nullptr, true, &sb);
+      if (st != SQC_OK) return st;
+    }
+    BatchLaunch L = sb->L;
+    L.out = out_bins;
+    L.total = total_prob;
+    StageScope scope(ctx, s, SQC_STAGE_CONTRACT);
+    CK(launch_batch(L, sb->grid, s));
+    ctx->launches += 1;
+    return SQC_OK;
+  }
 
   if (P.steps.empty()) {
     // one subcircuit: the merge writes the bins directly
@@ -1365,12 +1558,19 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
         a.kind = kind;
         a.plane_stride = last ? 0 : Z.plane_stride;
         a.alpha = last ? alpha : 1.0;
-        a.chunk = 0;
+        // the cross-chunk FP64 sum (Section 6.3): same rule as the SIMT path
+        a.chunk = (last && out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges &&
+                   st.Kd > ctx->cfg.chunk_terms)
+                      ? ctx->cfg.chunk_terms
+                      : 0;
+        a.accumulate = last && sg > 0;
         a.partials = sums_here ? P.partials : nullptr;
         a.counter = P.counter;
         a.total = total_prob;
         a.err = P.err;
         a.contig16 = st.contig16;
+        a.pairs = ctx->cfg.tc_pairs;
+        a.wait_ns = wait_ns(ctx);
         CK(launch_gemm_tc(a, s));
       } else {
         GemmArgs a{};
@@ -1448,135 +1648,15 @@ SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id*
   if (!ctx || !qs || !outs || !out_b || n < 1) return fail(ctx, SQC_EINVAL, "batch: null argument or n < 1");
   if (out_dtype != SQC_F32 && out_dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "out_dtype must be F32 or F64");
   DeviceGuard g(ctx->device);
-  const int out_kind = out_dtype == SQC_F64 ? OUT_F64 : OUT_F32;
-  std::vector<MergeDesc> mdescs;
-  std::vector<BatchStep> steps;
-  std::vector<unsigned> expected;
-  struct Pending { BatchItem it; int level; };
-  std::vector<Pending> items;
-  std::vector<int64_t> part_off;     // per batch step with a probability sum: offset into partials
-  int64_t n_parts = 0;
+  std::vector<Query*> qv(n);
   for (int j = 0; j < n; ++j) {
     auto it = ctx->queries.find(qs[j]);
     if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "batch: unknown query");
-    Query& q = *it->second;
-    auto cit = ctx->circuits.find(q.circuit);
-    if (cit == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "batch: circuit of a query was unloaded");
-    const Circuit& c = *cit->second;
-    Plan& P = q.plans[SQC_PREC_FP32];
-    if (P.steps.empty()) return fail(ctx, SQC_EINVAL, "batch: every query needs at least two subcircuits");
-    if (P.n_slices > 1) return fail(ctx, SQC_EINVAL, "batch: sliced queries (cfg.slice_edges > 0) run one at a time");
-    if (!outs[j]) return fail(ctx, SQC_EINVAL, "batch: null output");
-    // tensor slots of this query
-    std::vector<int> slot(P.tensors.size(), -1), level(P.tensors.size(), 0);
-    for (size_t t = 0; t < P.tensors.size(); ++t) {
-      if (int(t) == P.final_tensor) continue;
-      slot[t] = int(expected.size());
-      expected.push_back(0);
-    }
-    for (int i = 0; i < c.nC; ++i) {
-      const int di = int(mdescs.size());
-      mdescs.push_back(P.merge_host[i]);
-      const MergeDesc& d = P.merge_host[i];
-      const int64_t per = 256 / d.lanes;
-      const int64_t nblk = ((d.rows << d.a) + per - 1) / per;
-      for (int64_t b = 0; b < nblk; ++b) items.push_back({{kItemMerge, di, b, -1, -1, slot[i]}, 0});
-      expected[slot[i]] = unsigned(nblk);
-    }
-    const double alpha = std::ldexp(1.0, -c.K);
-    for (size_t si = 0; si < P.steps.size(); ++si) {
-      const Step& st = P.steps[si];
-      const bool last = si + 1 == P.steps.size();
-      BatchStep bs{};
-      GemmArgs& a = bs.a;
-      a.A = static_cast<const float*>(P.tensors[st.x].buf);
-      a.B = static_cast<const float*>(P.tensors[st.y].buf);
-      a.M = st.M;
-      a.N = st.N;
-      a.K = st.Kd;
-      a.rowmap = st.rowmap;
-      a.colmap = st.colmap;
-      a.vec4 = st.vec4;
-      a.C = last ? outs[j] : P.tensors[st.z].buf;
-      a.kind = last ? out_kind : OUT_F32;
-      a.alpha = last ? alpha : 1.0;
-      a.chunk = (last && out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
-                    ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
-                    : 0;
-      int64_t bm = 0, bn = 0;
-      bs.cfg = batch_tile_cfg(a.M, a.N, a.K, a.chunk > 0, a.chunk, &bm, &bn, ctx->batch_policy);
-      bs.ntiles = ((a.M + bm - 1) / bm) * ((a.N + bn - 1) / bn);
-      if (last && totals) {
-        part_off.push_back(n_parts);
-        bs.total = totals + j;
-        n_parts += bs.ntiles;
-      } else {
-        part_off.push_back(-1);
-      }
-      const int lvl = 1 + std::max(level[st.x], level[st.y]);
-      level[st.z] = lvl;
-      const int si_b = int(steps.size());
-      steps.push_back(bs);
-      for (int64_t t = 0; t < bs.ntiles; ++t)
-        items.push_back({{kItemGemm, si_b, t, slot[st.x], slot[st.y], last ? -1 : slot[st.z]}, lvl});
-      if (!last) expected[slot[st.z]] = unsigned(bs.ntiles);
-    }
+    qv[j] = it->second.get();
   }
-  // dependency order: merges, then steps level by level (stable)
-  std::stable_sort(items.begin(), items.end(), [](const Pending& a, const Pending& b) { return a.level < b.level; });
-
-  auto B = std::make_unique<Batch>();
-  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
-  size_t off = 0;
-  const size_t o_items = off; off = align(off + sizeof(BatchItem) * items.size());
-  const size_t o_md = off; off = align(off + sizeof(MergeDesc) * mdescs.size());
-  const size_t o_st = off; off = align(off + sizeof(BatchStep) * steps.size());
-  const size_t o_cnt = off; off = align(off + sizeof(unsigned) * expected.size());
-  const size_t o_exp = off; off = align(off + sizeof(unsigned) * expected.size());
-  const size_t o_part = off; off = align(off + sizeof(double) * size_t(std::max<int64_t>(n_parts, 1)));
-  const size_t o_pc = off; off = align(off + sizeof(unsigned) * steps.size());
-  const size_t o_ctl = off; off = align(off + 64);
-  B->work_bytes = off;
-  sqc_status st = dev_alloc(ctx, &B->work, off);
+  std::unique_ptr<Batch> B;
+  sqc_status st = build_batch(ctx, n, qv.data(), outs, out_dtype == SQC_F64 ? OUT_F64 : OUT_F32, totals, false, &B);
   if (st != SQC_OK) return st;
-  char* base = static_cast<char*>(B->work);
-  for (size_t k = 0; k < steps.size(); ++k) {
-    steps[k].counter = reinterpret_cast<unsigned*>(base + o_pc) + k;
-    if (part_off[k] >= 0) {
-      steps[k].partials = reinterpret_cast<double*>(base + o_part) + part_off[k];
-      steps[k].a.partials = steps[k].partials;     // marks the query's last step
-      steps[k].a.counter = steps[k].counter;
-      steps[k].a.total = steps[k].total;
-    }
-  }
-  std::vector<BatchItem> flat(items.size());
-  for (size_t k = 0; k < items.size(); ++k) flat[k] = items[k].it;
-  cudaError_t e = upload(ctx, base + o_items, flat.data(), sizeof(BatchItem) * flat.size());
-  if (e == cudaSuccess && !mdescs.empty()) e = upload(ctx, base + o_md, mdescs.data(), sizeof(MergeDesc) * mdescs.size());
-  if (e == cudaSuccess) e = upload(ctx, base + o_st, steps.data(), sizeof(BatchStep) * steps.size());
-  if (e == cudaSuccess) e = upload(ctx, base + o_exp, expected.data(), sizeof(unsigned) * expected.size());
-  if (e == cudaSuccess) e = zero(ctx, base + o_cnt, sizeof(unsigned) * expected.size());
-  if (e == cudaSuccess) e = zero(ctx, base + o_pc, sizeof(unsigned) * steps.size());
-  if (e == cudaSuccess) e = zero(ctx, base + o_ctl, 64);
-  if (e != cudaSuccess) {
-    dev_free(ctx, B->work, B->work_bytes);
-    return cuda_fail(ctx, e, "batch upload");
-  }
-  BatchLaunch& L = B->L;
-  L.items = reinterpret_cast<const BatchItem*>(base + o_items);
-  L.n_items = int64_t(flat.size());
-  L.mdescs = reinterpret_cast<const MergeDesc*>(base + o_md);
-  L.steps = reinterpret_cast<const BatchStep*>(base + o_st);
-  L.counts = reinterpret_cast<unsigned*>(base + o_cnt);
-  L.expected = reinterpret_cast<const unsigned*>(base + o_exp);
-  L.n_slots = int64_t(expected.size());
-  L.head = reinterpret_cast<unsigned long long*>(base + o_ctl);
-  L.done = reinterpret_cast<unsigned*>(base + o_ctl + 8);
-  L.abort = reinterpret_cast<int*>(base + o_ctl + 16);
-  L.err = reinterpret_cast<int*>(base + o_ctl + 20);
-  int sms = 152, per = 2;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  B->grid = int(std::min<int64_t>(int64_t(sms) * per, L.n_items));
   B->queries.assign(qs, qs + n);
   const int64_t id = ctx->next_id++;
   ctx->batches[id] = std::move(B);
@@ -1609,6 +1689,21 @@ SQC_API sqc_status sqc_batch_status(sqc_ctx* ctx, sqc_batch_id b) {
     CK(cudaMemcpy(it->second->L.err, &zero, sizeof(int), cudaMemcpyHostToDevice));
     return fail(ctx, SQC_ETIMEOUT, "batch: a bounded device wait gave up");
   }
+  return SQC_OK;
+}
+
+SQC_API sqc_status sqc_batch_inject_stall(sqc_ctx* ctx, sqc_batch_id b, int32_t on) {
+  if (!ctx) return SQC_EINVAL;
+  auto it = ctx->batches.find(b);
+  if (it == ctx->batches.end()) return fail(ctx, SQC_ENOTFOUND, "unknown batch");
+  Batch& B = *it->second;
+  if (B.expected.empty()) return fail(ctx, SQC_EINVAL, "batch has no intermediate tensor to stall");
+  DeviceGuard g(ctx->device);
+  std::vector<unsigned> e = B.expected;
+  if (on) e.back() += 1u;        // one completion more than its producers will ever deliver
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(const_cast<unsigned*>(B.L.expected), e.data(), sizeof(unsigned) * e.size(),
+                cudaMemcpyHostToDevice));
   return SQC_OK;
 }
 
@@ -1730,12 +1825,6 @@ SQC_API sqc_status sqc_top_bins_noalloc(int device, const void* probs, sqc_dtype
     return fail(nullptr, e != cudaSuccess ? SQC_ECUDA : SQC_EINVAL, "no such CUDA device");
   }
   DeviceGuard g(device);
-  static thread_local bool configured[64] = {false};
-  if (device < 64 && !configured[device]) {
-    e = select_configure();
-    if (e != cudaSuccess) return fail(nullptr, SQC_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(e));
-    configured[device] = true;
-  }
   e = launch_select_static(device, probs, dtype == SQC_F64, n, k, threshold,
                            reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found,
                            static_cast<cudaStream_t>(stream));

@@ -20,7 +20,11 @@ namespace sqc {
 
 namespace {
 
-constexpr uint32_t kWaitLimit = 1u << 22;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -29,8 +33,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 // Per-query FP64 probability sum over the final step's tiles: each tile
-// stores its partial, the last one adds them in tile order.
-__device__ __forceinline__ void finish_query_total(double mine, const BatchStep& st, int64_t tile, double* red) {
+// stores its partial, the last one adds them in tile order into *total.
+__device__ __forceinline__ void finish_query_total(double mine, const BatchStep& st, int64_t tile, double* total,
+                                                   double* red) {
   __shared__ bool is_last;
   const double bs = block_sum(mine, red);
   if (threadIdx.x == 0) {
@@ -46,18 +51,18 @@ __device__ __forceinline__ void finish_query_total(double mine, const BatchStep&
   for (int64_t i = threadIdx.x; i < st.ntiles; i += blockDim.x) s += static_cast<volatile double*>(st.partials)[i];
   const double tot = block_sum(s, red);
   if (threadIdx.x == 0) {
-    *st.total = tot;
+    *total = tot;
     *st.counter = 0u;
   }
 }
 
 template <int BM, int BN, int TM, int TN, bool CH, int BK>
-__device__ __forceinline__ double run_tile(const BatchStep& st, int64_t tile, float* smem) {
+__device__ __forceinline__ double run_tile(const BatchStep& st, int64_t tile, float* smem, void* C) {
   const int64_t tiles_n = (st.a.N + BN - 1) / BN;
   const int tn_shift = __ffsll(tiles_n) - 1;
   const int64_t m0 = (tile >> tn_shift) * BM;
   const int64_t n0 = (tile & (tiles_n - 1)) * BN;
-  return gemm_tile<BM, BN, TM, TN, CH, BK>(st.a, m0, n0, smem, smem + BK * (BM + 4));
+  return gemm_tile<BM, BN, TM, TN, CH, BK>(st.a, m0, n0, smem, smem + BK * (BM + 4), C);
 }
 
 __global__ void __launch_bounds__(kOpThreads, 2) batch_kernel(BatchLaunch L) {
@@ -81,11 +86,18 @@ __global__ void __launch_bounds__(kOpThreads, 2) batch_kernel(BatchLaunch L) {
         const int dep = k ? item.dep1 : item.dep0;
         if (dep < 0) continue;
         uint32_t i = 0;
+        uint64_t t0 = 0;
         while (ld_acquire(L.counts + dep) < L.expected[dep]) {
-          if (++i > kWaitLimit || *static_cast<volatile int*>(L.abort)) {
-            atomicExch(L.abort, 1);
-            atomicExch(L.err, 1);
-            break;
+          if (*static_cast<volatile int*>(L.abort)) break;     // another CTA gave up: drain
+          if ((++i & 31) == 0) {
+            const uint64_t now = global_ns();
+            if (t0 == 0) {
+              t0 = now;
+            } else if (now - t0 > L.wait_ns) {
+              atomicExch(L.abort, 1);
+              atomicExch(L.err, 1);
+              break;
+            }
           }
           if (i > 32) __nanosleep(64);
         }
@@ -99,17 +111,21 @@ __global__ void __launch_bounds__(kOpThreads, 2) batch_kernel(BatchLaunch L) {
         merge_block(md, item.tile);
       } else {
         const BatchStep& st = L.steps[item.idx];
+        // a single-query launch names its output and probability sum per
+        // run; a batch baked them into its steps
+        void* C = st.from_launch ? L.out : st.a.C;
+        double* total = st.from_launch ? L.total : st.total;
         double mine;
         switch (st.cfg) {
-          case 0: mine = run_tile<32, 32, 2, 2, false, 16>(st, item.tile, smem); break;
-          case 1: mine = run_tile<64, 64, 4, 4, false, 16>(st, item.tile, smem); break;
-          case 2: mine = run_tile<128, 64, 8, 4, false, 16>(st, item.tile, smem); break;
-          case 3: mine = run_tile<32, 32, 2, 2, false, 64>(st, item.tile, smem); break;
-          case 4: mine = run_tile<64, 64, 4, 4, false, 64>(st, item.tile, smem); break;
-          case 5: mine = run_tile<32, 32, 2, 2, true, 16>(st, item.tile, smem); break;
-          default: mine = run_tile<64, 64, 4, 4, true, 16>(st, item.tile, smem); break;
+          case 0: mine = run_tile<32, 32, 2, 2, false, 16>(st, item.tile, smem, C); break;
+          case 1: mine = run_tile<64, 64, 4, 4, false, 16>(st, item.tile, smem, C); break;
+          case 2: mine = run_tile<128, 64, 8, 4, false, 16>(st, item.tile, smem, C); break;
+          case 3: mine = run_tile<32, 32, 2, 2, false, 64>(st, item.tile, smem, C); break;
+          case 4: mine = run_tile<64, 64, 4, 4, false, 64>(st, item.tile, smem, C); break;
+          case 5: mine = run_tile<32, 32, 2, 2, true, 16>(st, item.tile, smem, C); break;
+          default: mine = run_tile<64, 64, 4, 4, true, 16>(st, item.tile, smem, C); break;
         }
-        if (st.a.partials) finish_query_total(mine, st, item.tile, red);
+        if (st.a.partials && total) finish_query_total(mine, st, item.tile, total, red);
       }
     }
     __syncthreads();

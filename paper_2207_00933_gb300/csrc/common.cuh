@@ -7,6 +7,36 @@
 
 namespace sqc {
 
+// Exact widening of an FP32 value to FP64 by moving its bits (IEEE 754
+// binary32 -> binary64: same sign, exponent rebiased from 127 to 1023, the
+// 23 fraction bits at the top of the 52-bit fraction; subnormals
+// normalised; infinities and NaNs keep their payload).  Integer operations
+// only: the FP64 pipe of this GPU is narrow, and an FP64 output would
+// otherwise spend it on one conversion per element.
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t m = u & 0x7fffffu;
+  uint32_t hi, lo;
+  if (e - 1u < 0xfeu) {                      // normal: 1 <= e <= 254
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  } else if (e == 0xffu) {                   // infinity or NaN
+    hi = sign | 0x7ff00000u | (m >> 3);
+    lo = m << 29;
+  } else if (m == 0u) {                      // signed zero
+    hi = sign;
+    lo = 0u;
+  } else {                                   // subnormal: m 2^-149, leading one at bit p
+    const int p = 31 - __clz(m);
+    const uint64_t f52 = uint64_t(m ^ (1u << p)) << (52 - p);
+    hi = sign | (uint32_t(p + 874) << 20) | uint32_t(f52 >> 32);
+    lo = uint32_t(f52);
+  }
+  return __hiloint2double(int(hi), int(lo));
+}
+
 // Write one result element in the destination's number format: FP32, FP64,
 // or three BF16 planes hi + mid + lo (each the round-to-nearest of what the
 // previous planes left), the operand format of the split-BF16 steps.
@@ -34,7 +64,7 @@ __device__ __forceinline__ void store_out_f(void* dst, int kind, int64_t plane_s
   if (kind == OUT_F32) {
     static_cast<float*>(dst)[off] = f;
   } else if (kind == OUT_F64) {
-    static_cast<double*>(dst)[off] = double(f);
+    static_cast<double*>(dst)[off] = f2d(f);
   } else {
     __nv_bfloat16* p = static_cast<__nv_bfloat16*>(dst);
     const __nv_bfloat16 hi = __float2bfloat16_rn(f);

@@ -63,12 +63,13 @@ constexpr int gemm_tile_smem_floats() {
 }
 
 // One BM x BN tile (origin m0, n0) of C = A B^T (Section 6.1) on 256 threads,
-// epilogue through the layout maps; returns this thread's sum of the values
-// it wrote (for the probability check).  smem_a / smem_b: kBK x (BM+4) and
-// kBK x (BN+4) floats of shared memory.
+// epilogue through the layout maps into Cout (the step's own output, or
+// the one a single-query launch names); returns this thread's sum of the
+// values it wrote (for the probability check).  smem_a / smem_b: kBK x
+// (BM+4) and kBK x (BN+4) floats of shared memory.
 template <int BM, int BN, int TM, int TN, bool CHUNKED, int kBK>
 __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64_t n0, float* smem_a,
-                                            float* smem_b) {
+                                            float* smem_b, void* Cout) {
   constexpr int kThreads = kOpThreads;
   static_assert((BM / TM) * (BN / TN) == kThreads, "tile shape");
   constexpr int TX = BN / TN;
@@ -127,7 +128,7 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
         for (int i = 0; i < TM; ++i)
 #pragma unroll
           for (int j = 0; j < TN; ++j) {
-            acc64[i][j] += double(acc[i][j] * alpha_f);
+            acc64[i][j] += f2d(acc[i][j] * alpha_f);
             acc[i][j] = 0.f;
           }
       }
@@ -152,7 +153,7 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
           q.x = acc[i][j] * alpha_f; q.y = acc[i][j + 1] * alpha_f;
           q.z = acc[i][j + 2] * alpha_f; q.w = acc[i][j + 3] * alpha_f;
           sum_f += (q.x + q.y) + (q.z + q.w);
-          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(a.C) + rbase + a.colmap[c0 + j]);
+          float4* dst = reinterpret_cast<float4*>(static_cast<float*>(Cout) + rbase + a.colmap[c0 + j]);
           if (a.accumulate) {
             const float4 o = *dst;
             q.x += o.x; q.y += o.y; q.z += o.z; q.w += o.w;
@@ -166,7 +167,7 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
           if (col >= a.N) continue;
           const float v = acc[i][j] * alpha_f;
           sum_f += v;
-          float* dst = static_cast<float*>(a.C) + rbase + a.colmap[col];
+          float* dst = static_cast<float*>(Cout) + rbase + a.colmap[col];
           *dst = a.accumulate ? *dst + v : v;
         }
       }
@@ -176,16 +177,16 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
         const int64_t col = c0 + j;
         if (col >= a.N) continue;
         double v;
-        if constexpr (CHUNKED) v = acc64[i][j]; else v = double(acc[i][j] * alpha_f);
+        if constexpr (CHUNKED) v = acc64[i][j]; else v = f2d(acc[i][j] * alpha_f);
         if (a.kind == OUT_F64) sum_d += v; else sum_f += float(v);
         if (a.accumulate && a.kind == OUT_F64) {
-          double* dst = static_cast<double*>(a.C) + rbase + a.colmap[col];
+          double* dst = static_cast<double*>(Cout) + rbase + a.colmap[col];
           *dst += v;                          // slices add up in FP64
         } else if (a.accumulate && a.kind == OUT_F32) {
-          float* dst = static_cast<float*>(a.C) + rbase + a.colmap[col];
+          float* dst = static_cast<float*>(Cout) + rbase + a.colmap[col];
           *dst += float(v);
         } else {
-          store_out(a.C, a.kind, a.plane_stride, rbase + a.colmap[col], v);
+          store_out(Cout, a.kind, a.plane_stride, rbase + a.colmap[col], v);
         }
       }
     }

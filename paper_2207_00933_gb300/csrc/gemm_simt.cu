@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs a) {
   const int64_t tile = int64_t(blockIdx.y) * gridDim.x + blockIdx.x;
   const int64_t m0 = (tile >> tn_shift) * BM;
   const int64_t n0 = (tile & (tiles_n - 1)) * BN;
-  const double mysum = gemm_tile<BM, BN, TM, TN, CHUNKED, kBK>(a, m0, n0, As, Bs);
+  const double mysum = gemm_tile<BM, BN, TM, TN, CHUNKED, kBK>(a, m0, n0, As, Bs, a.C);
   if (a.partials) finish_total(mysum, a.partials, a.counter, a.total, red);
 }
 

@@ -7,23 +7,45 @@
 // lo*hi -- all accumulated in one FP32 accumulator in tensor memory, which
 // gives about FP32 accuracy for the signed I/X/Y/Z sums.
 //
-// Persistent CTAs (one per SM) walk the 128 x 128 output tiles; 6 warps:
-//   warp 0 (one thread): TMA producer -- for each 64-wide block of the
-//     shared index it loads the three A planes and three B planes
-//     (128 x 64 BF16 each, 128-byte swizzle) into one of two pipeline stages;
-//   warp 1 (one thread): allocates 2 x 128 TMEM columns and issues
-//     tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, N = 128, K = 16):
-//     6 plane pairs x 4 K-slices per stage, then commits the stage back to
-//     the producer;
-//   warps 2-5: epilogue -- wait for a tile's last commit, read the
-//     accumulator rows with tcgen05.ld (warp w reads TMEM lanes 32*(w%4) ..
-//     +31), scale by alpha, write through rowmap/colmap (vector stores where
-//     the 16 columns are contiguous; FP32, FP64 or BF16 planes), add the
+// Persistent CTAs (one per SM) walk the output units; 10 warps:
+//   warp 0 (one thread): TMA producer -- for each BK-wide block of the
+//     shared index it loads the three A planes and three B planes into one
+//     of the pipeline stages;
+//   warp 1: allocates 2 x BN TMEM columns; one thread issues tcgen05.mma
+//     (kind::f16, BF16 x BF16 -> FP32, K = 16 per instruction): 6 plane pairs
+//     per 16-wide slice of the shared index, commits each stage back to the
+//     producer and each accumulator pass to the epilogue;
+//   warps 2-9: epilogue -- wait for a pass, read the accumulator rows with
+//     tcgen05.ld (warp w reads TMEM lanes 32*(w%4) .. +31 and half of the
+//     columns), scale by alpha, write through rowmap/colmap (vector stores
+//     where 16 columns are contiguous; FP32, FP64 or BF16 planes), add the
 //     written values into the per-CTA probability sum, and hand the TMEM
-//     buffer back.  Two accumulator buffers let the epilogue of one tile run
-//     under the MMAs of the next.
-// Every mbarrier wait is bounded; on timeout the CTA records an error code,
-// drains its own copies (bounded) and frees its TMEM before returning.
+//     buffer back.  Two accumulator buffers let the epilogue of one pass
+//     run under the MMAs of the next.
+//
+// Cross-chunk FP64 sum (Section 6.3, the 4^K edge terms for K >= 12): with
+// `chunk` > 0 a unit's shared index is summed in passes of `chunk` terms,
+// each pass accumulating in FP32 in TMEM; the epilogue adds every pass into
+// the FP64 output (the first pass stores, later passes read-add-write; a
+// unit's passes all run on one CTA, one after another, and each output
+// element is always handled by the same thread, so the additions are
+// ordered).  `accumulate` adds the step's result into C instead of
+// overwriting it (first-level slices).
+//
+// Pairs (Cfg::PAIR): clusters of two CTAs compute one 256 x BN unit with
+// tcgen05.mma.cta_group::2 (M = 256): each CTA loads its own 128 rows of A
+// and its own half of the B rows into its own shared memory with plain TMA
+// loads; the MMA, issued by the even CTA, reads both halves and leaves each
+// CTA's 128 output rows in that CTA's TMEM.  The odd CTA's warp 1 forwards
+// the completion of its loads to the even CTA's stage barrier, its epilogue
+// warps return the accumulator to the even CTA's barrier, and the even
+// CTA's commits arrive on the barriers of both.  When the units leave a
+// last wave at most half full, that wave runs as half-width units
+// (N = BN / 2).
+//
+// Every mbarrier wait is bounded in time; on timeout the CTA (and its pair
+// partner) records an error code, waits (bounded) for its own copies in
+// flight and frees its TMEM before returning.
 #include <cuda.h>
 
 #include "common.cuh"
@@ -36,37 +58,58 @@ constexpr int kBM = 128;
 constexpr int kKAlign = 64;        // the shared index is padded to a multiple of this
 constexpr int kEpiWarps = 8;       // two per TMEM lane quarter, each half of the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // default limit of one wait: 2 s
 
-// Tile configurations: BN output columns per tile, BK shared-index columns
+constexpr uint32_t make_idesc(int m, int n) {
+  // D = FP32, A = B = BF16, both K-major, M x N
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
+}
+
+// Tile configurations: BN output columns per unit, BK shared-index columns
 // per stage (BK BF16 = one swizzle row: 64 -> 128-byte swizzle, 32 ->
 // 64-byte swizzle), STAGES pipeline stages.
 //   128 x 128, BK 64, 2 stages of 96 KB (narrow steps)
 //   128 x 256, BK 32, 3 stages of 72 KB: 25% less operand traffic per flop
-template <int BN_, int BK_, int STAGES_>
+//   256 x 256 in 2-CTA pairs, BK 32, 4 stages of 48 KB per CTA
+template <int BN_, int BK_, int STAGES_, bool PAIR_>
 struct TcCfg {
   static constexpr int BN = BN_, BK = BK_, STAGES = STAGES_;
+  static constexpr bool PAIR = PAIR_;
+  static constexpr int kRowsB = PAIR ? BN / 2 : BN;   // B rows one CTA holds per plane
+  static constexpr int kBoxB = PAIR ? BN / 4 : BN;    // rows per B load (a half-width pair unit loads one box)
   static constexpr int kTileA = kBM * BK * 2;
-  static constexpr int kTileB = BN * BK * 2;
+  static constexpr int kTileB = kRowsB * BK * 2;
   static constexpr int kStageBytes = 3 * kTileA + 3 * kTileB;
+  // guard band after the stages: every operand read of the pair's MMA
+  // stays inside this CTA's allocation even for a full-height B tile
+  static constexpr int kGuardBytes = PAIR ? 16384 : 0;
   static constexpr int kTmemCols = BN;          // one FP32 accumulator buffer
-  static constexpr int kSmemBytes = STAGES * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int kSmemBytes = STAGES * kStageBytes + kGuardBytes + 1024 /*align*/ + 256 /*barriers*/;
   static constexpr int kSwizzleBytes = BK * 2;
-  // instruction descriptor: D = FP32, A = B = BF16, both K-major, M x N
-  static constexpr uint32_t kIdesc =
-      (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(kBM >> 4) << 24);
-  // the same with N = BN / 2 (half-width tail units of the pair kernel)
-  static constexpr uint32_t kIdescHalf =
-      (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 4) << 17) | (uint32_t(kBM >> 4) << 24);
+  static constexpr uint32_t kIdesc = make_idesc(PAIR ? 2 * kBM : kBM, BN);
+  static constexpr uint32_t kIdescHalf = make_idesc(PAIR ? 2 * kBM : kBM, BN / 2);
 };
-using CfgNarrow = TcCfg<128, 64, 2>;
-using CfgWide = TcCfg<256, 32, 3>;
-//   the same in 2-CTA pairs sharing B (a 16-deep, 6-stage, 32-byte-swizzle
-//   variant measured 19% slower)
-using CfgPair = CfgWide;
+using CfgNarrow = TcCfg<128, 64, 2, false>;
+using CfgWide = TcCfg<256, 32, 3, false>;
+using CfgPair = TcCfg<256, 32, 4, true>;
+static_assert(CfgPair::kSmemBytes <= 227 * 1024, "pair stages exceed shared memory");
+static_assert(CfgWide::kSmemBytes <= 227 * 1024, "wide stages exceed shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -78,27 +121,58 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive_local(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Arrive on a barrier of another CTA of the cluster (release at cluster scope).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+template <bool CLUSTER>
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
+  if constexpr (CLUSTER) {
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+  }
   return ok != 0;
 }
 
-// Bounded wait for the phase of `parity` to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if (i > 64) __nanosleep(32);
+// Wait for the phase of `parity` to complete, at most limit_ns; gives up
+// early when `failed` is set (unless drain: waits for own copies ignore it).
+template <bool CLUSTER>
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* failed,
+                                          uint64_t limit_ns, bool drain = false) {
+  uint64_t t0 = 0;
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_test<CLUSTER>(bar, parity)) return true;
+    if ((i & 63) == 63) {
+      if (!drain && *failed) return false;
+      const uint64_t now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > limit_ns) return false;
+      __nanosleep(64);
+    }
   }
-  return false;
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
@@ -106,17 +180,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(smem_u32(dst)),
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// The same load delivered to every CTA of the cluster in `mask`, at the same
-// shared-memory offset, completing on the barrier at the same offset in each.
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, "
-      "{%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(mask)
       : "memory");
 }
 
@@ -138,30 +201,40 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
+template <bool PAIR>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-      "}\n" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if constexpr (PAIR) {
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// Commit arriving on the barrier at the same offset in every CTA of `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
+// Commit: the barrier at `addr` (shared::cluster; this CTA's or the pair
+// partner's) receives one arrival when the MMAs issued so far complete.
+template <bool PAIR>
+__device__ __forceinline__ void mma_commit(uint32_t addr) {
+  if constexpr (PAIR)
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(addr)
+                 : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(addr)
+                 : "memory");
 }
 
 // 32 consecutive accumulator columns of this thread's TMEM lane (one
@@ -195,7 +268,7 @@ __device__ __forceinline__ void store16(const GemmTcArgs& a, uint64_t off, bool 
     if (a.kind == OUT_F64) {
       double2* p = reinterpret_cast<double2*>(static_cast<double*>(a.C) + off);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) p[q] = make_double2(double(f[2 * q]), double(f[2 * q + 1]));
+      for (int q = 0; q < 8; ++q) p[q] = make_double2(f2d(f[2 * q]), f2d(f[2 * q + 1]));
       return;
     }
   }
@@ -204,26 +277,80 @@ __device__ __forceinline__ void store16(const GemmTcArgs& a, uint64_t off, bool 
     if (j < ncols) store_out_f(a.C, a.kind, a.plane_stride, rbase + colmap[col0 + j], f[j]);
 }
 
-// Persistent: grid = min(tiles, SMs); CTA b takes tiles b, b + grid, ...
-// The accumulator is double-buffered in TMEM (2 x BN columns) so that the
-// epilogue of one tile overlaps the loads and MMAs of the next.
-// PAIR: clusters of two CTAs on vertically adjacent tiles (same columns)
-// share every B tile: each CTA loads half of its rows and multicasts them to
-// both, so B is read from L2 once per pair.  A stage of either CTA is then
-// refilled only after both CTAs' MMAs have consumed it (the MMA commits
-// arrive on both CTAs' `empty` barriers).  When the pair units leave a last
-// wave at most half full, its units are split into two half-width units
-// (N = BN / 2, B loaded by rank 0 alone and multicast), so that the tail
-// takes about half a unit's time instead of a whole one.
-template <class Cfg, bool PAIR>
+// Add 16 consecutive columns of one output row into C (FP32 or FP64
+// output), or store them (load_old false; FP64 only: the first pass of a
+// chunked unit).  Returns the sum of the values now in C.
+__device__ __forceinline__ double add16(const GemmTcArgs& a, uint64_t off, bool contig, const float* f,
+                                        const uint64_t* colmap, int64_t col0, uint64_t rbase, int ncols,
+                                        bool load_old) {
+  double s = 0.0;
+  if (a.kind == OUT_F64) {
+    double* C = static_cast<double*>(a.C);
+    if (contig && ncols == 16) {
+      double2* p = reinterpret_cast<double2*>(C + off);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        double2 o;
+        if (load_old) {
+          o = p[q];
+          o.x += f2d(f[2 * q]);
+          o.y += f2d(f[2 * q + 1]);
+        } else {
+          o = make_double2(f2d(f[2 * q]), f2d(f[2 * q + 1]));
+        }
+        p[q] = o;
+        s += o.x + o.y;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < ncols) {
+          double* d = C + rbase + colmap[col0 + j];
+          const double v = load_old ? *d + f2d(f[j]) : f2d(f[j]);
+          *d = v;
+          s += v;
+        }
+    }
+  } else {
+    float* C = static_cast<float*>(a.C);
+    float sf = 0.f;
+    if (contig && ncols == 16) {
+      float4* p = reinterpret_cast<float4*>(C + off);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float4 o = load_old ? p[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        o.x += f[4 * q]; o.y += f[4 * q + 1]; o.z += f[4 * q + 2]; o.w += f[4 * q + 3];
+        p[q] = o;
+        sf += (o.x + o.y) + (o.z + o.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (j < ncols) {
+          float* d = C + rbase + colmap[col0 + j];
+          const float v = (load_old ? *d : 0.f) + f[j];
+          *d = v;
+          sf += v;
+        }
+    }
+    s = double(sf);
+  }
+  return s;
+}
+
+// Persistent: CTA (or pair) b takes units b, b + grid, ...  The
+// accumulator is double-buffered in TMEM (2 x BN columns).
+template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmTcArgs a) {
+  constexpr bool PAIR = Cfg::PAIR;
   constexpr int kBN = Cfg::BN, kBK = Cfg::BK, kStages = Cfg::STAGES;
   constexpr int kTileA = Cfg::kTileA, kTileB = Cfg::kTileB, kStageBytes = Cfg::kStageBytes;
   constexpr int kTmemCols = Cfg::kTmemCols, kSW = Cfg::kSwizzleBytes;
+  constexpr int kSlices = kBK / 16;          // 16-wide shared-index slices per stage
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + Cfg::kGuardBytes);
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;      // [2]: MMA -> epilogue
   uint64_t* acc_empty = acc_full + 2;        // [2]: epilogue -> MMA
@@ -232,22 +359,26 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   __shared__ int failed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tiles_n = a.Np / kBN;
-  const int tn_shift = __ffsll(tiles_n) - 1;
-  const int64_t ntiles = (a.Mp / kBM) * tiles_n;
-  const int nk = int(a.Kp / kBK);
-  // work units: tiles, or (PAIR) pairs of vertically adjacent tiles, this
-  // CTA taking the one of its cluster rank
   uint32_t rank = 0;
   if constexpr (PAIR) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const bool leader = rank == 0;
+  const uint64_t wlim = a.wait_ns ? a.wait_ns : kWaitNs;
+  const int64_t tiles_n = a.Np / kBN;
+  const int tn_shift = __ffsll(tiles_n) - 1;
+  const int64_t nwide = (a.Mp / (PAIR ? 2 * kBM : kBM)) * tiles_n;
+  const int nk = int(a.Kp / kBK);
   const int64_t unit0 = PAIR ? int64_t(blockIdx.x >> 1) : int64_t(blockIdx.x);
   const int64_t unit_step = PAIR ? int64_t(gridDim.x >> 1) : int64_t(gridDim.x);
-  const int64_t nwide = PAIR ? ntiles / 2 : ntiles;
   const int64_t tail = nwide % unit_step;
   const bool split = PAIR && tail > 0 && 2 * tail <= unit_step;
   const int64_t wide_end = split ? nwide - tail : nwide;        // units [wide_end, nunits) are half-width
   const int64_t nunits = split ? wide_end + 2 * tail : nwide;
-  // unit u -> (tile row origin, column origin, half width)
+  // accumulator passes per unit: the shared index in chunks of `chunk`
+  // terms (16-wide slices), each summed in FP32 and added in FP64
+  const int nsl = int(a.Kp / 16);
+  const int sl_chunk = (a.chunk > 0 && a.chunk / 16 < nsl) ? int(a.chunk / 16) : nsl;
+  const int npass = nsl / sl_chunk;
+  // unit u -> (this CTA's first row, the unit's first column, half width)
   auto unit_of = [&](int64_t u, int64_t* m0, int64_t* n0, bool* half) {
     int64_t wu = u, noff = 0;
     *half = u >= wide_end;
@@ -258,31 +389,45 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     *m0 = ((wu >> tn_shift) * (PAIR ? 2 : 1) + rank) * kBM;
     *n0 = (wu & (tiles_n - 1)) * kBN + noff;
   };
+  // record a failure here and, in a pair, in the partner
+  auto set_failed = [&]() {
+    atomicExch(&failed, 1);
+    if constexpr (PAIR)
+      asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr(&failed, rank ^ 1u)), "r"(1) : "memory");
+  };
 
   if (threadIdx.x == 0) {
     failed = 0;
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], PAIR ? 2 : 1);     // PAIR: both CTAs' MMAs
+      // pair leader: its producer's arrival and the partner's forwarded one
+      mbar_init(&full[s], PAIR && leader ? 2 : 1);
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], kEpiWarps);    // one arrival per epilogue warp
+      mbar_init(&acc_empty[b], PAIR ? 2 * kEpiWarps : kEpiWarps);   // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(2 * kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"(2 * kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  // the partner's multicasts and commits target this CTA's barriers: both
-  // CTAs' barriers are initialised before either starts
+  // a pair's barriers receive the partner's arrivals: both are initialised
+  // (and both TMEM allocations done) before either CTA starts
   if constexpr (PAIR) cluster_sync();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
@@ -290,9 +435,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   double sum_d = 0.0;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer: one continuous ring of stages across all tiles
+    // ---- TMA producer: one continuous ring of stages across all units
     int64_t it = 0, issued = 0;
-    for (int64_t u = unit0; u < nunits && !failed; u += unit_step) {
+    bool ok = true;
+    for (int64_t u = unit0; u < nunits && ok; u += unit_step) {
       int64_t um0, un0;
       bool half;
       unit_of(u, &um0, &un0, &half);
@@ -300,90 +446,124 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       for (int kb = 0; kb < nk; ++kb, ++it) {
         const int s = int(it % kStages);
         const int64_t use = it / kStages;
-        if (use > 0 && !mbar_wait(&empty[s], uint32_t((use - 1) & 1))) {
-          atomicExch(&failed, 1);
+        if (use > 0 && !mbar_wait<PAIR>(&empty[s], uint32_t((use - 1) & 1), &failed, wlim)) {
+          set_failed();
+          ok = false;
           break;
         }
         uint8_t* st = smem + s * kStageBytes;
-        // a half-width unit's stage holds the A planes and the first BN / 2
-        // rows of each B plane
-        mbar_expect_tx(&full[s], half ? 3 * kTileA + 3 * (kTileB / 2) : kStageBytes);
-        for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
+        uint8_t* stb = st + 3 * kTileA;
         if constexpr (PAIR) {
+          // this CTA's B rows: half of the unit's columns (full width: two
+          // boxes of BN / 4 rows; half width: one box)
+          mbar_expect_tx(&full[s], 3 * kTileA + 3 * (half ? kTileB / 2 : kTileB));
+          for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
           if (half) {
-            // the unit's BN / 2 B rows (one box of the map), loaded by rank
-            // 0 alone, to both CTAs
-            if (rank == 0)
-              for (int p = 0; p < 3; ++p)
-                tma_load_3d_mc(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s], uint16_t(0x3));
-          } else {
-            // this CTA's half of the B rows, to both CTAs
             for (int p = 0; p < 3; ++p)
-              tma_load_3d_mc(st + 3 * kTileA + p * kTileB + int(rank) * (kTileB / 2), &tmB, kb * kBK,
-                             n0 + int(rank) * (kBN / 2), p, &full[s], uint16_t(0x3));
+              tma_load_3d(stb + p * kTileB, &tmB, kb * kBK, n0 + int(rank) * (kBN / 4), p, &full[s]);
+          } else {
+            for (int p = 0; p < 3; ++p)
+              for (int h = 0; h < 2; ++h)
+                tma_load_3d(stb + p * kTileB + h * (kTileB / 2), &tmB, kb * kBK,
+                            n0 + int(rank) * (kBN / 2) + h * (kBN / 4), p, &full[s]);
           }
         } else {
-          for (int p = 0; p < 3; ++p) tma_load_3d(st + 3 * kTileA + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
+          mbar_expect_tx(&full[s], kStageBytes);
+          for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
+          for (int p = 0; p < 3; ++p) tma_load_3d(stb + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
         }
         issued = it + 1;
       }
     }
-    // drain: every stage we filled must have landed before the CTA exits
-    for (int64_t j = (issued > kStages ? issued - kStages : 0); j < issued; ++j)
-      if (!mbar_wait(&full[j % kStages], uint32_t((j / kStages) & 1))) atomicExch(&failed, 1);
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
+    // drain: every copy this CTA issued has landed, and (normal end) every
+    // commit that frees a stage has arrived, before the CTA exits
+    const int64_t j0 = issued > kStages ? issued - kStages : 0;
+    for (int64_t j = j0; j < issued; ++j)
+      if (!mbar_wait<PAIR>(&full[j % kStages], uint32_t((j / kStages) & 1), &failed, wlim, true)) set_failed();
+    if (!failed)
+      for (int64_t j = j0; j < issued; ++j)
+        if (!mbar_wait<PAIR>(&empty[j % kStages], uint32_t((j / kStages) & 1), &failed, wlim)) set_failed();
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---- MMA issuer (the pair's even CTA)
     constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
     constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
+    const uint32_t peer = rank ^ 1u;
     int64_t it = 0, t = 0;
-    for (int64_t u = unit0; u < nunits && !failed; u += unit_step, ++t) {
+    bool ok = true;
+    for (int64_t u = unit0; u < nunits && ok; u += unit_step) {
       const uint32_t idesc = u >= wide_end ? Cfg::kIdescHalf : Cfg::kIdesc;
-      const int buf = int(t & 1);
-      const int64_t use = t >> 1;
-      if (use > 0 && !mbar_wait(&acc_empty[buf], uint32_t((use - 1) & 1))) {
-        atomicExch(&failed, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dacc = tmem + uint32_t(buf * kTmemCols);
-      bool ok = true;
-      for (int kb = 0; kb < nk; ++kb, ++it) {
-        const int s = int(it % kStages);
-        if (!mbar_wait(&full[s], uint32_t((it / kStages) & 1)) || failed) {
-          atomicExch(&failed, 1);
-          ok = false;
-          break;
+      for (int sl = 0; sl < nsl; ++sl) {
+        const int kk = sl % kSlices;
+        const int cs = sl % sl_chunk;
+        if (cs == 0) {
+          const int64_t use = t >> 1;
+          if (use > 0 && !mbar_wait<PAIR>(&acc_empty[t & 1], uint32_t((use - 1) & 1), &failed, wlim)) {
+            set_failed();
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int s = int(it % kStages);
+        if (kk == 0) {
+          if (!mbar_wait<PAIR>(&full[s], uint32_t((it / kStages) & 1), &failed, wlim)) {
+            set_failed();
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
         const uint32_t base = smem_u32(smem + s * kStageBytes);
+        const uint32_t dacc = tmem + uint32_t((t & 1) * kTmemCols);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           const uint64_t da = smem_desc<kSW>(base + pa[q] * kTileA);
           const uint64_t db = smem_desc<kSW>(base + 3 * kTileA + pb[q] * kTileB);
-#pragma unroll
-          for (int kk = 0; kk < kBK / 16; ++kk)   // K = 16 per instruction: +32 bytes = +2 in the address field
-            mma_bf16(dacc, da + 2 * kk, db + 2 * kk, idesc, (kb | q | kk) != 0);
+          // K = 16 per instruction: +32 bytes = +2 in the address field
+          mma_bf16<PAIR>(dacc, da + 2 * kk, db + 2 * kk, idesc, (cs | q) != 0);
         }
-        if constexpr (PAIR) mma_commit_mc(&empty[s], uint16_t(0x3));
-        else mma_commit(&empty[s]);
+        if (kk == kSlices - 1) {
+          mma_commit<PAIR>(smem_u32(&empty[s]));
+          if constexpr (PAIR) mma_commit<PAIR>(cluster_addr(&empty[s], peer));
+          ++it;
+        }
+        if (cs == sl_chunk - 1) {
+          mma_commit<PAIR>(smem_u32(&acc_full[t & 1]));
+          if constexpr (PAIR) mma_commit<PAIR>(cluster_addr(&acc_full[t & 1], peer));
+          ++t;
+        }
       }
-      mma_commit(&acc_full[buf]);
-      if (!ok) break;
     }
+    // normal end: the epilogues (a pair: both CTAs') have released the last
+    // accumulator buffers, so no arrival is still on its way here
+    if (ok && !failed)
+      for (int64_t j = t > 2 ? t - 2 : 0; j < t; ++j)
+        if (!mbar_wait<PAIR>(&acc_empty[j & 1], uint32_t((j >> 1) & 1), &failed, wlim)) set_failed();
+  } else if (PAIR && warp == 1 && lane == 0) {
+    // ---- pair, odd CTA: forward the completion of this CTA's loads to the
+    // even CTA's stage barrier (its MMAs read both CTAs' stages)
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t u = unit0; u < nunits && ok; u += unit_step)
+      for (int kb = 0; kb < nk; ++kb, ++it) {
+        const int s = int(it % kStages);
+        if (!mbar_wait<PAIR>(&full[s], uint32_t((it / kStages) & 1), &failed, wlim)) {
+          set_failed();
+          ok = false;
+          break;
+        }
+        mbar_arrive_cluster(cluster_addr(&full[s], 0));
+      }
   } else if (warp >= 2) {
     // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (its rows) and
-    // half (w-2)/4 of the tile's columns, 32 columns per TMEM load
+    // half (w-2)/4 of the unit's columns, 32 columns per TMEM load
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int hc = (warp - 2) >> 2;
     const float alpha_f = float(a.alpha);
+    const bool plain = npass == 1 && !a.accumulate;
     int64_t t = 0;
-    for (int64_t u = unit0; u < nunits; u += unit_step, ++t) {
-      const int buf = int(t & 1);
-      if (!mbar_wait(&acc_full[buf], uint32_t((t >> 1) & 1)) || failed) {
-        atomicExch(&failed, 1);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    bool ok = true;
+    for (int64_t u = unit0; u < nunits && ok; u += unit_step) {
       int64_t m0, n0;
       bool half_unit;
       unit_of(u, &m0, &n0, &half_unit);
@@ -391,41 +571,67 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       const int64_t row = m0 + quad * 32 + lane;
       const bool row_ok = row < a.M;
       const uint64_t rbase = row_ok ? a.rowmap[row] : 0;
-      for (int c0 = half * (width / 2); c0 < (half + 1) * (width / 2); c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + uint32_t(buf * kTmemCols) + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
-        if (!row_ok) continue;
+      for (int pass = 0; pass < npass; ++pass, ++t) {
+        const int buf = int(t & 1);
+        if (!mbar_wait<PAIR>(&acc_full[buf], uint32_t((t >> 1) & 1), &failed, wlim)) {
+          set_failed();
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool load_old = pass > 0 || a.accumulate;
+        const bool last_pass = pass == npass - 1;
+        for (int c0 = hc * (width / 2); c0 < (hc + 1) * (width / 2); c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + uint32_t(buf * kTmemCols) + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
+          if (!row_ok) continue;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int64_t col0 = n0 + c0 + 16 * h;
-          const int ncols = int(a.N - col0 < 16 ? (a.N - col0 > 0 ? a.N - col0 : 0) : 16);
-          if (ncols == 0) continue;
-          float* f = v + 16 * h;
-          // probability check: the 16 values summed in FP32, the chunks in FP64
-          float cs = 0.f;
+          for (int h = 0; h < 2; ++h) {
+            const int64_t col0 = n0 + c0 + 16 * h;
+            const int ncols = int(a.N - col0 < 16 ? (a.N - col0 > 0 ? a.N - col0 : 0) : 16);
+            if (ncols == 0) continue;
+            float* f = v + 16 * h;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            f[j] *= alpha_f;
-            if (j < ncols) cs += f[j];
+            for (int j = 0; j < 16; ++j) f[j] *= alpha_f;   // alpha is a power of two: exact
+            const uint64_t c_first = a.colmap[col0];
+            const bool contig = a.contig16 && ncols == 16;
+            if (plain) {
+              // probability check: the 16 values summed in FP32, the groups in FP64
+              float cs = 0.f;
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (j < ncols) cs += f[j];
+              sum_d += double(cs);
+              store16(a, rbase + c_first, contig, f, a.colmap, col0, rbase, ncols);
+            } else {
+              const double s = add16(a, rbase + c_first, contig, f, a.colmap, col0, rbase, ncols, load_old);
+              if (last_pass) sum_d += s;
+            }
           }
-          sum_d += double(cs);
-          const uint64_t c_first = a.colmap[col0];
-          store16(a, rbase + c_first, a.contig16 && ncols == 16, f, a.colmap, col0, rbase, ncols);
+        }
+        // hand the accumulator back to the MMA thread
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if (PAIR && !leader) mbar_arrive_cluster(cluster_addr(&acc_empty[buf], 0));
+          else mbar_arrive_local(&acc_empty[buf]);
         }
       }
-      // hand the accumulator back to the MMA warp
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[buf])) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  // neither CTA leaves while the partner may still signal its barriers
+  // neither CTA of a pair leaves (or frees TMEM) while the partner may
+  // still use it or signal its barriers
   if constexpr (PAIR) cluster_sync();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols)
+                   : "memory");
   }
   if (failed && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
   if (a.partials) finish_total(sum_d, a.partials, a.counter, a.total, red);
@@ -467,11 +673,11 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t Kp, int bk
 template <class Cfg>
 cudaError_t launch_cfg(const GemmTcArgs& a, cudaStream_t s) {
   CUtensorMap ma, mb;
-  if (!make_map(&ma, a.A, a.Mp, a.Kp, Cfg::BK, kBM) || !make_map(&mb, a.B, a.Np, a.Kp, Cfg::BK, Cfg::BN))
+  if (!make_map(&ma, a.A, a.Mp, a.Kp, Cfg::BK, kBM) || !make_map(&mb, a.B, a.Np, a.Kp, Cfg::BK, Cfg::kBoxB))
     return cudaErrorInvalidValue;
   const int64_t tiles = (a.Mp / kBM) * (a.Np / Cfg::BN);
   const int64_t grid = tiles < 152 ? tiles : 152;    // persistent: at most one CTA per SM
-  gemm_tc_kernel<Cfg, false><<<unsigned(grid), kThreads, Cfg::kSmemBytes, s>>>(ma, mb, a);
+  gemm_tc_kernel<Cfg><<<unsigned(grid), kThreads, Cfg::kSmemBytes, s>>>(ma, mb, a);
   return cudaGetLastError();
 }
 
@@ -490,7 +696,7 @@ int pair_clusters() {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int c = 0;
-    if (cudaOccupancyMaxActiveClusters(&c, gemm_tc_kernel<CfgPair, true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&c, gemm_tc_kernel<CfgPair>, &cfg) != cudaSuccess) {
       cudaGetLastError();
       c = 0;
     }
@@ -501,9 +707,8 @@ int pair_clusters() {
 
 cudaError_t launch_pair(const GemmTcArgs& a, int clusters, cudaStream_t s) {
   CUtensorMap ma, mb;
-  // B is loaded in halves (BN / 2 rows) by the two CTAs of a pair
   if (!make_map(&ma, a.A, a.Mp, a.Kp, CfgPair::BK, kBM) ||
-      !make_map(&mb, a.B, a.Np, a.Kp, CfgPair::BK, CfgPair::BN / 2))
+      !make_map(&mb, a.B, a.Np, a.Kp, CfgPair::BK, CfgPair::kBoxB))
     return cudaErrorInvalidValue;
   const int64_t units = (a.Mp / (2 * kBM)) * (a.Np / CfgPair::BN);
   const int64_t nc = units < clusters ? units : clusters;
@@ -519,7 +724,7 @@ cudaError_t launch_pair(const GemmTcArgs& a, int clusters, cudaStream_t s) {
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<CfgPair, true>, ma, mb, a);
+  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<CfgPair>, ma, mb, a);
 }
 
 }  // namespace
@@ -530,13 +735,13 @@ int gemm_tc_min_rows() { return kBM; }
 int gemm_tc_k_align() { return kKAlign; }
 
 cudaError_t gemm_tc_configure() {
-  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<CfgNarrow, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, CfgNarrow::kSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<CfgNarrow>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       CfgNarrow::kSmemBytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gemm_tc_kernel<CfgWide, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(gemm_tc_kernel<CfgWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              CfgWide::kSmemBytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(gemm_tc_kernel<CfgPair, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(gemm_tc_kernel<CfgPair>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              CfgPair::kSmemBytes);
   return e;
 }
@@ -547,13 +752,17 @@ cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s) {
   // TMEM lane can leave the operands
   if (a.Mp % kBM || a.Np % 128 || a.Kp % kKAlign || a.Kp <= 0 || a.M > a.Mp || a.N > a.Np || a.K > a.Kp)
     return cudaErrorInvalidValue;
+  // chunked passes: a power of two >= 16 terms, FP64 output only
+  if (a.chunk < 0 || (a.chunk > 0 && (a.chunk < 16 || (a.chunk & (a.chunk - 1)) || a.kind != OUT_F64)))
+    return cudaErrorInvalidValue;
+  if (a.accumulate && a.kind != OUT_F32 && a.kind != OUT_F64) return cudaErrorInvalidValue;
   // TMA wants 16-byte aligned global operands (the 1024-byte alignment the
   // swizzle needs applies to the shared-memory stages only)
   if ((reinterpret_cast<uintptr_t>(a.A) | reinterpret_cast<uintptr_t>(a.B)) & 15) return cudaErrorInvalidValue;
-  // 256-wide tiles when they still fill every SM at least once; in pairs
-  // sharing B when the row tiles pair up and the pairs fill the clusters
+  // 256-wide units when they still fill every SM at least once; in 2-SM
+  // pairs when allowed, the row tiles pair up and the pairs fill the clusters
   if (a.Np % 256 == 0 && (a.Mp / kBM) * (a.Np / 256) >= 152) {
-    const int clusters = pair_clusters();
+    const int clusters = a.pairs ? pair_clusters() : 0;
     if (a.Mp % (2 * kBM) == 0 && clusters > 0 && (a.Mp / (2 * kBM)) * (a.Np / 256) >= clusters)
       return launch_pair(a, clusters, s);
     return launch_cfg<CfgWide>(a, s);

@@ -128,12 +128,15 @@ struct GemmTcArgs {
   int kind;
   int64_t plane_stride;
   double alpha;
-  int64_t chunk;
+  int64_t chunk;            // FP32 terms per pass before the FP64 add (0 = one pass; FP64 output only)
+  int accumulate;           // add into C instead of overwriting (later slices, FP32/FP64 outputs)
   double* partials;
   unsigned* counter;
   double* total;
   int* err;                 // device error flag (bounded waits)
   int contig16;             // colmap: runs of 16 consecutive 4-aligned offsets, rowmap 4-aligned
+  int pairs;                // allow 2-SM units (tcgen05.mma.cta_group::2) where they fill the SMs
+  uint64_t wait_ns;         // limit of each barrier wait (0: 2 s)
 };
 cudaError_t launch_gemm_tc(const GemmTcArgs& a, cudaStream_t s);
 bool gemm_tc_available();          // the driver's tensor-map encoder is reachable
@@ -153,6 +156,7 @@ struct BatchItem {
 struct BatchStep {
   GemmArgs a;        // a.partials != null: the query's last step (probability sum)
   int cfg;           // tile configuration id (batch_tile_cfg)
+  int from_launch;   // the output and the probability sum are BatchLaunch::out / total
   int64_t ntiles;
   double* partials;  // per-tile partial sums of the query's bins
   unsigned* counter;
@@ -170,6 +174,9 @@ struct BatchLaunch {
   unsigned* done;
   int* abort;
   int* err;
+  uint64_t wait_ns;          // limit of each dependency wait
+  void* out;                 // output of the steps marked from_launch (a single-query launch)
+  double* total;             // their probability sum (nullable)
 };
 cudaError_t launch_batch(const BatchLaunch& L, int grid, cudaStream_t s);
 cudaError_t batch_configure();
@@ -232,6 +239,7 @@ struct sqc_ctx;
 namespace sqc {
 void ctx_set_alloc_stream(sqc_ctx* ctx, cudaStream_t s);   // nullptr: synchronous allocation again
 int ctx_device(const sqc_ctx* ctx);
+void ctx_set_fused(sqc_ctx* ctx, bool on);                  // cfg.fused_query
 int32_t ctx_alloc(sqc_ctx* ctx, void** p, size_t bytes);    // budget-checked (SQC_EBUSY when over)
 void ctx_free(sqc_ctx* ctx, void* p, size_t bytes);
 int32_t ctx_fail(sqc_ctx* ctx, int32_t st, const char* msg);

@@ -350,6 +350,8 @@ SQC_API sqc_status sqc_server_create(sqc_ctx* ctx, const sqc_server_config* cfg,
     const unsigned hc = std::thread::hardware_concurrency();
     srv->planner_threads = hc >= 4 ? std::min<size_t>(8, hc / 2) : 1;
   }
+  // the plain baseline keeps one launch per stage for every request
+  if (srv->cfg.plain) sqc::ctx_set_fused(ctx, false);
   srv->th = std::thread([srv] { srv->loop(); });
   *out = srv;
   return SQC_OK;

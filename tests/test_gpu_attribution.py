@@ -70,5 +70,51 @@ def test_large_tiles_match_oracle(ctx, case):
         ctx.reconstruct(qid, out)
         torch.cuda.synchronize()
         err = np.abs(out.double().cpu().numpy() - ref).max()
-        assert err <= ABS_TOL and err <= REL_TOL * scale + 1e-12, (case, form, err)
+        assert err <= ABS_TOL and err <= REL_TOL * scale + 1e-15, (case, form, err)
         ctx.unload(cid)
+
+
+def _star_circuit(kout_on_b: bool):
+    """Two upstream subcircuits each hand 4 wires to a third (8 incoming cut
+    edges: more than the fused kernel's 7, so the attribution takes the
+    two-pass form -- outcome weights per outgoing edge, then the 4 x 4
+    prepared-state expansion per incoming edge).  With kout_on_b the third
+    subcircuit also hands one received wire on to a fourth."""
+    from synthetic.circuits import Block, CutCircuit
+    blocks = [Block([0, 1, 2, 3, 4], [("h", 4), ("cz", 3, 4)]),
+              Block([5, 6, 7, 8, 9], [("h", 5), ("cz", 5, 6)]),
+              Block([0, 1, 2, 3, 5, 6, 7, 8], [("sx", 0), ("cz", 3, 5)])]
+    if kout_on_b:
+        blocks.append(Block([0, 10], [("h", 10), ("cz", 0, 10)]))
+        return CutCircuit(11, blocks).finalize()
+    return CutCircuit(10, blocks).finalize()
+
+
+@pytest.mark.parametrize("kout_on_b,forms", [(False, ("fp32_aligned", "fp64")), (True, ("fp32_aligned",))])
+def test_eight_incoming_edges_two_pass_form(ctx, kout_on_b, forms):
+    import torch
+    from synthetic.qpu import random_variant_probs
+    from synthetic.workloads import Workload
+    c = _star_circuit(kout_on_b)
+    b = 2
+    assert len(c.in_edges[b]) == 8 and len(c.out_edges[b]) == (1 if kout_on_b else 0)
+    rng = np.random.default_rng(41)
+    probs = [random_variant_probs(c, i, rng).astype(np.float32) for i in range(c.n_subcircuits)]
+    g = O.Graph.from_arrays(c.n_qubits, *c.graph_arrays())
+    rr = np.random.default_rng(42)
+    for roles in (np.zeros(c.n_qubits, dtype=np.int8),
+                  rr.choice([O.ACTIVE, O.ACTIVE, O.MERGED, O.ZOOM0, O.ZOOM1], c.n_qubits).astype(np.int8)):
+        w = Workload("star8", c, probs, roles)
+        ref = O.reconstruct(g, [p.astype(np.float64) for p in probs], roles)
+        scale = np.abs(ref).max()
+        for form in forms:
+            dev = [_device_input(p, form) for p in probs]
+            cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), dev)
+            qid, na = ctx.set_qubit_roles(cid, w.roles)
+            out = torch.empty(1 << na, dtype=torch.float64, device="cuda")
+            ctx.reconstruct(qid, out)
+            torch.cuda.synchronize()
+            err = np.abs(out.cpu().numpy() - ref).max()
+            assert err <= ABS_TOL and err <= REL_TOL * scale + 1e-15, (kout_on_b, form, err)
+            ctx.unload(cid)
+            del dev

@@ -18,6 +18,10 @@ pytestmark = pytest.mark.gpu
 
 ABS_TOL = 1e-6
 REL_TOL = 1e-5
+# bins that are exactly zero in exact arithmetic come out of the FP64 oracle as
+# rounding noise of ~1e-17 (sums of products of order-one terms): the
+# relative check allows that much absolute difference
+ORACLE_FLOOR = 1e-15
 
 
 @pytest.fixture(scope="module")
@@ -62,9 +66,8 @@ def check(P, ref, rel=REL_TOL):
     err = np.abs(P - ref).max()
     scale = np.abs(ref).max()
     assert err <= ABS_TOL, err
-    # relative to the largest bin, with a floor for bins that are exactly
-    # zero in exact arithmetic (the oracle's FP64 rounding leaves ~1e-17)
-    assert err <= rel * scale + 1e-12, (err, scale)
+    # relative to the largest bin
+    assert err <= rel * scale + ORACLE_FLOOR, (err, scale)
     return err
 
 
@@ -212,14 +215,24 @@ def test_top_bins_matches_oracle_exactly(ctx):
         assert nf == eb.size
         assert b[:nf].cpu().numpy().tolist() == eb.tolist()
         assert np.array_equal(v[:nf].cpu().numpy(), ev)
-    # the GPU's selection agrees with the FP64 oracle's up to near-ties
+    # the GPU's selection agrees with the FP64 oracle's up to near-ties:
+    # every bin that only one of the two selected lies within 2x the
+    # measured max-abs error of the oracle's k-th value, and the selected
+    # bins agree where the values are separated by more than that
     ref = oracle_run(w)
-    eb, ev = O.top_bins(ref, 64)
-    b, v, n = ctx.top_bins(qid, out, 64)
-    gb = b.cpu().numpy()
     err = np.abs(P - ref).max()
-    gap_ok = np.abs(ev[-1] - ref[gb[-1]]) <= 2 * err
-    assert set(gb.tolist()) == set(eb.tolist()) or gap_ok
+    for k in (1, 64, 1000, 4096):
+        eb, ev = O.top_bins(ref, k)
+        b, v, n = ctx.top_bins(qid, out, k)
+        torch.cuda.synchronize()
+        gb = b[: int(n.item())].cpu().numpy()
+        assert gb.size == eb.size == k
+        kth = ev[-1]
+        for bb in set(gb.tolist()) ^ set(eb.tolist()):
+            assert abs(ref[bb] - kth) <= 2 * err, (k, bb, ref[bb], kth, err)
+        # bins clearly above the k-th value are selected by both
+        sure = set(np.nonzero(ref > kth + 2 * err)[0].tolist())
+        assert sure <= set(gb.tolist()) and sure <= set(eb.tolist())
     ctx.unload(cid)
 
 
@@ -285,3 +298,25 @@ def test_hbm_budget_admission(ctx):
         with pytest.raises(SQCError) as ei:
             small.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in w.probs])
         assert ei.value.status == 6
+
+
+@pytest.mark.parametrize("wl,out", [("merged_30q", "float32"), ("grid_40q", "float64"), ("full_state_12q", "float64")])
+def test_single_launch_equals_per_stage_launches(wl, out):
+    """An FP32 query runs its merge and every contraction step as one
+    persistent launch (the default) or as one launch per stage: every bin is
+    summed by one thread in the same order either way, so the bins are the
+    same bit for bit, and both match the oracle; the FP64 probability sums
+    agree to rounding."""
+    import torch
+    from paper_2207_00933_gb300 import Context
+    w = getattr(W, wl)()
+    ref = oracle_run(w)
+    res = {}
+    for fused in (True, False):
+        with Context(0, fused_query=fused) as c:
+            P, tot = gpu_run(c, w, out_dtype=out)
+            res[fused] = (P, tot)
+    assert np.array_equal(res[True][0], res[False][0])
+    check(res[True][0], ref)
+    assert abs(res[True][1] - res[False][1]) <= 1e-12
+    torch.cuda.synchronize()

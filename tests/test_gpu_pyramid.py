@@ -23,7 +23,7 @@ def _oracle(c, probs, roles):
 
 def _check(P, ref):
     err = np.abs(P - ref).max()
-    assert err <= ABS_TOL and err <= REL_TOL * np.abs(ref).max() + 1e-12, err
+    assert err <= ABS_TOL and err <= REL_TOL * np.abs(ref).max() + 1e-15, err
 
 
 @pytest.fixture(scope="module")

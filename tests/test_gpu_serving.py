@@ -62,14 +62,32 @@ def test_served_results_equal_alone(mode):
         assert st["admitted"] == len(tickets)
         if mode == "batched":
             assert st["launches"] < len(tickets)            # requests shared launches
-    for j in (0, 17, 40):
-        ci, roles = b.queries[j]
-        c = b.circuits[ci]
-        ref = O.reconstruct(O.Graph.from_arrays(c.n_qubits, *c.graph_arrays()),
-                            [p.astype(np.float64) for p in b.probs[ci]], roles)
-        err = np.abs(alone[j].astype(np.float64) - ref).max()
-        assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-12
     ctx.close()
+
+
+def test_every_served_query_matches_the_oracle():
+    # all 48 queries (forests of chains of 100-400 qubits, zoom prefixes,
+    # 12-20 active qubits) through the batching server, each against the
+    # FP64 oracle
+    from paper_2207_00933_gb300 import Context, Server, _build
+    _build.build()
+    b = _workload()
+    graphs = [O.Graph.from_arrays(c.n_qubits, *c.graph_arrays()) for c in b.circuits]
+    probs64 = [[p.astype(np.float64) for p in ps] for ps in b.probs]
+    with Context(0) as ctx:
+        cids = _load(ctx, b)
+        with Server(ctx, max_batch=16, n_streams=3) as srv:
+            tickets = [srv.submit(cids[ci], roles) for ci, roles in b.queries]
+            srv.drain(120.0)
+            for j, t in enumerate(tickets):
+                ci, roles = b.queries[j]
+                state, _, na = srv.poll(t)
+                assert state == 2
+                P = srv.result(t).astype(np.float64)
+                ref = O.reconstruct(graphs[ci], probs64[ci], roles)
+                assert P.size == ref.size == 1 << na
+                err = np.abs(P - ref).max()
+                assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-15, (j, err)
 
 
 def test_admission_by_hbm_footprint():

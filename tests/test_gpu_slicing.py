@@ -40,7 +40,7 @@ def test_sliced_equals_unsliced_and_oracle(wl, S, prec, out):
     bins = [1 << sum(1 for q in dq if w.roles[q] == O.ACTIVE) for dq in c.data_qubits]
     assert sliced == O.greedy_slicing(g, bins, 0)[:S]
     err = np.abs(P - ref).max()
-    assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-12
+    assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-15
     assert abs(tot - O.total_probability(ref)) < 1e-6
     P0, _, none = _run(w, 0, prec, out)
     assert none == []
@@ -76,7 +76,7 @@ def test_input_budget_slicing_follows_the_papers_rule(wl):
     assert O.sliced_sizes(g, bins, set(sliced)) <= 2 ** log2_budget
     ref = O.reconstruct(g, [p.astype(np.float64) for p in w.probs], w.roles)
     err = np.abs(P - ref).max()
-    assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-12
+    assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-15
 
 
 @pytest.mark.parametrize("wl", ["merged_30q", "grid_40q"])
@@ -95,7 +95,7 @@ def test_intermediate_budget_slicing(wl):
     assert max(m * n for m, n, _ in steps[:-1]) <= 2 ** log2_budget
     ref = O.reconstruct(g, [p.astype(np.float64) for p in w.probs], w.roles)
     err = np.abs(P - ref).max()
-    assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-12
+    assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-15
 
 
 def test_unreachable_slicing_budget_is_refused():

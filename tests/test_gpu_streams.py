@@ -31,7 +31,7 @@ def setup(request):
 
 def _check(P, ref):
     err = np.abs(P - ref).max()
-    assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-12, err
+    assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-15, err
 
 
 @pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
@@ -70,6 +70,10 @@ def test_streams_graphs_and_profiled_capture(setup, precision):
         assert tot2.item() == tot0.item()
         if prof:
             r = ctx.profile_read()
-            assert r["ms"]["contract"] > 0 and r["ms"]["final"] > 0, r
+            # FP32 runs the merge and every step as one launch (recorded as
+            # the contraction stage); split-BF16 launches per stage
+            assert r["ms"]["contract"] > 0, r
+            if precision == "split_bf16":
+                assert r["ms"]["final"] > 0, r
         del g
     ctx.profile_enable(0)
