@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the microbenchmarks, batch and serving runs")
-    ap.add_argument("--extra", choices=["tensor", "hbm", "batch", "serving"],
+    ap.add_argument("--extra", choices=["tensor", "hbm", "batch", "serving", "grid40", "recursion"],
                     help="run only this microbenchmark and print its JSON line")
     return ap.parse_args()
 
@@ -115,31 +115,144 @@ def tensor_microbench(dev, reps: int = 20) -> dict:
     g = O.Graph.from_arrays(c.n_qubits, *c.graph_arrays())
     ref = O.reconstruct(g, [p.astype(np.float64) for p in w.probs], w.roles)
     out = {}
+    for pairs in (False, True):
+        # per-stage launches, so that the last step has its own stage events
+        with Context(dev.index or 0, tc_pairs=pairs, fused_query=False) as ctx:
+            cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).to(dev) for p in w.probs])
+            qid, na = ctx.set_qubit_roles(cid, w.roles)
+            M, N, K = ctx.query_steps(qid)[-1]
+            res = torch.empty(1 << na, dtype=torch.float32, device=dev)
+            for prec in (("split_bf16",) if pairs else ("split_bf16", "fp32")):
+                for _ in range(3):
+                    ctx.reconstruct(qid, res, prec)
+                torch.cuda.synchronize(dev)
+                ctx.profile_enable(True)
+                for _ in range(reps):
+                    ctx.reconstruct(qid, res, prec)
+                pr = ctx.profile_read()
+                ctx.profile_enable(False)
+                ms = pr["ms"]["final"] / max(1, pr["calls"]["final"])
+                err = float(np.abs(res.double().cpu().numpy() - ref).max())
+                alg = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+                d = {"ms": ms, "alg_tflops": alg, "max_abs_err_vs_fp64": err}
+                if prec == "split_bf16":
+                    peak, src = bf16_peak()
+                    d.update({"hw_tflops": 6 * alg, "peak_tflops": peak, "peak_source": src,
+                              "tensor_frac": 6 * alg / peak,
+                              "form": "2-SM pairs (cta_group::2, 256 x 256 units)" if pairs else
+                                      "one SM per 128 x 256 unit"})
+                out[prec + ("_pairs" if pairs else "")] = d
+            ctx.unload(cid)
+    return {"shape": {"M": M, "N": N, "K": K}, "workload": "randline32_K4_a24 (two subcircuits, 4 shared cuts)", **out}
+
+
+def grid40_bench(dev, reps: int = 20) -> dict:
+    """The mixed-precision configuration: the 40-qubit 5 x 8 grid circuit cut
+    at K = 12 into 5 subcircuits, 22 active qubits (2^22 bins), FP64 output
+    (K >= 12: the last step sums its shared index in FP32 and adds it in
+    FP64).  The whole step (attribution, merge, contraction, FP64 check,
+    top-1024) replayed from a CUDA graph with L2 flushed between steps, in
+    split-BF16 and FP32, each checked against the FP64 oracle; plus the
+    event-timed last contraction step (tcgen05 in split-BF16) against the
+    HBM roofline (its output write dominates its bytes)."""
+    import torch
+    import oracle as O
+    from paper_2207_00933_gb300 import Context
+    from synthetic import workloads as W
+    w = W.grid_40q()
+    c = w.circuit
+    ref = O.reconstruct(O.Graph.from_arrays(c.n_qubits, *c.graph_arrays()),
+                        [p.astype(np.float64) for p in w.probs], w.roles)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    hbm, src = peaks()
+    res = {"workload": "grid40_K12_a22 (5 x 8 grid, depth 8, K = 12, 22 active qubits, FP64 output)"}
     with Context(dev.index or 0) as ctx:
-        cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).to(dev) for p in w.probs])
+        probs = [torch.from_numpy(p).to(dev) for p in w.probs]
+        cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), probs)
         qid, na = ctx.set_qubit_roles(cid, w.roles)
+        out = torch.empty(1 << na, dtype=torch.float64, device=dev)
+        tot = torch.zeros(1, dtype=torch.float64, device=dev)
+        kb = torch.empty(TOPK, dtype=torch.int64, device=dev)
+        kp = torch.empty(TOPK, dtype=torch.float64, device=dev)
+        kn = torch.empty(1, dtype=torch.int32, device=dev)
         M, N, K = ctx.query_steps(qid)[-1]
-        res = torch.empty(1 << na, dtype=torch.float32, device=dev)
         for prec in ("split_bf16", "fp32"):
+            def step():
+                ctx.update_subcircuit_outputs(cid, probs)
+                ctx.reconstruct(qid, out, prec, tot)
+                ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
             for _ in range(3):
-                ctx.reconstruct(qid, res, prec)
+                step()
             torch.cuda.synchronize(dev)
+            err = float(np.abs(out.cpu().numpy() - ref).max())
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step()
+            for _ in range(3):
+                g.replay()
+            torch.cuda.synchronize(dev)
+            tt = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.replay()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                tt += e0.elapsed_time(e1)
+            ms = tt / reps
+            del g
+            # the last step alone (stage events, separate run)
             ctx.profile_enable(True)
             for _ in range(reps):
-                ctx.reconstruct(qid, res, prec)
+                flush.zero_()
+                ctx.reconstruct(qid, out, prec, tot)
             pr = ctx.profile_read()
             ctx.profile_enable(False)
-            ms = pr["ms"]["final"] / max(1, pr["calls"]["final"])
-            err = float(np.abs(res.double().cpu().numpy() - ref).max())
-            alg = 2.0 * M * N * K / (ms * 1e-3) / 1e12
-            d = {"ms": ms, "alg_tflops": alg, "max_abs_err_vs_fp64": err}
+            d = {"ms_per_step": ms, "bins_per_s": (1 << na) / (ms * 1e-3), "max_abs_err_vs_fp64": err,
+                 "total_prob": float(tot.item())}
             if prec == "split_bf16":
-                peak, src = bf16_peak()
-                d.update({"hw_tflops": 6 * alg, "peak_tflops": peak, "peak_source": src,
-                          "tensor_frac": 6 * alg / peak})
-            out[prec] = d
+                fin = pr["ms"]["final"] / max(1, pr["calls"]["final"])
+                byts = 6 * (M * K + N * K) + 8 * M * N
+                d["last_step"] = {"shape": [M, N, K], "kernel": "gemm_tc_kernel", "us": 1e3 * fin,
+                                  "roofline": {"bound": "hbm", "achieved": byts / (fin * 1e-3) / 1e9, "peak": hbm,
+                                               "unit": "GB/s", "frac": byts / (fin * 1e-3) / 1e9 / hbm,
+                                               "peak_source": src, "algorithmic_bytes": byts},
+                                  "alg_tflops": 2.0 * M * N * K / (fin * 1e-3) / 1e12,
+                                  "tc_steps": ctx.query_tc_steps(qid)}
+            res[prec] = d
         ctx.unload(cid)
-    return {"shape": {"M": M, "N": N, "K": K}, "workload": "randline32_K4_a24 (two subcircuits, 4 shared cuts)", **out}
+    return res
+
+
+def recursion_bench(dev) -> dict:
+    """Algorithm 1 at the paper's scale (Section 8.1): a 1000-qubit
+    Bernstein-Vazirani circuit cut into a chain of 59 subcircuits of at most
+    18 qubits, M = 2^20 bins per recursion, run to its single solution:
+    recursions, seconds per recursion (planning, reconstruction and
+    selection of each level, host planning included) and whether the
+    hidden string was found."""
+    import torch
+    from paper_2207_00933_gb300 import Context, recursion
+    from synthetic.circuits import bernstein_vazirani_chain
+    from synthetic.qpu import product_variant_probs
+    c, s = bernstein_vazirani_chain(5, [18] * 58 + [14], [1] * 58)
+    graph = (c.n_qubits, *c.graph_arrays())
+    M = 2 ** 20
+    with Context(dev.index or 0) as ctx:
+        probs = [torch.from_numpy(product_variant_probs(c, i, np.float32)).to(dev) for i in range(c.n_subcircuits)]
+        cid = ctx.load_subcircuit_outputs(*graph, probs)
+        del probs
+        recursion.search(ctx, cid, graph, M, R=2, keep=4, threshold=1e-3)       # warm-up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sols, r = recursion.search(ctx, cid, graph, M, R=64, keep=4, threshold=1e-3)
+        dt = time.perf_counter() - t0
+    found = len(sols) == 1 and sols[0][0] == s
+    return {"workload": "bv1000: 1000-qubit Bernstein-Vazirani, 59 subcircuits <= 18 qubits, 58 cuts, M = 2^20",
+            "recursions": r, "expected": recursion.recursions_needed(c.n_qubits, M), "solution_found": found,
+            "probability": sols[0][1] if sols else None, "seconds": dt, "seconds_per_recursion": dt / max(1, r)}
 
 
 def hbm_microbench(dev, reps: int = 10) -> dict:
@@ -160,7 +273,7 @@ def hbm_microbench(dev, reps: int = 10) -> dict:
     hbm, src = peaks()
     out = {"workload": "randline40_K2_a24 (subcircuits of 20 and 22 measured qubits, 2 cuts, 10+14 active)",
            "peak_gbs": hbm, "peak_source": src}
-    with Context(dev.index or 0) as ctx:
+    with Context(dev.index or 0, fused_query=False) as ctx:     # the merge as its own launch
         probs_dev = [torch.from_numpy(p).to(dev) for p in w.probs]
         cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), probs_dev)
         qid, na = ctx.set_qubit_roles(cid, w.roles)
@@ -257,12 +370,9 @@ def oracle_step(w, g, probs64, k):
     return P
 
 
-def cpu_baseline(name: str, budget_s: float = 12.0) -> dict:
-    """Time the oracle, as it stands, on a bounded sample of the same
-    workload in a single-threaded subprocess."""
-    code = f"""
+_ORACLE_LOOP = """
 import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, {root!r})
 import numpy as np
 import bench, oracle as O
 w = bench.make_workload({name!r})
@@ -274,20 +384,53 @@ while True:
     bench.oracle_step(w, g, probs, bench.TOPK)
     n += 1
     dt = time.perf_counter() - t0
-    if dt >= {budget_s} or n >= 200:
+    if dt >= {budget} or n >= 200:
         break
 print(json.dumps({{"reps": n, "seconds": dt, "bins": 1 << w.n_active}}))
 """
+
+
+def _oracle_procs(name: str, budget_s: float, procs: int) -> list:
+    """`procs` single-threaded oracle loops side by side (fresh interpreters,
+    no fork of this GPU process); each reports (reps, seconds, bins)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
-    if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["reps"] * d["bins"] / d["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{d['reps']} full reconstructions (attribution, merge, pairwise contraction, top-{TOPK}, "
-                      f"FP64 sum) of {name}, {d['seconds']:.1f} s"}
+    code = _ORACLE_LOOP.format(root=ROOT, name=name, budget=budget_s)
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           env=env) for _ in range(procs)]
+    out = []
+    for p in ps:
+        o, e = p.communicate(timeout=900)
+        if p.returncode != 0:
+            raise RuntimeError(e[-300:])
+        out.append(json.loads(o.strip().splitlines()[-1]))
+    return out
+
+
+def cpu_baseline(name: str, budget_s: float = 12.0) -> dict:
+    """Time the oracle, as it stands, on a bounded sample of the same
+    workload: one single-threaded process, and one process per host core
+    (independent reconstructions side by side: the whole host's oracle
+    throughput).  `value` is the single-thread figure, `all_cores` the
+    host-wide one with its core count."""
+    try:
+        one = _oracle_procs(name, budget_s, 1)[0]
+    except Exception as ex:  # noqa: BLE001
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+    res = {"value": one["reps"] * one["bins"] / one["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{one['reps']} full reconstructions (attribution, merge, pairwise contraction, top-{TOPK}, "
+                     f"FP64 sum) of {name}, {one['seconds']:.1f} s, one thread"}
+    cores = os.cpu_count() or 1
+    try:
+        many = _oracle_procs(name, budget_s, cores)
+        res["all_cores"] = {"value": sum(d["reps"] * d["bins"] / d["seconds"] for d in many), "unit": UNIT,
+                            "cores": cores,
+                            "sample": f"{cores} single-threaded processes, {sum(d['reps'] for d in many)} "
+                                      f"reconstructions in {max(d['seconds'] for d in many):.1f} s"}
+    except Exception as ex:  # noqa: BLE001
+        res["all_cores"] = {"value": None, "cores": cores, "sample": f"failed: {ex}"}
+    return res
 
 
 def batch_bench(dev, reps: int = 10) -> dict:
@@ -307,7 +450,8 @@ def batch_bench(dev, reps: int = 10) -> dict:
     stream = torch.cuda.current_stream(dev)
     res = {"workload": f"{len(b.queries)} queries, circuits {b.meta['n_qubits']} qubits, cuts {b.meta['cuts']}, "
                        f"subcircuits {b.meta['subcircuits']}, active 10-20"}
-    with Context(dev.index or 0) as ctx:
+    # the plain form launches every stage of every query on its own
+    with Context(dev.index or 0, fused_query=False) as ctx:
         cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).to(dev) for p in ps])
                 for c, ps in zip(b.circuits, b.probs)]
         qs = [ctx.set_qubit_roles(cids[ci], roles) for ci, roles in b.queries]
@@ -350,7 +494,7 @@ def batch_bench(dev, reps: int = 10) -> dict:
         res["batch_fp32"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "launches": 1, "max_abs_err_vs_fp64": err()}
         ctx.batch_release(bid)
         # the tile policy picked by the autotuner (sqc_batch_autotune), timed the same way
-        best, pol_ms = ctx.batch_autotune([q for q, _ in qs], outs, totals, reps=5)
+        best, order, pol_ms = ctx.batch_autotune([q for q, _ in qs], outs, totals, reps=5)
         bid = ctx.batch_create([q for q, _ in qs], outs, totals)
         graph = torch.cuda.CUDAGraph()
         ctx.batch_run(bid)
@@ -359,17 +503,34 @@ def batch_bench(dev, reps: int = 10) -> dict:
         ms = timed(graph.replay)
         ctx.batch_status(bid)
         res["batch_fp32_autotuned"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "launches": 1,
-                                       "policy": best, "policy_ms_unflushed": pol_ms,
-                                       "max_abs_err_vs_fp64": err()}
+                                       "policy": best, "order": ["greedy", "fewest multiplications"][order],
+                                       "ms_unflushed_by_order_and_policy": pol_ms, "max_abs_err_vs_fp64": err()}
         for prec in ("fp32", "split_bf16"):
             def plain():
                 for (q, _), o in zip(qs, outs):
                     ctx.reconstruct(q, o, prec)
             ms = timed(plain)
             res[f"plain_{prec}"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "max_abs_err_vs_fp64": err()}
+            if prec == "split_bf16":
+                tc = [ctx.query_tc_steps(q) for q, _ in qs]
+                res["plain_split_bf16"]["tc_steps"] = sum(a for a, _ in tc)
+                res["plain_split_bf16"]["steps"] = sum(b for _, b in tc)
         res["batch_vs_plain_fp32"] = res["plain_fp32"]["ms"] / res["batch_fp32"]["ms"]
         res["bins"] = bins
         ctx.batch_release(bid)
+    # one query at a time, each as ONE persistent launch (merge and every
+    # step; the library's default for FP32 queries)
+    with Context(dev.index or 0) as ctx:
+        cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).to(dev) for p in ps])
+                for c, ps in zip(b.circuits, b.probs)]
+        qs = [ctx.set_qubit_roles(cids[ci], roles) for ci, roles in b.queries]
+
+        def single_launch():
+            for (q, _), o in zip(qs, outs):
+                ctx.reconstruct(q, o, "fp32")
+        ms = timed(single_launch)
+        res["plain_fp32_single_launch"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "launches": len(qs),
+                                           "max_abs_err_vs_fp64": err()}
     # the same batch with the merge pyramid (merges read the level that
     # holds the sums over each subcircuit's merged qubits)
     with Context(dev.index or 0, merge_pyramid=True) as ctx:
@@ -387,7 +548,7 @@ def batch_bench(dev, reps: int = 10) -> dict:
                                      "max_abs_err_vs_fp64": err()}
         ctx.batch_release(bid)
         # pyramid and the autotuned tile policy together
-        best, pol_ms = ctx.batch_autotune([q for q, _ in qs], outs, totals, reps=5)
+        best, order, pol_ms = ctx.batch_autotune([q for q, _ in qs], outs, totals, reps=5)
         bid = ctx.batch_create([q for q, _ in qs], outs, totals)
         graph = torch.cuda.CUDAGraph()
         ctx.batch_run(bid)
@@ -396,7 +557,8 @@ def batch_bench(dev, reps: int = 10) -> dict:
         ms = timed(graph.replay)
         ctx.batch_status(bid)
         res["batch_fp32_pyramid_autotuned"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "launches": 1,
-                                               "policy": best, "policy_ms_unflushed": pol_ms,
+                                               "policy": best, "order": ["greedy", "fewest multiplications"][order],
+                                               "ms_unflushed_by_order_and_policy": pol_ms,
                                                "max_abs_err_vs_fp64": err()}
         ctx.batch_release(bid)
     return res
@@ -464,6 +626,21 @@ def serving_bench(dev, rates=(100, 300, 1000, 3000, 5000), seconds: float = 0.6,
     return out
 
 
+def bench_config(args, w) -> dict:
+    """The workload description both arms print (identical dicts): which
+    circuit, how many bins, the selection size, the output format and the
+    precision of the GPU arm, the seed, and how the timing treats L2."""
+    c = w.circuit
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return {"workload": args.workload, "bins": 1 << w.n_active, "active_qubits": int(w.n_active),
+            "cuts": c.n_edges, "subcircuits": c.n_subcircuits, "topk": TOPK,
+            "out_dtype": "float64" if args.workload == "grid40_K12_a22" else "float32",
+            "precision": args.precision, "seed": w.meta.get("seed"),
+            "parallelism": f"{world} independent circuits" if world > 1 else "1 gpu",
+            "l2": "inputs resident in HBM; the GPU arm flushes L2 between steps (256 MiB write outside the "
+                  "timed events)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -487,7 +664,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "bins": bins, "topk": TOPK},
+            "config": bench_config(args, w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{len(times)} full reconstructions of {args.workload} "
                                        f"({multiprocessing.cpu_count()} host cores present; numpy oracle)"},
@@ -528,7 +705,8 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         dev = torch.device("cuda", 0)
-        fn = {"tensor": tensor_microbench, "hbm": hbm_microbench, "batch": batch_bench, "serving": serving_bench}
+        fn = {"tensor": tensor_microbench, "hbm": hbm_microbench, "batch": batch_bench, "serving": serving_bench,
+              "grid40": grid40_bench, "recursion": recursion_bench}
         print(json.dumps({"extra": args.extra, **fn[args.extra](dev)}), flush=True)
         return
 
@@ -730,12 +908,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "bf16x3", "data": "synthetic",
-            "config": {"workload": args.workload, "bins": bins, "active_qubits": na, "cuts": c.n_edges,
-                       "subcircuits": c.n_subcircuits, "topk": TOPK, "out_dtype": str(out_dtype).split(".")[-1],
-                       "l2": "flushed between steps (256 MiB write outside the timed events)",
-                       "cuda_graph": use_graph,
-                       "parallelism": f"{world} independent circuits" if world > 1 else "1 gpu",
-                       "seed": w.meta.get("seed")},
+            "config": bench_config(args, w),
+            "timing": {"cuda_graph": use_graph, "events": "CUDA events on the launching stream per step"},
             "max_abs_err_vs_fp64": err,
             "tflops": info["flops"] / (ms_per_step * 1e-3) / 1e12,
             "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
@@ -749,12 +923,21 @@ def main():
                     "ms_per_step": e2e_total / args.steps, "results_match_device": e2e_ok,
                     "eager_value": bins * args.steps / (sum(e2e_eager_ms) * 1e-3)},
         }
-        line["config"]["precision"] = prec
         if world == 1 and not args.no_extras:
-            line["tensor_microbench"] = tensor_microbench(dev)
-            line["hbm_microbench"] = hbm_microbench(dev)
+            tm = line["tensor_microbench"] = tensor_microbench(dev)
+            hm = line["hbm_microbench"] = hbm_microbench(dev)
             line["batched_level"] = batch_bench(dev)
             line["serving"] = serving_bench(dev)
+            g40 = line["grid40_K12_a22"] = grid40_bench(dev)
+            rec = line["recursion_bv1000"] = recursion_bench(dev)
+            line["bv1000_seconds_per_recursion"] = rec["seconds_per_recursion"]
+            # the microbenchmarks' roofline fractions, as named fields
+            line["tensor_frac"] = tm["split_bf16"]["tensor_frac"]
+            line["tensor_frac_pairs"] = tm.get("split_bf16_pairs", {}).get("tensor_frac")
+            line["attribute_hbm_frac"] = hm["attribute"]["frac"]
+            line["merge_hbm_frac"] = hm["merge"]["frac"]
+            line["grid40_bins_per_s"] = g40["split_bf16"]["bins_per_s"]
+            line["grid40_max_abs_err_vs_fp64"] = g40["split_bf16"]["max_abs_err_vs_fp64"]
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)

@@ -133,7 +133,7 @@ typedef struct {
    * a wait that runs out records SQC_ETIMEOUT and the kernel drains and
    * returns.  0 = the default, 2000 ms. */
   int32_t wait_limit_ms;
-  /* FP32 reconstructions (1 = on, the default): the merge and every
+  /* FP32 reconstructions (1 = on, default 0): the merge and every
    * contraction step of a query run as ONE persistent launch whose merge
    * blocks and step tiles wait (bounded) only for the tensors they read,
    * instead of one launch per stage; the bins are the same bit for bit.
@@ -141,7 +141,24 @@ typedef struct {
    * that launch's work list (allocates).  Sliced queries and split-BF16
    * keep one launch per stage. */
   int32_t fused_query;
+  /* Programmatic dependent launch (1 = on, the default): each kernel of a
+   * call is launched while the previous kernel on the stream finishes and
+   * waits on the device (griddepcontrol.wait) for its results, which hides
+   * most of the launch gap between the short kernels of a reconstruction.
+   * Results do not change. */
+  int32_t pdl;
+  /* Pairwise contraction order of new query plans (Section 6.2 cost, the
+   * multiplications of each step): SQC_ORDER_GREEDY (default) pairs the
+   * connected tensors of fewest multiplications one step at a time;
+   * SQC_ORDER_MIN_MULT takes the order with the fewest multiplications over
+   * all pairwise trees (exact search over subsets, queries of up to 14
+   * subcircuits; larger ones fall back to greedy).  Fewer multiplications
+   * do not always mean less time for small, latency-bound steps:
+   * sqc_query_autotune and sqc_batch_autotune choose by measurement. */
+  int32_t contraction_order;
 } sqc_config;
+
+enum { SQC_ORDER_GREEDY = 0, SQC_ORDER_MIN_MULT = 1 };
 
 /* Compute graph (Section 5, Fig. 3d).  Vertices are subcircuits 0..n_C-1;
  * edge k runs from subcircuit edge_up[k] (which measures the wire) to
@@ -160,8 +177,8 @@ typedef struct {
 } sqc_graph;
 
 /* Fill `cfg` with the defaults (no budget, 32 active qubits, FP64 chunking
- * from 12 edges, 256 terms per chunk, resident selection, single-launch
- * FP32 queries; everything else off). */
+ * from 12 edges, 256 terms per chunk, resident selection, programmatic
+ * dependent launch; everything else off). */
 SQC_API void sqc_default_config(sqc_config* cfg);
 
 /* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
@@ -275,17 +292,33 @@ SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b);
  * with SQC_EINVAL for a batch without intermediate tensors. */
 SQC_API sqc_status sqc_batch_inject_stall(sqc_ctx* ctx, sqc_batch_id b, int32_t on);
 /* Project-written autotuner of the batched launch (the paper has no
- * counterpart): builds the batch of sqc_batch_create(n, qs, outs, out_dtype,
- * totals) under each tile policy -- 0 by occupancy, 1 small 32 x 32 tiles,
- * 2 large 64 x 64 / 128 x 64 tiles -- times `reps` launches of each on the
- * default stream (CUDA events, after one warm-up launch), releases them, and
- * makes the fastest policy the context's choice for later batches (also
- * the serving loop's).  ms[3] (may be NULL) receives the mean time per
- * launch of each policy.  The bins do not depend on the policy (each bin is
- * summed in the same order); the outputs are overwritten.  Synchronises the
- * device. */
+ * counterpart): for each contraction order (SQC_ORDER_GREEDY, then
+ * SQC_ORDER_MIN_MULT) it plans the n queries again under that order and
+ * builds the batch of sqc_batch_create(n, qs, outs, out_dtype, totals)
+ * under each tile policy -- 0 by occupancy, 1 small 32 x 32 tiles, 2 large
+ * 64 x 64 / 128 x 64 tiles -- times `reps` launches of each on the default
+ * stream (CUDA events, after one warm-up launch) and releases it.  The
+ * fastest (order, policy) wins: the queries keep plans under that order
+ * and the policy becomes the context's choice for later batches (also the
+ * serving loop's).  ms[6] (may be NULL) receives the mean time per launch,
+ * order-major (ms[3 * order + policy]).  Under one order the bins do not
+ * depend on the policy (each bin is summed in the same order); another
+ * contraction order rounds differently.  The outputs are overwritten.
+ * Synchronises the device. */
 SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
                                       sqc_dtype out_dtype, double* totals, int32_t reps, int32_t* best_policy,
+                                      int32_t* best_order, float* ms);
+
+/* Contraction-order autotuner of one query (the paper has no counterpart;
+ * Section 6.2 counts multiplications, which does not rank orders of
+ * latency-bound steps): plans query q under SQC_ORDER_GREEDY and under
+ * SQC_ORDER_MIN_MULT, times `reps` reconstructions of each into out_bins
+ * (arguments as in sqc_reconstruct, on the default stream, after a
+ * warm-up) and keeps the plan of the faster order (*best_order).  ms[2]
+ * (may be NULL): mean ms per reconstruction under each order (equal when
+ * both orders give the same plan).  Synchronises the device; allocates. */
+SQC_API sqc_status sqc_query_autotune(sqc_ctx* ctx, sqc_query_id q, sqc_precision precision, void* out_bins,
+                                      sqc_dtype out_dtype, uint64_t out_bytes, int32_t reps, int32_t* best_order,
                                       float* ms);
 
 /* Serving loop: continuous batching of zoom queries (one recursion level

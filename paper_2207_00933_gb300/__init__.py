@@ -40,7 +40,8 @@ class _Config(ctypes.Structure):
                 ("slice_edges", ctypes.c_int32), ("select_resident", ctypes.c_int32),
                 ("merge_pyramid", ctypes.c_int32), ("slice_input_log2", ctypes.c_int32),
                 ("slice_intermediate_log2", ctypes.c_int32), ("tc_pairs", ctypes.c_int32),
-                ("wait_limit_ms", ctypes.c_int32), ("fused_query", ctypes.c_int32)]
+                ("wait_limit_ms", ctypes.c_int32), ("fused_query", ctypes.c_int32), ("pdl", ctypes.c_int32),
+                ("contraction_order", ctypes.c_int32)]
 
 
 class _Graph(ctypes.Structure):
@@ -80,6 +81,8 @@ _SIGS = {
     "sqc_plan_preview": (_c.c_int32, [_P, _P, _P, _c.POINTER(_c.c_int32), _P, _c.c_int32,
                                       _c.POINTER(_c.c_int32), _P, _c.c_int32, _P, _P, _c.c_char_p, _c.c_int32]),
     "sqc_batch_autotune": (_c.c_int32, [_P, _c.c_int32, _P, _P, _c.c_int, _P, _c.c_int32,
+                                        _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32), _P]),
+    "sqc_query_autotune": (_c.c_int32, [_P, _c.c_int64, _c.c_int, _P, _c.c_int, _c.c_uint64, _c.c_int32,
                                         _c.POINTER(_c.c_int32), _P]),
     "sqc_server_default_config": (None, [_P]),
     "sqc_server_create": (_c.c_int32, [_P, _P, _c.POINTER(_P)]),
@@ -158,7 +161,7 @@ class Context:
                  fp64_chunk_min_edges: int = 12, chunk_terms: int = 256, slice_edges: int = 0,
                  select_resident: bool = True, merge_pyramid: bool = False, slice_input_log2: int = 0,
                  slice_intermediate_log2: int = 0, tc_pairs: bool | None = None, wait_limit_ms: int = 0,
-                 fused_query: bool = True):
+                 fused_query: bool = False, pdl: bool = True, contraction_order: int = 0):
         self._lib = load_library()
         cfg = _Config()
         self._lib.sqc_default_config(ctypes.byref(cfg))
@@ -175,6 +178,8 @@ class Context:
             cfg.tc_pairs = int(bool(tc_pairs))
         cfg.wait_limit_ms = wait_limit_ms
         cfg.fused_query = int(bool(fused_query))
+        cfg.pdl = int(bool(pdl))
+        cfg.contraction_order = int(contraction_order)
         h = _P()
         st = self._lib.sqc_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != 0:
@@ -338,18 +343,29 @@ class Context:
         self._check(self._lib.sqc_batch_inject_stall(self._h, batch, int(bool(on))))
 
     def batch_autotune(self, queries: list[int], outs: list, totals=None, reps: int = 5):
-        """Time the batched launch of `queries` under each tile policy
-        (sqc_batch_autotune) and keep the fastest for later batches.
-        Returns (best policy, mean ms per launch of each policy)."""
+        """Time the batched launch of `queries` under each contraction order
+        and tile policy (sqc_batch_autotune) and keep the fastest.  Returns
+        (best tile policy, best order, mean ms per launch [order][policy])."""
         n = len(queries)
         qa = (ctypes.c_int64 * n)(*queries)
         oa = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
         dt = _dtype_code(outs[0])
         if any(_dtype_code(o) != dt for o in outs):
             raise ValueError("batch outputs must share one dtype")
+        best, order = ctypes.c_int32(), ctypes.c_int32()
+        ms = (ctypes.c_float * 6)()
+        self._check(self._lib.sqc_batch_autotune(self._h, n, qa, oa, dt, _ptr(totals), reps, ctypes.byref(best),
+                                                 ctypes.byref(order), ms))
+        return best.value, order.value, [list(ms[0:3]), list(ms[3:6])]
+
+    def query_autotune(self, query: int, out, precision: str = "fp32", reps: int = 5):
+        """Time reconstructions of `query` under the greedy and the
+        fewest-multiplications contraction order (sqc_query_autotune) and keep
+        the faster plan.  Returns (best order, [ms greedy, ms fewest])."""
         best = ctypes.c_int32()
-        ms = (ctypes.c_float * 3)()
-        self._check(self._lib.sqc_batch_autotune(self._h, n, qa, oa, dt, _ptr(totals), reps, ctypes.byref(best), ms))
+        ms = (ctypes.c_float * 2)()
+        self._check(self._lib.sqc_query_autotune(self._h, query, PREC[precision], _ptr(out), _dtype_code(out),
+                                                 out.numel() * out.element_size(), reps, ctypes.byref(best), ms))
         return best.value, list(ms)
 
     def top_bins(self, query: int, probs, k: int, threshold: float = -math.inf, bins_out=None, probs_out=None,

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <set>
@@ -15,8 +16,16 @@
 
 #include "../../include/sqc.h"
 #include "internal.h"
+#include "launch.cuh"
 
 using namespace sqc;
+
+namespace sqc {
+bool& pdl_flag() {
+  static thread_local bool on = false;
+  return on;
+}
+}  // namespace sqc
 
 namespace {
 
@@ -102,6 +111,7 @@ struct Plan {
   double flops = 0.0;
   std::vector<int> sliced;       // first-level sliced edges (Section 6.3), in greedy order
   int64_t n_slices = 1;          // 4^{sliced edges}: merge descriptor sets, one per slice
+  int order = 0;                 // contraction order the plan follows (SQC_ORDER_*)
 };
 
 struct Batch {
@@ -115,6 +125,7 @@ struct Batch {
 
 struct Query {
   sqc_circuit_id circuit = 0;
+  int order = -1;                // contraction order of its plans (SQC_ORDER_*; -1: the context's)
   std::vector<int8_t> roles;
   int n_active = 0;
   int64_t out_elems = 1;
@@ -541,6 +552,65 @@ void resolve_roles(const Circuit& c, Query* q) {
 
 sqc_status finalize_plan(sqc_ctx* ctx, Plan* P);
 
+// The pairwise contraction order with the fewest multiplications (Section
+// 6.2 cost: a step costs the product of all its index dimensions) over every
+// contraction tree, by dynamic programming over subsets of the subcircuit
+// tensors.  emask[i]: open cut edges of T_i; bins[i]: its bin bits.  A
+// subset's result keeps the edges that join it to the rest (each edge joins
+// two tensors, so the XOR of the members' masks) and all their bins.  Ties:
+// the smaller largest intermediate, then the first split found.  Returns the
+// pairs in execution order (tensor indices, intermediates numbered n, n+1,
+// ... as they are made), or nothing when n is beyond kMaxMinMultSub.
+constexpr int kMaxMinMultSub = 14;
+std::vector<std::pair<int, int>> min_mult_order(const std::vector<uint64_t>& emask, const std::vector<int>& bins) {
+  const int n = int(emask.size());
+  std::vector<std::pair<int, int>> pairs;
+  if (n < 2 || n > kMaxMinMultSub) return pairs;
+  const uint32_t full = (1u << n) - 1u;
+  std::vector<uint64_t> open(size_t(1) << n, 0);
+  std::vector<int> bits(size_t(1) << n, 0);
+  for (uint32_t S = 1; S <= full; ++S) {
+    const int low = __builtin_ctz(S);
+    const uint32_t rest = S & (S - 1);
+    open[S] = open[rest] ^ emask[low];
+    bits[S] = bits[rest] + bins[low];
+  }
+  for (uint32_t S = 1; S <= full; ++S) bits[S] += 2 * __builtin_popcountll(open[S]);
+  std::vector<double> best(size_t(1) << n, 0.0), peak(size_t(1) << n, 0.0);
+  std::vector<uint32_t> split(size_t(1) << n, 0);
+  for (uint32_t S = 1; S <= full; ++S) {
+    if ((S & (S - 1)) == 0) continue;               // one tensor: nothing to do
+    const uint32_t low = S & (0u - S);
+    bool have = false;
+    // every split into A (holding S's lowest member) and B = S \ A
+    for (uint32_t A = (S - 1) & S; A; A = (A - 1) & S) {
+      if (!(A & low)) continue;
+      const uint32_t B = S ^ A;
+      if (!B) continue;
+      const int sh = __builtin_popcountll(open[A] & open[B]);
+      const double c = std::ldexp(1.0, bits[A] + bits[B] - 2 * sh);
+      const double tot = best[A] + best[B] + c;
+      const double pk = std::max({peak[A], peak[B], std::ldexp(1.0, bits[S])});
+      if (!have || tot < best[S] || (tot == best[S] && pk < peak[S])) {
+        best[S] = tot;
+        peak[S] = pk;
+        split[S] = A;
+        have = true;
+      }
+    }
+  }
+  // post-order: both halves first, then the pair that joins them
+  std::function<int(uint32_t)> emit = [&](uint32_t S) -> int {
+    if ((S & (S - 1)) == 0) return __builtin_ctz(S);
+    const int a = emit(split[S]);
+    const int b = emit(S ^ split[S]);
+    pairs.push_back({a, b});
+    return n + int(pairs.size()) - 1;
+  };
+  emit(full);
+  return pairs;
+}
+
 // Host part of a plan; with defer the device part (finalize_plan) is left
 // for the caller.
 sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan* P, bool defer = false) {
@@ -733,7 +803,8 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
   }
   q->merge_bytes = merge_bytes;
 
-  // greedy contraction order on the Section 6.2 cost (multiplications);
+  // contraction order on the Section 6.2 cost (multiplications): greedy
+  // pair by pair, or the fewest multiplications over all pairwise trees;
   // open edges as 64-bit masks (K <= 60) so that a pair's shared edges are
   // one popcount
   std::vector<int> alive;
@@ -747,11 +818,23 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     alive.push_back(i);
     emask.push_back(mask_of(P->tensors[i].edges));
   }
+  const int order = q->order >= 0 ? q->order : ctx->cfg.contraction_order;
+  std::vector<std::pair<int, int>> schedule;      // the pairs in execution order (fewest multiplications)
+  if (order == SQC_ORDER_MIN_MULT && nC > 2) {
+    std::vector<int> nbits(nC);
+    for (int i = 0; i < nC; ++i) nbits[i] = int(P->tensors[i].bits.size()) - 2 * int(P->tensors[i].edges.size());
+    schedule = min_mult_order(emask, nbits);
+  }
+  P->order = schedule.empty() ? SQC_ORDER_GREEDY : SQC_ORDER_MIN_MULT;
   while (alive.size() > 1) {
     int bx = -1, by = -1;
     double best = 0, best_out = 0;
     bool best_conn = false;
-    for (size_t a = 0; a < alive.size(); ++a)
+    if (!schedule.empty()) {
+      bx = schedule[P->steps.size()].first;
+      by = schedule[P->steps.size()].second;
+    }
+    for (size_t a = 0; a < alive.size() && schedule.empty(); ++a)
       for (size_t b = a + 1; b < alive.size(); ++b) {
         const Tensor& X = P->tensors[alive[a]];
         const Tensor& Y = P->tensors[alive[b]];
@@ -985,6 +1068,23 @@ sqc_status ensure_select_work(sqc_ctx* ctx, Query* q) {
   return SQC_OK;
 }
 
+// Plan query q again under contraction order `order` (SQC_ORDER_*): its
+// plans and single-launch work lists are freed, the FP32 plan is rebuilt
+// (the split-BF16 plan is rebuilt by the next split-BF16 reconstruct).
+sqc_status replan(sqc_ctx* ctx, Query& q, int order) {
+  auto cit = ctx->circuits.find(q.circuit);
+  if (cit == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "circuit of the query was unloaded");
+  if (!ctx->async_alloc) cudaDeviceSynchronize();
+  for (auto& b : q.solo)
+    if (b) {
+      dev_free(ctx, b->work, b->work_bytes);
+      b.reset();
+    }
+  for (Plan& p : q.plans) free_plan(ctx, &p);
+  q.order = order;
+  return build_plan(ctx, *cit->second, &q, false, &q.plans[SQC_PREC_FP32]);
+}
+
 // Work list of one persistent launch over the FP32 plans of n queries
 // (shared by sqc_batch_create and the single-query launch of
 // sqc_reconstruct).  solo: one query whose output and probability sum are
@@ -1208,6 +1308,9 @@ std::string config_error(const sqc_config& c) {
   if (c.tc_pairs != 0 && c.tc_pairs != 1) return "tc_pairs must be 0 or 1";
   if (c.wait_limit_ms < 0 || c.wait_limit_ms > 600000) return "wait_limit_ms must be in [0, 600000]";
   if (c.fused_query != 0 && c.fused_query != 1) return "fused_query must be 0 or 1";
+  if (c.pdl != 0 && c.pdl != 1) return "pdl must be 0 or 1";
+  if (c.contraction_order != SQC_ORDER_GREEDY && c.contraction_order != SQC_ORDER_MIN_MULT)
+    return "contraction_order must be SQC_ORDER_GREEDY or SQC_ORDER_MIN_MULT";
   if (c.slice_input_log2 < 0 || c.slice_input_log2 > 62 || c.slice_intermediate_log2 < 0 ||
       c.slice_intermediate_log2 > 62)
     return "slice_input_log2 and slice_intermediate_log2 must be in [0, 62]";
@@ -1227,7 +1330,8 @@ SQC_API void sqc_default_config(sqc_config* cfg) {
   cfg->fp64_chunk_min_edges = 12;
   cfg->chunk_terms = 256;
   cfg->select_resident = 1;
-  cfg->fused_query = 1;
+  cfg->fused_query = 0;
+  cfg->pdl = 1;
 }
 
 SQC_API const char* sqc_last_error(const sqc_ctx* ctx) {
@@ -1287,6 +1391,7 @@ SQC_API sqc_status sqc_load_subcircuit_outputs(sqc_ctx* ctx, const sqc_graph* gr
   if (!ctx || !out_id || !probs) return fail(ctx, SQC_EINVAL, "null argument");
   if (dtype != SQC_F32 && dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "dtype must be SQC_F32 or SQC_F64");
   DeviceGuard g(ctx->device);
+  PdlScope pdl(ctx->cfg.pdl != 0);
   auto c = std::make_unique<Circuit>();
   sqc_status st = build_circuit(ctx, graph, c.get());
   if (st != SQC_OK) return st;
@@ -1351,6 +1456,7 @@ SQC_API sqc_status sqc_update_subcircuit_outputs(sqc_ctx* ctx, sqc_circuit_id id
       return fail(ctx, SQC_ESHAPE, "host-input update needs the circuit loaded from host data in this dtype");
   }
   DeviceGuard g(ctx->device);
+  PdlScope pdl(ctx->cfg.pdl != 0);
   return attribute_all(ctx, c, probs, dtype, probs_on_device, static_cast<cudaStream_t>(stream));
 }
 
@@ -1476,6 +1582,7 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
   if (out_bytes < need)
     return fail(ctx, SQC_ESHAPE, "out_bytes " + std::to_string(out_bytes) + " < " + std::to_string(need));
   DeviceGuard g(ctx->device);
+  PdlScope pdl(ctx->cfg.pdl != 0);
   Plan& P = q.plans[precision];
   if (!P.built) {
     // the first split-BF16 call on a query plans that precision (allocates)
@@ -1622,6 +1729,7 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* prob
   auto it = ctx->queries.find(qid);
   if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
   DeviceGuard g(ctx->device);
+  PdlScope pdl(ctx->cfg.pdl != 0);
   {
     // the first selection on a query allocates its workspace
     sqc_status st = ensure_select_work(ctx, it->second.get());
@@ -1669,6 +1777,7 @@ SQC_API sqc_status sqc_batch_run(sqc_ctx* ctx, sqc_batch_id b, void* stream) {
   auto it = ctx->batches.find(b);
   if (it == ctx->batches.end()) return fail(ctx, SQC_ENOTFOUND, "unknown batch");
   DeviceGuard g(ctx->device);
+  PdlScope pdl(ctx->cfg.pdl != 0);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StageScope scope(ctx, s, SQC_STAGE_CONTRACT);
   CK(launch_batch(it->second->L, it->second->grid, s));
@@ -1718,11 +1827,14 @@ SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b) {
   return SQC_OK;
 }
 
-SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
-                                      sqc_dtype out_dtype, double* totals, int32_t reps, int32_t* best_policy,
-                                      float* ms) {
-  if (!ctx || !best_policy || reps < 1) return fail(ctx, SQC_EINVAL, "batch autotune: null argument or reps < 1");
-  DeviceGuard g(ctx->device);
+}  // extern "C"
+
+namespace {
+// The batched launch of n queries (their current plans) under every tile
+// policy: mean ms per launch into ms[kBatchPolicies], the fastest into
+// *best_policy; leaves ctx->batch_policy as it found it.
+sqc_status batch_autotune_tiles(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
+                                sqc_dtype out_dtype, double* totals, int32_t reps, int32_t* best_policy, float* ms) {
   const int saved = ctx->batch_policy;
   int best = -1;
   float best_ms = 0.f;
@@ -1758,8 +1870,105 @@ SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_i
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ctx->batch_policy = st == SQC_OK ? best : saved;
+  ctx->batch_policy = saved;
   if (st == SQC_OK) *best_policy = best;
+  return st;
+}
+}  // namespace
+
+extern "C" {
+
+SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
+                                      sqc_dtype out_dtype, double* totals, int32_t reps, int32_t* best_policy,
+                                      int32_t* best_order, float* ms) {
+  if (!ctx || !best_policy || !best_order || reps < 1 || n < 1 || !qs)
+    return fail(ctx, SQC_EINVAL, "batch autotune: null argument, n < 1 or reps < 1");
+  DeviceGuard g(ctx->device);
+  std::vector<Query*> qv(n);
+  for (int j = 0; j < n; ++j) {
+    auto it = ctx->queries.find(qs[j]);
+    if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "batch autotune: unknown query");
+    qv[j] = it->second.get();
+  }
+  const int saved = ctx->batch_policy;
+  int best = -1, best_o = SQC_ORDER_GREEDY;
+  float best_ms = 0.f;
+  sqc_status st = SQC_OK;
+  for (int o = 0; o < 2 && st == SQC_OK; ++o) {
+    for (Query* q : qv)
+      if (st == SQC_OK && (q->plans[SQC_PREC_FP32].order != o || !q->plans[SQC_PREC_FP32].built)) st = replan(ctx, *q, o);
+    if (st != SQC_OK) break;
+    int32_t pol = -1;
+    float t3[kBatchPolicies] = {0.f, 0.f, 0.f};
+    st = batch_autotune_tiles(ctx, n, qs, outs, out_dtype, totals, reps, &pol, t3);
+    if (st != SQC_OK) break;
+    for (int p = 0; p < kBatchPolicies; ++p) {
+      if (ms) ms[o * kBatchPolicies + p] = t3[p];
+      if (best < 0 || t3[p] < best_ms) { best = p; best_ms = t3[p]; best_o = o; }
+    }
+  }
+  if (st == SQC_OK) {
+    for (Query* q : qv)
+      if (st == SQC_OK && q->plans[SQC_PREC_FP32].order != best_o) st = replan(ctx, *q, best_o);
+  }
+  ctx->batch_policy = st == SQC_OK ? best : saved;
+  if (st == SQC_OK) {
+    *best_policy = best;
+    *best_order = best_o;
+  }
+  return st;
+}
+
+
+SQC_API sqc_status sqc_query_autotune(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
+                                      sqc_dtype out_dtype, uint64_t out_bytes, int32_t reps, int32_t* best_order,
+                                      float* ms) {
+  if (!ctx || !best_order || !out_bins || reps < 1)
+    return fail(ctx, SQC_EINVAL, "query autotune: null argument or reps < 1");
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  Query& q = *it->second;
+  DeviceGuard g(ctx->device);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  const cudaError_t ee = cudaEventCreate(&e1);
+  if (ee != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ctx, ee, "query autotune events");
+  }
+  const int orders[2] = {SQC_ORDER_GREEDY, SQC_ORDER_MIN_MULT};
+  float t_of[2] = {0.f, 0.f};
+  int planned[2] = {-1, -1};          // the order each candidate's plan actually followed
+  sqc_status st = SQC_OK;
+  for (int j = 0; j < 2 && st == SQC_OK; ++j) {
+    st = replan(ctx, q, orders[j]);
+    if (st != SQC_OK) break;
+    planned[j] = q.plans[SQC_PREC_FP32].order;
+    if (j == 1 && planned[1] != SQC_ORDER_MIN_MULT) {   // too many subcircuits: the same greedy plan
+      t_of[1] = t_of[0];
+      break;
+    }
+    st = sqc_reconstruct(ctx, qid, precision, out_bins, out_dtype, out_bytes, nullptr, nullptr);   // warm-up
+    cudaError_t e = cudaSuccess;
+    if (st == SQC_OK) e = cudaEventRecord(e0, nullptr);
+    for (int r = 0; r < reps && st == SQC_OK && e == cudaSuccess; ++r)
+      st = sqc_reconstruct(ctx, qid, precision, out_bins, out_dtype, out_bytes, nullptr, nullptr);
+    if (st == SQC_OK && e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+    if (st == SQC_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (st == SQC_OK && e == cudaSuccess) e = cudaEventElapsedTime(&t_of[j], e0, e1);
+    if (st == SQC_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "query autotune timing");
+    t_of[j] /= float(reps);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SQC_OK) return st;
+  const int best = (planned[1] == SQC_ORDER_MIN_MULT && t_of[1] < t_of[0]) ? SQC_ORDER_MIN_MULT : SQC_ORDER_GREEDY;
+  if (ms) {
+    ms[0] = t_of[0];
+    ms[1] = t_of[1];
+  }
+  if (q.plans[SQC_PREC_FP32].order != best || q.order != best) st = replan(ctx, q, best);
+  if (st == SQC_OK) *best_order = best;
   return st;
 }
 

@@ -10,6 +10,7 @@
 // is stored bit-reversed so that, under the recursion's roles (zoomed =
 // low data qubits, merged = high), a bin's states are one contiguous run.
 #include "internal.h"
+#include "launch.cuh"
 
 namespace sqc {
 
@@ -21,6 +22,8 @@ __device__ __forceinline__ uint32_t rev_bits(uint32_t x, int n) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) fold_kernel(FoldArgs a) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   const T* p = static_cast<const T*>(a.p);
   const int64_t X = int64_t(1) << a.n;
   const int64_t total = a.V * X;
@@ -45,6 +48,8 @@ __global__ void __launch_bounds__(256) fold_kernel(FoldArgs a) {
 }
 
 __global__ void __launch_bounds__(256) mix_kernel(MixArgs a) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   const int64_t X = int64_t(1) << a.n;
   const int64_t total = a.rows * X;
   for (int64_t o = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; o < total;
@@ -512,6 +517,8 @@ __device__ void fill_tile_ctx(const AttrDesc& d, AttrTileCtx& t) {
 enum : int { kAttrAll = 0, kAttrVec = 1, kAttrOne = 2 };
 template <int MODE>
 __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   extern __shared__ float val[];
   __shared__ AttrDesc d;
   __shared__ AttrTileCtx tc;
@@ -591,11 +598,8 @@ inline int grid_for(int64_t total) {
 
 cudaError_t launch_fold(const FoldArgs& a, cudaStream_t s) {
   const int64_t total = a.V << a.n;
-  if (a.in_f64)
-    fold_kernel<double><<<grid_for(total), 256, 0, s>>>(a);
-  else
-    fold_kernel<float><<<grid_for(total), 256, 0, s>>>(a);
-  return cudaGetLastError();
+  if (a.in_f64) return launch_k(fold_kernel<double>, dim3(grid_for(total)), dim3(256), 0, s, false, a);
+  return launch_k(fold_kernel<float>, dim3(grid_for(total)), dim3(256), 0, s, false, a);
 }
 
 cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s) {
@@ -622,13 +626,10 @@ cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_byte
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem_bytes) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int64_t grid = blocks < int64_t(sms) * per_sm ? blocks : int64_t(sms) * per_sm;
-  if (all_vec)
-    attr_fused_kernel<kAttrVec><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
-  else if (all_one)
-    attr_fused_kernel<kAttrOne><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
-  else
-    attr_fused_kernel<kAttrAll><<<unsigned(grid), 256, smem_bytes, s>>>(L, blocks);
-  return cudaGetLastError();
+  const dim3 g(unsigned(grid), 1, 1);
+  if (all_vec) return launch_k(attr_fused_kernel<kAttrVec>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
+  if (all_one) return launch_k(attr_fused_kernel<kAttrOne>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
+  return launch_k(attr_fused_kernel<kAttrAll>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
 }
 
 cudaError_t attr_configure() {
@@ -643,8 +644,7 @@ cudaError_t attr_configure() {
 
 cudaError_t launch_mix(const MixArgs& a, cudaStream_t s) {
   const int64_t total = a.rows << a.n;
-  mix_kernel<<<grid_for(total), 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(mix_kernel, dim3(grid_for(total)), dim3(256), 0, s, false, a);
 }
 
 }  // namespace sqc

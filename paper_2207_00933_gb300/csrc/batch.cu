@@ -66,6 +66,8 @@ __device__ __forceinline__ double run_tile(const BatchStep& st, int64_t tile, fl
 }
 
 __global__ void __launch_bounds__(kOpThreads, 2) batch_kernel(BatchLaunch L) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   extern __shared__ __align__(16) float smem[];
   __shared__ MergeDesc md;
   __shared__ BatchItem item;
@@ -164,8 +166,7 @@ cudaError_t batch_configure() {
 
 cudaError_t launch_batch(const BatchLaunch& L, int grid, cudaStream_t s) {
   if (L.n_items <= 0) return cudaSuccess;
-  batch_kernel<<<grid, kOpThreads, batch_smem_bytes(), s>>>(L);
-  return cudaGetLastError();
+  return launch_k(batch_kernel, dim3(unsigned(grid)), dim3(kOpThreads), size_t(batch_smem_bytes()), s, false, L);
 }
 
 // Tile configuration ids of the batch kernel for one step, under a tile

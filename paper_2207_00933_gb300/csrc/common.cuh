@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "internal.h"
+#include "launch.cuh"
 
 namespace sqc {
 

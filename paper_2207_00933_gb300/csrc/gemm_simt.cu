@@ -21,6 +21,8 @@ constexpr int kThreads = kOpThreads;
 
 template <int BM, int BN, int TM, int TN, bool CHUNKED, int kBK>
 __global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs a) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   __shared__ __align__(16) float As[kBK * (BM + 4)];
   __shared__ __align__(16) float Bs[kBK * (BN + 4)];
   __shared__ double red[kThreads / 32];
@@ -45,11 +47,11 @@ cudaError_t launch_cfg(const GemmArgs& a, cudaStream_t s) {
     // fall back to an exact power-of-two split
     int64_t x = 32768;
     while (tiles % x) x >>= 1;
-    gemm_simt_kernel<BM, BN, TM, TN, CH, BK><<<dim3(unsigned(x), unsigned(tiles / x)), kThreads, 0, s>>>(a);
-  } else {
-    gemm_simt_kernel<BM, BN, TM, TN, CH, BK><<<dim3(unsigned(gx), unsigned(gy)), kThreads, 0, s>>>(a);
+    return launch_k(gemm_simt_kernel<BM, BN, TM, TN, CH, BK>, dim3(unsigned(x), unsigned(tiles / x)), dim3(kThreads),
+                    0, s, false, a);
   }
-  return cudaGetLastError();
+  return launch_k(gemm_simt_kernel<BM, BN, TM, TN, CH, BK>, dim3(unsigned(gx), unsigned(gy)), dim3(kThreads), 0, s,
+                  false, a);
 }
 
 }  // namespace

@@ -39,9 +39,11 @@
 // CTA's 128 output rows in that CTA's TMEM.  The odd CTA's warp 1 forwards
 // the completion of its loads to the even CTA's stage barrier, its epilogue
 // warps return the accumulator to the even CTA's barrier, and the even
-// CTA's commits arrive on the barriers of both.  When the units leave a
-// last wave at most half full, that wave runs as half-width units
-// (N = BN / 2).
+// CTA's commits arrive on the barriers of both.
+//
+// Tail: when the units leave a last wave at most half full, that wave runs
+// as half-width units (N = BN / 2), so that the busiest CTA does half a
+// unit less.
 //
 // Every mbarrier wait is bounded in time; on timeout the CTA (and its pair
 // partner) records an error code, waits (bounded) for its own copies in
@@ -76,7 +78,7 @@ struct TcCfg {
   static constexpr int BN = BN_, BK = BK_, STAGES = STAGES_;
   static constexpr bool PAIR = PAIR_;
   static constexpr int kRowsB = PAIR ? BN / 2 : BN;   // B rows one CTA holds per plane
-  static constexpr int kBoxB = PAIR ? BN / 4 : BN;    // rows per B load (a half-width pair unit loads one box)
+  static constexpr int kBoxB = PAIR ? BN / 4 : BN / 2;  // rows per B load (a half-width unit loads one box)
   static constexpr int kTileA = kBM * BK * 2;
   static constexpr int kTileB = kRowsB * BK * 2;
   static constexpr int kStageBytes = 3 * kTileA + 3 * kTileB;
@@ -237,6 +239,32 @@ __device__ __forceinline__ void mma_commit(uint32_t addr) {
                  : "memory");
 }
 
+// Start loading 32 consecutive accumulator columns of this thread's TMEM
+// lane into r; the values may be read only after tmem_wait(r).
+__device__ __forceinline__ void tmem_ld32_start(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+// Wait for every TMEM load of this thread; r is passed through the wait so
+// that no read of it can be scheduled before the data has arrived.
+__device__ __forceinline__ void tmem_wait(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
 // 32 consecutive accumulator columns of this thread's TMEM lane (one
 // load, one wait).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
@@ -288,18 +316,23 @@ __device__ __forceinline__ double add16(const GemmTcArgs& a, uint64_t off, bool 
     double* C = static_cast<double*>(a.C);
     if (contig && ncols == 16) {
       double2* p = reinterpret_cast<double2*>(C + off);
+      double2 o[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) o[q] = make_double2(f2d(f[2 * q]), f2d(f[2 * q + 1]));
+      if (load_old) {
+        double2 old[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) old[q] = p[q];          // all loads in flight together
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          o[q].x += old[q].x;
+          o[q].y += old[q].y;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        double2 o;
-        if (load_old) {
-          o = p[q];
-          o.x += f2d(f[2 * q]);
-          o.y += f2d(f[2 * q + 1]);
-        } else {
-          o = make_double2(f2d(f[2 * q]), f2d(f[2 * q + 1]));
-        }
-        p[q] = o;
-        s += o.x + o.y;
+        p[q] = o[q];
+        s += o[q].x + o[q].y;
       }
     } else {
 #pragma unroll
@@ -343,6 +376,8 @@ __device__ __forceinline__ double add16(const GemmTcArgs& a, uint64_t off, bool 
 template <class Cfg>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmTcArgs a) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   constexpr bool PAIR = Cfg::PAIR;
   constexpr int kBN = Cfg::BN, kBK = Cfg::BK, kStages = Cfg::STAGES;
   constexpr int kTileA = Cfg::kTileA, kTileB = Cfg::kTileB, kStageBytes = Cfg::kStageBytes;
@@ -370,7 +405,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const int64_t unit0 = PAIR ? int64_t(blockIdx.x >> 1) : int64_t(blockIdx.x);
   const int64_t unit_step = PAIR ? int64_t(gridDim.x >> 1) : int64_t(gridDim.x);
   const int64_t tail = nwide % unit_step;
-  const bool split = PAIR && tail > 0 && 2 * tail <= unit_step;
+  const bool split = tail > 0 && 2 * tail <= unit_step;
   const int64_t wide_end = split ? nwide - tail : nwide;        // units [wide_end, nunits) are half-width
   const int64_t nunits = split ? wide_end + 2 * tail : nwide;
   // accumulator passes per unit: the shared index in chunks of `chunk`
@@ -468,9 +503,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                             n0 + int(rank) * (kBN / 2) + h * (kBN / 4), p, &full[s]);
           }
         } else {
-          mbar_expect_tx(&full[s], kStageBytes);
+          // the unit's B rows: two boxes of BN / 2 rows (half width: one)
+          mbar_expect_tx(&full[s], 3 * kTileA + 3 * (half ? kTileB / 2 : kTileB));
           for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
-          for (int p = 0; p < 3; ++p) tma_load_3d(stb + p * kTileB, &tmB, kb * kBK, n0, p, &full[s]);
+          for (int p = 0; p < 3; ++p)
+            for (int h = 0; h < (half ? 1 : 2); ++h)
+              tma_load_3d(stb + p * kTileB + h * (kTileB / 2), &tmB, kb * kBK, n0 + h * (kBN / 2), p, &full[s]);
         }
         issued = it + 1;
       }
@@ -556,7 +594,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       }
   } else if (warp >= 2) {
     // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (its rows) and
-    // half (w-2)/4 of the unit's columns, 32 columns per TMEM load
+    // half (w-2)/4 of the unit's columns, 32 columns per TMEM load; the next
+    // 32 columns load while the current ones are stored
+    constexpr int kChunks = kBN / 64;          // 32-column chunks in a warp's half of a full-width unit
     const int quad = warp & 3;
     const int hc = (warp - 2) >> 2;
     const float alpha_f = float(a.alpha);
@@ -567,10 +607,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
       int64_t m0, n0;
       bool half_unit;
       unit_of(u, &m0, &n0, &half_unit);
-      const int width = half_unit ? kBN / 2 : kBN;
+      const int cw = (half_unit ? kBN / 2 : kBN) / 2;      // this warp's columns
+      const int nchunk = cw / 32;
+      const int64_t c_lo = n0 + int64_t(hc) * cw;
       const int64_t row = m0 + quad * 32 + lane;
       const bool row_ok = row < a.M;
+      // the row's and the columns' offsets, loaded together before the
+      // accumulator is ready (one memory latency per unit, not one per group)
       const uint64_t rbase = row_ok ? a.rowmap[row] : 0;
+      uint64_t cb[2 * kChunks];
+#pragma unroll
+      for (int g = 0; g < 2 * kChunks; ++g) {
+        const int64_t col0 = c_lo + 16 * g;
+        cb[g] = (g < 2 * nchunk && col0 < a.N) ? a.colmap[col0] : 0;
+      }
       for (int pass = 0; pass < npass; ++pass, ++t) {
         const int buf = int(t & 1);
         if (!mbar_wait<PAIR>(&acc_full[buf], uint32_t((t >> 1) & 1), &failed, wlim)) {
@@ -581,33 +631,42 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const bool load_old = pass > 0 || a.accumulate;
         const bool last_pass = pass == npass - 1;
-        for (int c0 = hc * (width / 2); c0 < (hc + 1) * (width / 2); c0 += 32) {
-          float v[32];
-          tmem_ld32(tmem + uint32_t(buf * kTmemCols) + (uint32_t(quad * 32) << 16) + uint32_t(c0), v);
-          if (!row_ok) continue;
+        const uint32_t tbase = tmem + uint32_t(buf * kTmemCols) + (uint32_t(quad * 32) << 16) +
+                               uint32_t(hc * cw);
+        uint32_t r[2][32];
+        tmem_ld32_start(tbase, r[0]);
+        tmem_wait(r[0]);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int64_t col0 = n0 + c0 + 16 * h;
-            const int ncols = int(a.N - col0 < 16 ? (a.N - col0 > 0 ? a.N - col0 : 0) : 16);
-            if (ncols == 0) continue;
-            float* f = v + 16 * h;
+        for (int i = 0; i < kChunks; ++i) {
+          if (i >= nchunk) break;
+          uint32_t* cur = r[i & 1];
+          if (i + 1 < nchunk) tmem_ld32_start(tbase + uint32_t(32 * (i + 1)), r[(i + 1) & 1]);
+          if (row_ok) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) f[j] *= alpha_f;   // alpha is a power of two: exact
-            const uint64_t c_first = a.colmap[col0];
-            const bool contig = a.contig16 && ncols == 16;
-            if (plain) {
-              // probability check: the 16 values summed in FP32, the groups in FP64
-              float cs = 0.f;
+            for (int h = 0; h < 2; ++h) {
+              const int64_t col0 = c_lo + 32 * i + 16 * h;
+              const int ncols = int(a.N - col0 < 16 ? (a.N - col0 > 0 ? a.N - col0 : 0) : 16);
+              if (ncols == 0) continue;
+              float f[16];
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                if (j < ncols) cs += f[j];
-              sum_d += double(cs);
-              store16(a, rbase + c_first, contig, f, a.colmap, col0, rbase, ncols);
-            } else {
-              const double s = add16(a, rbase + c_first, contig, f, a.colmap, col0, rbase, ncols, load_old);
-              if (last_pass) sum_d += s;
+              for (int j = 0; j < 16; ++j) f[j] = __uint_as_float(cur[16 * h + j]) * alpha_f;   // exact: 2^-K
+              const uint64_t c_first = cb[2 * i + h];
+              const bool contig = a.contig16 && ncols == 16;
+              if (plain) {
+                // probability check: the 16 values summed in FP32, the groups in FP64
+                float cs = 0.f;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  if (j < ncols) cs += f[j];
+                sum_d += double(cs);
+                store16(a, rbase + c_first, contig, f, a.colmap, col0, rbase, ncols);
+              } else {
+                const double sv = add16(a, rbase + c_first, contig, f, a.colmap, col0, rbase, ncols, load_old);
+                if (last_pass) sum_d += sv;
+              }
             }
           }
+          if (i + 1 < nchunk) tmem_wait(r[(i + 1) & 1]);
         }
         // hand the accumulator back to the MMA thread
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -677,8 +736,8 @@ cudaError_t launch_cfg(const GemmTcArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
   const int64_t tiles = (a.Mp / kBM) * (a.Np / Cfg::BN);
   const int64_t grid = tiles < 152 ? tiles : 152;    // persistent: at most one CTA per SM
-  gemm_tc_kernel<Cfg><<<unsigned(grid), kThreads, Cfg::kSmemBytes, s>>>(ma, mb, a);
-  return cudaGetLastError();
+  return launch_k(gemm_tc_kernel<Cfg>, dim3(unsigned(grid)), dim3(kThreads), size_t(Cfg::kSmemBytes), s, false, ma,
+                  mb, a);
 }
 
 // Co-resident 2-CTA clusters of the pair kernel (0: none), once per process.
@@ -713,18 +772,26 @@ cudaError_t launch_pair(const GemmTcArgs& a, int clusters, cudaStream_t s) {
   const int64_t units = (a.Mp / (2 * kBM)) * (a.Np / CfgPair::BN);
   const int64_t nc = units < clusters ? units : clusters;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.gridDim = dim3(unsigned(2 * nc), 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.dynamicSmemBytes = CfgPair::kSmemBytes;
   cfg.stream = s;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, gemm_tc_kernel<CfgPair>, ma, mb, a);
+  cfg.numAttrs = pdl_flag() ? 2 : 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, gemm_tc_kernel<CfgPair>, ma, mb, a);
+  if (e != cudaSuccess && cfg.numAttrs == 2) {
+    cudaGetLastError();
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, gemm_tc_kernel<CfgPair>, ma, mb, a);
+  }
+  return e;
 }
 
 }  // namespace

@@ -21,6 +21,8 @@ namespace {
 // into it.
 __global__ void __launch_bounds__(256) merge_kernel(const MergeDesc* __restrict__ descs, int n,
                                                     int64_t total_blocks) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   __shared__ MergeDesc d;
   __shared__ int cur;
   __shared__ int64_t next_begin;
@@ -48,6 +50,8 @@ __global__ void __launch_bounds__(256) merge_kernel(const MergeDesc* __restrict_
 // memory (pairwise sums) and writes every level's share.
 __global__ void __launch_bounds__(256) pyramid_kernel(const float* __restrict__ src, float* pyr, int64_t V, int n,
                                                       int s, int c) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   __shared__ float buf[1 << kPyramidLevelsPerPass];
   const int C = 1 << c;
   const int row_shift = n - s - c;                   // chunks per row = 2^row_shift
@@ -90,8 +94,7 @@ cudaError_t launch_pyramid(const float* A, float* pyr, int64_t V, int n, cudaStr
     const float* src = lev == 0 ? A : pyr + V * ((int64_t(1) << n) - (int64_t(1) << (n - lev + 1)));
     const int64_t total = V << (n - lev - c);
     const int64_t grid = total < 152 * 8 ? total : 152 * 8;
-    pyramid_kernel<<<unsigned(grid), 256, 0, s>>>(src, pyr, V, n, lev, c);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_k(pyramid_kernel, dim3(unsigned(grid)), dim3(256), 0, s, false, src, pyr, V, n, lev, c);
     if (e != cudaSuccess) return e;
     lev += c;
   }
@@ -102,8 +105,7 @@ cudaError_t launch_merge_blocks(const MergeDesc* d_descs, int n, int64_t total_b
   if (n <= 0 || total_blocks <= 0) return cudaSuccess;
   // 8 CTAs of 256 threads per SM
   const int64_t grid = total_blocks < 152 * 8 ? total_blocks : 152 * 8;
-  merge_kernel<<<unsigned(grid), 256, 0, s>>>(d_descs, n, total_blocks);
-  return cudaGetLastError();
+  return launch_k(merge_kernel, dim3(unsigned(grid)), dim3(256), 0, s, false, d_descs, n, total_blocks);
 }
 
 }  // namespace sqc

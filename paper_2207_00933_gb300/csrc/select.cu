@@ -150,6 +150,8 @@ template <bool is_f64>
 __global__ void __launch_bounds__(kSelThreads)
 radix_pass(const void* x, int aligned, uint64_t n, unsigned long long key_thr, int k, int pass,
            int last_pass, int cap, unsigned* hist_all, unsigned long long* st) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   __shared__ unsigned shw[kSelThreads / 32][kRadix];   // one histogram per warp
   unsigned* sh = shw[0];
   __shared__ bool is_last;
@@ -248,6 +250,8 @@ template <bool is_f64>
 __global__ void __launch_bounds__(kSelThreads)
 compact(const void* x, int aligned, uint64_t n, unsigned long long key_thr, unsigned long long* st,
         unsigned long long* ck, unsigned long long* ci) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   const unsigned long long done = st[ST_DONE];
   const int bits = int(st[ST_BITS]);
   const unsigned long long pv = bits ? (st[ST_PREFIX] >> (64 - bits)) : 0ull;
@@ -289,6 +293,8 @@ compact(const void* x, int aligned, uint64_t n, unsigned long long key_thr, unsi
 __global__ void __launch_bounds__(kSelThreads)
 tie_count(const void* x, int is_f64, uint64_t n, unsigned long long key_thr, const unsigned long long* st,
           unsigned* counts, uint64_t range) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   if (st[ST_DONE] != 3) return;
   __shared__ unsigned s;
   if (threadIdx.x == 0) s = 0;
@@ -311,6 +317,8 @@ tie_count(const void* x, int is_f64, uint64_t n, unsigned long long key_thr, con
 __global__ void __launch_bounds__(kSelThreads)
 tie_write(const void* x, int is_f64, uint64_t n, unsigned long long key_thr, unsigned long long* st,
           const unsigned* counts, uint64_t range, unsigned long long* ck, unsigned long long* ci) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   if (st[ST_DONE] != 3) return;
   __shared__ unsigned long long base;
   __shared__ unsigned wsum[kSelThreads / 32];
@@ -365,6 +373,8 @@ constexpr int kRankGrid = kMaxSort / 32;
 __global__ void __launch_bounds__(32 * kRankWarps)
 rank_emit(const void* x, int is_f64, unsigned long long* st, const unsigned long long* ck,
           const unsigned long long* ci, unsigned long long* bins_out, double* probs_out, int* n_found) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   __shared__ unsigned long long part[kRankWarps][32];
   __shared__ bool is_last;
   const unsigned long long done = st[ST_DONE];
@@ -417,6 +427,8 @@ rank_emit(const void* x, int is_f64, unsigned long long* st, const unsigned long
 
 __global__ void __launch_bounds__(kSelThreads)
 sum_kernel(const void* x, int is_f64, uint64_t n, double* partials, unsigned* counter, double* total) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   __shared__ double red[kSelThreads / 32];
   double s = 0.0;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x)
@@ -493,23 +505,34 @@ cudaError_t launch_select(const SelectWork& w, const void* x, int is_f64, uint64
   const int g = vec_grid(n);
   const int passes = is_f64 ? kPasses : 4;
   for (int p = 0; p < passes; ++p) {
-    if (is_f64)
-      radix_pass<true><<<g, kSelThreads, 0, s>>>(x, aligned, n, kt, k, p, p == passes - 1, cap, w.hist, st);
-    else
-      radix_pass<false><<<g, kSelThreads, 0, s>>>(x, aligned, n, kt, k, p, p == passes - 1, cap, w.hist, st);
+    const int last = p == passes - 1;
+    const cudaError_t e =
+        is_f64 ? launch_k(radix_pass<true>, dim3(g), dim3(kSelThreads), 0, s, false, x, aligned, n, kt, k, p, last,
+                          cap, w.hist, st)
+               : launch_k(radix_pass<false>, dim3(g), dim3(kSelThreads), 0, s, false, x, aligned, n, kt, k, p, last,
+                          cap, w.hist, st);
+    if (e != cudaSuccess) return e;
   }
-  if (is_f64)
-    compact<true><<<g, kSelThreads, 0, s>>>(x, aligned, n, kt, st, w.cand_key, w.cand_idx);
-  else
-    compact<false><<<g, kSelThreads, 0, s>>>(x, aligned, n, kt, st, w.cand_key, w.cand_idx);
+  {
+    const cudaError_t e =
+        is_f64 ? launch_k(compact<true>, dim3(g), dim3(kSelThreads), 0, s, false, x, aligned, n, kt, st, w.cand_key,
+                          w.cand_idx)
+               : launch_k(compact<false>, dim3(g), dim3(kSelThreads), 0, s, false, x, aligned, n, kt, st, w.cand_key,
+                          w.cand_idx);
+    if (e != cudaSuccess) return e;
+  }
   const uint64_t range = (n + w.max_blocks - 1) / w.max_blocks;
   const unsigned tb = unsigned((n + range - 1) / (range ? range : 1));
   const uint64_t rng = range ? range : 1;
-  tie_count<<<tb ? tb : 1, kSelThreads, 0, s>>>(x, is_f64, n, kt, st, w.tie_count, rng);
-  tie_write<<<tb ? tb : 1, kSelThreads, 0, s>>>(x, is_f64, n, kt, st, w.tie_count, rng, w.cand_key, w.cand_idx);
-  rank_emit<<<kRankGrid, 32 * kRankWarps, 0, s>>>(x, is_f64, st, w.cand_key, w.cand_idx, bins_out, probs_out,
-                                                 n_found);
-  return cudaGetLastError();
+  const dim3 tg(tb ? tb : 1);
+  cudaError_t e = launch_k(tie_count, tg, dim3(kSelThreads), 0, s, false, x, is_f64, n, kt, st, w.tie_count, rng);
+  if (e == cudaSuccess)
+    e = launch_k(tie_write, tg, dim3(kSelThreads), 0, s, false, x, is_f64, n, kt, st, w.tie_count, rng, w.cand_key,
+                 w.cand_idx);
+  if (e == cudaSuccess)
+    e = launch_k(rank_emit, dim3(kRankGrid), dim3(32 * kRankWarps), 0, s, false, x, is_f64, st, w.cand_key,
+                 w.cand_idx, bins_out, probs_out, n_found);
+  return e;
 }
 
 namespace {
@@ -583,6 +606,8 @@ template <bool is_f64>
 __global__ void __launch_bounds__(kCoopThreads)
 select_coop_kernel(const void* x, int aligned, uint64_t n, unsigned long long key_thr, int k, int cap,
                    CoopWork w, unsigned long long* bins_out, double* probs_out, int* n_found, int* err) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   extern __shared__ unsigned shw[];               // [kCoopWarps][kCRadix]
   __shared__ unsigned long long s_prefix, s_krem, s_take;
   __shared__ int s_bits, s_done;
@@ -971,6 +996,8 @@ template <bool F64>
 __global__ void __launch_bounds__(kRThreads, 1)
 select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, unsigned long long key_thr64, int k,
                        int cap, ResWork w, unsigned long long* bins_out, double* probs_out, int* n_found, int* err) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   // Shared memory holds one 32-bit word per value: the whole key of an FP32
   // value, the high word of the 64-bit key of an FP64 value (its low word
   // is read back from the input only for values whose high word equals the
@@ -1401,13 +1428,13 @@ cudaError_t launch_select_resident(void* work, int grid, const void* x, int is_f
   w.tie_count = reinterpret_cast<unsigned*>(p + sizeof(unsigned long long) * 32 + 2 * sizeof(unsigned long long) * kMaxSort +
                                             sizeof(unsigned) * kCPasses * kCopies * kCRadix + sizeof(unsigned) * kMaxSort);
   w.hist = reinterpret_cast<unsigned*>(p + ((coop_part_bytes(select_coop_grid()) + 255) & ~size_t(255)));
-  int aligned = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
-  unsigned long long kt = threshold_key(is_f64, threshold);
-  void* args[] = {const_cast<void**>(&x), &aligned, &n, &per, &kt, &k, const_cast<int*>(&cap), &w, &bins_out,
-                  &probs_out, &n_found, &err};
-  const void* fn = is_f64 ? reinterpret_cast<const void*>(select_resident_kernel<true>)
-                          : reinterpret_cast<const void*>(select_resident_kernel<false>);
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kRThreads), args, smem, s);
+  const int aligned = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+  const unsigned long long kt = threshold_key(is_f64, threshold);
+  if (is_f64)
+    return launch_k(select_resident_kernel<true>, dim3(grid), dim3(kRThreads), smem, s, true, x, aligned, n, per, kt,
+                    k, cap, w, bins_out, probs_out, n_found, err);
+  return launch_k(select_resident_kernel<false>, dim3(grid), dim3(kRThreads), smem, s, true, x, aligned, n, per, kt,
+                  k, cap, w, bins_out, probs_out, n_found, err);
 }
 
 cudaError_t launch_select_coop(void* work, int grid, const void* x, int is_f64, uint64_t n, int k, double threshold,
@@ -1428,13 +1455,13 @@ cudaError_t launch_select_coop(void* work, int grid, const void* x, int is_f64, 
   w.rank = reinterpret_cast<unsigned*>(p);
   p += sizeof(unsigned) * kMaxSort;
   w.tie_count = reinterpret_cast<unsigned*>(p);
-  int aligned = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
-  unsigned long long kt = threshold_key(is_f64, threshold);
-  void* args[] = {const_cast<void**>(&x), &aligned, &n, &kt, &k, const_cast<int*>(&cap), &w, &bins_out, &probs_out,
-                  &n_found, &err};
-  const void* fn = is_f64 ? reinterpret_cast<const void*>(select_coop_kernel<true>)
-                          : reinterpret_cast<const void*>(select_coop_kernel<false>);
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kCoopThreads), args, kCSmem, s);
+  const int aligned = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+  const unsigned long long kt = threshold_key(is_f64, threshold);
+  if (is_f64)
+    return launch_k(select_coop_kernel<true>, dim3(grid), dim3(kCoopThreads), size_t(kCSmem), s, true, x, aligned, n,
+                    kt, k, cap, w, bins_out, probs_out, n_found, err);
+  return launch_k(select_coop_kernel<false>, dim3(grid), dim3(kCoopThreads), size_t(kCSmem), s, true, x, aligned, n,
+                  kt, k, cap, w, bins_out, probs_out, n_found, err);
 }
 
 // ---- allocation-free variant -------------------------------------------------
@@ -1486,8 +1513,7 @@ cudaError_t select_configure() { return cudaSuccess; }
 cudaError_t launch_sum(const void* x, int is_f64, uint64_t n, double* partials, unsigned* counter, double* total,
                        cudaStream_t s) {
   const int g = stream_grid(n, 1024);
-  sum_kernel<<<g, kSelThreads, 0, s>>>(x, is_f64, n, partials, counter, total);
-  return cudaGetLastError();
+  return launch_k(sum_kernel, dim3(g), dim3(kSelThreads), 0, s, false, x, is_f64, n, partials, counter, total);
 }
 
 }  // namespace sqc

@@ -168,3 +168,44 @@ def random_variant_probs(c: CutCircuit, i: int, rng: np.random.Generator) -> np.
             src = np.where(d == 0, src + (3 << (2 * p)), src)  # I row := Z row
         out = out[src]
     return out
+
+
+def product_variant_probs(c: CutCircuit, i: int, dtype=np.float64) -> np.ndarray:
+    """What subcircuit_variant_probs returns, for a block with one-qubit
+    gates only: every wire then evolves on its own, so each variant's
+    output distribution is the product of its wires' distributions (exact,
+    no statevector of the whole block).  Used for wide single-qubit-gate
+    blocks (Bernstein-Vazirani in phase-oracle form), where a block of 18
+    wires has 16 variants of 2^18 outcomes."""
+    blk = c.blocks[i]
+    if any(g[0] == "cz" for g in blk.gates):
+        raise ValueError("product_variant_probs needs a block without two-qubit gates")
+    wires = list(blk.qubits)
+    edge_q = {eid: c.edges[eid][2] for eid in c.incident[i]}
+    ins, outs = c.in_edges[i], c.out_edges[i]
+    unitary = {q: np.eye(2, dtype=np.complex128) for q in wires}
+    for g in blk.gates:
+        u = rz(g[2]) if g[0] == "rz" else GATES[g[0]]
+        unitary[g[1]] = u @ unitary[g[1]]
+    ybits = list(c.data_qubits[i]) + [edge_q[e] for e in outs]     # y bit j -> wire
+    assert sorted(ybits) == sorted(wires)
+    inc = c.incident[i]
+    k = len(inc)
+    out = np.empty((4 ** k, 1 << len(ybits)), dtype=dtype)
+    in_wire = {edge_q[e]: e for e in ins}
+    out_wire = {edge_q[e]: e for e in outs}
+    for v in range(4 ** k):
+        digit = {eid: (v >> (2 * (k - 1 - pos))) & 3 for pos, eid in enumerate(inc)}
+        vec = np.ones(1)
+        for q in ybits:                                  # bit 0 first: it ends up least significant
+            st = INIT_STATES[digit[in_wire[q]]] if q in in_wire else np.array([1, 0], dtype=np.complex128)
+            st = unitary[q] @ st
+            if q in out_wire:
+                basis = digit[out_wire[q]]
+                if basis == 1:
+                    st = GATES["h"] @ st
+                elif basis == 2:
+                    st = GATES["h"] @ (GATES["sdg"] @ st)
+            vec = np.kron(np.abs(st) ** 2, vec)
+        out[v] = vec
+    return out

@@ -79,16 +79,18 @@ def test_batch_replays_from_a_cuda_graph(setup):
 
 
 def test_autotune_policies_give_the_same_bins(setup):
-    """sqc_batch_autotune times the three tile policies; every policy sums
-    each bin in the same order, so the bins equal the one-at-a-time runs bit
-    for bit whichever policy wins, and the chosen policy is then used."""
+    """sqc_batch_autotune times the two contraction orders x the three tile
+    policies; under the chosen order every policy sums each bin in the same
+    order, so the bins equal the one-at-a-time runs (planned under that
+    order) bit for bit, and match the oracle."""
     import torch
     ctx, b, qs = setup
     outs = [torch.full((1 << na,), -1.0, dtype=torch.float32, device="cuda") for _, na in qs]
     totals = torch.zeros(len(qs), dtype=torch.float64, device="cuda")
-    best, ms = ctx.batch_autotune([q for q, _ in qs], outs, totals, reps=3)
-    assert best in (0, 1, 2)
-    assert all(t > 0 for t in ms) and ms[best] == min(ms)
+    best, order, ms = ctx.batch_autotune([q for q, _ in qs], outs, totals, reps=3)
+    assert best in (0, 1, 2) and order in (0, 1)
+    flat = ms[0] + ms[1]
+    assert all(t > 0 for t in flat) and ms[order][best] == min(flat)
     after_tune = [o.clone() for o in outs]
     for o in outs:
         o.fill_(-1.0)
@@ -103,7 +105,46 @@ def test_autotune_policies_give_the_same_bins(setup):
         assert torch.equal(single, outs[j]), j
         assert torch.equal(single, after_tune[j]), j
         assert abs(tot1.item() - totals[j].item()) <= 1e-12 * max(1.0, abs(tot1.item())) + 1e-15
+        ref = _oracle(b, j)
+        err = np.abs(outs[j].double().cpu().numpy() - ref).max()
+        assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-15, (j, err)
     ctx.batch_release(bid)
+
+
+def test_query_autotune_keeps_the_faster_order():
+    """sqc_query_autotune times a query under the greedy and the
+    fewest-multiplications order and keeps the faster plan; both orders
+    reconstruct the oracle's bins, and the kept plan is the one later calls
+    run (same bins as the last timed run of that order)."""
+    import torch
+    from paper_2207_00933_gb300 import Context
+    b = W.batch_level(seed=5, n_circuits=3, n_queries=6, a_range=(8, 12), max_log_input=18, min_qubits=30)
+    with Context(0) as ctx:
+        cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in ps])
+                for c, ps in zip(b.circuits, b.probs)]
+        for j, (ci, roles) in enumerate(b.queries):
+            q, na = ctx.set_qubit_roles(cids[ci], roles)
+            res = {}
+            for order in (0, 1):
+                with Context(0, contraction_order=order) as c2:
+                    cc = b.circuits[ci]
+                    cid2 = c2.load_subcircuit_outputs(cc.n_qubits, *cc.graph_arrays(),
+                                                      [torch.from_numpy(p).cuda() for p in b.probs[ci]])
+                    q2, _ = c2.set_qubit_roles(cid2, roles)
+                    o2 = torch.empty(1 << na, dtype=torch.float32, device="cuda")
+                    c2.reconstruct(q2, o2)
+                    torch.cuda.synchronize()
+                    res[order] = o2.cpu()
+            out = torch.empty(1 << na, dtype=torch.float32, device="cuda")
+            best, ms = ctx.query_autotune(q, out, reps=3)
+            assert best in (0, 1) and all(t > 0 for t in ms)
+            ctx.reconstruct(q, out)
+            torch.cuda.synchronize()
+            assert torch.equal(out.cpu(), res[best]), j
+            ref = _oracle(b, j)
+            for order in (0, 1):
+                err = np.abs(res[order].double().numpy() - ref).max()
+                assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-15, (j, order, err)
 
 
 def test_autotune_rejects_bad_arguments(setup):

@@ -320,3 +320,17 @@ def test_single_launch_equals_per_stage_launches(wl, out):
     check(res[True][0], ref)
     assert abs(res[True][1] - res[False][1]) <= 1e-12
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fewest_multiplications_order_matches_oracle(seed):
+    """Plans under the fewest-multiplications contraction order (exact search
+    over subsets of subcircuits, Section 6.2 cost) reconstruct the oracle's
+    bins in both precisions, on random compute graphs with mixed roles."""
+    from paper_2207_00933_gb300 import Context
+    w = W.small_random(seed + 40, n_qubits=12, n_blocks=6, max_block=5, roles="mixed")
+    ref = oracle_run(w)
+    with Context(0, contraction_order=1) as c:
+        for prec in ("fp32", "split_bf16"):
+            P, _ = gpu_run(c, w, out_dtype="float64", precision=prec)
+            check(P, ref)

@@ -77,3 +77,42 @@ def test_streams_graphs_and_profiled_capture(setup, precision):
                 assert r["ms"]["final"] > 0, r
         del g
     ctx.profile_enable(0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+def test_programmatic_launch_changes_nothing(precision):
+    """With programmatic dependent launch every kernel starts while its
+    predecessor finishes and waits on the device for its results: the
+    bins, the probability sum and the selected bins are the same as with
+    plain launches, eagerly and replayed from a CUDA graph."""
+    import math
+    import torch
+    from paper_2207_00933_gb300 import Context
+    w = W.merged_30q()
+    c = w.circuit
+    res = {}
+    for pdl in (True, False):
+        with Context(0, pdl=pdl) as ctx:
+            probs = [torch.from_numpy(p).cuda() for p in w.probs]
+            cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), probs)
+            qid, na = ctx.set_qubit_roles(cid, w.roles)
+            out = torch.empty(1 << na, dtype=torch.float32, device="cuda")
+            tot = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+            def step():
+                ctx.update_subcircuit_outputs(cid, probs)
+                ctx.reconstruct(qid, out, precision, tot)
+                return ctx.top_bins(qid, out, 256, -math.inf)
+            b, v, n = step()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                b2, v2, n2 = step()
+            out.fill_(-1.0)
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(b, b2) and torch.equal(v, v2)
+            res[pdl] = (out.cpu().clone(), tot.item(), b2.cpu().clone())
+            ctx.unload(cid)
+    assert torch.equal(res[True][0], res[False][0])
+    assert res[True][1] == res[False][1]
+    assert torch.equal(res[True][2], res[False][2])

@@ -166,3 +166,23 @@ def test_errors(sqc, workloads):
     with pytest.raises(SQCError) as ei:
         sqc.plan_preview(c.n_qubits, arr[0], arr[1], arr[2], arr[3][::-1].copy() * 0, roles)   # not a permutation
     assert ei.value.status == 1
+
+
+def test_fewest_multiplications_order_is_never_costlier(sqc):
+    """The exact order (dynamic programming over subsets) needs at most the
+    greedy order's multiplications on every query, and strictly fewer on
+    some, with the same number of steps and the same result size."""
+    from synthetic import workloads as W
+    fewer = 0
+    for seed in range(30):
+        w = W.small_random(seed, n_qubits=14, n_blocks=7, max_block=5, roles="mixed")
+        c = w.circuit
+        g = sqc.plan_preview(c.n_qubits, *c.graph_arrays(), w.roles)
+        d = sqc.plan_preview(c.n_qubits, *c.graph_arrays(), w.roles, contraction_order=1)
+        assert d["flops"] <= g["flops"]
+        assert len(d["steps"]) == len(g["steps"])
+        gm, gn, _ = g["steps"][-1]
+        dm, dn, _ = d["steps"][-1]
+        assert gm * gn == dm * dn
+        fewer += d["flops"] < g["flops"]
+    assert fewer > 0
