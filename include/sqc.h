@@ -141,11 +141,12 @@ typedef struct {
    * that launch's work list (allocates).  Sliced queries and split-BF16
    * keep one launch per stage. */
   int32_t fused_query;
-  /* Programmatic dependent launch (1 = on, the default): each kernel of a
+  /* Programmatic dependent launch (1 = on, default 0): each kernel of a
    * call is launched while the previous kernel on the stream finishes and
-   * waits on the device (griddepcontrol.wait) for its results, which hides
-   * most of the launch gap between the short kernels of a reconstruction.
-   * Results do not change. */
+   * waits on the device (griddepcontrol.wait) for its results.  Results do
+   * not change; on the 2^20-bin step it measured no faster (each kernel's
+   * early-resident CTAs slowed the kernel before them by about what the
+   * overlap saved). */
   int32_t pdl;
   /* Pairwise contraction order of new query plans (Section 6.2 cost, the
    * multiplications of each step): SQC_ORDER_GREEDY (default) pairs the
@@ -177,8 +178,8 @@ typedef struct {
 } sqc_graph;
 
 /* Fill `cfg` with the defaults (no budget, 32 active qubits, FP64 chunking
- * from 12 edges, 256 terms per chunk, resident selection, programmatic
- * dependent launch; everything else off). */
+ * from 12 edges, 256 terms per chunk, resident selection; everything else
+ * off). */
 SQC_API void sqc_default_config(sqc_config* cfg);
 
 /* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
@@ -246,6 +247,30 @@ SQC_API sqc_status sqc_release_query(sqc_ctx* ctx, sqc_query_id q);
 SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id q, sqc_precision precision,
                                    void* out_bins, sqc_dtype out_dtype, uint64_t out_bytes,
                                    double* total_prob, void* stream);
+
+/* One recursion step on fresh subcircuit outputs (Algorithm 1 runs the
+ * subcircuits again for every recursion; states merging, Section 4, applied
+ * while attributing, Eq. 1): the bins of query q for the outputs `probs`
+ * (layout, dtype and probs_on_device as in sqc_load_subcircuit_outputs),
+ * with the attribution fused into the merge -- per subcircuit only the
+ * states the query keeps (zoomed qubits at their fixed values) are
+ * attributed, in shared-memory tiles that sum the merged qubits and write
+ * the merged tensors T_i directly; no A_i is written or read.  Then the
+ * contraction steps and outputs as sqc_reconstruct.  The circuit's
+ * resident tensors are NOT changed: other queries keep using the outputs
+ * of the last load or update.
+ * Applies when every subcircuit's roles follow the recursion's pattern
+ * (data qubits in data_qubit order: the zoomed ones first, then the active
+ * ones, then at most 8 merged ones -- what sqc_recursion_roles assigns),
+ * no subcircuit has more than 7 incoming cut edges, and the query is not
+ * sliced; otherwise it fails with SQC_EINVAL (then use
+ * sqc_update_subcircuit_outputs + sqc_reconstruct).  Host inputs are
+ * staged in the circuit's staging buffer and synchronised as in an update.
+ * Asynchronous on `stream` for device inputs. */
+SQC_API sqc_status sqc_reconstruct_outputs(sqc_ctx* ctx, sqc_query_id q, const void* const* probs, sqc_dtype dtype,
+                                           int probs_on_device, sqc_precision precision, void* out_bins,
+                                           sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob,
+                                           void* stream);
 
 /* Select bins (Algorithm 1: keep the largest bins): among the n values at
  * device pointer `probs` (dtype), those >= threshold, ordered by value

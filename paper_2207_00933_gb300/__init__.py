@@ -64,6 +64,8 @@ _SIGS = {
     "sqc_set_qubit_roles": (_c.c_int32, [_P, _c.c_int64, _P, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int32)]),
     "sqc_release_query": (_c.c_int32, [_P, _c.c_int64]),
     "sqc_reconstruct": (_c.c_int32, [_P, _c.c_int64, _c.c_int, _P, _c.c_int, _c.c_uint64, _P, _P]),
+    "sqc_reconstruct_outputs": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _P,
+                                             _c.c_int, _c.c_uint64, _P, _P]),
     "sqc_top_bins": (_c.c_int32, [_P, _c.c_int64, _P, _c.c_int, _c.c_uint64, _c.c_int32, _c.c_double, _P, _P,
                                   _P, _P]),
     "sqc_query_info": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_double),
@@ -161,7 +163,7 @@ class Context:
                  fp64_chunk_min_edges: int = 12, chunk_terms: int = 256, slice_edges: int = 0,
                  select_resident: bool = True, merge_pyramid: bool = False, slice_input_log2: int = 0,
                  slice_intermediate_log2: int = 0, tc_pairs: bool | None = None, wait_limit_ms: int = 0,
-                 fused_query: bool = False, pdl: bool = True, contraction_order: int = 0):
+                 fused_query: bool = False, pdl: bool = False, contraction_order: int = 0):
         self._lib = load_library()
         cfg = _Config()
         self._lib.sqc_default_config(ctypes.byref(cfg))
@@ -314,6 +316,20 @@ class Context:
         self._check(self._lib.sqc_reconstruct(self._h, query, PREC[precision], _ptr(out), _dtype_code(out),
                                               out.numel() * out.element_size(), _ptr(total_prob),
                                               _stream_handle(stream)))
+
+    def reconstruct_outputs(self, query: int, probs: list, out, precision: str = "fp32", total_prob=None,
+                            stream=None):
+        """Bins of `query` for fresh subcircuit outputs `probs` (one recursion
+        step, sqc_reconstruct_outputs): attribution fused into the merge; the
+        circuit's resident tensors are not changed."""
+        if not out.is_cuda:
+            raise ValueError("out must be a device tensor")
+        if total_prob is not None and (not total_prob.is_cuda or str(total_prob.dtype) != "torch.float64"):
+            raise ValueError("total_prob must be a device float64 tensor")
+        on_dev, ptrs, dt = self._prob_ptrs(probs)
+        self._check(self._lib.sqc_reconstruct_outputs(self._h, query, ptrs, dt, on_dev, PREC[precision], _ptr(out),
+                                                      _dtype_code(out), out.numel() * out.element_size(),
+                                                      _ptr(total_prob), _stream_handle(stream)))
 
     # -- batches ----------------------------------------------------------
     def batch_create(self, queries: list[int], outs: list, totals=None) -> int:

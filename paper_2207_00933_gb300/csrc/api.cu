@@ -1068,6 +1068,84 @@ sqc_status ensure_select_work(sqc_ctx* ctx, Query* q) {
   return SQC_OK;
 }
 
+// The fused attribution + merge of query q on fresh outputs src[i] (device
+// pointers, FP64 if in_f64): one descriptor per subcircuit, the tile shape
+// per subcircuit.  Returns false (with the reason) when some subcircuit's
+// roles do not follow the recursion's pattern (zoomed lowest, active next,
+// at most 8 merged highest), it has more than kMaxFusedIn incoming edges,
+// its tile does not fit shared memory, or the query is sliced.
+bool build_attr_merge(const Circuit& c, const Query& q, const Plan& P, const void* const* src, int in_f64,
+                      void* out_bins, int out_kind, double alpha, std::vector<AttrMergeLaunch>* launches,
+                      std::vector<int64_t>* blocks, std::vector<int>* smem, std::string* why) {
+  if (P.n_slices != 1) {
+    *why = "sliced queries take sqc_update_subcircuit_outputs + sqc_reconstruct";
+    return false;
+  }
+  launches->assign(1, AttrMergeLaunch{});
+  blocks->assign(1, 0);
+  smem->assign(1, 0);
+  for (int i = 0; i < c.nC; ++i) {
+    const int n = c.ndata[i], kin = int(c.ins[i].size()), kout = int(c.outs[i].size());
+    if (kin > kMaxFusedIn) {
+      *why = "a subcircuit has more than 7 incoming cut edges";
+      return false;
+    }
+    // roles in data-index order: zoomed, then active, then merged
+    int z = 0, a = 0, m = 0, t = 0;
+    uint32_t zval = 0;
+    for (; t < n && (q.roles[c.dq[i][t]] == SQC_ROLE_ZOOM0 || q.roles[c.dq[i][t]] == SQC_ROLE_ZOOM1); ++t, ++z)
+      if (q.roles[c.dq[i][t]] == SQC_ROLE_ZOOM1) zval |= 1u << t;
+    for (; t < n && q.roles[c.dq[i][t]] == SQC_ROLE_ACTIVE; ++t) ++a;
+    for (; t < n && q.roles[c.dq[i][t]] == SQC_ROLE_MERGED; ++t) ++m;
+    if (t != n || m > 8) {
+      *why = "the roles of a subcircuit do not follow the recursion's pattern (zoomed lowest data qubits, "
+             "then active, then at most 8 merged)";
+      return false;
+    }
+    const int64_t S = int64_t(1) << (2 * kin);
+    int L1 = std::min(a, 8 - m);
+    while (L1 > 0 && (S << (L1 + m)) > kAttrSmemMax / 4) --L1;
+    if ((S << (L1 + m)) > kAttrSmemMax / 4) {
+      *why = "a subcircuit's attribution tile does not fit shared memory";
+      return false;
+    }
+    // more, smaller tiles while a subcircuit has few (keep 8 consecutive reads)
+    while (L1 > 3 && ((int64_t(1) << (a - L1)) << (2 * kout)) < 64) --L1;
+    AttrMergeLaunch& L = launches->back();
+    AttrMergeDesc& d = L.d[L.n];
+    d.p = src[i];
+    d.in_f64 = in_f64;
+    d.n = n;
+    d.kin = kin;
+    d.kout = kout;
+    d.z = z;
+    d.a = a;
+    d.zval = zval;
+    d.L1 = L1;
+    d.L2 = m;
+    for (int u = 0; u < kin; ++u) d.inshift[u] = digit_shift(c, i, c.ins[i][u]);
+    for (int u = 0; u < kout; ++u) d.outshift[u] = digit_shift(c, i, c.outs[i][u]);
+    const MergeDesc& md = P.merge_host[i];
+    d.rowmap = md.rowmap;
+    d.colmap = md.colmap;
+    const bool direct = P.steps.empty();
+    d.dst = direct ? out_bins : P.tensors[i].buf;
+    d.kind = direct ? out_kind : P.tensors[i].kind;
+    d.plane_stride = direct ? 0 : P.tensors[i].plane_stride;
+    d.alpha = float(direct ? alpha : 1.0);
+    d.block_begin = blocks->back();
+    blocks->back() += (int64_t(1) << (a - L1)) << (2 * kout);
+    d.block_end = blocks->back();
+    smem->back() = std::max<int>(smem->back(), int(S << (L1 + m)) * 4);
+    if (++L.n == kAttrPerLaunch && i + 1 < c.nC) {
+      launches->push_back(AttrMergeLaunch{});
+      blocks->push_back(0);
+      smem->push_back(0);
+    }
+  }
+  return true;
+}
+
 // Plan query q again under contraction order `order` (SQC_ORDER_*): its
 // plans and single-launch work lists are freed, the FP32 plan is rebuilt
 // (the split-BF16 plan is rebuilt by the next split-BF16 reconstruct).
@@ -1331,7 +1409,7 @@ SQC_API void sqc_default_config(sqc_config* cfg) {
   cfg->chunk_terms = 256;
   cfg->select_resident = 1;
   cfg->fused_query = 0;
-  cfg->pdl = 1;
+  cfg->pdl = 0;
 }
 
 SQC_API const char* sqc_last_error(const sqc_ctx* ctx) {
@@ -1566,8 +1644,76 @@ SQC_API sqc_status sqc_query_tc_steps(const sqc_ctx* cctx, sqc_query_id qid, int
   return SQC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Fresh subcircuit outputs for a fused attribution + merge (device
+// pointers; FP64 if in_f64).
+struct FusedSrc {
+  const void* const* src;
+  int in_f64;
+};
+
+sqc_status reconstruct_core(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
+                            sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream,
+                            const FusedSrc* fused);
+}  // namespace
+
+extern "C" {
+
 SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
                                    sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream) {
+  return reconstruct_core(ctx, qid, precision, out_bins, out_dtype, out_bytes, total_prob, stream, nullptr);
+}
+
+SQC_API sqc_status sqc_reconstruct_outputs(sqc_ctx* ctx, sqc_query_id qid, const void* const* probs,
+                                           sqc_dtype dtype, int probs_on_device, sqc_precision precision,
+                                           void* out_bins, sqc_dtype out_dtype, uint64_t out_bytes,
+                                           double* total_prob, void* stream) {
+  if (!ctx || !probs || !out_bins) return fail(ctx, SQC_EINVAL, "null argument");
+  if (dtype != SQC_F32 && dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "dtype must be F32 or F64");
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  auto cit = ctx->circuits.find(it->second->circuit);
+  if (cit == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "circuit of the query was unloaded");
+  Circuit& c = *cit->second;
+  for (int i = 0; i < c.nC; ++i)
+    if (!probs[i]) return fail(ctx, SQC_EINVAL, "probs[i] is null");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // host inputs are staged back to back in the circuit's staging buffer
+  // (the same copies as an update)
+  const size_t esz = dtype == SQC_F64 ? 8 : 4;
+  std::vector<const void*> src(c.nC);
+  size_t off = 0;
+  for (int i = 0; i < c.nC; ++i) {
+    const size_t nbytes = size_t(c.V[i]) * (size_t(1) << c.w[i]) * esz;
+    if (probs_on_device) {
+      src[i] = probs[i];
+    } else {
+      if (off + nbytes > c.staging_bytes) return fail(ctx, SQC_ESHAPE, "staging buffer too small for these inputs");
+      char* dst = static_cast<char*>(c.staging) + off;
+      CK(cudaMemcpyAsync(dst, probs[i], nbytes, cudaMemcpyHostToDevice, s));
+      src[i] = dst;
+      off += (nbytes + 255) & ~size_t(255);
+    }
+  }
+  const FusedSrc fs{src.data(), dtype == SQC_F64};
+  sqc_status st = reconstruct_core(ctx, qid, precision, out_bins, out_dtype, out_bytes, total_prob, stream, &fs);
+  if (st == SQC_OK && !probs_on_device) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusNone) CK(cudaStreamSynchronize(s));
+  }
+  return st;
+}
+
+}  // extern "C"
+
+namespace {
+sqc_status reconstruct_core(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
+                            sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream,
+                            const FusedSrc* fused) {
   if (!ctx || !out_bins) return fail(ctx, SQC_EINVAL, "null argument");
   auto it = ctx->queries.find(qid);
   if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
@@ -1593,7 +1739,31 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
   const int out_kind = out_dtype == SQC_F64 ? OUT_F64 : OUT_F32;
   const double alpha = std::ldexp(1.0, -c.K);
 
-  if (precision == SQC_PREC_FP32 && ctx->cfg.fused_query && P.n_slices == 1 && !P.steps.empty()) {
+  // fresh outputs: attribution fused into the merge replaces the merge launch
+  std::vector<AttrMergeLaunch> am;
+  std::vector<int64_t> am_blocks;
+  std::vector<int> am_smem;
+  if (fused) {
+    std::string why;
+    if (!build_attr_merge(c, q, P, fused->src, fused->in_f64, out_bins, out_kind, alpha, &am, &am_blocks, &am_smem,
+                          &why))
+      return fail(ctx, SQC_EINVAL, "sqc_reconstruct_outputs: " + why);
+  }
+  auto run_merge = [&](const MergeDesc* descs, int nd) -> sqc_status {
+    StageScope scope(ctx, s, SQC_STAGE_MERGE);
+    if (fused) {
+      for (size_t j = 0; j < am.size(); ++j) {
+        CK(launch_attr_merge(am[j], am_blocks[j], am_smem[j], s));
+        ctx->launches += 1;
+      }
+      return SQC_OK;
+    }
+    CK(launch_merge_blocks(descs, nd, P.merge_blocks, s));
+    ctx->launches += 1;
+    return SQC_OK;
+  };
+
+  if (!fused && precision == SQC_PREC_FP32 && ctx->cfg.fused_query && P.n_slices == 1 && !P.steps.empty()) {
     // the merge and every contraction step in ONE persistent launch: merge
     // blocks and step tiles form a dependency-ordered work list, each item
     // waiting only for the tensors it reads (the batched level's kernel
@@ -1615,15 +1785,16 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
 
   if (P.steps.empty()) {
     // one subcircuit: the merge writes the bins directly
-    MergeDesc d = P.merge_host[0];
-    d.dst = out_bins;
-    d.kind = out_kind;
-    d.alpha = alpha;
-    CK(cudaMemcpyAsync(P.merge_dev, &d, sizeof(MergeDesc), cudaMemcpyHostToDevice, s));
+    if (!fused) {
+      MergeDesc d = P.merge_host[0];
+      d.dst = out_bins;
+      d.kind = out_kind;
+      d.alpha = alpha;
+      CK(cudaMemcpyAsync(P.merge_dev, &d, sizeof(MergeDesc), cudaMemcpyHostToDevice, s));
+    }
     {
-      StageScope scope(ctx, s, SQC_STAGE_MERGE);
-      CK(launch_merge_blocks(P.merge_dev, int(P.merge_host.size()), P.merge_blocks, s));
-      ctx->launches += 1;
+      const sqc_status ms = run_merge(P.merge_dev, int(P.merge_host.size()));
+      if (ms != SQC_OK) return ms;
     }
     if (total_prob) {
       StageScope scope(ctx, s, SQC_STAGE_FINAL);
@@ -1637,9 +1808,8 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
   const int nCm = int(P.merge_host.size());
   for (int64_t sg = 0; sg < P.n_slices; ++sg) {
     {
-      StageScope scope(ctx, s, SQC_STAGE_MERGE);
-      CK(launch_merge_blocks(P.merge_dev + sg * nCm, nCm, P.merge_blocks, s));
-      ctx->launches += 1;
+      const sqc_status ms = run_merge(P.merge_dev + sg * nCm, nCm);
+      if (ms != SQC_OK) return ms;
     }
     for (size_t si = 0; si < P.steps.size(); ++si) {
       const Step& st = P.steps[si];
@@ -1717,6 +1887,10 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
   }
   return SQC_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* probs, sqc_dtype dtype, uint64_t n,
                                 int32_t k, double threshold, uint64_t* bins_out, double* probs_out, int32_t* n_found,

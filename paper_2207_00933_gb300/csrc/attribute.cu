@@ -9,8 +9,7 @@
 // combines the prepared states s of the incoming cut wires.  The data index
 // is stored bit-reversed so that, under the recursion's roles (zoomed =
 // low data qubits, merged = high), a bin's states are one contiguous run.
-#include "internal.h"
-#include "launch.cuh"
+#include "common.cuh"
 
 namespace sqc {
 
@@ -141,8 +140,8 @@ __device__ __forceinline__ int v4_pos(int j) {
   else return j;
 }
 
-template <int NC, bool F64>
-__device__ __forceinline__ void fold_phase(const AttrDesc& d, const AttrTileCtx& t, float* val, int S, int lt,
+template <int NC, bool F64, class Desc>
+__device__ __forceinline__ void fold_phase(const Desc& d, const AttrTileCtx& t, float* val, int S, int lt,
                                            uint64_t x, int pos, uint64_t vbase, uint32_t signed_mask) {
   constexpr int kU = NC >= 8 ? 2 : (NC >= 4 ? 4 : 8);
   const int n = d.n;
@@ -494,7 +493,8 @@ __device__ __forceinline__ void v4_finish(const AttrDesc& d, const AttrTileCtx& 
   }
 }
 
-__device__ void fill_tile_ctx(const AttrDesc& d, AttrTileCtx& t) {
+template <class Desc>
+__device__ void fill_tile_ctx(const Desc& d, AttrTileCtx& t) {
   for (int i = threadIdx.x; i < 256 + 64; i += blockDim.x) {
     const int s = i < 256 ? i : ((i - 256) << 8);
     uint64_t v = 0;
@@ -588,6 +588,116 @@ __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kern
   }
 }
 
+// One tile of the fused attribution + merge (AttrMergeDesc): phases 1-2 as
+// attr_tile over the kept states x = zval | jl << z | xa << (z + L1) |
+// jh << (n - L2), then every (row, active value) sums its 2^L2 merged
+// slots in ascending order and writes T through the maps.
+template <bool F64>
+__device__ __forceinline__ void attr_merge_tile(const AttrMergeDesc& d, const AttrTileCtx& tc, int64_t t,
+                                                float* val) {
+  const uint64_t o = uint64_t(t) & ((uint64_t(1) << (2 * d.kout)) - 1);
+  const uint64_t xa = uint64_t(t) >> (2 * d.kout);
+  const int S = 1 << (2 * d.kin);
+  const int L1 = d.L1, L2 = d.L2, lt = L1 + L2;
+  const int TX = 1 << lt;
+  const int n = d.n, z = d.z;
+  const int step = int(blockDim.x) >> lt;
+  uint64_t vbase = 0;
+  uint32_t signed_mask = 0;
+  for (int u = 0; u < d.kout; ++u) {
+    const uint64_t dig = (o >> (2 * u)) & 3;
+    vbase |= dig << d.outshift[u];
+    if (dig) signed_mask |= 1u << u;
+  }
+  const int j = int(threadIdx.x) & (TX - 1);
+  const uint64_t jl = uint64_t(j & ((1 << L1) - 1)), jh = uint64_t(j >> L1);
+  const uint64_t x = uint64_t(d.zval) | (jl << z) | (xa << (z + L1)) | (jh << (n - L2));
+  const int pos = slot_pos(j, L1, L2);
+  if (F64 && d.in_f64) {
+    switch (d.kout) {
+      case 0: fold_phase<1, true>(d, tc, val, S, lt, x, pos, vbase, signed_mask); break;
+      case 1: fold_phase<2, true>(d, tc, val, S, lt, x, pos, vbase, signed_mask); break;
+      case 2: fold_phase<4, true>(d, tc, val, S, lt, x, pos, vbase, signed_mask); break;
+      default: fold_phase<8, true>(d, tc, val, S, lt, x, pos, vbase, signed_mask); break;
+    }
+  } else {
+    switch (d.kout) {
+      case 0: fold_phase<1, false>(d, tc, val, S, lt, x, pos, vbase, signed_mask); break;
+      case 1: fold_phase<2, false>(d, tc, val, S, lt, x, pos, vbase, signed_mask); break;
+      case 2: fold_phase<4, false>(d, tc, val, S, lt, x, pos, vbase, signed_mask); break;
+      default: fold_phase<8, false>(d, tc, val, S, lt, x, pos, vbase, signed_mask); break;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < d.kin; ++q) {
+    const int lowmask = (1 << (2 * q)) - 1;
+    const int st = TX << (2 * q);
+    for (int g = int(threadIdx.x) >> lt; g < (S >> 2); g += step) {
+      const int s0 = ((g & ~lowmask) << 2) | (g & lowmask);
+      float* a = val + s0 * TX + pos;
+      const float v0 = a[0], v1 = a[st], v2 = a[2 * st], v3 = a[3 * st];
+      const float sum = v0 + v1;
+      a[0] = sum;                 // I
+      a[st] = 2.f * v2 - sum;     // X
+      a[2 * st] = 2.f * v3 - sum; // Y
+      a[3 * st] = v0 - v1;        // Z
+    }
+    __syncthreads();
+  }
+  // merge: the merged slots of (row s, active value jl), in ascending order
+  const int na = 1 << L1, nm = 1 << L2;
+  for (int idx = int(threadIdx.x); idx < (S << L1); idx += int(blockDim.x)) {
+    const int s = idx >> L1, l = idx & (na - 1);
+    const float* row = val + s * TX;
+    float acc = 0.f;
+    for (int h = 0; h < nm; ++h) acc += row[slot_pos(l | (h << L1), L1, L2)];
+    const uint64_t e = in_digits(tc, s) | vbase;
+    const uint32_t b = rev_bits(uint32_t(uint64_t(l) | (xa << L1)), d.a);
+    store_out_f(d.dst, d.kind, d.plane_stride, d.rowmap[e] + d.colmap[b], acc * d.alpha);
+  }
+}
+
+// Persistent over the tiles of up to kAttrPerLaunch subcircuits (the same
+// walk as attr_fused_kernel).
+template <bool F64>
+__global__ void __launch_bounds__(256, 4) attr_merge_kernel(AttrMergeLaunch L, int64_t total_tiles) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
+  extern __shared__ float val[];
+  __shared__ AttrMergeDesc d;
+  __shared__ AttrTileCtx tc;
+  __shared__ int cur, changed;
+  if (threadIdx.x == 0) cur = -1;
+  __syncthreads();
+  for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int di = 0;
+#pragma unroll
+      for (int i = 1; i < kAttrPerLaunch; ++i)
+        if (i < L.n && L.d[i].block_begin <= tile) di = i;
+      changed = di != cur;
+      if (changed) {
+        switch (di) {
+#define SQC_ATTR_CASE(k) case k: d = L.d[k]; break;
+          SQC_ATTR_CASE(0) SQC_ATTR_CASE(1) SQC_ATTR_CASE(2) SQC_ATTR_CASE(3) SQC_ATTR_CASE(4) SQC_ATTR_CASE(5)
+          SQC_ATTR_CASE(6) SQC_ATTR_CASE(7) SQC_ATTR_CASE(8) SQC_ATTR_CASE(9) SQC_ATTR_CASE(10) SQC_ATTR_CASE(11)
+          SQC_ATTR_CASE(12) SQC_ATTR_CASE(13) SQC_ATTR_CASE(14) SQC_ATTR_CASE(15)
+#undef SQC_ATTR_CASE
+          default: break;
+        }
+        cur = di;
+      }
+    }
+    __syncthreads();
+    if (changed) {
+      fill_tile_ctx(d, tc);
+      __syncthreads();
+    }
+    attr_merge_tile<F64>(d, tc, tile - d.block_begin, val);
+    __syncthreads();
+  }
+}
+
 inline int grid_for(int64_t total) {
   int64_t g = (total + 255) / 256;
   const int64_t cap = 152 * 16;
@@ -632,6 +742,27 @@ cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_byte
   return launch_k(attr_fused_kernel<kAttrAll>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
 }
 
+cudaError_t launch_attr_merge(const AttrMergeLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s) {
+  if (L.n <= 0 || blocks <= 0) return cudaSuccess;
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    return n;
+  }();
+  bool any64 = false;
+  for (int i = 0; i < L.n; ++i) any64 = any64 || L.d[i].in_f64;
+  const void* fn = any64 ? reinterpret_cast<const void*>(attr_merge_kernel<true>)
+                         : reinterpret_cast<const void*>(attr_merge_kernel<false>);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem_bytes) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int64_t grid = blocks < int64_t(sms) * per_sm ? blocks : int64_t(sms) * per_sm;
+  if (any64)
+    return launch_k(attr_merge_kernel<true>, dim3(unsigned(grid)), dim3(256), size_t(smem_bytes), s, false, L, blocks);
+  return launch_k(attr_merge_kernel<false>, dim3(unsigned(grid)), dim3(256), size_t(smem_bytes), s, false, L, blocks);
+}
+
 cudaError_t attr_configure() {
   cudaError_t e = cudaFuncSetAttribute(attr_fused_kernel<kAttrAll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kAttrSmemMax);
@@ -639,6 +770,10 @@ cudaError_t attr_configure() {
     e = cudaFuncSetAttribute(attr_fused_kernel<kAttrVec>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(attr_fused_kernel<kAttrOne>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(attr_merge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(attr_merge_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
   return e;
 }
 

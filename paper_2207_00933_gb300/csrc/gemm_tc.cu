@@ -34,12 +34,12 @@
 //
 // Pairs (Cfg::PAIR): clusters of two CTAs compute one 256 x BN unit with
 // tcgen05.mma.cta_group::2 (M = 256): each CTA loads its own 128 rows of A
-// and its own half of the B rows into its own shared memory with plain TMA
-// loads; the MMA, issued by the even CTA, reads both halves and leaves each
-// CTA's 128 output rows in that CTA's TMEM.  The odd CTA's warp 1 forwards
-// the completion of its loads to the even CTA's stage barrier, its epilogue
-// warps return the accumulator to the even CTA's barrier, and the even
-// CTA's commits arrive on the barriers of both.
+// and its own half of the B rows into its own shared memory by TMA; the
+// MMA, issued by the even CTA, reads both halves and leaves each
+// CTA's 128 output rows in that CTA's TMEM.  The odd CTA's loads complete on
+// the even CTA's stage barrier (the cta_group::2 form of the TMA load), its
+// epilogue warps return the accumulator to the even CTA's barrier, and the
+// even CTA's commits arrive on the barriers of both.
 //
 // Tail: when the units leave a last wave at most half full, that wave runs
 // as half-width units (N = BN / 2), so that the busiest CTA does half a
@@ -182,6 +182,17 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];" ::"r"(smem_u32(dst)),
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// The same load by the odd CTA of a pair: the data lands in this CTA's
+// shared memory and the completion is counted on the even CTA's barrier
+// (`bar` is its shared::cluster address), whose MMAs read both CTAs' stages.
+__device__ __forceinline__ void tma_load_3d_peer(void* dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, %3, "
+      "%4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
 
@@ -434,8 +445,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   if (threadIdx.x == 0) {
     failed = 0;
     for (int s = 0; s < kStages; ++s) {
-      // pair leader: its producer's arrival and the partner's forwarded one
-      mbar_init(&full[s], PAIR && leader ? 2 : 1);
+      // pair: only the even CTA's stage barriers count (both CTAs' bytes)
+      mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -489,18 +500,24 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         uint8_t* st = smem + s * kStageBytes;
         uint8_t* stb = st + 3 * kTileA;
         if constexpr (PAIR) {
-          // this CTA's B rows: half of the unit's columns (full width: two
-          // boxes of BN / 4 rows; half width: one box)
-          mbar_expect_tx(&full[s], 3 * kTileA + 3 * (half ? kTileB / 2 : kTileB));
-          for (int p = 0; p < 3; ++p) tma_load_3d(st + p * kTileA, &tmA, kb * kBK, m0, p, &full[s]);
+          // this CTA's A rows and B rows (half of the unit's columns: two
+          // boxes of BN / 4 rows, one for a half-width unit); the even CTA's
+          // barrier expects both CTAs' bytes, the odd CTA's loads count on it
+          const uint32_t bytes = 3 * kTileA + 3 * (half ? kTileB / 2 : kTileB);
+          const uint32_t lead_full = cluster_addr(&full[s], 0);
+          auto load = [&](void* dst, const CUtensorMap* map, int x, int y, int z) {
+            if (leader) tma_load_3d(dst, map, x, y, z, &full[s]);
+            else tma_load_3d_peer(dst, map, x, y, z, lead_full);
+          };
+          if (leader) mbar_expect_tx(&full[s], 2 * bytes);
+          for (int p = 0; p < 3; ++p) load(st + p * kTileA, &tmA, kb * kBK, m0, p);
           if (half) {
-            for (int p = 0; p < 3; ++p)
-              tma_load_3d(stb + p * kTileB, &tmB, kb * kBK, n0 + int(rank) * (kBN / 4), p, &full[s]);
+            for (int p = 0; p < 3; ++p) load(stb + p * kTileB, &tmB, kb * kBK, n0 + int(rank) * (kBN / 4), p);
           } else {
             for (int p = 0; p < 3; ++p)
               for (int h = 0; h < 2; ++h)
-                tma_load_3d(stb + p * kTileB + h * (kTileB / 2), &tmB, kb * kBK,
-                            n0 + int(rank) * (kBN / 2) + h * (kBN / 4), p, &full[s]);
+                load(stb + p * kTileB + h * (kTileB / 2), &tmB, kb * kBK, n0 + int(rank) * (kBN / 2) + h * (kBN / 4),
+                     p);
           }
         } else {
           // the unit's B rows: two boxes of BN / 2 rows (half width: one)
@@ -513,11 +530,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         issued = it + 1;
       }
     }
-    // drain: every copy this CTA issued has landed, and (normal end) every
-    // commit that frees a stage has arrived, before the CTA exits
+    // drain: every copy this CTA issued has landed (a pair's odd CTA: the
+    // commit that frees a stage follows the even CTA's wait for both CTAs'
+    // bytes), and (normal end) every commit that frees a stage has arrived,
+    // before the CTA exits
     const int64_t j0 = issued > kStages ? issued - kStages : 0;
-    for (int64_t j = j0; j < issued; ++j)
-      if (!mbar_wait<PAIR>(&full[j % kStages], uint32_t((j / kStages) & 1), &failed, wlim, true)) set_failed();
+    if (leader)
+      for (int64_t j = j0; j < issued; ++j)
+        if (!mbar_wait<PAIR>(&full[j % kStages], uint32_t((j / kStages) & 1), &failed, wlim, true)) set_failed();
     if (!failed)
       for (int64_t j = j0; j < issued; ++j)
         if (!mbar_wait<PAIR>(&empty[j % kStages], uint32_t((j / kStages) & 1), &failed, wlim)) set_failed();
@@ -577,21 +597,6 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     if (ok && !failed)
       for (int64_t j = t > 2 ? t - 2 : 0; j < t; ++j)
         if (!mbar_wait<PAIR>(&acc_empty[j & 1], uint32_t((j >> 1) & 1), &failed, wlim)) set_failed();
-  } else if (PAIR && warp == 1 && lane == 0) {
-    // ---- pair, odd CTA: forward the completion of this CTA's loads to the
-    // even CTA's stage barrier (its MMAs read both CTAs' stages)
-    int64_t it = 0;
-    bool ok = true;
-    for (int64_t u = unit0; u < nunits && ok; u += unit_step)
-      for (int kb = 0; kb < nk; ++kb, ++it) {
-        const int s = int(it % kStages);
-        if (!mbar_wait<PAIR>(&full[s], uint32_t((it / kStages) & 1), &failed, wlim)) {
-          set_failed();
-          ok = false;
-          break;
-        }
-        mbar_arrive_cluster(cluster_addr(&full[s], 0));
-      }
   } else if (warp >= 2) {
     // ---- epilogue: warp w reads TMEM lanes 32*(w%4) .. +31 (its rows) and
     // half (w-2)/4 of the unit's columns, 32 columns per TMEM load; the next

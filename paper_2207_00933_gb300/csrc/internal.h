@@ -64,6 +64,39 @@ struct AttrLaunch {
 cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s);
 cudaError_t attr_configure();
 
+// Attribution fused into the merge (one recursion step on fresh outputs,
+// states merging of Section 4 applied while attributing, Eq. 1): for a
+// subcircuit whose roles follow the recursion's pattern -- the z lowest data
+// bits zoomed, the next a active, the m = n - z - a highest merged -- only
+// the 2^(a+m) kept states are attributed, in shared-memory tiles of 2^L1
+// consecutive active values x all 2^L2 = 2^m merged values, and every tile
+// writes the merged entries T[e][b] (b = the bit-reversed active bits,
+// merged bits summed) through the merge's layout maps.  The resident A_i is
+// not written.
+struct AttrMergeDesc {
+  const void* p;
+  int in_f64;
+  int n, kin, kout;
+  int z, a;                  // zoomed (lowest data bits) and active (next) bit counts
+  uint32_t zval;             // values of the zoomed bits (data-index order)
+  int L1, L2;                // tile: 2^L1 active values x 2^L2 merged values (L2 = m <= 8)
+  int inshift[kMaxFusedIn];
+  int outshift[16];
+  const uint64_t* rowmap;    // T's layout: the merge descriptor's maps
+  const uint64_t* colmap;
+  void* dst;                 // T_i, or the bins of a one-subcircuit query
+  int kind;
+  int64_t plane_stride;
+  float alpha;
+  int64_t block_begin;
+  int64_t block_end;
+};
+struct AttrMergeLaunch {
+  AttrMergeDesc d[kAttrPerLaunch];
+  int n;
+};
+cudaError_t launch_attr_merge(const AttrMergeLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s);
+
 // ---- merge / zoom (Section 4, Algorithm 2) ----------------------------------
 // T[e][b] = sum over data states with the zoom bits fixed and active bits
 // spelling b of A[e][state]; written to dst + rowmap[e] + colmap[b].

@@ -1418,7 +1418,11 @@ cudaError_t launch_select_resident(void* work, int grid, const void* x, int is_f
   uint64_t per = 0;
   const size_t smem = select_resident_smem(n, is_f64, grid, &per);
   if (!smem) return cudaErrorInvalidValue;
-  const int cap = (k > 512 ? k : 512) < kMaxSort - k ? (k > 512 ? k : 512) : kMaxSort - k;
+  // refinement stops once the k-th value's bucket holds at most cap values:
+  // the values above it (< k) and the bucket then fit the ranking's
+  // kMaxSort candidates, which costs less than another digit pass and its
+  // grid barrier
+  const int cap = kMaxSort - k;
   char* p = static_cast<char*>(work);
   ResWork w;
   w.ctl = reinterpret_cast<unsigned long long*>(p + kRCtlOffset);
