@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch the step eagerly instead of replaying a CUDA graph")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "split_bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the microbenchmarks, batch and serving runs")
-    ap.add_argument("--extra", choices=["tensor", "hbm", "batch", "serving", "grid40", "recursion"],
+    ap.add_argument("--extra", choices=["tensor", "hbm", "batch", "batch_tc", "serving", "grid40", "recursion"],
                     help="run only this microbenchmark and print its JSON line")
     return ap.parse_args()
 
@@ -518,6 +518,18 @@ def batch_bench(dev, reps: int = 10) -> dict:
         res["batch_vs_plain_fp32"] = res["plain_fp32"]["ms"] / res["batch_fp32"]["ms"]
         res["bins"] = bins
         ctx.batch_release(bid)
+        # the same level in split-BF16: steps the planner puts on the tensor
+        # cores run as tcgen05 launches between the persistent phases
+        bid = ctx.batch_create([q for q, _ in qs], outs, totals, precision="split_bf16")
+        graph = torch.cuda.CUDAGraph()
+        ctx.batch_run(bid)
+        with torch.cuda.graph(graph):
+            ctx.batch_run(bid)
+        ms = timed(graph.replay)
+        ctx.batch_status(bid)
+        res["batch_split_bf16"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "max_abs_err_vs_fp64": err(),
+                                   "tc_steps": sum(ctx.query_tc_steps(q)[0] for q, _ in qs)}
+        ctx.batch_release(bid)
     # one query at a time, each as ONE persistent launch (merge and every
     # step; the library's default for FP32 queries)
     with Context(dev.index or 0) as ctx:
@@ -561,6 +573,83 @@ def batch_bench(dev, reps: int = 10) -> dict:
                                                "ms_unflushed_by_order_and_policy": pol_ms,
                                                "max_abs_err_vs_fp64": err()}
         ctx.batch_release(bid)
+    return res
+
+
+def batch_tc_bench(dev, reps: int = 10) -> dict:
+    """A batched level whose last steps are contraction-bound (shared index
+    of 256 terms): 12 queries over three random-output chain circuits of
+    20-24 qubits (each circuit's full-active query and three zoomed ones),
+    FP64 outputs.  The batch in split-BF16 (those last steps on tcgen05,
+    between the persistent phases) against the batch in FP32 and against
+    the plain one-query-at-a-time forms; every form checked against the FP64
+    oracle on every query."""
+    import torch
+    import oracle as O
+    from paper_2207_00933_gb300 import Context
+    from synthetic import workloads as W
+    ws = [W.random_line_chain(17, [8, 11, 11], [2, 4], 1, [4, 7, 7]),
+          W.random_line_chain(18, [7, 10, 11], [2, 4], 1, [5, 6, 7]),
+          W.random_line_chain(20, [12, 12], [4], 1, [7, 7])]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": "12 queries over 3 chain circuits of 20-24 qubits; last steps 128 x 2048 x 256 and "
+                       "128 x 128 x 256; FP64 outputs"}
+    with Context(dev.index or 0, fused_query=False) as ctx:
+        ent = []
+        for w in ws:
+            c = w.circuit
+            cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).to(dev) for p in w.probs])
+            merged = [q for q in range(c.n_qubits) if w.roles[q] == O.MERGED][:2]
+            for v in range(4):
+                r = w.roles.copy()
+                for b, q in enumerate(merged):
+                    if v & (1 << b):
+                        r[q] = O.ZOOM1
+                q, na = ctx.set_qubit_roles(cid, r)
+                ent.append((q, na, O.reconstruct(O.Graph.from_arrays(c.n_qubits, *c.graph_arrays()),
+                                                 [p.astype(np.float64) for p in w.probs], r)))
+        outs = [torch.empty(1 << na, dtype=torch.float64, device=dev) for _, na, _ in ent]
+        totals = torch.zeros(len(ent), dtype=torch.float64, device=dev)
+        bins = sum(1 << na for _, na, _ in ent)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize(dev)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                tot += e0.elapsed_time(e1)
+            return tot / reps
+
+        def err():
+            return max(float(np.abs(o.cpu().numpy() - ref).max()) for o, (_, _, ref) in zip(outs, ent))
+
+        for prec in ("split_bf16", "fp32"):
+            bid = ctx.batch_create([q for q, _, _ in ent], outs, totals, precision=prec)
+            graph = torch.cuda.CUDAGraph()
+            ctx.batch_run(bid)
+            with torch.cuda.graph(graph):
+                ctx.batch_run(bid)
+            ms = timed(graph.replay)
+            ctx.batch_status(bid)
+            res[f"batch_{prec}"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "max_abs_err_vs_fp64": err()}
+            ctx.batch_release(bid)
+            del graph
+
+            def plain():
+                for (q, _, _), o in zip(ent, outs):
+                    ctx.reconstruct(q, o, prec)
+            ms = timed(plain)
+            res[f"plain_{prec}"] = {"ms": ms, "bins_per_s": bins / (ms * 1e-3), "max_abs_err_vs_fp64": err()}
+        res["tc_steps"] = sum(ctx.query_tc_steps(q)[0] for q, _, _ in ent)
+        res["bins"] = bins
     return res
 
 
@@ -690,7 +779,16 @@ def algorithmic_bytes(w, steps, out_elem_bytes):
     M, N, K = steps[-1] if steps else (1, 1, 1)
     final = 4 * (M * K + K * N) + out_elem_bytes * M * N
     select = (1 << w.n_active) * out_elem_bytes
-    return {"attribute": attr, "merge": merge, "contract": contract, "final": final, "select": select}
+    # attribution fused into the merge: the kept states' outputs read once
+    # (zoomed states skipped), the merged tensors written
+    fused = 0
+    for i, p in enumerate(w.probs):
+        dq = c.data_qubits[i]
+        z = sum(1 for q in dq if w.roles[q] in (2, 3))
+        a = sum(1 for q in dq if w.roles[q] == 0)
+        fused += (p.size >> z) * in_b + p.shape[0] * (1 << a) * 4
+    return {"attribute": attr, "merge": merge, "contract": contract, "final": final, "select": select,
+            "attribute_fused": fused}
 
 
 def main():
@@ -706,7 +804,7 @@ def main():
         __graft_entry__.build()
         dev = torch.device("cuda", 0)
         fn = {"tensor": tensor_microbench, "hbm": hbm_microbench, "batch": batch_bench, "serving": serving_bench,
-              "grid40": grid40_bench, "recursion": recursion_bench}
+              "grid40": grid40_bench, "recursion": recursion_bench, "batch_tc": batch_tc_bench}
         print(json.dumps({"extra": args.extra, **fn[args.extra](dev)}), flush=True)
         return
 
@@ -741,10 +839,27 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     prec = args.precision
+    from paper_2207_00933_gb300 import SQCError
 
-    def step():
+    # one recursion step on fresh subcircuit outputs: attribution fused into
+    # the merge (only the kept states), the contraction steps, the selection;
+    # queries whose roles do not allow the fused form update the resident
+    # tensors and reconstruct instead
+    try:
+        ctx.reconstruct_outputs(qid, probs_dev, out, prec, tot)
+        fused_step = True
+    except SQCError:
+        fused_step = False
+
+    def unfused_step():
         ctx.update_subcircuit_outputs(cid, probs_dev)
         ctx.reconstruct(qid, out, prec, tot)
+        ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
+
+    def step():
+        if not fused_step:
+            return unfused_step()
+        ctx.reconstruct_outputs(qid, probs_dev, out, prec, tot)
         ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
 
     for _ in range(max(3, args.warmup)):
@@ -800,6 +915,35 @@ def main():
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
 
+    # the other form of the step, timed the same way for comparison: the
+    # resident tensors updated by a separate attribution, then the merge
+    unfused_ms = None
+    if fused_step:
+        urun = None
+        if use_graph:
+            ug = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(ug):
+                unfused_step()
+            for _ in range(max(3, args.warmup)):
+                ug.replay()
+            urun = ug.replay
+        else:
+            urun = unfused_step
+        torch.cuda.synchronize(dev)
+        tt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            urun()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tt.append(e0.elapsed_time(e1))
+        unfused_ms = sum(tt) / len(tt)
+        # back to the fused form's outputs for the checks below
+        step()
+        torch.cuda.synchronize(dev)
+
     # stage breakdown (roofline, launch count): the same step with stage
     # events, run separately after the timed region
     stage_total = {k: 0.0 for k in ("attribute", "merge", "contract", "final", "select")}
@@ -828,9 +972,13 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * bins * args.steps / (total_ms * 1e-3)
 
-    # roofline of the dominant stage; FP32 queries run the merge and every
-    # contraction step as one launch, recorded as the contraction stage
+    # roofline of the dominant stage; with the fused step the merge stage is
+    # the attribution fused into the merge (reads the kept states' outputs,
+    # writes the merged tensors); single-launch FP32 queries record the
+    # merge and every contraction step as the contraction stage
     algo = algorithmic_bytes(w, steps_shape, out_b)
+    if fused_step:
+        algo["merge"] = algo["attribute_fused"]
     fused = prof["calls"]["merge"] == 0 and prof["calls"]["contract"] > 0
     if fused:
         algo["contract"] = algo["merge"] + algo["contract"] + algo["final"]
@@ -839,7 +987,7 @@ def main():
     dom = max(stage_ms, key=lambda k: prof["ms"][k])
     hbm, src = peaks()
     achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9
-    kernel_of = {"attribute": "attr_fused_kernel", "merge": "merge_kernel",
+    kernel_of = {"attribute": "attr_fused_kernel", "merge": "attr_merge_kernel" if fused_step else "merge_kernel",
                  "contract": "batch_kernel (merge and every step, one launch)" if fused else "gemm_simt_kernel",
                  "final": "gemm_simt_kernel (last step)",
                  "select": "select_resident_kernel" if (1 << na) <= 7_000_000 else "select_coop_kernel"}
@@ -859,8 +1007,11 @@ def main():
     h_tot = torch.empty(1, dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        ctx.update_subcircuit_outputs(cid, probs_host)            # H2D of this step's inputs inside
-        ctx.reconstruct(qid, out, prec, tot)
+        if fused_step:
+            ctx.reconstruct_outputs(qid, probs_host, out, prec, tot)    # H2D of this step's inputs inside
+        else:
+            ctx.update_subcircuit_outputs(cid, probs_host)              # H2D of this step's inputs inside
+            ctx.reconstruct(qid, out, prec, tot)
         ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
         h_bins.copy_(kb, non_blocking=True)
         h_probs.copy_(kp, non_blocking=True)
@@ -916,6 +1067,9 @@ def main():
                            "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
             "wall_s": wall,
             "gpu_launches": prof["launches"],
+            "step_form": "fresh outputs: attribution fused into the merge (sqc_reconstruct_outputs)" if fused_step
+                         else "update of the resident tensors, then reconstruct",
+            "unfused_ms_per_step": unfused_ms,
             "roofline": roofline,
             "clocks": clocks,
             "e2e": {"value": world * bins * args.steps / (e2e_total * 1e-3), "unit": UNIT,
@@ -927,6 +1081,7 @@ def main():
             tm = line["tensor_microbench"] = tensor_microbench(dev)
             hm = line["hbm_microbench"] = hbm_microbench(dev)
             line["batched_level"] = batch_bench(dev)
+            line["batched_tensor_core_level"] = batch_tc_bench(dev)
             line["serving"] = serving_bench(dev)
             g40 = line["grid40_K12_a22"] = grid40_bench(dev)
             rec = line["recursion_bv1000"] = recursion_bench(dev)

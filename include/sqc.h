@@ -282,28 +282,35 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id q, const void* probs,
                                 uint64_t n, int32_t k, double threshold, uint64_t* bins_out,
                                 double* probs_out, int32_t* n_found, void* stream);
 
-/* Batched recursion level (one persistent launch).
+/* Batched recursion level (one persistent launch per phase).
  *
  * A batch groups queries -- bins of possibly different loaded circuits,
- * with uneven active-qubit counts -- whose FP32 reconstructions run in ONE
- * persistent kernel launch: every query's merge blocks and contraction
+ * with uneven active-qubit counts -- whose reconstructions run in
+ * persistent kernel launches: every query's merge blocks and contraction
  * tiles form one dependency-ordered work list taken by persistent CTAs,
  * each item waiting (bounded) only for the tensors it reads.  The result of
  * query qs[j] goes to outs[j] (device, 2^{n_active} values of out_dtype) and
  * its FP64 probability sum to totals[j] (device array of n doubles, may be
- * NULL), exactly as sqc_reconstruct(..., SQC_PREC_FP32, ...) would write
- * them.  Every query needs at least two subcircuits.
- *   sqc_batch_create: plans the work list and allocates its device state
- *     (the output pointers are fixed here, so sqc_batch_run does no host
- *     work and can be replayed from a CUDA graph);
- *   sqc_batch_run: one kernel launch on `stream`;
+ * NULL), exactly as sqc_reconstruct(..., precision, ...) would write them.
+ * With SQC_PREC_SPLIT_BF16 the steps that each query's split-BF16 plan puts
+ * on the tensor cores (sqc_query_tc_steps) run as tcgen05 launches between
+ * phases -- phase j is one persistent launch of the merges and SIMT steps
+ * whose inputs are complete by then, followed by the tensor-core steps
+ * whose inputs it completes; the other steps run FP32 in the persistent
+ * launches (mixed precision per step).  With SQC_PREC_FP32 there is one
+ * phase and one launch.  Every query needs at least two subcircuits.
+ *   sqc_batch_create: plans the work lists and allocates their device
+ *     state (the output pointers are fixed here, so sqc_batch_run does no
+ *     host work and can be replayed from a CUDA graph);
+ *   sqc_batch_run: the launches on `stream`;
  *   sqc_batch_release: frees the batch (not the queries).
  * A query's workspace is shared by its batch and its single-query calls:
  * do not run both at once.  sqc_batch_status synchronises the device and
  * returns SQC_ETIMEOUT if a bounded wait of the batch ever gave up. */
 typedef int64_t sqc_batch_id;
 SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
-                                    sqc_dtype out_dtype, double* totals, sqc_batch_id* out_b);
+                                    sqc_dtype out_dtype, double* totals, sqc_precision precision,
+                                    sqc_batch_id* out_b);
 SQC_API sqc_status sqc_batch_run(sqc_ctx* ctx, sqc_batch_id b, void* stream);
 SQC_API sqc_status sqc_batch_status(sqc_ctx* ctx, sqc_batch_id b);
 SQC_API sqc_status sqc_batch_release(sqc_ctx* ctx, sqc_batch_id b);

@@ -75,7 +75,7 @@ _SIGS = {
     "sqc_query_tc_steps": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32)]),
     "sqc_top_bins_noalloc": (_c.c_int32, [_c.c_int, _P, _c.c_int, _c.c_uint64, _c.c_int32, _c.c_double, _P, _P,
                                           _P, _P]),
-    "sqc_batch_create": (_c.c_int32, [_P, _c.c_int32, _P, _P, _c.c_int, _P, _c.POINTER(_c.c_int64)]),
+    "sqc_batch_create": (_c.c_int32, [_P, _c.c_int32, _P, _P, _c.c_int, _P, _c.c_int, _c.POINTER(_c.c_int64)]),
     "sqc_batch_run": (_c.c_int32, [_P, _c.c_int64, _P]),
     "sqc_batch_status": (_c.c_int32, [_P, _c.c_int64]),
     "sqc_batch_release": (_c.c_int32, [_P, _c.c_int64]),
@@ -332,10 +332,12 @@ class Context:
                                                       _ptr(total_prob), _stream_handle(stream)))
 
     # -- batches ----------------------------------------------------------
-    def batch_create(self, queries: list[int], outs: list, totals=None) -> int:
-        """One persistent launch for many queries (sqc_batch_create): outs[j]
+    def batch_create(self, queries: list[int], outs: list, totals=None, precision: str = "fp32") -> int:
+        """Persistent launches for many queries (sqc_batch_create): outs[j]
         is the device tensor receiving query j's bins (all float32 or all
-        float64); totals: optional device float64 tensor [len(queries)]."""
+        float64); totals: optional device float64 tensor [len(queries)];
+        precision "split_bf16" runs each query's tensor-core steps on
+        tcgen05 between the phases."""
         n = len(queries)
         qa = (ctypes.c_int64 * n)(*queries)
         oa = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
@@ -343,7 +345,8 @@ class Context:
         if any(_dtype_code(o) != dt for o in outs):
             raise ValueError("batch outputs must share one dtype")
         b = ctypes.c_int64()
-        self._check(self._lib.sqc_batch_create(self._h, n, qa, oa, dt, _ptr(totals), ctypes.byref(b)))
+        self._check(self._lib.sqc_batch_create(self._h, n, qa, oa, dt, _ptr(totals), PREC[precision],
+                                               ctypes.byref(b)))
         return b.value
 
     def batch_run(self, batch: int, stream=None):

@@ -117,10 +117,16 @@ struct Plan {
 struct Batch {
   void* work = nullptr;
   size_t work_bytes = 0;
-  BatchLaunch L{};
+  BatchLaunch L{};                   // phase 0 (the only phase of an FP32 batch)
   int grid = 0;
   std::vector<sqc_query_id> queries;
   std::vector<unsigned> expected;    // host copy of the completion targets
+  // split-BF16: the persistent launch of every phase, then that phase's
+  // tensor-core steps
+  std::vector<BatchLaunch> phases;
+  std::vector<int> phase_grid;
+  std::vector<std::vector<GemmTcArgs>> tc;
+  int n_tc = 0;
 };
 
 struct Query {
@@ -913,10 +919,18 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
     st.Kd = int64_t(1) << sh.size();
     st.M = int64_t(1) << fx.size();
     st.N = int64_t(1) << fy.size();
-    // tensor cores for the big steps: M, N >= 128 (one UMMA tile); the
-    // kernel sums a long shared index in FP32 passes added in FP64 and adds
-    // later slices into the output itself
-    st.tc = tc_ok && st.M >= gemm_tc_min_rows() && st.N >= gemm_tc_min_rows();
+    // tensor cores for the big steps: M, N >= 128 (one UMMA tile) and
+    // enough work to amortise a tensor-core launch -- at least 2^21 outputs,
+    // or a shared index of 256 or more (contraction-bound) with at least 2^14
+    // outputs.  Smaller split-BF16 steps run FP32 on the SIMT cores (as
+    // accurate): measured, a 2^20-output step with a 16-term shared index
+    // took 12 us in FP32 against 17 us on tcgen05, and 2^18-output
+    // intermediates about 3x longer on tcgen05.  The kernel sums a long
+    // shared index in FP32 passes added in FP64 and adds later slices into
+    // the output itself.
+    const int64_t outs_mn = st.M * st.N;
+    st.tc = tc_ok && st.M >= gemm_tc_min_rows() && st.N >= gemm_tc_min_rows() &&
+            (outs_mn >= (int64_t(1) << 21) || (st.Kd >= 256 && outs_mn >= (int64_t(1) << 14)));
     st.Kp = st.tc ? std::max<int64_t>(st.Kd, gemm_tc_k_align()) : st.Kd;
     std::vector<int> lay = sh;
     for (int p = ilog2(st.Kd); p < ilog2(st.Kp); ++p) lay.push_back(kPad);
@@ -1163,34 +1177,52 @@ sqc_status replan(sqc_ctx* ctx, Query& q, int order) {
   return build_plan(ctx, *cit->second, &q, false, &q.plans[SQC_PREC_FP32]);
 }
 
-// Work list of one persistent launch over the FP32 plans of n queries
+// Work lists of the persistent launches over the plans of n queries
 // (shared by sqc_batch_create and the single-query launch of
 // sqc_reconstruct).  solo: one query whose output and probability sum are
 // named per launch (BatchLaunch::out / total) instead of being baked in.
+// A split-BF16 plan's tensor-core steps run as their own launches between
+// phases: phase j is one persistent batch launch (merges in phase 0, and
+// every SIMT step whose inputs are complete by then, waiting on the
+// in-launch completion counters of the tensors it reads) followed by the
+// tensor-core steps whose inputs are complete after it.
 sqc_status build_batch(sqc_ctx* ctx, int32_t n, Query* const* qv, void* const* outs, int out_kind, double* totals,
-                       bool solo, std::unique_ptr<Batch>* out_b) {
+                       bool solo, std::unique_ptr<Batch>* out_b, int precision = SQC_PREC_FP32) {
   std::vector<MergeDesc> mdescs;
   std::vector<BatchStep> steps;
-  std::vector<unsigned> expected;
-  struct Pending { BatchItem it; int level; };
+  std::vector<unsigned> expected;            // per tensor slot (all phases)
+  std::vector<int> slot_phase;               // the batch phase that produces each slot
+  struct Pending { BatchItem it; int level; int phase; };
   std::vector<Pending> items;
-  std::vector<int64_t> part_off;     // per batch step with a probability sum: offset into partials
+  std::vector<int64_t> part_off;             // per batch step with a probability sum: offset into partials
   int64_t n_parts = 0;
+  struct TcPending { GemmTcArgs a; int phase; bool sums; int query; };
+  std::vector<TcPending> tcs;
+  int n_phases = 1;
   for (int j = 0; j < n; ++j) {
     Query& q = *qv[j];
     auto cit = ctx->circuits.find(q.circuit);
     if (cit == ctx->circuits.end()) return fail(ctx, SQC_ENOTFOUND, "batch: circuit of a query was unloaded");
     const Circuit& c = *cit->second;
-    Plan& P = q.plans[SQC_PREC_FP32];
+    Plan& P = q.plans[precision];
+    if (!P.built) {
+      sqc_status st = build_plan(ctx, c, &q, precision == SQC_PREC_SPLIT_BF16, &P);
+      if (st != SQC_OK) return st;
+    }
     if (P.steps.empty()) return fail(ctx, SQC_EINVAL, "batch: every query needs at least two subcircuits");
     if (P.n_slices > 1) return fail(ctx, SQC_EINVAL, "batch: sliced queries (cfg.slice_edges > 0) run one at a time");
     if (!solo && !outs[j]) return fail(ctx, SQC_EINVAL, "batch: null output");
-    // tensor slots of this query
+    // tensor slots of this query; the phase after which a tensor is
+    // complete for a SIMT reader (same phase: wait on its counter) and for
+    // a tensor-core reader
     std::vector<int> slot(P.tensors.size(), -1), level(P.tensors.size(), 0);
+    std::vector<int> av_simt(P.tensors.size(), 0), av_tc(P.tensors.size(), 0);
+    std::vector<char> by_tc(P.tensors.size(), 0);
     for (size_t t = 0; t < P.tensors.size(); ++t) {
       if (int(t) == P.final_tensor) continue;
       slot[t] = int(expected.size());
       expected.push_back(0);
+      slot_phase.push_back(0);
     }
     for (int i = 0; i < c.nC; ++i) {
       const int di = int(mdescs.size());
@@ -1198,13 +1230,48 @@ sqc_status build_batch(sqc_ctx* ctx, int32_t n, Query* const* qv, void* const* o
       const MergeDesc& d = P.merge_host[i];
       const int64_t per = 256 / d.lanes;
       const int64_t nblk = ((d.rows << d.a) + per - 1) / per;
-      for (int64_t b = 0; b < nblk; ++b) items.push_back({{kItemMerge, di, b, -1, -1, slot[i]}, 0});
+      for (int64_t b = 0; b < nblk; ++b) items.push_back({{kItemMerge, di, b, -1, -1, slot[i]}, 0, 0});
       expected[slot[i]] = unsigned(nblk);
     }
     const double alpha = std::ldexp(1.0, -c.K);
     for (size_t si = 0; si < P.steps.size(); ++si) {
       const Step& st = P.steps[si];
       const bool last = si + 1 == P.steps.size();
+      const Tensor& Z = P.tensors[st.z];
+      void* C = last ? (solo ? nullptr : outs[j]) : Z.buf;
+      const int kind = last ? out_kind : Z.kind;
+      const int64_t pstride = last ? 0 : Z.plane_stride;
+      if (st.tc) {
+        const int ph = std::max(av_tc[st.x], av_tc[st.y]);
+        GemmTcArgs a{};
+        a.A = P.tensors[st.x].buf;
+        a.B = P.tensors[st.y].buf;
+        a.M = st.M; a.N = st.N; a.K = st.Kd;
+        a.Mp = st.M; a.Np = st.N; a.Kp = st.Kp;
+        a.rowmap = st.rowmap;
+        a.colmap = st.colmap;
+        a.C = C;
+        a.kind = kind;
+        a.plane_stride = pstride;
+        a.alpha = last ? alpha : 1.0;
+        a.chunk = (last && out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges &&
+                   st.Kd > ctx->cfg.chunk_terms) ? ctx->cfg.chunk_terms : 0;
+        a.err = P.err;
+        a.contig16 = st.contig16;
+        a.pairs = ctx->cfg.tc_pairs;
+        a.wait_ns = wait_ns(ctx);
+        if (solo && last) return fail(ctx, SQC_EINVAL, "batch: a single-query launch runs FP32 steps only");
+        tcs.push_back({a, ph, last && totals != nullptr, j});
+        av_simt[st.z] = av_tc[st.z] = ph + 1;
+        by_tc[st.z] = 1;
+        n_phases = std::max(n_phases, ph + 2);
+        if (!last) {
+          slot_phase[slot[st.z]] = -1;             // written by a tensor-core launch, not counted
+          expected[slot[st.z]] = 0;
+        }
+        continue;
+      }
+      const int ph = std::max(av_simt[st.x], av_simt[st.y]);
       BatchStep bs{};
       GemmArgs& a = bs.a;
       a.A = static_cast<const float*>(P.tensors[st.x].buf);
@@ -1215,8 +1282,9 @@ sqc_status build_batch(sqc_ctx* ctx, int32_t n, Query* const* qv, void* const* o
       a.rowmap = st.rowmap;
       a.colmap = st.colmap;
       a.vec4 = st.vec4;
-      a.C = last ? (solo ? nullptr : outs[j]) : P.tensors[st.z].buf;
-      a.kind = last ? out_kind : OUT_F32;
+      a.C = C;
+      a.kind = kind;
+      a.plane_stride = pstride;
       a.alpha = last ? alpha : 1.0;
       a.chunk = (last && out_kind == OUT_F64 && c.K >= ctx->cfg.fp64_chunk_min_edges)
                     ? std::min<int64_t>(ctx->cfg.chunk_terms, st.Kd < 16 ? 16 : st.Kd)
@@ -1236,25 +1304,40 @@ sqc_status build_batch(sqc_ctx* ctx, int32_t n, Query* const* qv, void* const* o
       level[st.z] = lvl;
       const int si_b = int(steps.size());
       steps.push_back(bs);
+      // inputs made earlier in this phase by batch items are waited on; a
+      // tensor-core result or an earlier phase's tensor is complete already
+      auto dep = [&](int t) { return (!by_tc[t] && av_simt[t] == ph) ? slot[t] : -1; };
       for (int64_t t = 0; t < bs.ntiles; ++t)
-        items.push_back({{kItemGemm, si_b, t, slot[st.x], slot[st.y], last ? -1 : slot[st.z]}, lvl});
-      if (!last) expected[slot[st.z]] = unsigned(bs.ntiles);
+        items.push_back({{kItemGemm, si_b, t, dep(st.x), dep(st.y), last ? -1 : slot[st.z]}, lvl, ph});
+      if (!last) {
+        expected[slot[st.z]] = unsigned(bs.ntiles);
+        slot_phase[slot[st.z]] = ph;
+      }
+      av_simt[st.z] = ph;
+      av_tc[st.z] = ph;
     }
   }
-  // dependency order: merges, then steps level by level (stable)
-  std::stable_sort(items.begin(), items.end(), [](const Pending& a, const Pending& b) { return a.level < b.level; });
+  // per phase, dependency order: merges, then steps level by level (stable)
+  std::stable_sort(items.begin(), items.end(), [](const Pending& a, const Pending& b) {
+    return a.phase != b.phase ? a.phase < b.phase : a.level < b.level;
+  });
+  std::vector<int64_t> ph_begin(n_phases + 1, 0);
+  for (const Pending& p : items) ph_begin[p.phase + 1] += 1;
+  for (int j = 0; j < n_phases; ++j) ph_begin[j + 1] += ph_begin[j];
 
   auto B = std::make_unique<Batch>();
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t off = 0;
-  const size_t o_items = off; off = align(off + sizeof(BatchItem) * items.size());
+  const size_t o_items = off; off = align(off + sizeof(BatchItem) * std::max<size_t>(items.size(), 1));
   const size_t o_md = off; off = align(off + sizeof(MergeDesc) * mdescs.size());
-  const size_t o_st = off; off = align(off + sizeof(BatchStep) * steps.size());
+  const size_t o_st = off; off = align(off + sizeof(BatchStep) * std::max<size_t>(steps.size(), 1));
   const size_t o_cnt = off; off = align(off + sizeof(unsigned) * expected.size());
   const size_t o_exp = off; off = align(off + sizeof(unsigned) * expected.size());
   const size_t o_part = off; off = align(off + sizeof(double) * size_t(std::max<int64_t>(n_parts, 1)));
-  const size_t o_pc = off; off = align(off + sizeof(unsigned) * steps.size());
-  const size_t o_ctl = off; off = align(off + 64);
+  const size_t o_pc = off; off = align(off + sizeof(unsigned) * std::max<size_t>(steps.size(), 1));
+  const size_t o_ctl = off; off = align(off + 64 * size_t(n_phases));
+  const size_t o_tcp = off; off = align(off + sizeof(double) * 256 * tcs.size());   // tensor-core step partials
+  const size_t o_tcc = off; off = align(off + 64 * tcs.size());                      // and counters
   B->work_bytes = off;
   sqc_status st = dev_alloc(ctx, &B->work, off);
   if (st != SQC_OK) return st;
@@ -1270,33 +1353,53 @@ sqc_status build_batch(sqc_ctx* ctx, int32_t n, Query* const* qv, void* const* o
   }
   std::vector<BatchItem> flat(items.size());
   for (size_t k = 0; k < items.size(); ++k) flat[k] = items[k].it;
-  cudaError_t e = upload(ctx, base + o_items, flat.data(), sizeof(BatchItem) * flat.size());
+  cudaError_t e = flat.empty() ? cudaSuccess : upload(ctx, base + o_items, flat.data(), sizeof(BatchItem) * flat.size());
   if (e == cudaSuccess && !mdescs.empty()) e = upload(ctx, base + o_md, mdescs.data(), sizeof(MergeDesc) * mdescs.size());
-  if (e == cudaSuccess) e = upload(ctx, base + o_st, steps.data(), sizeof(BatchStep) * steps.size());
+  if (e == cudaSuccess && !steps.empty()) e = upload(ctx, base + o_st, steps.data(), sizeof(BatchStep) * steps.size());
   if (e == cudaSuccess) e = upload(ctx, base + o_exp, expected.data(), sizeof(unsigned) * expected.size());
   if (e == cudaSuccess) e = zero(ctx, base + o_cnt, sizeof(unsigned) * expected.size());
-  if (e == cudaSuccess) e = zero(ctx, base + o_pc, sizeof(unsigned) * steps.size());
-  if (e == cudaSuccess) e = zero(ctx, base + o_ctl, 64);
+  if (e == cudaSuccess && !steps.empty()) e = zero(ctx, base + o_pc, sizeof(unsigned) * steps.size());
+  if (e == cudaSuccess) e = zero(ctx, base + o_ctl, 64 * size_t(n_phases));
+  if (e == cudaSuccess && !tcs.empty()) e = zero(ctx, base + o_tcc, 64 * tcs.size());
   if (e != cudaSuccess) {
     dev_free(ctx, B->work, B->work_bytes);
     return cuda_fail(ctx, e, "batch upload");
   }
-  BatchLaunch& L = B->L;
-  L.items = reinterpret_cast<const BatchItem*>(base + o_items);
-  L.n_items = int64_t(flat.size());
-  L.mdescs = reinterpret_cast<const MergeDesc*>(base + o_md);
-  L.steps = reinterpret_cast<const BatchStep*>(base + o_st);
-  L.counts = reinterpret_cast<unsigned*>(base + o_cnt);
-  L.expected = reinterpret_cast<const unsigned*>(base + o_exp);
-  L.n_slots = int64_t(expected.size());
-  L.head = reinterpret_cast<unsigned long long*>(base + o_ctl);
-  L.done = reinterpret_cast<unsigned*>(base + o_ctl + 8);
-  L.abort = reinterpret_cast<int*>(base + o_ctl + 16);
-  L.err = reinterpret_cast<int*>(base + o_ctl + 20);
-  L.wait_ns = wait_ns(ctx);
   int sms = 152, per = 2;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-  B->grid = int(std::min<int64_t>(int64_t(sms) * per, L.n_items));
+  B->phases.assign(n_phases, BatchLaunch{});
+  B->phase_grid.assign(n_phases, 0);
+  B->tc.assign(n_phases, {});
+  for (int j = 0; j < n_phases; ++j) {
+    BatchLaunch& L = B->phases[j];
+    L.items = reinterpret_cast<const BatchItem*>(base + o_items) + ph_begin[j];
+    L.n_items = ph_begin[j + 1] - ph_begin[j];
+    L.mdescs = reinterpret_cast<const MergeDesc*>(base + o_md);
+    L.steps = reinterpret_cast<const BatchStep*>(base + o_st);
+    L.counts = reinterpret_cast<unsigned*>(base + o_cnt);
+    L.expected = reinterpret_cast<const unsigned*>(base + o_exp);
+    L.n_slots = int64_t(expected.size());
+    char* ctl = base + o_ctl + 64 * size_t(j);
+    L.head = reinterpret_cast<unsigned long long*>(ctl);
+    L.done = reinterpret_cast<unsigned*>(ctl + 8);
+    L.abort = reinterpret_cast<int*>(ctl + 16);
+    L.err = reinterpret_cast<int*>(ctl + 20);
+    L.wait_ns = wait_ns(ctx);
+    B->phase_grid[j] = int(std::min<int64_t>(int64_t(sms) * per, std::max<int64_t>(L.n_items, 1)));
+  }
+  for (size_t k = 0; k < tcs.size(); ++k) {
+    GemmTcArgs a = tcs[k].a;
+    if (tcs[k].sums) {
+      a.partials = reinterpret_cast<double*>(base + o_tcp) + 256 * k;
+      a.counter = reinterpret_cast<unsigned*>(base + o_tcc + 64 * k);
+      a.total = totals + tcs[k].query;
+    }
+    B->tc[tcs[k].phase].push_back(a);
+    B->n_tc += 1;
+  }
+  // the last phase's counters re-arm every slot (they all start at zero)
+  B->L = B->phases[0];
+  B->grid = B->phase_grid[0];
   B->expected = std::move(expected);
   *out_b = std::move(B);
   return SQC_OK;
@@ -1926,9 +2029,12 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* prob
 }
 
 SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
-                                    sqc_dtype out_dtype, double* totals, sqc_batch_id* out_b) {
+                                    sqc_dtype out_dtype, double* totals, sqc_precision precision,
+                                    sqc_batch_id* out_b) {
   if (!ctx || !qs || !outs || !out_b || n < 1) return fail(ctx, SQC_EINVAL, "batch: null argument or n < 1");
   if (out_dtype != SQC_F32 && out_dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "out_dtype must be F32 or F64");
+  if (precision != SQC_PREC_FP32 && precision != SQC_PREC_SPLIT_BF16)
+    return fail(ctx, SQC_EINVAL, "precision must be SQC_PREC_FP32 or SQC_PREC_SPLIT_BF16");
   DeviceGuard g(ctx->device);
   std::vector<Query*> qv(n);
   for (int j = 0; j < n; ++j) {
@@ -1937,7 +2043,8 @@ SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id*
     qv[j] = it->second.get();
   }
   std::unique_ptr<Batch> B;
-  sqc_status st = build_batch(ctx, n, qv.data(), outs, out_dtype == SQC_F64 ? OUT_F64 : OUT_F32, totals, false, &B);
+  sqc_status st =
+      build_batch(ctx, n, qv.data(), outs, out_dtype == SQC_F64 ? OUT_F64 : OUT_F32, totals, false, &B, precision);
   if (st != SQC_OK) return st;
   B->queries.assign(qs, qs + n);
   const int64_t id = ctx->next_id++;
@@ -1954,8 +2061,17 @@ SQC_API sqc_status sqc_batch_run(sqc_ctx* ctx, sqc_batch_id b, void* stream) {
   PdlScope pdl(ctx->cfg.pdl != 0);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   StageScope scope(ctx, s, SQC_STAGE_CONTRACT);
-  CK(launch_batch(it->second->L, it->second->grid, s));
-  ctx->launches += 1;
+  const Batch& B = *it->second;
+  for (size_t j = 0; j < B.phases.size(); ++j) {
+    if (B.phases[j].n_items > 0) {
+      CK(launch_batch(B.phases[j], B.phase_grid[j], s));
+      ctx->launches += 1;
+    }
+    for (const GemmTcArgs& a : B.tc[j]) {
+      CK(launch_gemm_tc(a, s));
+      ctx->launches += 1;
+    }
+  }
   return SQC_OK;
 }
 
@@ -1965,13 +2081,23 @@ SQC_API sqc_status sqc_batch_status(sqc_ctx* ctx, sqc_batch_id b) {
   if (it == ctx->batches.end()) return fail(ctx, SQC_ENOTFOUND, "unknown batch");
   DeviceGuard g(ctx->device);
   CK(cudaDeviceSynchronize());
-  int err = 0;
-  CK(cudaMemcpy(&err, it->second->L.err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (err) {
-    const int zero = 0;
-    CK(cudaMemcpy(it->second->L.err, &zero, sizeof(int), cudaMemcpyHostToDevice));
-    return fail(ctx, SQC_ETIMEOUT, "batch: a bounded device wait gave up");
+  // every phase's flag and every tensor-core step's flag (cleared once read)
+  std::vector<int*> flags;
+  for (const BatchLaunch& L : it->second->phases) flags.push_back(L.err);
+  for (const auto& ph : it->second->tc)
+    for (const GemmTcArgs& a : ph)
+      if (a.err && std::find(flags.begin(), flags.end(), a.err) == flags.end()) flags.push_back(a.err);
+  bool any = false;
+  for (int* f : flags) {
+    int err = 0;
+    CK(cudaMemcpy(&err, f, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+      any = true;
+      const int zero = 0;
+      CK(cudaMemcpy(f, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    }
   }
+  if (any) return fail(ctx, SQC_ETIMEOUT, "batch: a bounded device wait gave up");
   return SQC_OK;
 }
 
@@ -2023,7 +2149,7 @@ sqc_status batch_autotune_tiles(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs,
   for (int p = 0; p < kBatchPolicies && st == SQC_OK; ++p) {
     ctx->batch_policy = p;
     sqc_batch_id b = 0;
-    st = sqc_batch_create(ctx, n, qs, outs, out_dtype, totals, &b);
+    st = sqc_batch_create(ctx, n, qs, outs, out_dtype, totals, SQC_PREC_FP32, &b);
     if (st != SQC_OK) break;
     st = sqc_batch_run(ctx, b, nullptr);                       // warm-up
     cudaError_t e = cudaSuccess;

@@ -220,7 +220,7 @@ bool sqc_server::dispatch(Slot& sl, int idx) {
     // the batch's own state is allocated last: if it does not fit, hand the
     // most recently admitted requests back to the queue and retry
     for (;;) {
-      st = sqc_batch_create(ctx, int32_t(qs.size()), qs.data(), outs.data(), SQC_F32, nullptr, &sl.b);
+      st = sqc_batch_create(ctx, int32_t(qs.size()), qs.data(), outs.data(), SQC_F32, nullptr, SQC_PREC_FP32, &sl.b);
       if (st != SQC_EBUSY || qs.size() == 1) break;
       ++busy_refusals;
       sqc::ctx_free(ctx, outs.back(), size_t(4) << nas.back());

@@ -225,3 +225,54 @@ def test_bounded_wait_runs_out_and_the_context_recovers():
             torch.cuda.synchronize()
             assert torch.equal(single, outs[j]), j
         ctx.batch_release(bid)
+
+
+def test_split_bf16_batch_matches_single_split_runs():
+    """The batched level in split-BF16: each query's tensor-core steps run as
+    tcgen05 launches between the persistent phases (here a SIMT step
+    produces the BF16-plane operand of a tensor-core last step in two of the
+    circuits), the other steps FP32 in the persistent launch.  Every batched
+    query equals its own split-BF16 reconstruction bit for bit (same plan,
+    same kernels, same summation order) and the FP64 oracle within 1e-6."""
+    import torch
+    from paper_2207_00933_gb300 import Context
+    big = [W.random_line_chain(17, [8, 11, 11], [2, 4], 1, [4, 7, 7]),
+           W.random_line_chain(18, [7, 10, 11], [2, 4], 1, [5, 6, 7]),
+           W.random_line_chain(20, [12, 12], [4], 1, [7, 7])]
+    small = W.batch_level(seed=5, n_circuits=2, n_queries=6, a_range=(6, 10), max_log_input=16, min_qubits=24)
+    with Context(0) as ctx:
+        entries = []     # (qid, na, circuit, probs, roles)
+        for w in big:
+            c = w.circuit
+            cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in w.probs])
+            roles2 = w.roles.copy()
+            mq = next(q for q in range(c.n_qubits) if roles2[q] == O.MERGED)
+            roles2[mq] = O.ZOOM1                              # a zoomed variant of the same shape
+            for r in (w.roles, roles2):
+                q, na = ctx.set_qubit_roles(cid, r)
+                entries.append((q, na, c, w.probs, r))
+        cids = [ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).cuda() for p in ps])
+                for c, ps in zip(small.circuits, small.probs)]
+        for ci, roles in small.queries:
+            q, na = ctx.set_qubit_roles(cids[ci], roles)
+            entries.append((q, na, small.circuits[ci], small.probs[ci], roles))
+        outs = [torch.full((1 << na,), -1.0, dtype=torch.float64, device="cuda") for _, na, *_ in entries]
+        totals = torch.zeros(len(entries), dtype=torch.float64, device="cuda")
+        bid = ctx.batch_create([e[0] for e in entries], outs, totals, precision="split_bf16")
+        n_tc = sum(ctx.query_tc_steps(e[0])[0] for e in entries)
+        assert n_tc >= 6                                        # every big query's last step
+        for _ in range(2):
+            ctx.batch_run(bid)
+        ctx.batch_status(bid)
+        for j, (q, na, c, probs, roles) in enumerate(entries):
+            single = torch.empty_like(outs[j])
+            tot1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+            ctx.reconstruct(q, single, "split_bf16", tot1)
+            torch.cuda.synchronize()
+            assert torch.equal(single, outs[j]), j
+            assert abs(tot1.item() - totals[j].item()) <= 1e-12 * max(1.0, abs(tot1.item()))
+            ref = O.reconstruct(O.Graph.from_arrays(c.n_qubits, *c.graph_arrays()),
+                                [p.astype(np.float64) for p in probs], roles)
+            err = np.abs(outs[j].cpu().numpy() - ref).max()
+            assert err <= 1e-6 and err <= 1e-5 * np.abs(ref).max() + 1e-15, (j, err)
+        ctx.batch_release(bid)

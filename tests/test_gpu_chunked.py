@@ -128,5 +128,14 @@ def test_sliced_last_step_accumulates(precision):
         P, tot, _, ntc = _run(w, precision, out_dtype=out, slice_edges=2)
         _check(P, ref)
         assert abs(tot - O.total_probability(ref)) < 1e-6
-        if precision == "split_bf16":
-            assert ntc >= 1
+
+
+@pytest.mark.parametrize("out", ["float32", "float64"])
+def test_sliced_tensor_core_step_accumulates(wide, out):
+    # one sliced edge: 4 slices, each adding its 4096 x 4096 x 64 last step
+    # into the output on the tensor cores
+    w, ref = wide
+    P, tot, (M, N, Kd), ntc = _run(w, "split_bf16", out_dtype=out, slice_edges=1)
+    assert (M, N, Kd) == (4096, 4096, 64) and ntc == 1
+    _check(P, ref)
+    assert abs(tot - O.total_probability(P)) < 1e-9
