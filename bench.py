@@ -841,26 +841,33 @@ def main():
     prec = args.precision
     from paper_2207_00933_gb300 import SQCError
 
-    # one recursion step on fresh subcircuit outputs: attribution fused into
-    # the merge (only the kept states), the contraction steps, the selection;
-    # queries whose roles do not allow the fused form update the resident
-    # tensors and reconstruct instead
+    # one recursion step on fresh subcircuit outputs in one call
+    # (sqc_reconstruct_select): attribution fused into the merge (only the
+    # kept states), then the contraction steps, the bins and the selection
+    # in one cooperative launch where the plan allows it; queries whose roles
+    # do not allow the fused attribution update the resident tensors and
+    # reconstruct instead
     try:
         ctx.reconstruct_outputs(qid, probs_dev, out, prec, tot)
         fused_step = True
     except SQCError:
         fused_step = False
+    tail_steps = ctx.query_fused_select(qid) if (prec == "fp32" and out_dtype == torch.float32) else 0
 
     def unfused_step():
         ctx.update_subcircuit_outputs(cid, probs_dev)
         ctx.reconstruct(qid, out, prec, tot)
         ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
 
+    def staged_step():
+        ctx.reconstruct_outputs(qid, probs_dev, out, prec, tot)
+        ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
+
     def step():
         if not fused_step:
             return unfused_step()
-        ctx.reconstruct_outputs(qid, probs_dev, out, prec, tot)
-        ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
+        ctx.reconstruct_select(qid, out, TOPK, -math.inf, probs=probs_dev, precision=prec, total_prob=tot,
+                               bins_out=kb, probs_out=kp, n_found=kn)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -915,31 +922,36 @@ def main():
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
 
-    # the other form of the step, timed the same way for comparison: the
-    # resident tensors updated by a separate attribution, then the merge
-    unfused_ms = None
-    if fused_step:
-        urun = None
+    # the other forms of the step, timed the same way for comparison: the
+    # separate calls (attribution fused into the merge, contraction steps,
+    # selection), and the resident tensors updated by a separate attribution
+    # before the merge
+    def time_form(fn):
         if use_graph:
-            ug = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(ug):
-                unfused_step()
+            fg = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(fg):
+                fn()
             for _ in range(max(3, args.warmup)):
-                ug.replay()
-            urun = ug.replay
+                fg.replay()
+            frun = fg.replay
         else:
-            urun = unfused_step
+            frun = fn
         torch.cuda.synchronize(dev)
         tt = []
         for _ in range(args.steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            urun()
+            frun()
             e1.record(stream)
             torch.cuda.synchronize(dev)
             tt.append(e0.elapsed_time(e1))
-        unfused_ms = sum(tt) / len(tt)
+        return sum(tt) / len(tt)
+
+    unfused_ms = staged_ms = None
+    if fused_step:
+        unfused_ms = time_form(unfused_step)
+        staged_ms = time_form(staged_step)
         # back to the fused form's outputs for the checks below
         step()
         torch.cuda.synchronize(dev)
@@ -979,6 +991,10 @@ def main():
     algo = algorithmic_bytes(w, steps_shape, out_b)
     if fused_step:
         algo["merge"] = algo["attribute_fused"]
+    if fused_step and tail_steps:
+        # the selection launch runs the contraction steps and writes the bins
+        # once; they are not read back
+        algo["select"] = algo["contract"] + algo["final"]
     fused = prof["calls"]["merge"] == 0 and prof["calls"]["contract"] > 0
     if fused:
         algo["contract"] = algo["merge"] + algo["contract"] + algo["final"]
@@ -990,7 +1006,9 @@ def main():
     kernel_of = {"attribute": "attr_fused_kernel", "merge": "attr_merge_kernel" if fused_step else "merge_kernel",
                  "contract": "batch_kernel (merge and every step, one launch)" if fused else "gemm_simt_kernel",
                  "final": "gemm_simt_kernel (last step)",
-                 "select": "select_resident_kernel" if (1 << na) <= 7_000_000 else "select_coop_kernel"}
+                 "select": ("select_resident_kernel (fused: contraction steps, bins, selection)"
+                            if fused_step and tail_steps else
+                            "select_resident_kernel" if (1 << na) <= 7_000_000 else "select_coop_kernel")}
     traffic = NCU_TRAFFIC.get((args.workload, prec, kernel_of[dom]))
     roofline = {"bound": "hbm", "kernel": kernel_of[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
@@ -1008,11 +1026,13 @@ def main():
 
     def e2e_step():
         if fused_step:
-            ctx.reconstruct_outputs(qid, probs_host, out, prec, tot)    # H2D of this step's inputs inside
+            # H2D of this step's inputs inside
+            ctx.reconstruct_select(qid, out, TOPK, -math.inf, probs=probs_host, precision=prec, total_prob=tot,
+                                   bins_out=kb, probs_out=kp, n_found=kn)
         else:
             ctx.update_subcircuit_outputs(cid, probs_host)              # H2D of this step's inputs inside
             ctx.reconstruct(qid, out, prec, tot)
-        ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
+            ctx.top_bins(qid, out, TOPK, -math.inf, kb, kp, kn)
         h_bins.copy_(kb, non_blocking=True)
         h_probs.copy_(kp, non_blocking=True)
         h_n.copy_(kn, non_blocking=True)
@@ -1067,8 +1087,11 @@ def main():
                            "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
             "wall_s": wall,
             "gpu_launches": prof["launches"],
-            "step_form": "fresh outputs: attribution fused into the merge (sqc_reconstruct_outputs)" if fused_step
-                         else "update of the resident tensors, then reconstruct",
+            "step_form": ("fresh outputs, one call (sqc_reconstruct_select): attribution fused into the merge, "
+                          + ("then the contraction steps, bins and selection in one cooperative launch"
+                             if tail_steps else "then the contraction steps and the selection")) if fused_step
+                         else "update of the resident tensors, then reconstruct and select",
+            "separate_calls_ms_per_step": staged_ms,
             "unfused_ms_per_step": unfused_ms,
             "roofline": roofline,
             "clocks": clocks,

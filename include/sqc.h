@@ -157,6 +157,15 @@ typedef struct {
    * do not always mean less time for small, latency-bound steps:
    * sqc_query_autotune and sqc_batch_autotune choose by measurement. */
   int32_t contraction_order;
+  /* sqc_reconstruct_select (1 = on, default 1): when a query's FP32 plan
+   * allows it (sqc_query_fused_select), the contraction steps, the bins and
+   * their selection run in ONE cooperative launch -- the steps before the
+   * last level by level between grid barriers, then every CTA computes its
+   * slice of the last step's bins into shared memory, writes them, and the
+   * resident selection runs on them without reading them back.  Results
+   * are those of the per-stage launches (the bins and the selected bins bit
+   * for bit; the FP64 sum within rounding).  0 = per-stage launches. */
+  int32_t fused_select;
 } sqc_config;
 
 enum { SQC_ORDER_GREEDY = 0, SQC_ORDER_MIN_MULT = 1 };
@@ -272,6 +281,35 @@ SQC_API sqc_status sqc_reconstruct_outputs(sqc_ctx* ctx, sqc_query_id q, const v
                                            sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob,
                                            void* stream);
 
+/* One recursion step of Algorithm 1 in one call: the bins of query q (as
+ * sqc_reconstruct when probs is NULL, as sqc_reconstruct_outputs on the
+ * fresh outputs `probs` otherwise; same arguments) followed by the
+ * selection of their largest bins (as sqc_top_bins on out_bins with
+ * n = 2^{n_active} values of out_dtype; same k, threshold and outputs).
+ * With cfg.fused_select and an FP32 plan that allows it
+ * (sqc_query_fused_select > 0), precision SQC_PREC_FP32 and out_dtype
+ * SQC_F32, the contraction steps, the bins and the selection run in one
+ * cooperative launch after the merges: the bins are computed into shared
+ * memory slice by slice, written once and selected without being read
+ * back.  Every output equals that of the separate calls bit for bit,
+ * except total_prob (the same FP64 sum in another order: within
+ * rounding).  Errors as the separate calls.  Asynchronous on `stream`
+ * (host inputs: as sqc_reconstruct_outputs). */
+SQC_API sqc_status sqc_reconstruct_select(sqc_ctx* ctx, sqc_query_id q, const void* const* probs, sqc_dtype dtype,
+                                          int probs_on_device, sqc_precision precision, void* out_bins,
+                                          sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, int32_t k,
+                                          double threshold, uint64_t* bins_out, double* probs_out,
+                                          int32_t* n_found, void* stream);
+
+/* How many contraction steps of query q's FP32 plan sqc_reconstruct_select
+ * runs inside its fused selection launch (all of them), or 0 when it runs
+ * per-stage launches for this query: the plan is sliced, the last step's
+ * shared index exceeds 64 values or its bin maps are not plain bit
+ * deposits, the steps span more than 8 dependency levels, the bins plus the
+ * last step's second operand do not fit the shared memory of one CTA per
+ * SM, or cfg.fused_select / cfg.select_resident is off.  Host values. */
+SQC_API sqc_status sqc_query_fused_select(sqc_ctx* ctx, sqc_query_id q, int32_t* n_steps);
+
 /* Select bins (Algorithm 1: keep the largest bins): among the n values at
  * device pointer `probs` (dtype), those >= threshold, ordered by value
  * descending then bin index ascending, at most k (1 <= k <= 4096).
@@ -335,7 +373,8 @@ SQC_API sqc_status sqc_batch_inject_stall(sqc_ctx* ctx, sqc_batch_id b, int32_t 
  * serving loop's).  ms[6] (may be NULL) receives the mean time per launch,
  * order-major (ms[3 * order + policy]).  Under one order the bins do not
  * depend on the policy (each bin is summed in the same order); another
- * contraction order rounds differently.  The outputs are overwritten.
+ * contraction order rounds differently.  The outputs and totals end as the
+ * chosen order and policy write them (one more launch after the timing).
  * Synchronises the device. */
 SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
                                       sqc_dtype out_dtype, double* totals, int32_t reps, int32_t* best_policy,

@@ -41,7 +41,7 @@ class _Config(ctypes.Structure):
                 ("merge_pyramid", ctypes.c_int32), ("slice_input_log2", ctypes.c_int32),
                 ("slice_intermediate_log2", ctypes.c_int32), ("tc_pairs", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32), ("fused_query", ctypes.c_int32), ("pdl", ctypes.c_int32),
-                ("contraction_order", ctypes.c_int32)]
+                ("contraction_order", ctypes.c_int32), ("fused_select", ctypes.c_int32)]
 
 
 class _Graph(ctypes.Structure):
@@ -68,6 +68,9 @@ _SIGS = {
                                              _c.c_int, _c.c_uint64, _P, _P]),
     "sqc_top_bins": (_c.c_int32, [_P, _c.c_int64, _P, _c.c_int, _c.c_uint64, _c.c_int32, _c.c_double, _P, _P,
                                   _P, _P]),
+    "sqc_reconstruct_select": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _P,
+                                            _c.c_int, _c.c_uint64, _P, _c.c_int32, _c.c_double, _P, _P, _P, _P]),
+    "sqc_query_fused_select": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_c.c_int32)]),
     "sqc_query_info": (_c.c_int32, [_P, _c.c_int64, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_double),
                                     _c.POINTER(_c.c_double), _c.POINTER(_c.c_uint64)]),
     "sqc_query_step": (_c.c_int32, [_P, _c.c_int64, _c.c_int32, _c.POINTER(_c.c_int64), _c.POINTER(_c.c_int64),
@@ -163,7 +166,8 @@ class Context:
                  fp64_chunk_min_edges: int = 12, chunk_terms: int = 256, slice_edges: int = 0,
                  select_resident: bool = True, merge_pyramid: bool = False, slice_input_log2: int = 0,
                  slice_intermediate_log2: int = 0, tc_pairs: bool | None = None, wait_limit_ms: int = 0,
-                 fused_query: bool = False, pdl: bool = False, contraction_order: int = 0):
+                 fused_query: bool = False, pdl: bool = False, contraction_order: int = 0,
+                 fused_select: bool = True):
         self._lib = load_library()
         cfg = _Config()
         self._lib.sqc_default_config(ctypes.byref(cfg))
@@ -182,6 +186,7 @@ class Context:
         cfg.fused_query = int(bool(fused_query))
         cfg.pdl = int(bool(pdl))
         cfg.contraction_order = int(contraction_order)
+        cfg.fused_select = int(bool(fused_select))
         h = _P()
         st = self._lib.sqc_create(ctypes.byref(h), device, ctypes.byref(cfg))
         if st != 0:
@@ -330,6 +335,43 @@ class Context:
         self._check(self._lib.sqc_reconstruct_outputs(self._h, query, ptrs, dt, on_dev, PREC[precision], _ptr(out),
                                                       _dtype_code(out), out.numel() * out.element_size(),
                                                       _ptr(total_prob), _stream_handle(stream)))
+
+    def reconstruct_select(self, query: int, out, k: int, threshold: float = -math.inf, probs: list | None = None,
+                           precision: str = "fp32", total_prob=None, bins_out=None, probs_out=None, n_found=None,
+                           stream=None):
+        """One recursion step (sqc_reconstruct_select): the bins of `query`
+        into `out` (from the resident tensors, or from fresh outputs `probs`),
+        then their k largest (value descending, bin ascending, >= threshold),
+        fused into one launch where the plan allows it.  Returns device
+        tensors (bins int64 [k], probs float64 [k], n_found int32 [1])."""
+        import torch
+        if not out.is_cuda:
+            raise ValueError("out must be a device tensor")
+        if total_prob is not None and (not total_prob.is_cuda or str(total_prob.dtype) != "torch.float64"):
+            raise ValueError("total_prob must be a device float64 tensor")
+        dev = out.device
+        if bins_out is None:
+            bins_out = torch.empty(k, dtype=torch.int64, device=dev)
+        if probs_out is None:
+            probs_out = torch.empty(k, dtype=torch.float64, device=dev)
+        if n_found is None:
+            n_found = torch.empty(1, dtype=torch.int32, device=dev)
+        if probs is None:
+            ptrs, dt, on_dev = None, F32, 1
+        else:
+            on_dev, ptrs, dt = self._prob_ptrs(probs)
+        self._check(self._lib.sqc_reconstruct_select(self._h, query, ptrs, dt, on_dev, PREC[precision], _ptr(out),
+                                                     _dtype_code(out), out.numel() * out.element_size(),
+                                                     _ptr(total_prob), k, float(threshold), _ptr(bins_out),
+                                                     _ptr(probs_out), _ptr(n_found), _stream_handle(stream)))
+        return bins_out, probs_out, n_found
+
+    def query_fused_select(self, query: int) -> int:
+        """Contraction steps sqc_reconstruct_select runs inside its fused
+        selection launch for this query (0: per-stage launches)."""
+        n = ctypes.c_int32()
+        self._check(self._lib.sqc_query_fused_select(self._h, query, ctypes.byref(n)))
+        return n.value
 
     # -- batches ----------------------------------------------------------
     def batch_create(self, queries: list[int], outs: list, totals=None, precision: str = "fp32") -> int:

@@ -112,6 +112,10 @@ struct Plan {
   std::vector<int> sliced;       // first-level sliced edges (Section 6.3), in greedy order
   int64_t n_slices = 1;          // 4^{sliced edges}: merge descriptor sets, one per slice
   int order = 0;                 // contraction order the plan follows (SQC_ORDER_*)
+  // FP32 plans: the steps and selection in one cooperative launch
+  // (launch_select_tail); tail.P, total, alpha are set per call
+  bool tail_ok = false;
+  TailArgs tail{};
 };
 
 struct Batch {
@@ -1008,6 +1012,119 @@ sqc_status build_plan(sqc_ctx* ctx, const Circuit& c, Query* q, bool split, Plan
   return defer ? SQC_OK : finalize_plan(ctx, P);
 }
 
+// Runs of consecutive bit positions of a deposit map m[0..cnt) (m[i] = the
+// bits of i spread over fixed positions, in order): false if m is not one or
+// needs more than kTailMaxRuns runs.
+bool pext_of_map(const uint64_t* m, int64_t cnt, TailPext* r) {
+  *r = TailPext{};
+  if (cnt < 1 || (cnt & (cnt - 1)) || m[0] != 0) return false;
+  const int nbits = ilog2(cnt);
+  std::vector<int> pos(nbits);
+  for (int t = 0; t < nbits; ++t) {
+    const uint64_t v = m[int64_t(1) << t];
+    if (!v || (v & (v - 1))) return false;
+    pos[t] = __builtin_ctzll(v);
+  }
+  for (int64_t i = 1; i < cnt; ++i)
+    if (m[i] != (m[i & (i - 1)] | m[i & -i])) return false;
+  for (int t = 0; t < nbits;) {
+    int e = t + 1;
+    while (e < nbits && pos[e] == pos[e - 1] + 1) ++e;
+    if (r->n == kTailMaxRuns) return false;
+    r->pos[r->n] = static_cast<unsigned char>(pos[t]);
+    r->len[r->n] = static_cast<unsigned char>(e - t);
+    r->out[r->n] = static_cast<unsigned char>(t);
+    ++r->n;
+    t = e;
+  }
+  return true;
+}
+
+// The fused contraction + selection launch of an FP32 plan (P->tail): the
+// steps before the last, ordered by dependency level with their tile
+// shapes (passed as kernel parameters), and the last step's operands and
+// bin-index runs.  Leaves P->tail_ok false when the plan does not fit the
+// launch: sliced, a shared index of the last step above 64, more than
+// kTailMaxLevels levels or kTailMaxPre steps before the last, or bin maps
+// with too many runs.
+cudaError_t prepare_tail(Plan* P, const PlanDraft& D) {
+  P->tail_ok = false;
+  P->tail = TailArgs{};
+  if (P->split || P->n_slices != 1 || P->steps.empty()) return cudaSuccess;
+  const int grid = select_resident_grid();
+  if (grid <= 0) return cudaSuccess;
+  const size_t ns = P->steps.size();
+  const Step& fin = P->steps.back();
+  if (fin.tc || fin.Kd > 64) return cudaSuccess;
+  TailArgs& T = P->tail;
+  if (!pext_of_map(D.maps.data() + D.step_map_off[ns - 1].first, fin.M, &T.rows) ||
+      !pext_of_map(D.maps.data() + D.step_map_off[ns - 1].second, fin.N, &T.cols))
+    return cudaSuccess;
+  // dependency levels: merged subcircuit tensors 0, a step 1 + its inputs'
+  std::vector<int> level(P->tensors.size(), 0);
+  int top = 0;
+  for (size_t si = 0; si + 1 < ns; ++si) {
+    const Step& st = P->steps[si];
+    if (st.tc) return cudaSuccess;
+    level[st.z] = 1 + std::max(level[st.x], level[st.y]);
+    top = std::max(top, level[st.z]);
+  }
+  if (top > kTailMaxLevels || ns - 1 > size_t(kTailMaxPre)) return cudaSuccess;
+  std::vector<TailStep> pre;
+  for (int l = 1; l <= top; ++l) {
+    for (size_t si = 0; si + 1 < ns; ++si) {
+      const Step& st = P->steps[si];
+      if (level[st.z] != l) continue;
+      TailStep ts{};
+      GemmArgs& a = ts.a;
+      a.A = static_cast<const float*>(P->tensors[st.x].buf);
+      a.B = static_cast<const float*>(P->tensors[st.y].buf);
+      a.M = st.M;
+      a.N = st.N;
+      a.K = st.Kd;
+      a.rowmap = st.rowmap;
+      a.colmap = st.colmap;
+      a.vec4 = st.vec4;
+      a.C = P->tensors[st.z].buf;
+      a.kind = P->tensors[st.z].kind;
+      a.plane_stride = P->tensors[st.z].plane_stride;
+      a.alpha = 1.0;
+      auto tiles = [&](int64_t b) { return ((st.M + b - 1) / b) * ((st.N + b - 1) / b); };
+      ts.cfg = tiles(128) >= grid ? 2 : (tiles(64) >= grid ? 1 : 0);
+      const int64_t edge = int64_t(32) << ts.cfg;
+      ts.ntiles = tiles(edge);
+      ts.tn_shift = ilog2((st.N + edge - 1) / edge);          // M, N and the edge are powers of two
+      pre.push_back(ts);
+    }
+    T.level_end[l - 1] = int(pre.size());
+  }
+  T.n_levels = top;
+  T.n_pre = int(pre.size());
+  for (size_t j = 0; j < pre.size(); ++j) T.pre[j] = pre[j];
+  // the operand with fewer rows is staged in shared memory (Y), the other
+  // read from L2 (X); fmaf is symmetric in its factors, so the bins do not
+  // depend on which is which
+  const bool swap = fin.M < fin.N;
+  if (swap) std::swap(T.rows, T.cols);
+  T.X = static_cast<const float*>(P->tensors[swap ? fin.y : fin.x].buf);
+  T.Y = static_cast<const float*>(P->tensors[swap ? fin.x : fin.y].buf);
+  T.M = swap ? fin.N : fin.M;
+  T.N = swap ? fin.M : fin.N;
+  T.Kd = int(fin.Kd);
+  T.ystride = fin.Kd >= 4 ? int(fin.Kd) + 4 : 1;
+  {
+    // a slice's X rows form a range when every bit X owns lies above every
+    // bit Y owns
+    int xlow = 64, yhigh = -1;
+    for (int t = 0; t < T.rows.n; ++t) xlow = std::min<int>(xlow, T.rows.pos[t]);
+    for (int t = 0; t < T.cols.n; ++t) yhigh = std::max<int>(yhigh, T.cols.pos[t] + T.cols.len[t] - 1);
+    T.x_range = xlow > yhigh;
+  }
+  T.partials = P->partials;
+  P->tail_ok = true;
+  return cudaSuccess;
+}
+
 // Device part of a plan: allocate the workspace, point the steps and merge
 // descriptors into it, upload maps and descriptors, zero what must start
 // at zero.
@@ -1060,6 +1177,7 @@ sqc_status finalize_plan(sqc_ctx* ctx, Plan* P) {
     e = upload(ctx, P->merge_dev, sets.data(), sizeof(MergeDesc) * sets.size());
   }
   if (e == cudaSuccess) e = zero(ctx, base + D.off_cnt, 64);
+  if (e == cudaSuccess && !P->split) e = prepare_tail(P, D);
   // BF16 operand padding (shared-index columns beyond K) must read as zero
   if (e == cudaSuccess && D.zero_end > D.zero_begin) e = zero(ctx, base + D.zero_begin, D.zero_end - D.zero_begin);
   if (e != cudaSuccess) {
@@ -1490,6 +1608,7 @@ std::string config_error(const sqc_config& c) {
   if (c.wait_limit_ms < 0 || c.wait_limit_ms > 600000) return "wait_limit_ms must be in [0, 600000]";
   if (c.fused_query != 0 && c.fused_query != 1) return "fused_query must be 0 or 1";
   if (c.pdl != 0 && c.pdl != 1) return "pdl must be 0 or 1";
+  if (c.fused_select != 0 && c.fused_select != 1) return "fused_select must be 0 or 1";
   if (c.contraction_order != SQC_ORDER_GREEDY && c.contraction_order != SQC_ORDER_MIN_MULT)
     return "contraction_order must be SQC_ORDER_GREEDY or SQC_ORDER_MIN_MULT";
   if (c.slice_input_log2 < 0 || c.slice_input_log2 > 62 || c.slice_intermediate_log2 < 0 ||
@@ -1513,6 +1632,7 @@ SQC_API void sqc_default_config(sqc_config* cfg) {
   cfg->select_resident = 1;
   cfg->fused_query = 0;
   cfg->pdl = 0;
+  cfg->fused_select = 1;
 }
 
 SQC_API const char* sqc_last_error(const sqc_ctx* ctx) {
@@ -1757,9 +1877,40 @@ struct FusedSrc {
   int in_f64;
 };
 
+// Selection of the largest bins after a reconstruction (sqc_top_bins'
+// arguments).
+struct SelectReq {
+  int k;
+  double threshold;
+  unsigned long long* bins;
+  double* probs;
+  int* n_found;
+};
+
 sqc_status reconstruct_core(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
                             sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream,
-                            const FusedSrc* fused);
+                            const FusedSrc* fused, const SelectReq* sel = nullptr, bool* selected = nullptr);
+
+// Select bins of query q's output (the body of sqc_top_bins).
+sqc_status select_bins(sqc_ctx* ctx, Query& q, const void* probs, bool is_f64, uint64_t n, const SelectReq& r,
+                       cudaStream_t s) {
+  {
+    // the first selection on a query allocates its workspace
+    sqc_status st = ensure_select_work(ctx, &q);
+    if (st != SQC_OK) return st;
+  }
+  StageScope scope(ctx, s, SQC_STAGE_SELECT);
+  ctx->launches += 1;
+  int* err = reinterpret_cast<int*>(static_cast<char*>(q.sel_mem) + q.sel_bytes - 64);
+  const int rgrid = ctx->cfg.select_resident ? select_resident_grid() : 0;
+  if (rgrid > 0 && select_resident_smem(n, is_f64, rgrid, nullptr))
+    CK(launch_select_resident(q.sel_mem, rgrid, probs, is_f64, n, r.k, r.threshold, r.bins, r.probs, r.n_found, err,
+                              s));
+  else
+    CK(launch_select_coop(q.sel_mem, q.sel_grid, probs, is_f64, n, r.k, r.threshold, r.bins, r.probs, r.n_found,
+                          err, s));
+  return SQC_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1769,10 +1920,14 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id qid, sqc_precision
   return reconstruct_core(ctx, qid, precision, out_bins, out_dtype, out_bytes, total_prob, stream, nullptr);
 }
 
-SQC_API sqc_status sqc_reconstruct_outputs(sqc_ctx* ctx, sqc_query_id qid, const void* const* probs,
-                                           sqc_dtype dtype, int probs_on_device, sqc_precision precision,
-                                           void* out_bins, sqc_dtype out_dtype, uint64_t out_bytes,
-                                           double* total_prob, void* stream) {
+}  // extern "C"
+
+namespace {
+// sqc_reconstruct_outputs (sel null) and sqc_reconstruct_select on fresh
+// outputs.
+sqc_status reconstruct_fresh(sqc_ctx* ctx, sqc_query_id qid, const void* const* probs, sqc_dtype dtype,
+                             int probs_on_device, sqc_precision precision, void* out_bins, sqc_dtype out_dtype,
+                             uint64_t out_bytes, double* total_prob, void* stream, const SelectReq* sel) {
   if (!ctx || !probs || !out_bins) return fail(ctx, SQC_EINVAL, "null argument");
   if (dtype != SQC_F32 && dtype != SQC_F64) return fail(ctx, SQC_EINVAL, "dtype must be F32 or F64");
   auto it = ctx->queries.find(qid);
@@ -1802,7 +1957,8 @@ SQC_API sqc_status sqc_reconstruct_outputs(sqc_ctx* ctx, sqc_query_id qid, const
     }
   }
   const FusedSrc fs{src.data(), dtype == SQC_F64};
-  sqc_status st = reconstruct_core(ctx, qid, precision, out_bins, out_dtype, out_bytes, total_prob, stream, &fs);
+  sqc_status st =
+      reconstruct_core(ctx, qid, precision, out_bins, out_dtype, out_bytes, total_prob, stream, &fs, sel);
   if (st == SQC_OK && !probs_on_device) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cs));
@@ -1811,12 +1967,86 @@ SQC_API sqc_status sqc_reconstruct_outputs(sqc_ctx* ctx, sqc_query_id qid, const
   return st;
 }
 
+// Checks of sqc_top_bins' arguments shared by sqc_reconstruct_select.
+sqc_status check_select_args(sqc_ctx* ctx, int32_t k, double threshold, const void* bins_out, const void* probs_out,
+                             const void* n_found) {
+  if (k < 1 || k > kSelectMaxK) return fail(ctx, SQC_ESHAPE, "k must be in [1, 4096]");
+  if (!bins_out || !probs_out || !n_found) return fail(ctx, SQC_EINVAL, "null argument");
+  if (std::isnan(threshold)) return fail(ctx, SQC_EINVAL, "threshold is NaN");
+  return SQC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+SQC_API sqc_status sqc_reconstruct_outputs(sqc_ctx* ctx, sqc_query_id qid, const void* const* probs,
+                                           sqc_dtype dtype, int probs_on_device, sqc_precision precision,
+                                           void* out_bins, sqc_dtype out_dtype, uint64_t out_bytes,
+                                           double* total_prob, void* stream) {
+  return reconstruct_fresh(ctx, qid, probs, dtype, probs_on_device, precision, out_bins, out_dtype, out_bytes,
+                           total_prob, stream, nullptr);
+}
+
+SQC_API sqc_status sqc_reconstruct_select(sqc_ctx* ctx, sqc_query_id qid, const void* const* probs,
+                                          sqc_dtype dtype, int probs_on_device, sqc_precision precision,
+                                          void* out_bins, sqc_dtype out_dtype, uint64_t out_bytes,
+                                          double* total_prob, int32_t k, double threshold, uint64_t* bins_out,
+                                          double* probs_out, int32_t* n_found, void* stream) {
+  if (!ctx) return SQC_EINVAL;
+  {
+    const sqc_status st = check_select_args(ctx, k, threshold, bins_out, probs_out, n_found);
+    if (st != SQC_OK) return st;
+  }
+  const SelectReq r{k, threshold, reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found};
+  if (probs)
+    return reconstruct_fresh(ctx, qid, probs, dtype, probs_on_device, precision, out_bins, out_dtype, out_bytes,
+                             total_prob, stream, &r);
+  return reconstruct_core(ctx, qid, precision, out_bins, out_dtype, out_bytes, total_prob, stream, nullptr, &r);
+}
+
+SQC_API sqc_status sqc_query_fused_select(sqc_ctx* ctx, sqc_query_id qid, int32_t* n_steps) {
+  if (!ctx || !n_steps) return fail(ctx, SQC_EINVAL, "null argument");
+  auto it = ctx->queries.find(qid);
+  if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
+  const Query& q = *it->second;
+  const Plan& P = q.plans[SQC_PREC_FP32];
+  *n_steps = 0;
+  if (!P.built || !P.tail_ok || !ctx->cfg.fused_select || !ctx->cfg.select_resident) return SQC_OK;
+  DeviceGuard g(ctx->device);
+  const int rgrid = select_resident_grid();
+  if (rgrid > 0 && select_tail_smem(uint64_t(q.out_elems), P.tail, rgrid, nullptr)) *n_steps = P.tail.n_pre + 1;
+  return SQC_OK;
+}
+
 }  // extern "C"
 
 namespace {
+sqc_status reconstruct_stages(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
+                              sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream,
+                              const FusedSrc* fused, const SelectReq* sel, bool* selected);
+
+// A reconstruction, then (sel) the selection of its largest bins: in one
+// launch with the contraction steps when the plan allows it, else as
+// sqc_top_bins on the written bins.
 sqc_status reconstruct_core(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
                             sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream,
-                            const FusedSrc* fused) {
+                            const FusedSrc* fused, const SelectReq* sel, bool* selected) {
+  bool done = false;
+  sqc_status st = reconstruct_stages(ctx, qid, precision, out_bins, out_dtype, out_bytes, total_prob, stream, fused,
+                                     sel, &done);
+  if (st == SQC_OK && sel && !done) {
+    Query& q = *ctx->queries.find(qid)->second;
+    PdlScope pdl(ctx->cfg.pdl != 0);
+    st = select_bins(ctx, q, out_bins, out_dtype == SQC_F64, uint64_t(q.out_elems), *sel,
+                     static_cast<cudaStream_t>(stream));
+  }
+  if (selected) *selected = done;
+  return st;
+}
+
+sqc_status reconstruct_stages(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precision, void* out_bins,
+                              sqc_dtype out_dtype, uint64_t out_bytes, double* total_prob, void* stream,
+                              const FusedSrc* fused, const SelectReq* sel, bool* selected) {
   if (!ctx || !out_bins) return fail(ctx, SQC_EINVAL, "null argument");
   auto it = ctx->queries.find(qid);
   if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
@@ -1865,6 +2095,31 @@ sqc_status reconstruct_core(sqc_ctx* ctx, sqc_query_id qid, sqc_precision precis
     ctx->launches += 1;
     return SQC_OK;
   };
+
+  if (sel && ctx->cfg.fused_select && precision == SQC_PREC_FP32 && out_kind == OUT_F32 && P.tail_ok &&
+      ctx->cfg.select_resident) {
+    const int rgrid = select_resident_grid();
+    const uint64_t n = uint64_t(q.out_elems);
+    if (rgrid > 0 && select_tail_smem(n, P.tail, rgrid, nullptr)) {
+      // merges, then the contraction steps, the bins and their selection in
+      // one cooperative launch
+      sqc_status st = ensure_select_work(ctx, &q);
+      if (st != SQC_OK) return st;
+      st = run_merge(P.merge_dev, int(P.merge_host.size()));
+      if (st != SQC_OK) return st;
+      TailArgs T = P.tail;
+      T.alpha = float(alpha);
+      T.P = static_cast<float*>(out_bins);
+      T.total = total_prob;
+      int* err = reinterpret_cast<int*>(static_cast<char*>(q.sel_mem) + q.sel_bytes - 64);
+      StageScope scope(ctx, s, SQC_STAGE_SELECT);
+      CK(launch_select_tail(q.sel_mem, rgrid, T, n, sel->k, sel->threshold, sel->bins, sel->probs, sel->n_found,
+                            err, s));
+      ctx->launches += 1;
+      *selected = true;
+      return SQC_OK;
+    }
+  }
 
   if (!fused && precision == SQC_PREC_FP32 && ctx->cfg.fused_query && P.n_slices == 1 && !P.steps.empty()) {
     // the merge and every contraction step in ONE persistent launch: merge
@@ -2007,25 +2262,8 @@ SQC_API sqc_status sqc_top_bins(sqc_ctx* ctx, sqc_query_id qid, const void* prob
   if (it == ctx->queries.end()) return fail(ctx, SQC_ENOTFOUND, "unknown query");
   DeviceGuard g(ctx->device);
   PdlScope pdl(ctx->cfg.pdl != 0);
-  {
-    // the first selection on a query allocates its workspace
-    sqc_status st = ensure_select_work(ctx, it->second.get());
-    if (st != SQC_OK) return st;
-  }
-  StageScope scope(ctx, static_cast<cudaStream_t>(stream), SQC_STAGE_SELECT);
-  ctx->launches += 1;
-  Query& q = *it->second;
-  int* err = reinterpret_cast<int*>(static_cast<char*>(q.sel_mem) + q.sel_bytes - 64);
-  const int rgrid = ctx->cfg.select_resident ? select_resident_grid() : 0;
-  if (rgrid > 0 && select_resident_smem(n, dtype == SQC_F64, rgrid, nullptr))
-    CK(launch_select_resident(q.sel_mem, rgrid, probs, dtype == SQC_F64, n, k, threshold,
-                              reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found, err,
-                              static_cast<cudaStream_t>(stream)));
-  else
-    CK(launch_select_coop(q.sel_mem, q.sel_grid, probs, dtype == SQC_F64, n, k, threshold,
-                          reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found, err,
-                          static_cast<cudaStream_t>(stream)));
-  return SQC_OK;
+  const SelectReq r{k, threshold, reinterpret_cast<unsigned long long*>(bins_out), probs_out, n_found};
+  return select_bins(ctx, *it->second, probs, dtype == SQC_F64, n, r, static_cast<cudaStream_t>(stream));
 }
 
 SQC_API sqc_status sqc_batch_create(sqc_ctx* ctx, int32_t n, const sqc_query_id* qs, void* const* outs,
@@ -2212,6 +2450,18 @@ SQC_API sqc_status sqc_batch_autotune(sqc_ctx* ctx, int32_t n, const sqc_query_i
       if (st == SQC_OK && q->plans[SQC_PREC_FP32].order != best_o) st = replan(ctx, *q, best_o);
   }
   ctx->batch_policy = st == SQC_OK ? best : saved;
+  if (st == SQC_OK) {
+    // the outputs and totals end as the chosen order and policy write them
+    sqc_batch_id b = 0;
+    st = sqc_batch_create(ctx, n, qs, outs, out_dtype, totals, SQC_PREC_FP32, &b);
+    if (st == SQC_OK) {
+      st = sqc_batch_run(ctx, b, nullptr);
+      if (st == SQC_OK) st = sqc_batch_status(ctx, b);
+      const sqc_status rs = sqc_batch_release(ctx, b);
+      if (st == SQC_OK) st = rs;
+    }
+    if (st != SQC_OK) ctx->batch_policy = saved;
+  }
   if (st == SQC_OK) {
     *best_policy = best;
     *best_order = best_o;

@@ -62,7 +62,9 @@ __device__ __forceinline__ double run_tile(const BatchStep& st, int64_t tile, fl
   const int tn_shift = __ffsll(tiles_n) - 1;
   const int64_t m0 = (tile >> tn_shift) * BM;
   const int64_t n0 = (tile & (tiles_n - 1)) * BN;
-  return gemm_tile<BM, BN, TM, TN, CH, BK>(st.a, m0, n0, smem, smem + BK * (BM + 4), C);
+  // operands written by other CTAs of this launch: read from L2, not
+  // through the read-only path
+  return gemm_tile<BM, BN, TM, TN, CH, BK, kOpThreads, true>(st.a, m0, n0, smem, smem + BK * (BM + 4), C);
 }
 
 __global__ void __launch_bounds__(kOpThreads, 2) batch_kernel(BatchLaunch L) {

@@ -38,6 +38,16 @@ __device__ __forceinline__ double f2d(float f) {
   return __hiloint2double(int(hi), int(lo));
 }
 
+// FP32 value of a power of two held in FP64 (2^e with -126 <= e <= 127, as
+// every scale of the method is: 2^-K or 1) by moving its exponent field:
+// exact, integer operations only (a conversion would take the narrow FP64
+// pipe once per thread).
+__device__ __forceinline__ float pow2_to_float(double d) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  const int e = int((u >> 52) & 0x7ffu) - 1023;
+  return __uint_as_float(unsigned(u >> 63) << 31 | unsigned(e + 127) << 23);
+}
+
 // Write one result element in the destination's number format: FP32, FP64,
 // or three BF16 planes hi + mid + lo (each the round-to-nearest of what the
 // previous planes left), the operand format of the split-BF16 steps.

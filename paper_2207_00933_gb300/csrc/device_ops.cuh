@@ -52,7 +52,7 @@ __device__ __forceinline__ void merge_block(const MergeDesc& d, int64_t blk) {
   if (valid && lane == 0) {
     const int64_t e = o >> d.a;
     const uint32_t b = uint32_t(o & ((int64_t(1) << d.a) - 1));
-    store_out_f(d.dst, d.kind, d.plane_stride, d.rowmap[e] + d.colmap[b], acc * float(d.alpha));
+    store_out_f(d.dst, d.kind, d.plane_stride, d.rowmap[e] + d.colmap[b], acc * pow2_to_float(d.alpha));
   }
 }
 
@@ -62,15 +62,25 @@ constexpr int gemm_tile_smem_floats() {
   return kBK * (BM + 4) + kBK * (BN + 4);
 }
 
-// One BM x BN tile (origin m0, n0) of C = A B^T (Section 6.1) on 256 threads,
-// epilogue through the layout maps into Cout (the step's own output, or
-// the one a single-query launch names); returns this thread's sum of the
-// values it wrote (for the probability check).  smem_a / smem_b: kBK x
-// (BM+4) and kBK x (BN+4) floats of shared memory.
-template <int BM, int BN, int TM, int TN, bool CHUNKED, int kBK>
+// Operand load: through the read-only path, or from L2 only (CG) for
+// operands that other CTAs of the same launch wrote.
+template <bool CG>
+__device__ __forceinline__ float ld_operand(const float* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+
+// One BM x BN tile (origin m0, n0) of C = A B^T (Section 6.1) on NT threads
+// (256 unless a launch gives the whole CTA to one tile), epilogue through
+// the layout maps into Cout (the step's own output, or the one a
+// single-query launch names); returns this thread's sum of the values it
+// wrote (for the probability check).  smem_a / smem_b: kBK x (BM+4) and
+// kBK x (BN+4) floats of shared memory.  CG: read the operands from L2 (they
+// were written earlier in the same launch).
+template <int BM, int BN, int TM, int TN, bool CHUNKED, int kBK, int NT = kOpThreads, bool CG = false>
 __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64_t n0, float* smem_a,
                                             float* smem_b, void* Cout) {
-  constexpr int kThreads = kOpThreads;
+  constexpr int kThreads = NT;
   static_assert((BM / TM) * (BN / TN) == kThreads, "tile shape");
   constexpr int TX = BN / TN;
   float (*As)[BM + 4] = reinterpret_cast<float (*)[BM + 4]>(smem_a);
@@ -80,7 +90,7 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
   const int tx = tid % TX, ty = tid / TX;
 
   // alpha is a power of two: scaling an FP32 partial by it is exact
-  const float alpha_f = float(a.alpha);
+  const float alpha_f = pow2_to_float(a.alpha);
   float acc[TM][TN];
   double acc64[CHUNKED ? TM : 1][CHUNKED ? TN : 1];
 #pragma unroll
@@ -94,18 +104,47 @@ __device__ __forceinline__ double gemm_tile(const GemmArgs& a, int64_t m0, int64
       for (int j = 0; j < TN; ++j) acc64[i][j] = 0.0;
   }
 
+  // the operand loads of a stage are issued in groups of four before their
+  // shared-memory stores, so that four are in flight together (one memory
+  // round trip per group instead of one per load; four keeps the registers
+  // of the deep tile shapes in bounds)
+  constexpr int kLA = (BM * kBK + kThreads - 1) / kThreads;
+  constexpr int kLB = (BN * kBK + kThreads - 1) / kThreads;
+  constexpr int kG = 4;
   for (int64_t k0 = 0; k0 < a.K; k0 += kBK) {
-    for (int idx = tid; idx < BM * kBK; idx += kThreads) {
-      const int r = idx / kBK, kk = idx % kBK;
-      float v = 0.f;
-      if (m0 + r < a.M && k0 + kk < a.K) v = __ldg(a.A + (m0 + r) * a.K + k0 + kk);
-      As[kk][r] = v;
+#pragma unroll
+    for (int g0 = 0; g0 < kLA; g0 += kG) {
+      float rv[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int idx = tid + (g0 + u) * kThreads;
+        const int r = idx / kBK, kk = idx % kBK;
+        rv[u] = 0.f;
+        if (g0 + u < kLA && idx < BM * kBK && m0 + r < a.M && k0 + kk < a.K)
+          rv[u] = ld_operand<CG>(a.A + (m0 + r) * a.K + k0 + kk);
+      }
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int idx = tid + (g0 + u) * kThreads;
+        if (g0 + u < kLA && idx < BM * kBK) As[idx % kBK][idx / kBK] = rv[u];
+      }
     }
-    for (int idx = tid; idx < BN * kBK; idx += kThreads) {
-      const int r = idx / kBK, kk = idx % kBK;
-      float v = 0.f;
-      if (n0 + r < a.N && k0 + kk < a.K) v = __ldg(a.B + (n0 + r) * a.K + k0 + kk);
-      Bs[kk][r] = v;
+#pragma unroll
+    for (int g0 = 0; g0 < kLB; g0 += kG) {
+      float rv[kG];
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int idx = tid + (g0 + u) * kThreads;
+        const int r = idx / kBK, kk = idx % kBK;
+        rv[u] = 0.f;
+        if (g0 + u < kLB && idx < BN * kBK && n0 + r < a.N && k0 + kk < a.K)
+          rv[u] = ld_operand<CG>(a.B + (n0 + r) * a.K + k0 + kk);
+      }
+#pragma unroll
+      for (int u = 0; u < kG; ++u) {
+        const int idx = tid + (g0 + u) * kThreads;
+        if (g0 + u < kLB && idx < BN * kBK) Bs[idx % kBK][idx / kBK] = rv[u];
+      }
     }
     __syncthreads();
 #pragma unroll

@@ -20,7 +20,7 @@ namespace {
 constexpr int kThreads = kOpThreads;
 
 template <int BM, int BN, int TM, int TN, bool CHUNKED, int kBK>
-__global__ void __launch_bounds__(kThreads) gemm_simt_kernel(GemmArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) gemm_simt_kernel(GemmArgs a) {
   pdl_wait();      // the previous kernel on the stream has completed
   pdl_trigger();   // the next one may start launching
   __shared__ __align__(16) float As[kBK * (BM + 4)];

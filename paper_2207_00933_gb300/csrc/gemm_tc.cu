@@ -604,7 +604,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     constexpr int kChunks = kBN / 64;          // 32-column chunks in a warp's half of a full-width unit
     const int quad = warp & 3;
     const int hc = (warp - 2) >> 2;
-    const float alpha_f = float(a.alpha);
+    const float alpha_f = pow2_to_float(a.alpha);   // a power of two
     const bool plain = npass == 1 && !a.accumulate;
     int64_t t = 0;
     bool ok = true;

@@ -265,6 +265,53 @@ cudaError_t launch_select_resident(void* work, int grid, const void* x, int is_f
 cudaError_t select_configure();
 constexpr int kSelectMaxK = 4096;
 
+// ---- the last contraction steps fused into the resident selection ----------
+// Index extraction by runs of consecutive bits: bit run t of the source
+// index (len[t] bits from position pos[t]) lands at position out[t] of the
+// result.  rows/cols of the last step are the parts of the bin index each
+// operand owns (the bin is rowmap[i] + colmap[j], both bit deposits).
+constexpr int kTailMaxRuns = 8;
+struct TailPext {
+  int n;
+  unsigned char pos[kTailMaxRuns], len[kTailMaxRuns], out[kTailMaxRuns];
+};
+// One contraction step before the last, run in the same launch: its tiles
+// are split over the CTAs, one tile per CTA at a time, 1024 threads each.
+struct TailStep {
+  GemmArgs a;
+  int cfg;                  // tile shape: 0 = 32 x 32, 1 = 64 x 64, 2 = 128 x 128
+  int tn_shift;             // log2 of the tiles across N
+  int64_t ntiles;
+};
+constexpr int kTailMaxLevels = 8;
+constexpr int kTailMaxPre = 16;
+struct TailArgs {
+  TailStep pre[kTailMaxPre];  // steps ordered by dependency level (kernel parameters: no load from memory)
+  int n_pre;
+  int n_levels;
+  int level_end[kTailMaxLevels];   // steps [level_end[l-1], level_end[l]) form level l
+  // the last step: P[b] = alpha sum_k X[i(b)][k] Y[j(b)][k] for every bin b,
+  // i(b) by the runs `rows`, j(b) by `cols` (X and Y: the step's operands,
+  // the one with fewer rows as Y)
+  const float* X;           // [M][Kd]: read from L2, or (x_range) the rows a slice needs staged
+  const float* Y;           // [N][Kd], staged whole in shared memory
+  int64_t M, N;
+  int Kd;
+  int ystride;              // floats per staged Y row (and staged X row)
+  int x_range;              // i(b) is monotone in b (X's bits above Y's): a slice's rows are a range
+  int x_rows;               // rows of X staged per CTA (0: X read from L2; set at launch)
+  float alpha;
+  TailPext rows, cols;
+  float* P;                 // the bins (FP32), written in bin order
+  double* partials;         // [grid]
+  double* total;            // nullable: FP64 sum of all bins
+};
+// Shared memory of the fused launch for n bins (0: does not fit).
+size_t select_tail_smem(uint64_t n, const TailArgs& t, int grid, uint64_t* per);
+cudaError_t launch_select_tail(void* work, int grid, const TailArgs& t, uint64_t n, int k, double threshold,
+                               unsigned long long* bins_out, double* probs_out, int* n_found, int* err,
+                               cudaStream_t s);
+
 }  // namespace sqc
 
 // ---- serving-loop hooks into the context (defined with the C ABI) ----------

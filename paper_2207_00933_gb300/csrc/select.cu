@@ -24,7 +24,7 @@
 #include <limits>
 #include <mutex>
 
-#include "common.cuh"
+#include "device_ops.cuh"
 
 namespace sqc {
 
@@ -869,10 +869,10 @@ constexpr int kRWarps = kRThreads / 32;
 constexpr int kRBits = 12;
 constexpr int kRRadix = 1 << kRBits;
 constexpr int kRMaxPasses = 6;                      // 64-bit keys: 5 x 12 + 4 bits
-constexpr int kRRankMax = 128;                      // candidates one CTA ranks at most (kMaxSort / grid + 1)
-constexpr int kRTile = 1024;                        // candidates per ranking tile
+constexpr int kRTile = 1024;                        // candidates per ranking tile at least
 constexpr int kRHistBytes = kRRadix * 4;
 constexpr int kRRegionMin = kRTile * 16;            // the ranking tile reuses the key region
+static_assert(kRTile == kRThreads, "a ranking round takes at least one candidate per thread");
 constexpr int kRSmemMax = 200 * 1024;               // dynamic shared memory per CTA at most
 constexpr size_t kRCtlOffset = 128;                 // byte offset of this kernel's control words
 constexpr uint32_t kRBarrierLimit = 1u << 21;       // polls (~1-2 s) before a barrier gives up
@@ -992,10 +992,439 @@ __device__ __forceinline__ double value_of_key(unsigned long long key) {
   }
 }
 
+// s_hi + s_lo += v with the rounding error of the high part kept (Knuth's
+// TwoSum: t + e = s_hi + v exactly).
+__device__ __forceinline__ void two_sum_add(float& s_hi, float& s_lo, float v) {
+  const float t = s_hi + v;
+  const float bp = t - s_hi;
+  const float ap = t - bp;
+  s_lo += (s_hi - ap) + (v - bp);
+  s_hi = t;
+}
+
+// Sum of the (hi, lo) pairs of a warp, in every lane (butterfly order).
+__device__ __forceinline__ void pair_warp_sum(float& h, float& l) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, off);
+    const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
+    l += l2;
+    two_sum_add(h, l, h2);
+  }
+}
+
+// Bits of b taken run by run (TailPext) and packed into an index (bins
+// held in shared memory number fewer than 2^32).
+__device__ __forceinline__ uint32_t tail_pext(uint32_t b, const TailPext& r) {
+  uint32_t v = 0;
+  for (int t = 0; t < r.n; ++t) v |= ((b >> r.pos[t]) & ((1u << r.len[t]) - 1u)) << r.out[t];
+  return v;
+}
+
+// Shared memory a tile of the steps before the last needs (the largest of
+// the three tile shapes: 32 x 32 with 64-deep stages).
+constexpr int kTailStageBytes = 64 * (32 + 4) * 2 * 4;
+static_assert(kTailStageBytes >= 32 * (64 + 4) * 2 * 4 && kTailStageBytes >= 16 * (128 + 4) * 2 * 4,
+              "stage region of the 64 x 64 and 128 x 128 tiles");
+
+// Offset of the staged Y operand in the fused launch's shared memory.
+__host__ __device__ __forceinline__ uint64_t tail_y_offset(uint64_t per) {
+  uint64_t r = per * 4;
+  if (r < uint64_t(kRRegionMin)) r = kRRegionMin;
+  if (r < uint64_t(kTailStageBytes)) r = kTailStageBytes;
+  return uint64_t(kRHistBytes) + ((r + 15) & ~uint64_t(15));
+}
+
+// The contraction steps before the last, level by level: every CTA takes
+// tiles of the level's steps (the whole CTA on one tile), then all meet at
+// a grid barrier, so the next level reads complete tensors.  Returns false
+// when a barrier gave up.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// The larger tile shapes of the steps before the last, kept out of line:
+// the fused launch is long and its straight-line path should stay compact
+// in the instruction cache.
+template <int BM, int TMN, int BK>
+__device__ __noinline__ void tail_tile_apart(const GemmArgs& a, int64_t m0, int64_t n0, float* stage) {
+  gemm_tile<BM, BM, TMN, TMN, false, BK, kRThreads, true>(a, m0, n0, stage, stage + BK * (BM + 4), a.C);
+}
+
+__device__ __forceinline__ bool tail_pre_steps(const TailArgs& T, ResWork& w, unsigned nb, unsigned& bar,
+                                              float* stage) {
+  int lb = 0;
+  for (int l = 0; l < T.n_levels; ++l) {
+    const int le = T.level_end[l];
+    int64_t tot = 0;
+    for (int s = lb; s < le; ++s) tot += T.pre[s].ntiles;
+    for (int64_t t = blockIdx.x; t < tot; t += nb) {
+      int s = lb;
+      int64_t tl = t;
+      while (tl >= T.pre[s].ntiles) {
+        tl -= T.pre[s].ntiles;
+        ++s;
+      }
+      const TailStep& ts = T.pre[s];
+      const GemmArgs& a = ts.a;
+      const int bshift = 5 + ts.cfg;                       // tile edge 32, 64 or 128
+      const int64_t m0 = (tl >> ts.tn_shift) << bshift;
+      const int64_t n0 = (tl & ((int64_t(1) << ts.tn_shift) - 1)) << bshift;
+      {
+        // this tile's layout maps (cold at the start of a step) into L2
+        // while its operands load: 16 entries per 128-byte line
+        const int64_t r = int64_t(threadIdx.x) * 16, bm = int64_t(1) << bshift;
+        if (r < bm && m0 + r < a.M) prefetch_l2(a.rowmap + m0 + r);
+        else if (r >= 128 && r - 128 < bm && n0 + r - 128 < a.N) prefetch_l2(a.colmap + n0 + r - 128);
+      }
+      // operands may come from the level before (written in this launch):
+      // read them from L2.  Each stage of gemm_tile ends with a CTA
+      // barrier, so the next tile may reuse the shared memory at once.
+      if (ts.cfg == 0)
+        gemm_tile<32, 32, 1, 1, false, 64, kRThreads, true>(a, m0, n0, stage, stage + 64 * (32 + 4), a.C);
+      else if (ts.cfg == 1)
+        tail_tile_apart<64, 2, 32>(a, m0, n0, stage);
+      else
+        tail_tile_apart<128, 4, 16>(a, m0, n0, stage);
+    }
+    lb = le;
+    if (res_barrier(w.ctl, 1ull << 32, nb * ++bar) == 0ull) return false;
+  }
+  return true;
+}
+
+// Bins of a slice for any bit layout of the last step (one bin per thread
+// and round: bit runs, Y staged, X staged or read from L2), with their keys
+// and the first 12-bit histogram.  Out of line: the fused launch's common
+// layout takes the band path.
+__device__ __noinline__ void tail_slice_general(const TailArgs& T, const float* ys, const float* xs, uint32_t x0,
+                                                bool xst, uint32_t ustart, int cnt, unsigned key_thr,
+                                                unsigned* keys, unsigned* sh, float& s_hi, float& s_lo) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int kd = T.Kd;
+  const int kd_log2 = __ffs(kd) - 1;
+  const int ystride = T.ystride;
+  const bool runs1 = T.rows.n <= 1 && T.cols.n <= 1;
+  const uint32_t rpos = T.rows.n ? T.rows.pos[0] : 0u, rmask = T.rows.n ? (1u << T.rows.len[0]) - 1u : 0u;
+  const uint32_t cpos = T.cols.n ? T.cols.pos[0] : 0u, cmask = T.cols.n ? (1u << T.cols.len[0]) - 1u : 0u;
+  const float alpha = T.alpha;
+  float* P = T.P;
+  // the loop bound is the same for the whole CTA (warp_hist_add)
+  for (int i0 = 0; i0 < cnt; i0 += kRThreads) {
+    const int i = i0 + tid;
+    unsigned kv = 0u;
+    if (i < cnt) {
+      const uint32_t b = ustart + uint32_t(i);
+      uint32_t r, c;
+      if (runs1) {
+        r = (b >> rpos) & rmask;
+        c = (b >> cpos) & cmask;
+      } else {
+        r = tail_pext(b, T.rows);
+        c = tail_pext(b, T.cols);
+      }
+      float acc = 0.f;
+      if (kd >= 4) {
+        const float4* yr = reinterpret_cast<const float4*>(ys + c * ystride);
+        if (xst) {
+          const float4* xr = reinterpret_cast<const float4*>(xs + (r - x0) * ystride);
+#pragma unroll 4
+          for (int q = 0; q < (kd >> 2); ++q) {
+            const float4 xa = xr[q], yb = yr[q];
+            acc = fmaf(xa.x, yb.x, acc);
+            acc = fmaf(xa.y, yb.y, acc);
+            acc = fmaf(xa.z, yb.z, acc);
+            acc = fmaf(xa.w, yb.w, acc);
+          }
+        } else {
+          const float4* xr = reinterpret_cast<const float4*>(T.X + (size_t(r) << kd_log2));
+#pragma unroll 4
+          for (int q = 0; q < (kd >> 2); ++q) {
+            const float4 xa = __ldcg(xr + q), yb = yr[q];
+            acc = fmaf(xa.x, yb.x, acc);
+            acc = fmaf(xa.y, yb.y, acc);
+            acc = fmaf(xa.z, yb.z, acc);
+            acc = fmaf(xa.w, yb.w, acc);
+          }
+        }
+      } else {
+        const float xv = xst ? xs[(r - x0) * ystride] : __ldcg(T.X + r);
+        acc = fmaf(xv, ys[c * ystride], acc);
+      }
+      // the per-step kernel pads a shared index below 16 with zero terms
+      // (which turn -0 into +0)
+      if (kd < 16) acc = fmaf(0.f, 0.f, acc);
+      const float v = acc * alpha;
+      P[b] = v;
+      two_sum_add(s_hi, s_lo, v);
+      const unsigned u = __float_as_uint(v);
+      const bool nan = (u & 0x7fffffffu) > 0x7f800000u;
+      const unsigned kk = unsigned(key_f32(v) >> 32);
+      kv = (!nan && kk >= key_thr) ? kk : 0u;
+      keys[i] = kv;
+    }
+    warp_hist_add(sh, kv != 0, kv >> (32 - kRBits), lane);
+  }
+}
+
+// Exact ties of the k-th key beyond the candidate capacity (rare): written
+// in ascending bin order via per-CTA counts and an ordered scan of each
+// slice, after every larger value.  Out of line, like the other rare paths
+// of the resident kernel, to keep its common path compact in the
+// instruction cache.  Returns false when the grid barrier gave up.
 template <bool F64>
+__device__ __noinline__ bool tie_scan(ResWork& w, const unsigned* keys, int cnt, uint64_t start, const void* x,
+                                      const ResState& st, unsigned* wcnt, unsigned nb, unsigned& bar) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned long long tkey = st.prefix;
+  const unsigned tk_hi = F64 ? unsigned(tkey >> 32) : unsigned(tkey);
+  auto is_tie = [&](int i, unsigned kk) -> bool {
+    if (kk != tk_hi) return false;
+    if constexpr (F64) return unsigned(key_f64(static_cast<const double*>(x)[start + i])) == unsigned(tkey);
+    else return true;
+  };
+  unsigned my = 0;
+  for (int i = tid; i < cnt; i += kRThreads) my += is_tie(i, keys[i]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(0xffffffffu, my, off);
+  if (lane == 0) wcnt[warp] = my;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned c = 0;
+    for (int ww = 0; ww < kRWarps; ++ww) c += wcnt[ww];
+    w.tie_count[blockIdx.x] = c;
+  }
+  if (res_barrier(w.ctl, 1ull << 32, nb * ++bar) == 0ull) return false;
+  __shared__ unsigned long long tbase;
+  if (tid == 0) {
+    unsigned long long b = 0;
+    for (unsigned r = 0; r < blockIdx.x; ++r) b += __ldcg(w.tie_count + r);
+    tbase = b;
+  }
+  __syncthreads();
+  const unsigned long long need = st.krem, first = st.take - st.krem;
+  unsigned long long run = tbase;
+  for (int i0 = 0; i0 < cnt && run < need; i0 += kRThreads) {
+    const int i = i0 + tid;
+    const bool tie = i < cnt && is_tie(i, keys[i]);
+    const unsigned bal = __ballot_sync(0xffffffffu, tie);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    __syncthreads();
+    unsigned before = 0, all = 0;
+    for (int ww = 0; ww < kRWarps; ++ww) {
+      if (ww < warp) before += wcnt[ww];
+      all += wcnt[ww];
+    }
+    const unsigned long long rank = run + before + __popc(bal & ((1u << lane) - 1u));
+    if (tie && rank < need) {
+      w.cand_key[first + rank] = tkey;
+      w.cand_idx[first + rank] = start + i;
+    }
+    run += all;
+    __syncthreads();
+  }
+  return true;
+}
+
+// Bucket of a candidate key for the ranking: a monotone, log-scaled
+// function of its distance d = key - tmin above the lowest selectable key
+// (the leading-one position of d and the 7 (FP32) or 6 (FP64) bits after
+// it), numbered so that bucket 0 holds the largest keys.  Fine steps near
+// the selection boundary, where most candidates lie.
+template <bool F64>
+__device__ __forceinline__ unsigned rank_bucket(unsigned long long key, unsigned long long tmin) {
+  const unsigned long long d = key - tmin;
+  int val = 0;
+  if (d != 0) {
+    if constexpr (F64) {
+      const int lz = __clzll(static_cast<long long>(d));
+      val = 1 + ((63 - lz) << 6) + int(unsigned((d << lz) >> 57) & 63u);
+    } else {
+      const unsigned d32 = unsigned(d);
+      const int lz = __clz(d32);
+      val = 1 + ((31 - lz) << 7) + int(((d32 << lz) >> 24) & 127u);
+    }
+  }
+  if (val > kRRadix - 1) val = kRRadix - 1;
+  return unsigned(kRRadix - 1 - val);
+}
+
+// Bytes of shared memory (after the histogram) the ranking needs: bucket
+// starts and, per owned candidate, its key (FP32: packed with the bin), bin
+// (FP64) and bucket; FP32 also keeps every candidate's key word between
+// its two passes over the list.
+__host__ __device__ constexpr unsigned rank_region_bytes(bool f64) {
+  return unsigned(kRRadix) * 4u + unsigned(kMaxSort) * (f64 ? 20u : 16u);
+}
+
+// Final order of the nc candidates (value descending, bin ascending) and
+// the first `take` written at their ranks.  Every CTA counts the candidates
+// per bucket (rank_bucket: bucket order is key order), then owns the
+// buckets whose first position falls in its share of [0, nc) and ranks
+// their members among themselves: rank = candidates in earlier buckets +
+// members of the same bucket ahead.  With exact ties of the k-th key beyond
+// capacity (tie_by_pos), the ties were written in ascending bin order right
+// after every larger value, so their rank is their position.
+template <bool F64>
+__device__ __forceinline__ void rank_candidates(const ResWork& w, unsigned nc, unsigned long long take,
+                                                unsigned long long tmin, bool tie_by_pos,
+                                                unsigned long long tie_key, unsigned char* rsm, unsigned* sh,
+                                                unsigned* wsum, unsigned long long* bins_out, double* probs_out) {
+  const unsigned nb = gridDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned* bstart = reinterpret_cast<unsigned*>(rsm + kRHistBytes);                  // [kRRadix]
+  unsigned long long* lk = reinterpret_cast<unsigned long long*>(bstart + kRRadix);     // [kMaxSort]
+  unsigned long long* li = lk + kMaxSort;                                               // [kMaxSort] (FP64)
+  unsigned* lq = reinterpret_cast<unsigned*>(F64 ? li + kMaxSort : li);                 // [kMaxSort]
+  unsigned* kc = lq + kMaxSort;                                                         // [kMaxSort] (FP32)
+  __shared__ unsigned lcount;
+  for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
+  if (tid == 0) lcount = 0u;
+  __syncthreads();
+  // the CTAs read the same list: each starts at its own offset
+  const unsigned rot = (blockIdx.x * nc) / nb;
+  auto at = [&](unsigned e) { const unsigned f = e + rot; return f >= nc ? f - nc : f; };
+  for (unsigned e0 = 0; e0 < nc; e0 += 4 * kRThreads) {
+    unsigned long long kk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned e = e0 + u * kRThreads + tid;
+      if (e < nc) kk[u] = __ldcg(w.cand_key + at(e));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned e = e0 + u * kRThreads + tid;
+      if (e < nc) {
+        atomicAdd(&sh[rank_bucket<F64>(kk[u], tmin)], 1u);
+        if (!F64) kc[e] = unsigned(kk[u]);
+      }
+    }
+  }
+  __syncthreads();
+  // exclusive prefix over the buckets: 4 per thread, then warps, then CTA
+  {
+    const uint4 c4 = reinterpret_cast<const uint4*>(sh)[tid];
+    const unsigned own = c4.x + c4.y + c4.z + c4.w;
+    unsigned inc = own;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned o = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += o;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned v = wsum[lane];
+      unsigned x = v;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned o = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += o;
+      }
+      wsum[lane] = x - v;
+    }
+    __syncthreads();
+    const unsigned b0 = wsum[warp] + inc - own;
+    uint4 st4;
+    st4.x = b0;
+    st4.y = b0 + c4.x;
+    st4.z = st4.y + c4.y;
+    st4.w = st4.z + c4.z;
+    reinterpret_cast<uint4*>(bstart)[tid] = st4;
+  }
+  __syncthreads();
+  // the members of this CTA's buckets into shared memory; ties ranked by
+  // position are written at once by one CTA each
+  for (unsigned e0 = 0; e0 < nc; e0 += 4 * kRThreads) {
+    unsigned long long kk[4], ii[4];
+    unsigned ff[4];
+    bool mine[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned e = e0 + u * kRThreads + tid;
+      ff[u] = e < nc ? at(e) : 0u;
+      mine[u] = false;
+      if (e < nc) {
+        kk[u] = F64 ? __ldcg(w.cand_key + ff[u]) : (unsigned long long)kc[e];
+        if (tie_by_pos && kk[u] == tie_key) {
+          mine[u] = ff[u] % nb == blockIdx.x && ff[u] < take;
+        } else {
+          const unsigned q = rank_bucket<F64>(kk[u], tmin);
+          mine[u] = (bstart[q] * nb) / nc == blockIdx.x;
+        }
+        if (mine[u]) ii[u] = __ldcg(w.cand_idx + ff[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!mine[u]) continue;
+      if (tie_by_pos && kk[u] == tie_key) {
+        bins_out[ff[u]] = ii[u];
+        probs_out[ff[u]] = value_of_key<F64>(kk[u]);
+        continue;
+      }
+      const unsigned q = rank_bucket<F64>(kk[u], tmin);
+      const unsigned pos = atomicAdd(&lcount, 1u);        // < nc <= kMaxSort
+      if constexpr (F64) {
+        lk[pos] = kk[u];
+        li[pos] = ii[u];
+      } else {
+        lk[pos] = (kk[u] << 32) | (0xffffffffull - ii[u]);
+      }
+      lq[pos] = q;
+    }
+  }
+  __syncthreads();
+  const unsigned L = lcount;
+  for (unsigned i = tid; i < L; i += kRThreads) {
+    const unsigned long long ki = lk[i];
+    const unsigned long long xi = F64 ? li[i] : 0ull;
+    const unsigned q = lq[i];
+    unsigned c = bstart[q];
+    for (unsigned j = 0; j < L; ++j) {
+      if (lq[j] != q) continue;
+      if constexpr (F64)
+        c += (lk[j] > ki) || (lk[j] == ki && li[j] < xi);
+      else
+        c += lk[j] > ki;
+    }
+    if (c < take) {
+      if constexpr (F64) {
+        bins_out[c] = xi;
+        probs_out[c] = value_of_key<F64>(ki);
+      } else {
+        bins_out[c] = 0xffffffffull - (ki & 0xffffffffull);
+        probs_out[c] = value_of_key<F64>(ki >> 32);
+      }
+    }
+  }
+}
+
+// TAIL: the input is not read but computed -- the query's contraction
+// steps before the last run first (tail_pre_steps), then every CTA
+// computes its slice of the last step's bins itself (each bin one inner
+// product over the shared index, Y staged in shared memory, the FP32
+// multiply-adds in the order of the per-step kernel, so the bins are the
+// same bit for bit), writes them to T.P in bin order and keeps their keys
+// -- the bins are written once and never read back.
+template <bool F64, bool TAIL>
 __global__ void __launch_bounds__(kRThreads, 1)
 select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, unsigned long long key_thr64, int k,
-                       int cap, ResWork w, unsigned long long* bins_out, double* probs_out, int* n_found, int* err) {
+                       int cap, ResWork w, unsigned long long* bins_out, double* probs_out, int* n_found, int* err,
+                       TailArgs Tp) {
+  static_assert(!(F64 && TAIL), "the fused launch computes FP32 bins");
+  // the fused launch reads its arguments from shared memory (one parallel
+  // copy of the parameter block instead of scattered parameter loads)
+  const TailArgs* tq = &Tp;
+  if constexpr (TAIL) {
+    __shared__ __align__(16) TailArgs tsh;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&Tp);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&tsh);
+    for (int i = int(threadIdx.x); i < int(sizeof(TailArgs) / 8); i += kRThreads) dst[i] = src[i];
+    __syncthreads();
+    tq = &tsh;
+  }
+  const TailArgs& T = *tq;
   pdl_wait();      // the previous kernel on the stream has completed
   pdl_trigger();   // the next one may start launching
   // Shared memory holds one 32-bit word per value: the whole key of an FP32
@@ -1026,6 +1455,14 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
   };
   unsigned bar = 0;                                 // barriers met so far
   bool ok = true;
+  // the control word and the first two passes' histograms are cold at the
+  // start of a step: fetch them into L2 while the slice is produced
+  if (tid < 2) {
+    const unsigned line = blockIdx.x + unsigned(tid) * nb;          // 32 counters per 128-byte line
+    if (line < unsigned(2 * kRRadix / 32)) prefetch_l2(w.hist + size_t(line) * 32);
+  } else if (tid == 2 && blockIdx.x == 0) {
+    prefetch_l2(w.ctl);
+  }
   if (tid == 0) {
     st.prefix = 0ull;
     st.krem = (unsigned long long)k;
@@ -1033,12 +1470,137 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
     st.lo = KB;
     st.done = 0;
   }
+  if constexpr (TAIL) {
+    if (T.n_levels > 0) ok = tail_pre_steps(T, w, nb, bar, reinterpret_cast<float*>(rsm + kRHistBytes));
+  }
   for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
   __syncthreads();
   // pass 0 with the load: keys of excluded values (NaN or below the
   // threshold) are stored as 0, which no included value has (the smallest
   // included key word is 0x007fffff for FP32, 0x000fffff for FP64)
-  {
+  if constexpr (TAIL) {
+    __shared__ float2 tred[kRWarps];
+    // the thread's bins summed as an unevaluated FP32 pair (hi + lo, each
+    // addition error-free by Knuth's TwoSum), reduced over the CTA as pairs
+    // and converted to FP64 once: the FP64 pipe of this GPU is too narrow
+    // for one FP64 addition per bin
+    float s_hi = 0.f, s_lo = 0.f;
+    if (ok) {
+      // stage Y: row j at ys + j * ystride (16-byte aligned rows); and, when
+      // the slice's X rows are a range that fits, those rows at xs
+      float* ys = reinterpret_cast<float*>(rsm + tail_y_offset(per));
+      float* xs = ys + T.N * T.ystride;
+      const int kd = T.Kd;
+      const int kd_log2 = __ffs(kd) - 1;
+      const int ystride = T.ystride;
+      const uint32_t ustart = uint32_t(start);
+      const bool xst = T.x_rows > 0 && cnt > 0;
+      const uint32_t x0 = xst ? tail_pext(ustart, T.rows) : 0u;
+      const int nx = xst ? int(tail_pext(ustart + uint32_t(cnt) - 1u, T.rows) - x0) + 1 : 0;
+      // four loads in flight per thread and round; every CTA starts at its
+      // own offset, so that the CTAs (which all read the same rows) spread
+      // their requests over the L2 slices instead of queueing on the same
+      // lines at the same time
+      auto stage = [&](const float* src, float* dst, int rows) {
+        if (kd >= 4) {
+          const int q_log2 = kd_log2 - 2;
+          const unsigned tot4 = unsigned(rows) << q_log2;
+          const unsigned rot = (blockIdx.x * tot4) / nb;
+          const float4* s4 = reinterpret_cast<const float4*>(src);
+          for (unsigned e0 = 0; e0 < tot4; e0 += 4 * kRThreads) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const unsigned e = e0 + u * kRThreads + tid;
+              unsigned f = e + rot;
+              if (f >= tot4) f -= tot4;
+              if (e < tot4) v[u] = __ldcg(s4 + f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const unsigned e = e0 + u * kRThreads + tid;
+              unsigned f = e + rot;
+              if (f >= tot4) f -= tot4;
+              if (e < tot4) *reinterpret_cast<float4*>(dst + (f >> q_log2) * ystride + 4 * (f & ((1u << q_log2) - 1))) = v[u];
+            }
+          }
+        } else {
+          for (int e = tid; e < (rows << kd_log2); e += kRThreads)
+            dst[(e >> kd_log2) * ystride + (e & (kd - 1))] = __ldcg(src + e);
+        }
+      };
+      // one contiguous bit run per operand (the usual layout): a shift and
+      // a mask per index
+      const bool runs1 = T.rows.n <= 1 && T.cols.n <= 1;
+      const uint32_t rpos = T.rows.n ? T.rows.pos[0] : 0u, rmask = T.rows.n ? (1u << T.rows.len[0]) - 1u : 0u;
+      const uint32_t cpos = T.cols.n ? T.cols.pos[0] : 0u, cmask = T.cols.n ? (1u << T.cols.len[0]) - 1u : 0u;
+      const float alpha = T.alpha;
+      float* P = T.P;
+      // the bin is r * N + j (Y owns the low bits, X the rest) and a Y row
+      // fits in registers: thread j takes column j for every row of the
+      // slice, Y read once into registers, the slice's X rows from shared
+      // memory -- no staging of Y
+      const bool band = xst && T.rows.n == 1 && T.cols.n == 1 && cpos == 0 && rpos == T.cols.len[0] && kd >= 4 &&
+                        kd <= 16;
+      if (!band) stage(T.Y, ys, int(T.N));
+      if (xst) stage(T.X + (size_t(x0) << kd_log2), xs, nx);
+      __syncthreads();
+      if (band) {
+        const int nbits = T.cols.len[0];
+        const uint32_t ncol = 1u << nbits;
+        const uint32_t r_hi = (ustart + uint32_t(cnt) - 1u) >> nbits;      // x0 = ustart >> nbits
+        const float4* y4 = reinterpret_cast<const float4*>(T.Y);
+        const int q4 = kd >> 2;
+        for (uint32_t j0 = 0; j0 < ncol; j0 += kRThreads) {
+          const uint32_t j = j0 + uint32_t(tid);
+          float4 y[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q < q4 && j < ncol) y[q] = __ldcg(y4 + size_t(j) * q4 + q);
+          for (uint32_t r = x0; r <= r_hi; ++r) {
+            const uint32_t b = (r << nbits) | j;
+            const bool in = j < ncol && b >= ustart && b - ustart < uint32_t(cnt);
+            unsigned kv = 0u;
+            if (in) {
+              const float4* xr = reinterpret_cast<const float4*>(xs + (r - x0) * ystride);
+              float acc = 0.f;
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                if (q < q4) {
+                  const float4 xa = xr[q];
+                  acc = fmaf(xa.x, y[q].x, acc);
+                  acc = fmaf(xa.y, y[q].y, acc);
+                  acc = fmaf(xa.z, y[q].z, acc);
+                  acc = fmaf(xa.w, y[q].w, acc);
+                }
+              }
+              if (kd < 16) acc = fmaf(0.f, 0.f, acc);
+              const float v = acc * alpha;
+              P[b] = v;
+              two_sum_add(s_hi, s_lo, v);
+              const unsigned u = __float_as_uint(v);
+              const bool nan = (u & 0x7fffffffu) > 0x7f800000u;
+              const unsigned kk = unsigned(key_f32(v) >> 32);
+              kv = (!nan && kk >= unsigned(key_thr)) ? kk : 0u;
+              keys[b - ustart] = kv;
+            }
+            warp_hist_add(sh, kv != 0, kv >> (32 - kRBits), lane);
+          }
+        }
+      }
+      if (!band)
+        tail_slice_general(T, ys, xs, x0, xst, ustart, cnt, unsigned(key_thr), keys, sh, s_hi, s_lo);
+    }
+    // the CTA's sum as a pair, then one FP64 value per CTA
+    pair_warp_sum(s_hi, s_lo);
+    if (lane == 0) tred[warp] = make_float2(s_hi, s_lo);
+    __syncthreads();
+    if (warp == 0) {
+      float h = tred[lane].x, l = tred[lane].y;
+      pair_warp_sum(h, l);
+      if (lane == 0 && T.total) T.partials[blockIdx.x] = double(h) + double(l);
+    }
+  } else {
     // the loop bound is the same for the whole CTA: warp_hist_add needs
     // every lane of the warp
     for (int b0 = 0; b0 < cnt; b0 += kRThreads * V) {
@@ -1192,59 +1754,7 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
       }
     }
     __syncthreads();
-    if (done == 3) {
-      // exact ties of the k-th key beyond capacity: ascending bin order,
-      // via per-CTA counts and an ordered scan of each slice
-      const unsigned long long tkey = st.prefix;
-      const unsigned tk_hi = F64 ? unsigned(tkey >> 32) : unsigned(tkey);
-      auto is_tie = [&](int i, unsigned kk) -> bool {
-        if (kk != tk_hi) return false;
-        if constexpr (F64) return low_word(i) == unsigned(tkey);
-        else return true;
-      };
-      unsigned my = 0;
-      for (int i = tid; i < cnt; i += kRThreads) my += is_tie(i, keys[i]);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) my += __shfl_down_sync(0xffffffffu, my, off);
-      if (lane == 0) wcnt[warp] = my;
-      __syncthreads();
-      if (tid == 0) {
-        unsigned c = 0;
-        for (int ww = 0; ww < kRWarps; ++ww) c += wcnt[ww];
-        w.tie_count[blockIdx.x] = c;
-      }
-      ok = res_barrier(w.ctl, 1ull << 32, nb * ++bar) != 0ull;
-      if (ok) {
-        __shared__ unsigned long long tbase;
-        if (tid == 0) {
-          unsigned long long b = 0;
-          for (unsigned r = 0; r < blockIdx.x; ++r) b += __ldcg(w.tie_count + r);
-          tbase = b;
-        }
-        __syncthreads();
-        const unsigned long long need = st.krem, first = st.take - st.krem;
-        unsigned long long run = tbase;
-        for (int i0 = 0; i0 < cnt && run < need; i0 += kRThreads) {
-          const int i = i0 + tid;
-          const bool tie = i < cnt && is_tie(i, keys[i]);
-          const unsigned bal = __ballot_sync(0xffffffffu, tie);
-          if (lane == 0) wcnt[warp] = __popc(bal);
-          __syncthreads();
-          unsigned before = 0, all = 0;
-          for (int ww = 0; ww < kRWarps; ++ww) {
-            if (ww < warp) before += wcnt[ww];
-            all += wcnt[ww];
-          }
-          const unsigned long long rank = run + before + __popc(bal & ((1u << lane) - 1u));
-          if (tie && rank < need) {
-            w.cand_key[first + rank] = tkey;
-            w.cand_idx[first + rank] = start + i;
-          }
-          run += all;
-          __syncthreads();
-        }
-      }
-    }
+    if (done == 3) ok = tie_scan<F64>(w, keys, cnt, start, x, st, wcnt, nb, bar);
     // the last barrier also sums the candidate counts into the low word
     if (ok) {
       const unsigned long long word = res_barrier(w.ctl, (1ull << 32) | cta_taken, nb * ++bar);
@@ -1252,73 +1762,32 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
       nc = word & 0xffffffffull;
     }
   }
+  if constexpr (TAIL) {
+    // the FP64 probability sum, CTA partials in a fixed order, by the last
+    // CTA (which ranks the fewest candidates, if any): every partial was
+    // published before the first grid barrier
+    if (ok && T.total && blockIdx.x == nb - 1 && warp == 0) {
+      double v = 0.0;
+      for (unsigned c = lane; c < nb; c += 32) v += __ldcg(T.partials + c);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) *T.total = v;
+    }
+  }
   if (ok) {
     // the histograms are no longer read by anyone
     for (uint64_t i = uint64_t(blockIdx.x) * kRThreads + tid; i < uint64_t(kRMaxPasses) * kRRadix;
          i += uint64_t(nb) * kRThreads)
       w.hist[i] = 0u;
-    // ranking: CTA r owns a contiguous block of candidates; warp v of it
-    // counts, for owned candidates v, v + 32, ..., the candidates ahead in
-    // the final order over shared-memory tiles of the whole list.  For FP32
-    // keys that order (key descending, bin ascending) is one 64-bit compare
-    // of key << 32 | (2^32 - 1 - bin).
+    // ranking (rank_candidates): the lowest selectable key is the decided
+    // bucket's, or the threshold when every value is taken
     const unsigned long long take = st.take;
     if (st.done == 3) nc += st.krem;
     if (nc > (unsigned long long)kMaxSort) nc = kMaxSort;
-    const unsigned long long per_cta = (nc + nb - 1) / nb;
-    const unsigned long long cb0 = uint64_t(blockIdx.x) * per_cta;
-    const unsigned long long cb1 = cb0 + per_cta < nc ? cb0 + per_cta : nc;
-    if (cb0 < nc) {
-      const int m = int(cb1 - cb0);                   // <= kMaxSort / nb + 1 <= kRRankMax
-      unsigned long long* tk = reinterpret_cast<unsigned long long*>(rsm + kRHistBytes);   // [kRTile]
-      unsigned long long* ti = tk + kRTile;                                                // [kRTile] (FP64)
-      auto packed = [](unsigned long long kk, unsigned long long ii) {
-        return F64 ? kk : ((kk << 32) | (0xffffffffull - ii));
-      };
-      unsigned long long mk[kRRankMax / kRWarps], mi[kRRankMax / kRWarps];
-      unsigned cnt_ahead[kRRankMax / kRWarps];
-#pragma unroll
-      for (int j = 0; j < kRRankMax / kRWarps; ++j) {
-        const int c = warp + j * kRWarps;
-        const bool have = c < m;
-        const unsigned long long kk = have ? __ldcg(w.cand_key + cb0 + c) : 0ull;
-        mi[j] = have ? __ldcg(w.cand_idx + cb0 + c) : 0ull;
-        mk[j] = packed(kk, mi[j]);
-        cnt_ahead[j] = 0u;
-      }
-      for (unsigned long long t0 = 0; t0 < nc; t0 += kRTile) {
-        const int len = int(nc - t0 < kRTile ? nc - t0 : kRTile);
-        __syncthreads();
-        for (int e = tid; e < len; e += kRThreads) {
-          const unsigned long long kk = __ldcg(w.cand_key + t0 + e), ii = __ldcg(w.cand_idx + t0 + e);
-          tk[e] = packed(kk, ii);
-          if (F64) ti[e] = ii;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < kRRankMax / kRWarps; ++j) {
-          if (warp + j * kRWarps >= m) break;
-          unsigned c = 0;
-          for (int e = lane; e < len; e += 32) {
-            if constexpr (F64)
-              c += (tk[e] > mk[j]) || (tk[e] == mk[j] && ti[e] < mi[j]);
-            else
-              c += tk[e] > mk[j];
-          }
-          cnt_ahead[j] += c;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < kRRankMax / kRWarps; ++j) {
-        unsigned c = cnt_ahead[j];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
-        if (lane == 0 && warp + j * kRWarps < m && c < take) {
-          bins_out[c] = mi[j];
-          probs_out[c] = value_of_key<F64>(F64 ? mk[j] : (mk[j] >> 32));
-        }
-      }
-    }
+    const unsigned long long tmin = st.done == 2 ? key_thr : st.prefix;
+    if (nc > 0)
+      rank_candidates<F64>(w, unsigned(nc), take, tmin, st.done == 3, st.prefix, rsm, sh, wcnt, bins_out,
+                           probs_out);
     if (blockIdx.x == 0 && tid == 0) *n_found = int(take);
   } else if (tid == 0 && err) {
     atomicExch(err, 1);
@@ -1386,13 +1855,15 @@ int select_resident_grid() {
     int dev = 0, sms = 152, p32 = 0, p64 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(select_resident_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmemMax);
-    cudaFuncSetAttribute(select_resident_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmemMax);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, select_resident_kernel<false>, kRThreads, kRSmemMax);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, select_resident_kernel<true>, kRThreads, kRSmemMax);
-    int r = (p32 >= 1 && p64 >= 1) ? sms : 0;
+    cudaFuncSetAttribute(select_resident_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmemMax);
+    cudaFuncSetAttribute(select_resident_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmemMax);
+    cudaFuncSetAttribute(select_resident_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRSmemMax);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p32, select_resident_kernel<false, false>, kRThreads, kRSmemMax);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p64, select_resident_kernel<true, false>, kRThreads, kRSmemMax);
+    int pt = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pt, select_resident_kernel<false, true>, kRThreads, kRSmemMax);
+    int r = (p32 >= 1 && p64 >= 1 && pt >= 1) ? sms : 0;
     if (r > select_coop_grid()) r = select_coop_grid();   // tie counts live in the streaming part
-    if (r * kRRankMax < kMaxSort) r = 0;                   // each CTA ranks at most kRRankMax candidates
     return r;
   }();
   return g;
@@ -1405,11 +1876,30 @@ size_t select_resident_smem(uint64_t n, int is_f64, int grid, uint64_t* per) {
   if (grid <= 0) return 0;
   uint64_t p = (n + uint64_t(grid) - 1) / uint64_t(grid);
   p = (p + 3) & ~uint64_t(3);
-  const uint64_t region = p * 4;                   // one 32-bit key word per value
-  const uint64_t need = uint64_t(kRHistBytes) + (region > uint64_t(kRRegionMin) ? region : uint64_t(kRRegionMin));
+  uint64_t region = p * 4;                         // one 32-bit key word per value
+  // room for the ranking's bucket starts and owned candidates
+  const uint64_t rank = rank_region_bytes(is_f64 != 0);
+  if (region < rank) region = rank;
+  const uint64_t need = uint64_t(kRHistBytes) + region;
   if (per) *per = p;
   return need <= uint64_t(kRSmemMax) ? size_t(need) : 0;
 }
+
+namespace {
+// The resident kernel's part of the shared selection workspace.
+ResWork resident_work(void* work) {
+  char* p = static_cast<char*>(work);
+  ResWork w;
+  w.ctl = reinterpret_cast<unsigned long long*>(p + kRCtlOffset);
+  w.cand_key = reinterpret_cast<unsigned long long*>(p + sizeof(unsigned long long) * 32);
+  w.cand_idx = w.cand_key + kMaxSort;
+  // the streaming kernel's tie counts (layout of launch_select_coop)
+  w.tie_count = reinterpret_cast<unsigned*>(p + sizeof(unsigned long long) * 32 + 2 * sizeof(unsigned long long) * kMaxSort +
+                                            sizeof(unsigned) * kCPasses * kCopies * kCRadix + sizeof(unsigned) * kMaxSort);
+  w.hist = reinterpret_cast<unsigned*>(p + ((coop_part_bytes(select_coop_grid()) + 255) & ~size_t(255)));
+  return w;
+}
+}  // namespace
 
 cudaError_t launch_select_resident(void* work, int grid, const void* x, int is_f64, uint64_t n, int k,
                                    double threshold, unsigned long long* bins_out, double* probs_out, int* n_found,
@@ -1423,22 +1913,66 @@ cudaError_t launch_select_resident(void* work, int grid, const void* x, int is_f
   // kMaxSort candidates, which costs less than another digit pass and its
   // grid barrier
   const int cap = kMaxSort - k;
-  char* p = static_cast<char*>(work);
-  ResWork w;
-  w.ctl = reinterpret_cast<unsigned long long*>(p + kRCtlOffset);
-  w.cand_key = reinterpret_cast<unsigned long long*>(p + sizeof(unsigned long long) * 32);
-  w.cand_idx = w.cand_key + kMaxSort;
-  // the streaming kernel's tie counts (layout of launch_select_coop)
-  w.tie_count = reinterpret_cast<unsigned*>(p + sizeof(unsigned long long) * 32 + 2 * sizeof(unsigned long long) * kMaxSort +
-                                            sizeof(unsigned) * kCPasses * kCopies * kCRadix + sizeof(unsigned) * kMaxSort);
-  w.hist = reinterpret_cast<unsigned*>(p + ((coop_part_bytes(select_coop_grid()) + 255) & ~size_t(255)));
+  ResWork w = resident_work(work);
   const int aligned = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
   const unsigned long long kt = threshold_key(is_f64, threshold);
+  const TailArgs none{};
   if (is_f64)
-    return launch_k(select_resident_kernel<true>, dim3(grid), dim3(kRThreads), smem, s, true, x, aligned, n, per, kt,
-                    k, cap, w, bins_out, probs_out, n_found, err);
-  return launch_k(select_resident_kernel<false>, dim3(grid), dim3(kRThreads), smem, s, true, x, aligned, n, per, kt,
-                  k, cap, w, bins_out, probs_out, n_found, err);
+    return launch_k(select_resident_kernel<true, false>, dim3(grid), dim3(kRThreads), smem, s, true, x, aligned, n,
+                    per, kt, k, cap, w, bins_out, probs_out, n_found, err, none);
+  return launch_k(select_resident_kernel<false, false>, dim3(grid), dim3(kRThreads), smem, s, true, x, aligned, n,
+                  per, kt, k, cap, w, bins_out, probs_out, n_found, err, none);
+}
+
+// Rows of X a slice of `per` bins needs when they form a range (x_range):
+// at most ceil(per / N) + 1.
+int64_t tail_x_rows(const TailArgs& t, uint64_t per) {
+  if (!t.x_range || t.N < 1) return 0;
+  const int64_t r = int64_t((per + uint64_t(t.N) - 1) / uint64_t(t.N)) + 1;
+  return r < t.M ? r : t.M;
+}
+
+namespace {
+// Shared memory of the fused launch: histogram, slice keys (or the stage of
+// the steps before the last), staged Y, staged X rows when they form a
+// range and fit, at least the ranking's region.  0: Y does not fit.
+size_t tail_layout(uint64_t n, const TailArgs& t, int grid, uint64_t* per, int* x_rows) {
+  uint64_t p = 0;
+  if (!select_resident_smem(n, 0, grid, &p)) return 0;
+  const uint64_t y_end = tail_y_offset(p) + uint64_t(t.N) * uint64_t(t.ystride) * 4;
+  if (y_end > uint64_t(kRSmemMax)) return 0;
+  const int64_t xr = tail_x_rows(t, p);
+  const uint64_t x_end = y_end + uint64_t(xr) * uint64_t(t.ystride) * 4;
+  const bool stage_x = xr > 0 && x_end <= uint64_t(kRSmemMax);
+  uint64_t need = stage_x ? x_end : y_end;
+  const uint64_t rank = uint64_t(kRHistBytes) + rank_region_bytes(false);
+  if (need < rank) need = rank;
+  if (need > uint64_t(kRSmemMax)) return 0;
+  if (per) *per = p;
+  if (x_rows) *x_rows = stage_x ? int(xr) : 0;
+  return size_t(need);
+}
+}  // namespace
+
+size_t select_tail_smem(uint64_t n, const TailArgs& t, int grid, uint64_t* per) {
+  return tail_layout(n, t, grid, per, nullptr);
+}
+
+cudaError_t launch_select_tail(void* work, int grid, const TailArgs& t, uint64_t n, int k, double threshold,
+                               unsigned long long* bins_out, double* probs_out, int* n_found, int* err,
+                               cudaStream_t s) {
+  if (k < 1 || k > kSelectMaxK) return cudaErrorInvalidValue;
+  if (t.Kd < 1 || (t.Kd & (t.Kd - 1)) || t.n_levels < 0 || t.n_levels > kTailMaxLevels) return cudaErrorInvalidValue;
+  if (t.rows.n > kTailMaxRuns || t.cols.n > kTailMaxRuns || (t.total && !t.partials)) return cudaErrorInvalidValue;
+  uint64_t per = 0;
+  TailArgs ta = t;
+  const size_t smem = tail_layout(n, t, grid, &per, &ta.x_rows);
+  if (!smem) return cudaErrorInvalidValue;
+  const int cap = kMaxSort - k;
+  ResWork w = resident_work(work);
+  const unsigned long long kt = threshold_key(0, threshold);
+  return launch_k(select_resident_kernel<false, true>, dim3(grid), dim3(kRThreads), smem, s, true,
+                  static_cast<const void*>(nullptr), 0, n, per, kt, k, cap, w, bins_out, probs_out, n_found, err, ta);
 }
 
 cudaError_t launch_select_coop(void* work, int grid, const void* x, int is_f64, uint64_t n, int k, double threshold,
