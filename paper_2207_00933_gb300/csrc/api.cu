@@ -1241,8 +1241,11 @@ bool build_attr_merge(const Circuit& c, const Query& q, const Plan& P, const voi
       *why = "a subcircuit's attribution tile does not fit shared memory";
       return false;
     }
-    // more, smaller tiles while a subcircuit has few (keep 8 consecutive reads)
-    while (L1 > 3 && ((int64_t(1) << (a - L1)) << (2 * kout)) < 64) --L1;
+    // more, smaller tiles while a subcircuit has few: a tile's reads are
+    // latency-bound chains of 4^kin 2^(L1 + m) 2^kout loads over 256
+    // threads, so a small subcircuit spread over more CTAs finishes sooner
+    // (runs of 2 consecutive reads at least)
+    while (L1 > 1 && ((int64_t(1) << (a - L1)) << (2 * kout)) < 256) --L1;
     AttrMergeLaunch& L = launches->back();
     AttrMergeDesc& d = L.d[L.n];
     d.p = src[i];

@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(256, 4) attr_merge_kernel(AttrMergeLaunch L, i
   extern __shared__ float val[];
   __shared__ AttrMergeDesc d;
   __shared__ AttrTileCtx tc;
-  __shared__ int cur, changed;
+  __shared__ int cur, changed, sdi;
   if (threadIdx.x == 0) cur = -1;
   __syncthreads();
   for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
@@ -676,20 +676,23 @@ __global__ void __launch_bounds__(256, 4) attr_merge_kernel(AttrMergeLaunch L, i
       for (int i = 1; i < kAttrPerLaunch; ++i)
         if (i < L.n && L.d[i].block_begin <= tile) di = i;
       changed = di != cur;
-      if (changed) {
-        switch (di) {
-#define SQC_ATTR_CASE(k) case k: d = L.d[k]; break;
-          SQC_ATTR_CASE(0) SQC_ATTR_CASE(1) SQC_ATTR_CASE(2) SQC_ATTR_CASE(3) SQC_ATTR_CASE(4) SQC_ATTR_CASE(5)
-          SQC_ATTR_CASE(6) SQC_ATTR_CASE(7) SQC_ATTR_CASE(8) SQC_ATTR_CASE(9) SQC_ATTR_CASE(10) SQC_ATTR_CASE(11)
-          SQC_ATTR_CASE(12) SQC_ATTR_CASE(13) SQC_ATTR_CASE(14) SQC_ATTR_CASE(15)
-#undef SQC_ATTR_CASE
-          default: break;
-        }
-        cur = di;
-      }
+      sdi = di;
+      cur = di;
     }
     __syncthreads();
     if (changed) {
+      // the descriptor copied by all threads at once (its parameter words
+      // are fetched together), and its layout maps -- read at the end of
+      // the tile, cold at the start of a step -- requested into L2 now
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&L.d[sdi]);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&d);
+      for (int i = int(threadIdx.x); i < int(sizeof(AttrMergeDesc) / 8); i += int(blockDim.x)) dst[i] = src[i];
+      __syncthreads();
+      const int rows_lines = int(((int64_t(1) << (2 * (d.kin + d.kout))) + 15) >> 4);
+      const int cols_lines = int(((int64_t(1) << d.a) + 15) >> 4);
+      const int t = int(threadIdx.x);
+      if (t < 64 && t < rows_lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(d.rowmap + 16 * t));
+      else if (t >= 64 && t < 128 && t - 64 < cols_lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(d.colmap + 16 * (t - 64)));
       fill_tile_ctx(d, tc);
       __syncthreads();
     }
