@@ -1250,21 +1250,25 @@ __device__ __forceinline__ unsigned rank_bucket(unsigned long long key, unsigned
 }
 
 // Bytes of shared memory (after the histogram) the ranking needs: bucket
-// starts and, per owned candidate, its key (FP32: packed with the bin), bin
-// (FP64) and bucket; FP32 also keeps every candidate's key word between
-// its two passes over the list.
+// starts and the candidates grouped by bucket (FP32: the key packed with
+// the bin; FP64: key and bin), FP32 also every candidate's key word kept
+// between the passes over the list.
 __host__ __device__ constexpr unsigned rank_region_bytes(bool f64) {
-  return unsigned(kRRadix) * 4u + unsigned(kMaxSort) * (f64 ? 20u : 16u);
+  return unsigned(kRRadix) * 4u + unsigned(kMaxSort) * (f64 ? 16u : 12u);
 }
 
 // Final order of the nc candidates (value descending, bin ascending) and
 // the first `take` written at their ranks.  Every CTA counts the candidates
-// per bucket (rank_bucket: bucket order is key order), then owns the
-// buckets whose first position falls in its share of [0, nc) and ranks
-// their members among themselves: rank = candidates in earlier buckets +
-// members of the same bucket ahead.  With exact ties of the k-th key beyond
-// capacity (tie_by_pos), the ties were written in ascending bin order right
-// after every larger value, so their rank is their position.
+// per bucket (rank_bucket: bucket order is key order) and groups the whole
+// list by bucket in shared memory; then each CTA ranks its share of the
+// list, a warp per candidate: rank = candidates in earlier
+// buckets + members of its bucket ahead of it.  The work per CTA is its
+// share times the bucket sizes, so a bucket of thousands of exact ties
+// costs every CTA a little rather than one CTA a lot.  (Ownership is by
+// position in the candidate list, which every CTA sees alike.)  With exact ties of
+// the k-th key beyond capacity (tie_by_pos), those ties were written in
+// ascending bin order right after every larger value: their rank is their
+// position in the list.
 template <bool F64>
 __device__ __forceinline__ void rank_candidates(const ResWork& w, unsigned nc, unsigned long long take,
                                                 unsigned long long tmin, bool tie_by_pos,
@@ -1273,13 +1277,10 @@ __device__ __forceinline__ void rank_candidates(const ResWork& w, unsigned nc, u
   const unsigned nb = gridDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned* bstart = reinterpret_cast<unsigned*>(rsm + kRHistBytes);                  // [kRRadix]
-  unsigned long long* lk = reinterpret_cast<unsigned long long*>(bstart + kRRadix);     // [kMaxSort]
-  unsigned long long* li = lk + kMaxSort;                                               // [kMaxSort] (FP64)
-  unsigned* lq = reinterpret_cast<unsigned*>(F64 ? li + kMaxSort : li);                 // [kMaxSort]
-  unsigned* kc = lq + kMaxSort;                                                         // [kMaxSort] (FP32)
-  __shared__ unsigned lcount;
+  unsigned long long* gk = reinterpret_cast<unsigned long long*>(bstart + kRRadix);     // [kMaxSort]
+  unsigned long long* gi = gk + kMaxSort;                                               // [kMaxSort] (FP64)
+  unsigned* kc = reinterpret_cast<unsigned*>(F64 ? gi + kMaxSort : gi);                 // [kMaxSort] (FP32)
   for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
-  if (tid == 0) lcount = 0u;
   __syncthreads();
   // the CTAs read the same list: each starts at its own offset
   const unsigned rot = (blockIdx.x * nc) / nb;
@@ -1331,71 +1332,72 @@ __device__ __forceinline__ void rank_candidates(const ResWork& w, unsigned nc, u
     st4.z = st4.y + c4.y;
     st4.w = st4.z + c4.z;
     reinterpret_cast<uint4*>(bstart)[tid] = st4;
+    reinterpret_cast<uint4*>(sh)[tid] = st4;      // the grouping cursors
   }
   __syncthreads();
-  // the members of this CTA's buckets into shared memory; ties ranked by
-  // position are written at once by one CTA each
+  // the whole list grouped by bucket (order within a bucket is arbitrary:
+  // ranks compare keys and bins)
   for (unsigned e0 = 0; e0 < nc; e0 += 4 * kRThreads) {
     unsigned long long kk[4], ii[4];
-    unsigned ff[4];
-    bool mine[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const unsigned e = e0 + u * kRThreads + tid;
-      ff[u] = e < nc ? at(e) : 0u;
-      mine[u] = false;
       if (e < nc) {
-        kk[u] = F64 ? __ldcg(w.cand_key + ff[u]) : (unsigned long long)kc[e];
-        if (tie_by_pos && kk[u] == tie_key) {
-          mine[u] = ff[u] % nb == blockIdx.x && ff[u] < take;
-        } else {
-          const unsigned q = rank_bucket<F64>(kk[u], tmin);
-          mine[u] = (bstart[q] * nb) / nc == blockIdx.x;
-        }
-        if (mine[u]) ii[u] = __ldcg(w.cand_idx + ff[u]);
+        const unsigned f = at(e);
+        kk[u] = F64 ? __ldcg(w.cand_key + f) : (unsigned long long)kc[e];
+        ii[u] = __ldcg(w.cand_idx + f);
       }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (!mine[u]) continue;
-      if (tie_by_pos && kk[u] == tie_key) {
-        bins_out[ff[u]] = ii[u];
-        probs_out[ff[u]] = value_of_key<F64>(kk[u]);
-        continue;
-      }
-      const unsigned q = rank_bucket<F64>(kk[u], tmin);
-      const unsigned pos = atomicAdd(&lcount, 1u);        // < nc <= kMaxSort
+      const unsigned e = e0 + u * kRThreads + tid;
+      if (e >= nc) continue;
+      const unsigned pos = atomicAdd(&sh[rank_bucket<F64>(kk[u], tmin)], 1u);
       if constexpr (F64) {
-        lk[pos] = kk[u];
-        li[pos] = ii[u];
+        gk[pos] = kk[u];
+        gi[pos] = ii[u];
       } else {
-        lk[pos] = (kk[u] << 32) | (0xffffffffull - ii[u]);
+        gk[pos] = (kk[u] << 32) | (0xffffffffull - ii[u]);
       }
-      lq[pos] = q;
     }
   }
   __syncthreads();
-  const unsigned L = lcount;
-  for (unsigned i = tid; i < L; i += kRThreads) {
-    const unsigned long long ki = lk[i];
-    const unsigned long long xi = F64 ? li[i] : 0ull;
-    const unsigned q = lq[i];
-    unsigned c = bstart[q];
-    for (unsigned j = 0; j < L; ++j) {
-      if (lq[j] != q) continue;
+  // this CTA's share of the candidate list (by list position, the same in
+  // every CTA; the order inside a grouped bucket differs between CTAs), a
+  // warp per candidate
+  const unsigned per = (nc + nb - 1) / nb;
+  const unsigned p0 = blockIdx.x * per, p1 = p0 + per < nc ? p0 + per : nc;
+  for (unsigned f = p0 + unsigned(warp); f < p1; f += kRWarps) {
+    const unsigned long long key = __ldcg(w.cand_key + f);
+    const unsigned long long bin = __ldcg(w.cand_idx + f);
+    if (tie_by_pos && key == tie_key) continue;     // written by position below
+    const unsigned long long kp = F64 ? key : ((key << 32) | (0xffffffffull - bin));
+    const unsigned long long xp = F64 ? bin : 0ull;
+    const unsigned q = rank_bucket<F64>(key, tmin);
+    const unsigned b = bstart[q], e = sh[q];          // the bucket's segment
+    unsigned c = 0;
+    for (unsigned j = b + unsigned(lane); j < e; j += 32) {
       if constexpr (F64)
-        c += (lk[j] > ki) || (lk[j] == ki && li[j] < xi);
+        c += (gk[j] > kp) || (gk[j] == kp && gi[j] < xp);
       else
-        c += lk[j] > ki;
+        c += gk[j] > kp;
     }
-    if (c < take) {
-      if constexpr (F64) {
-        bins_out[c] = xi;
-        probs_out[c] = value_of_key<F64>(ki);
-      } else {
-        bins_out[c] = 0xffffffffull - (ki & 0xffffffffull);
-        probs_out[c] = value_of_key<F64>(ki >> 32);
-      }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
+    const unsigned rank = b + c;
+    if (lane == 0 && rank < take) {
+      bins_out[rank] = bin;
+      probs_out[rank] = value_of_key<F64>(key);
+    }
+  }
+  if (tie_by_pos) {
+    // ties written at their list positions (ascending bins after every
+    // larger value), each by one CTA
+    for (unsigned f = blockIdx.x + nb * unsigned(tid); f < nc && f < take; f += nb * kRThreads) {
+      const unsigned long long kk = __ldcg(w.cand_key + f);
+      if (kk != tie_key) continue;
+      bins_out[f] = __ldcg(w.cand_idx + f);
+      probs_out[f] = value_of_key<F64>(kk);
     }
   }
 }
