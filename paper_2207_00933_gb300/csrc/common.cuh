@@ -48,6 +48,18 @@ __device__ __forceinline__ float pow2_to_float(double d) {
   return __uint_as_float(unsigned(u >> 63) << 31 | unsigned(e + 127) << 23);
 }
 
+// s_hi + s_lo += v with the rounding error of the high part kept (Knuth's
+// TwoSum: t + e = s_hi + v exactly).  Sums of FP32 values kept as such a
+// pair and converted to FP64 once cost no FP64 instruction per value (the
+// FP64 pipe of this GPU is narrow).
+__device__ __forceinline__ void two_sum_add(float& s_hi, float& s_lo, float v) {
+  const float t = s_hi + v;
+  const float bp = t - s_hi;
+  const float ap = t - bp;
+  s_lo += (s_hi - ap) + (v - bp);
+  s_hi = t;
+}
+
 // Write one result element in the destination's number format: FP32, FP64,
 // or three BF16 planes hi + mid + lo (each the round-to-nearest of what the
 // previous planes left), the operand format of the split-BF16 steps.

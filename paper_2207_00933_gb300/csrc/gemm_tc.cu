@@ -295,17 +295,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // Store 16 consecutive columns of one output row.  `contig`: the columns'
 // offsets are consecutive and 16-byte aligned, so vector stores are used.
+// 32 bytes from registers to global memory in one 256-bit store (a whole
+// sector: a lane's row segment no longer reaches L2 as two half-sector
+// writes).  p must be 32-byte aligned.
+__device__ __forceinline__ void st_v8(float* p, const float* f) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(f[0]), "f"(f[1]), "f"(f[2]),
+               "f"(f[3]), "f"(f[4]), "f"(f[5]), "f"(f[6]), "f"(f[7])
+               : "memory");
+}
+__device__ __forceinline__ void st_v4d(double* p, double x0, double x1, double x2, double x3) {
+  asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(x0), "d"(x1), "d"(x2), "d"(x3) : "memory");
+}
+
 __device__ __forceinline__ void store16(const GemmTcArgs& a, uint64_t off, bool contig, const float* f,
                                         const uint64_t* colmap, int64_t col0, uint64_t rbase, int ncols) {
   if (contig && ncols == 16) {
     if (a.kind == OUT_F32) {
-      float4* p = reinterpret_cast<float4*>(static_cast<float*>(a.C) + off);
+      float* c = static_cast<float*>(a.C) + off;
+      if ((reinterpret_cast<uintptr_t>(c) & 31) == 0) {
+        st_v8(c, f);
+        st_v8(c + 8, f + 8);
+        return;
+      }
+      float4* p = reinterpret_cast<float4*>(c);
 #pragma unroll
       for (int q = 0; q < 4; ++q) p[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
       return;
     }
     if (a.kind == OUT_F64) {
-      double2* p = reinterpret_cast<double2*>(static_cast<double*>(a.C) + off);
+      double* c = static_cast<double*>(a.C) + off;
+      if ((reinterpret_cast<uintptr_t>(c) & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          st_v4d(c + 4 * q, f2d(f[4 * q]), f2d(f[4 * q + 1]), f2d(f[4 * q + 2]), f2d(f[4 * q + 3]));
+        return;
+      }
+      double2* p = reinterpret_cast<double2*>(c);
 #pragma unroll
       for (int q = 0; q < 8; ++q) p[q] = make_double2(f2d(f[2 * q]), f2d(f[2 * q + 1]));
       return;
@@ -479,6 +504,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
   const uint32_t tmem = *tmem_slot;
 
   double sum_d = 0.0;
+  float sum_hi = 0.f, sum_lo = 0.f;       // plain FP32 groups, as an FP32 pair
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: one continuous ring of stages across all units
@@ -658,12 +684,13 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
               const uint64_t c_first = cb[2 * i + h];
               const bool contig = a.contig16 && ncols == 16;
               if (plain) {
-                // probability check: the 16 values summed in FP32, the groups in FP64
+                // probability check: the 16 values summed in FP32, the groups
+                // added into an FP32 pair (no FP64 instruction per group)
                 float cs = 0.f;
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
                   if (j < ncols) cs += f[j];
-                sum_d += double(cs);
+                two_sum_add(sum_hi, sum_lo, cs);
                 store16(a, rbase + c_first, contig, f, a.colmap, col0, rbase, ncols);
               } else {
                 const double sv = add16(a, rbase + c_first, contig, f, a.colmap, col0, rbase, ncols, load_old);
@@ -698,7 +725,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                    : "memory");
   }
   if (failed && threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
-  if (a.partials) finish_total(sum_d, a.partials, a.counter, a.total, red);
+  if (a.partials) finish_total(sum_d + (double(sum_hi) + double(sum_lo)), a.partials, a.counter, a.total, red);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

@@ -992,16 +992,6 @@ __device__ __forceinline__ double value_of_key(unsigned long long key) {
   }
 }
 
-// s_hi + s_lo += v with the rounding error of the high part kept (Knuth's
-// TwoSum: t + e = s_hi + v exactly).
-__device__ __forceinline__ void two_sum_add(float& s_hi, float& s_lo, float v) {
-  const float t = s_hi + v;
-  const float bp = t - s_hi;
-  const float ap = t - bp;
-  s_lo += (s_hi - ap) + (v - bp);
-  s_hi = t;
-}
-
 // Sum of the (hi, lo) pairs of a warp, in every lane (butterfly order).
 __device__ __forceinline__ void pair_warp_sum(float& h, float& l) {
 #pragma unroll

@@ -257,6 +257,19 @@ def test_top_bins_ties_and_edges(ctx, dtype):
         assert m == eb.size
         assert b[:m].cpu().numpy().tolist() == eb.tolist()
         assert np.array_equal(v[:m].cpu().numpy(), ev)
+    # a group of exact ties at the top that fits the candidate capacity
+    # (ranked by bin inside one bucket), above a continuous tail
+    y = rng.random(1 << 20).astype(dtype) * 0.5
+    y[rng.choice(y.size, 2000, replace=False)] = 3.0
+    yd = torch.from_numpy(y).cuda()
+    for k, thr in ((1024, -math.inf), (2000, -math.inf), (2048, -math.inf), (7, 3.0)):
+        b, v, nf = ctx.top_bins(qid, yd, k, thr)
+        torch.cuda.synchronize()
+        eb, ev = O.top_bins(y.astype(np.float64), k, thr)
+        m = int(nf.item())
+        assert m == eb.size
+        assert b[:m].cpu().numpy().tolist() == eb.tolist()
+        assert np.array_equal(v[:m].cpu().numpy(), ev)
     # empty and tiny inputs
     for m in (1, 3):
         y = torch.from_numpy(x[:m].copy()).cuda()
