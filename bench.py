@@ -53,7 +53,9 @@ FALLBACK_HBM_GBS = 6800.0
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 # `bench.py --steps 3 --warmup 3 --no-extras --no-cpu-baseline` on this
 # workload; to be re-taken (or dropped) whenever that kernel changes
-NCU_TRAFFIC = {("line30_K8_a20", "fp32", "select_resident_kernel"): 4292608 + 256}
+# (the 4 MB of bins written stay in L2 at the end of that launch)
+NCU_TRAFFIC = {("line30_K8_a20", "fp32", "select_resident_kernel (fused: contraction steps, bins, selection)"):
+               411648 + 1280}
 
 
 def parse():
