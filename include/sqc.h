@@ -141,12 +141,14 @@ typedef struct {
    * that launch's work list (allocates).  Sliced queries and split-BF16
    * keep one launch per stage. */
   int32_t fused_query;
-  /* Programmatic dependent launch (1 = on, default 0): each kernel of a
-   * call is launched while the previous kernel on the stream finishes and
-   * waits on the device (griddepcontrol.wait) for its results.  Results do
-   * not change; on the 2^20-bin step it measured no faster (each kernel's
-   * early-resident CTAs slowed the kernel before them by about what the
-   * overlap saved). */
+  /* Programmatic dependent launch (1 = on, default 1): each kernel of a
+   * call is launched while the previous kernel on the stream finishes; it
+   * sets up what depends only on its parameters and shared memory, then
+   * waits on the device (griddepcontrol.wait) before its first access to
+   * memory the previous kernel may write.  Results do not change.  On the
+   * 2^20-bin one-call step it saves 1-2 us of the 42 (the fused selection
+   * launch's prologue overlaps the attribution-merge); on the per-stage
+   * chains it measured within noise. */
   int32_t pdl;
   /* Pairwise contraction order of new query plans (Section 6.2 cost, the
    * multiplications of each step): SQC_ORDER_GREEDY (default) pairs the

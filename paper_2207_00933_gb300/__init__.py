@@ -166,7 +166,7 @@ class Context:
                  fp64_chunk_min_edges: int = 12, chunk_terms: int = 256, slice_edges: int = 0,
                  select_resident: bool = True, merge_pyramid: bool = False, slice_input_log2: int = 0,
                  slice_intermediate_log2: int = 0, tc_pairs: bool | None = None, wait_limit_ms: int = 0,
-                 fused_query: bool = False, pdl: bool = False, contraction_order: int = 0,
+                 fused_query: bool = False, pdl: bool = True, contraction_order: int = 0,
                  fused_select: bool = True):
         self._lib = load_library()
         cfg = _Config()

@@ -1634,7 +1634,7 @@ SQC_API void sqc_default_config(sqc_config* cfg) {
   cfg->chunk_terms = 256;
   cfg->select_resident = 1;
   cfg->fused_query = 0;
-  cfg->pdl = 0;
+  cfg->pdl = 1;
   cfg->fused_select = 1;
 }
 

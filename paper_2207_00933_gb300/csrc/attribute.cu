@@ -661,8 +661,10 @@ __device__ __forceinline__ void attr_merge_tile(const AttrMergeDesc& d, const At
 // walk as attr_fused_kernel).
 template <bool F64>
 __global__ void __launch_bounds__(256, 4) attr_merge_kernel(AttrMergeLaunch L, int64_t total_tiles) {
-  pdl_wait();      // the previous kernel on the stream has completed
-  pdl_trigger();   // the next one may start launching
+  // the first descriptor and tile context (parameters and shared memory
+  // only) are set up before waiting on the previous kernel (programmatic
+  // dependent launch); the variant outputs are read after the wait
+  bool waited = false;
   extern __shared__ float val[];
   __shared__ AttrMergeDesc d;
   __shared__ AttrTileCtx tc;
@@ -695,6 +697,11 @@ __global__ void __launch_bounds__(256, 4) attr_merge_kernel(AttrMergeLaunch L, i
       else if (t >= 64 && t < 128 && t - 64 < cols_lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(d.colmap + 16 * (t - 64)));
       fill_tile_ctx(d, tc);
       __syncthreads();
+    }
+    if (!waited) {
+      pdl_wait();      // the previous kernel on the stream has completed
+      pdl_trigger();   // the next one may start launching
+      waited = true;
     }
     attr_merge_tile<F64>(d, tc, tile - d.block_begin, val);
     __syncthreads();

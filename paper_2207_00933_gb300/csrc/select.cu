@@ -1417,8 +1417,6 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
     tq = &tsh;
   }
   const TailArgs& T = *tq;
-  pdl_wait();      // the previous kernel on the stream has completed
-  pdl_trigger();   // the next one may start launching
   // Shared memory holds one 32-bit word per value: the whole key of an FP32
   // value, the high word of the 64-bit key of an FP64 value (its low word
   // is read back from the input only for values whose high word equals the
@@ -1462,10 +1460,15 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
     st.lo = KB;
     st.done = 0;
   }
+  for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
+  // everything above touches only parameters and shared memory (and L2
+  // hints): under a programmatic dependent launch it overlaps the end of
+  // the previous kernel
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
   if constexpr (TAIL) {
     if (T.n_levels > 0) ok = tail_pre_steps(T, w, nb, bar, reinterpret_cast<float*>(rsm + kRHistBytes));
   }
-  for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
   __syncthreads();
   // pass 0 with the load: keys of excluded values (NaN or below the
   // threshold) are stored as 0, which no included value has (the smallest

@@ -33,7 +33,8 @@ def test_default_config(lib):
     assert cfg.max_active_qubits == 32 and cfg.fp64_chunk_min_edges == 12 and cfg.chunk_terms == 256
     assert cfg.select_resident == 1
     assert cfg.merge_pyramid == 0 and cfg.slice_input_log2 == 0 and cfg.slice_intermediate_log2 == 0
-    assert cfg.tc_pairs == 0 and cfg.wait_limit_ms == 0 and cfg.fused_query == 0 and cfg.pdl == 0 and cfg.contraction_order == 0
+    assert cfg.tc_pairs == 0 and cfg.wait_limit_ms == 0 and cfg.fused_query == 0 and cfg.pdl == 1 and cfg.contraction_order == 0
+    assert cfg.fused_select == 1
 
 
 def test_create_without_gpu_fails_loudly(lib):
