@@ -869,10 +869,8 @@ constexpr int kRWarps = kRThreads / 32;
 constexpr int kRBits = 12;
 constexpr int kRRadix = 1 << kRBits;
 constexpr int kRMaxPasses = 6;                      // 64-bit keys: 5 x 12 + 4 bits
-constexpr int kRTile = 1024;                        // candidates per ranking tile at least
 constexpr int kRHistBytes = kRRadix * 4;
-constexpr int kRRegionMin = kRTile * 16;            // the ranking tile reuses the key region
-static_assert(kRTile == kRThreads, "a ranking round takes at least one candidate per thread");
+constexpr int kRRegionMin = 16 * 1024;              // shared memory after the histogram at least
 constexpr int kRSmemMax = 200 * 1024;               // dynamic shared memory per CTA at most
 constexpr size_t kRCtlOffset = 128;                 // byte offset of this kernel's control words
 constexpr uint32_t kRBarrierLimit = 1u << 21;       // polls (~1-2 s) before a barrier gives up
@@ -1426,7 +1424,7 @@ select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, uns
   constexpr int V = F64 ? 2 : 4;                    // values per 16-byte vector
   extern __shared__ __align__(16) unsigned char rsm[];
   unsigned* sh = reinterpret_cast<unsigned*>(rsm);                 // [kRRadix]
-  unsigned* keys = reinterpret_cast<unsigned*>(rsm + kRHistBytes); // [per], later the ranking tile
+  unsigned* keys = reinterpret_cast<unsigned*>(rsm + kRHistBytes); // [per], later the ranking's region
   __shared__ ResState st;
   __shared__ unsigned long long wtot[2 * kRWarps + 1];
   __shared__ unsigned wcnt[kRWarps];
