@@ -451,7 +451,7 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
       const int64_t tiles_i = (int64_t(1) << (n - L1 - L2)) << (2 * kout);
       blocks += (d.vec && kin == 0) ? tiles_i / 4 : tiles_i;
       d.block_end = blocks;
-      smem = std::max(smem, int((d.vec && kin == 0 ? 4 : (d.async2 ? 2 * S : S)) << (L1 + L2)) * 4);
+      smem = std::max(smem, int((d.vec && kin == 0 ? 4 : (d.async2 ? kAttrRing * S : S)) << (L1 + L2)) * 4);
       if (++L.n == kAttrPerLaunch) {
         sqc_status st = flush();
         if (st != SQC_OK) return st;

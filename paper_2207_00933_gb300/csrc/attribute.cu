@@ -525,8 +525,10 @@ __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kern
   __shared__ int cur, changed;
   if (threadIdx.x == 0) cur = -1;
   __syncthreads();
-  bool have_next = false;                 // the double-buffered form copied this tile already
-  int half = 0;                           // its current half of shared memory
+  // the ring-buffered form: tiles of this CTA already requested (the
+  // current one included) and the ring slot of the current one
+  int ahead = 0;
+  int head = 0;
   for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     if (threadIdx.x == 0) {
       int di = 0;
@@ -554,28 +556,28 @@ __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kern
     if (MODE == kAttrOne) {
       attr_tile<false>(d, tc, tile - d.block_begin, val);
     } else if (d.async2) {
+      // a ring of kAttrRing tile buffers: the CTA's next tiles of the same
+      // subcircuit are requested (cp.async) before the current one is
+      // expanded, so up to kAttrRing - 1 loads are in flight meanwhile
       const int64_t t = tile - d.block_begin;
       const int rows = (1 << (2 * d.kin)) * 256;
-      float* cur_buf = val + half * rows;
       const bool sq = d.L1 == 4;                     // 4/4 tile shape
-      if (!have_next) {
-        if (sq) v4_issue<4>(d, tc, t, cur_buf); else v4_issue<5>(d, tc, t, cur_buf);
+      while (ahead < kAttrRing && tile + int64_t(ahead) * gridDim.x < d.block_end) {
+        float* b = val + ((head + ahead) % kAttrRing) * rows;
+        const int64_t ta = t + int64_t(ahead) * gridDim.x;
+        if (sq) v4_issue<4>(d, tc, ta, b); else v4_issue<5>(d, tc, ta, b);
         cp_async_commit();
+        ++ahead;
       }
-      // this CTA's next tile, when it is of the same subcircuit
-      const bool next = tile + gridDim.x < d.block_end;
-      if (next) {
-        float* nb = val + (half ^ 1) * rows;
-        if (sq) v4_issue<4>(d, tc, t + gridDim.x, nb); else v4_issue<5>(d, tc, t + gridDim.x, nb);
-        cp_async_commit();
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
+      // the current tile's group is complete once at most ahead - 1 remain
+      if (ahead >= 3) cp_async_wait<2>();
+      else if (ahead == 2) cp_async_wait<1>();
+      else cp_async_wait<0>();
       __syncthreads();
+      float* cur_buf = val + head * rows;
       if (sq) v4_finish<4>(d, tc, t, cur_buf); else v4_finish<5>(d, tc, t, cur_buf);
-      have_next = next;
-      if (next) half ^= 1;
+      head = (head + 1) % kAttrRing;
+      --ahead;
     } else if (d.vec && d.kin == 0) {
       // (the host gives the 16 x 16 split to the double-buffered form only)
       attr_tiles_v4_kin0<5>(d, tile - d.block_begin, val);

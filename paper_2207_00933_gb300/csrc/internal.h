@@ -43,6 +43,7 @@ cudaError_t launch_mix(const MixArgs& a, cudaStream_t s);
 // fused fold + mix, shared-memory tiled (subcircuits with kin <= 7)
 constexpr int kMaxFusedIn = 7;
 constexpr int kAttrSmemMax = 64 * 1024;
+constexpr int kAttrRing = 3;               // tile buffers of the ring-buffered attribution form
 constexpr int kAttrPerLaunch = 16;
 struct AttrDesc {
   const void* p;
@@ -51,7 +52,7 @@ struct AttrDesc {
   int n, kin, kout;
   int L1, L2;                 // x tile: 2^L1 low values x 2^L2 top-bit values
   int vec;                    // 32 x 8 tile, FP32 input, 16-byte aligned: 4 states per thread
-  int async2;                 // vec, no outgoing edges, 4^kin <= 32: loads double-buffered by cp.async
+  int async2;                 // vec, no outgoing edges, 4^kin <= 32: loads ring-buffered by cp.async
   int inshift[kMaxFusedIn];
   int outshift[16];
   int64_t block_begin;
