@@ -859,9 +859,10 @@ fail:
 // 12-bit histogram on the way; the refinement passes, the compaction and
 // the tie scan then read shared memory only.  Grid barriers are a
 // monotonic arrival counter (one release-add per CTA, acquire polling, no
-// last-arriver step).  The ranking needs no barrier: every warp owns whole
-// candidates and counts the candidates ahead of each over shared-memory
-// tiles, then writes it at its rank.  Control flow is uniform across CTAs
+// last-arriver step).  The ranking needs no barrier (rank_candidates):
+// every CTA groups the candidate list by log-scaled key buckets in shared
+// memory, and a warp per owned candidate counts the members of its bucket
+// ahead of it.  Control flow is uniform across CTAs
 // (every CTA derives the same decisions from the same global histograms),
 // so every CTA meets every barrier.
 constexpr int kRThreads = 1024;
@@ -1393,10 +1394,10 @@ __device__ __forceinline__ void rank_candidates(const ResWork& w, unsigned nc, u
 // TAIL: the input is not read but computed -- the query's contraction
 // steps before the last run first (tail_pre_steps), then every CTA
 // computes its slice of the last step's bins itself (each bin one inner
-// product over the shared index, Y staged in shared memory, the FP32
-// multiply-adds in the order of the per-step kernel, so the bins are the
-// same bit for bit), writes them to T.P in bin order and keeps their keys
-// -- the bins are written once and never read back.
+// product over the shared index, the operands in registers or shared
+// memory, the FP32 multiply-adds in the order of the per-step kernel, so
+// the bins are the same bit for bit), writes them to T.P in bin order and
+// keeps their keys -- the bins are written once and never read back.
 template <bool F64, bool TAIL>
 __global__ void __launch_bounds__(kRThreads, 1)
 select_resident_kernel(const void* x, int aligned, uint64_t n, uint64_t per, unsigned long long key_thr64, int k,
