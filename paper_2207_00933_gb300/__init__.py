@@ -323,7 +323,7 @@ class Context:
                                               _stream_handle(stream)))
 
     def reconstruct_outputs(self, query: int, probs: list, out, precision: str = "fp32", total_prob=None,
-                            stream=None):
+                            stream=None, host_direct: bool = False):
         """Bins of `query` for fresh subcircuit outputs `probs` (one recursion
         step, sqc_reconstruct_outputs): attribution fused into the merge; the
         circuit's resident tensors are not changed."""
@@ -332,13 +332,15 @@ class Context:
         if total_prob is not None and (not total_prob.is_cuda or str(total_prob.dtype) != "torch.float64"):
             raise ValueError("total_prob must be a device float64 tensor")
         on_dev, ptrs, dt = self._prob_ptrs(probs)
+        if host_direct and not on_dev:
+            on_dev = 2          # pinned host tensors read in place by the kernels
         self._check(self._lib.sqc_reconstruct_outputs(self._h, query, ptrs, dt, on_dev, PREC[precision], _ptr(out),
                                                       _dtype_code(out), out.numel() * out.element_size(),
                                                       _ptr(total_prob), _stream_handle(stream)))
 
     def reconstruct_select(self, query: int, out, k: int, threshold: float = -math.inf, probs: list | None = None,
                            precision: str = "fp32", total_prob=None, bins_out=None, probs_out=None, n_found=None,
-                           stream=None):
+                           stream=None, host_direct: bool = False):
         """One recursion step (sqc_reconstruct_select): the bins of `query`
         into `out` (from the resident tensors, or from fresh outputs `probs`),
         then their k largest (value descending, bin ascending, >= threshold),
@@ -360,6 +362,8 @@ class Context:
             ptrs, dt, on_dev = None, F32, 1
         else:
             on_dev, ptrs, dt = self._prob_ptrs(probs)
+            if host_direct and not on_dev:
+                on_dev = 2      # pinned host tensors read in place by the kernels
         self._check(self._lib.sqc_reconstruct_select(self._h, query, ptrs, dt, on_dev, PREC[precision], _ptr(out),
                                                      _dtype_code(out), out.numel() * out.element_size(),
                                                      _ptr(total_prob), k, float(threshold), _ptr(bins_out),

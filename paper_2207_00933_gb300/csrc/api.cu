@@ -1947,10 +1947,21 @@ sqc_status reconstruct_fresh(sqc_ctx* ctx, sqc_query_id qid, const void* const* 
   const size_t esz = dtype == SQC_F64 ? 8 : 4;
   std::vector<const void*> src(c.nC);
   size_t off = 0;
+  if (probs_on_device < 0 || probs_on_device > 2) return fail(ctx, SQC_EINVAL, "probs_on_device must be 0, 1 or 2");
   for (int i = 0; i < c.nC; ++i) {
     const size_t nbytes = size_t(c.V[i]) * (size_t(1) << c.w[i]) * esz;
-    if (probs_on_device) {
+    if (probs_on_device == 1) {
       src[i] = probs[i];
+    } else if (probs_on_device == 2) {
+      // host memory the device reads in place (pinned and mapped): the
+      // attribution reads the kept states straight from it, no staging copy
+      cudaPointerAttributes pa{};
+      if (cudaPointerGetAttributes(&pa, probs[i]) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+          !pa.devicePointer) {
+        cudaGetLastError();
+        return fail(ctx, SQC_EINVAL, "probs[i] is not host memory mapped for the device (probs_on_device == 2)");
+      }
+      src[i] = pa.devicePointer;
     } else {
       if (off + nbytes > c.staging_bytes) return fail(ctx, SQC_ESHAPE, "staging buffer too small for these inputs");
       char* dst = static_cast<char*>(c.staging) + off;
@@ -1962,7 +1973,7 @@ sqc_status reconstruct_fresh(sqc_ctx* ctx, sqc_query_id qid, const void* const* 
   const FusedSrc fs{src.data(), dtype == SQC_F64};
   sqc_status st =
       reconstruct_core(ctx, qid, precision, out_bins, out_dtype, out_bytes, total_prob, stream, &fs, sel);
-  if (st == SQC_OK && !probs_on_device) {
+  if (st == SQC_OK && probs_on_device == 0) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cs));
     if (cs == cudaStreamCaptureStatusNone) CK(cudaStreamSynchronize(s));

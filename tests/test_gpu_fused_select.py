@@ -250,3 +250,43 @@ def test_forms_that_run_separately():
         torch.cuda.synchronize()
         assert torch.equal(out, out2) and torch.equal(b, b2) and torch.equal(v, v2)
         ctx.unload(cid)
+
+
+def test_pinned_host_inputs_read_in_place():
+    """Fresh outputs in pinned host memory read in place by the kernels
+    (probs_on_device == 2, no staging copy): the same bins and selection as
+    from device copies of the same outputs; pageable host memory is refused
+    in that mode."""
+    import torch
+    from paper_2207_00933_gb300 import Context, SQCError
+    w = W.merged_30q()
+    c = w.circuit
+    rng = np.random.default_rng(9)
+    fresh = [(p * (1.0 + 0.25 * rng.random(p.shape))).astype(np.float32) for p in w.probs]
+    ref = _oracle(c, fresh, w.roles)
+    with Context(0) as ctx:
+        cid, qid, na = _load(ctx, w)
+        pinned = [torch.from_numpy(p).pin_memory() for p in fresh]
+        on_dev = [torch.from_numpy(p).cuda() for p in fresh]
+        for k in (1024, 4096):
+            out = torch.empty(1 << na, dtype=torch.float32, device="cuda")
+            tot = torch.zeros(1, dtype=torch.float64, device="cuda")
+            b, v, n = ctx.reconstruct_select(qid, out, k, probs=pinned, total_prob=tot, host_direct=True)
+            torch.cuda.synchronize()
+            out2 = torch.empty_like(out)
+            tot2 = torch.zeros_like(tot)
+            b2, v2, n2 = ctx.reconstruct_select(qid, out2, k, probs=on_dev, total_prob=tot2)
+            torch.cuda.synchronize()
+            assert torch.equal(out, out2) and torch.equal(b, b2) and torch.equal(v, v2) and torch.equal(n, n2)
+            assert tot.item() == tot2.item()
+            err = float(np.abs(out.double().cpu().numpy() - ref).max())
+            assert err <= ABS_TOL, err
+        # the separate-call form reads pinned inputs in place too
+        out3 = torch.empty(1 << na, dtype=torch.float32, device="cuda")
+        ctx.reconstruct_outputs(qid, pinned, out3, host_direct=True)
+        torch.cuda.synchronize()
+        assert torch.equal(out3, out2)
+        with pytest.raises(SQCError) as ei:
+            ctx.reconstruct_select(qid, out3, 10, probs=list(fresh), host_direct=True)
+        assert ei.value.status == 1
+        ctx.unload(cid)
