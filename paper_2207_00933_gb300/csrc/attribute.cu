@@ -754,6 +754,40 @@ cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_byte
   return launch_k(attr_fused_kernel<kAttrAll>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
 }
 
+namespace {
+// Buffer blockIdx.y, CTAs along x striding over its 16-byte words, four
+// loads in flight per thread before their stores.
+__global__ void __launch_bounds__(256) stage_copy_kernel(StageCopy c) {
+  pdl_wait();      // the previous kernel on the stream has completed
+  pdl_trigger();   // the next one may start launching
+  const int b = blockIdx.y;
+  const uint4* src = static_cast<const uint4*>(c.src[b]);
+  uint4* dst = static_cast<uint4*>(c.dst[b]);
+  const uint64_t n = c.words[b];
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t w0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; w0 < n; w0 += 4 * stride) {
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (w0 + u * stride < n) v[u] = src[w0 + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (w0 + u * stride < n) dst[w0 + u * stride] = v[u];
+  }
+}
+}  // namespace
+
+cudaError_t launch_stage_copy(const StageCopy& c, cudaStream_t s) {
+  if (c.n <= 0) return cudaSuccess;
+  if (c.n > kAttrPerLaunch) return cudaErrorInvalidValue;
+  uint64_t most = 0;
+  for (int i = 0; i < c.n; ++i) most = c.words[i] > most ? c.words[i] : most;
+  // enough CTAs per buffer for every SM to keep loads in flight
+  const uint64_t per = (most + 4 * 256 - 1) / (4 * 256);
+  const unsigned gx = unsigned(per < 608 ? (per > 0 ? per : 1) : 608);
+  return launch_k(stage_copy_kernel, dim3(gx, unsigned(c.n)), dim3(256), 0, s, false, c);
+}
+
 cudaError_t launch_attr_merge(const AttrMergeLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s) {
   if (L.n <= 0 || blocks <= 0) return cudaSuccess;
   static const int sms = [] {

@@ -98,6 +98,19 @@ struct AttrMergeLaunch {
 };
 cudaError_t launch_attr_merge(const AttrMergeLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s);
 
+// Staging of host inputs by the SMs: every buffer's 16-byte words copied
+// from memory the device can read (mapped pinned host memory) to device
+// memory, one launch for up to kAttrPerLaunch buffers (each 16-byte
+// aligned, sizes multiples of 16 bytes).  Many loads in flight over the
+// host link instead of one copy-engine transfer per buffer.
+struct StageCopy {
+  const void* src[kAttrPerLaunch];
+  void* dst[kAttrPerLaunch];
+  uint64_t words[kAttrPerLaunch];   // 16-byte words
+  int n;
+};
+cudaError_t launch_stage_copy(const StageCopy& c, cudaStream_t s);
+
 // ---- merge / zoom (Section 4, Algorithm 2) ----------------------------------
 // T[e][b] = sum over data states with the zoom bits fixed and active bits
 // spelling b of A[e][state]; written to dst + rowmap[e] + colmap[b].

@@ -286,6 +286,33 @@ def test_pinned_host_inputs_read_in_place():
         ctx.reconstruct_outputs(qid, pinned, out3, host_direct=True)
         torch.cuda.synchronize()
         assert torch.equal(out3, out2)
+        ctx.unload(cid)
+        # pinned host inputs staged by the SMs' copy kernel (the default for
+        # mapped pinned memory): loads, updates and fresh steps
+        cid = ctx.load_subcircuit_outputs(c.n_qubits, *c.graph_arrays(), [torch.from_numpy(p).pin_memory()
+                                                                             for p in w.probs])
+        qid, na = ctx.set_qubit_roles(cid, w.roles)
+        out4 = torch.empty(1 << na, dtype=torch.float32, device="cuda")
+        ctx.reconstruct(qid, out4)
+        torch.cuda.synchronize()
+        err = float(np.abs(out4.double().cpu().numpy() - _oracle(c, w.probs, w.roles)).max())
+        assert err <= ABS_TOL, err
+        b4, v4, n4 = ctx.reconstruct_select(qid, out4, 1024, probs=pinned)
+        torch.cuda.synchronize()
+        b2, v2, n2 = ctx.reconstruct_select(qid, out2, 1024, probs=on_dev)
+        torch.cuda.synchronize()
+        assert torch.equal(out4, out2) and torch.equal(b4, b2) and torch.equal(v4, v2)
+        # an update from staged pinned inputs and one from device copies of
+        # the same outputs leave the same resident tensors
+        ctx.update_subcircuit_outputs(cid, pinned)
+        ctx.reconstruct(qid, out4)
+        ctx.update_subcircuit_outputs(cid, on_dev)
+        out5 = torch.empty_like(out4)
+        ctx.reconstruct(qid, out5)
+        torch.cuda.synchronize()
+        assert torch.equal(out4, out5)
+        err = float(np.abs(out4.double().cpu().numpy() - ref).max())
+        assert err <= ABS_TOL, err
         with pytest.raises(SQCError) as ei:
             ctx.reconstruct_select(qid, out3, 10, probs=list(fresh), host_direct=True)
         assert ei.value.status == 1
