@@ -215,7 +215,10 @@ SQC_API const char* sqc_last_error(const sqc_ctx* ctx);
  *             synchronised; while `stream` is being captured into a CUDA
  *             graph there is no synchronisation, and the buffers must be
  *             pinned and stay valid for every replay), else device
- *             pointers (read on `stream`).
+ *             pointers (read on `stream`).  Host inputs that are all
+ *             mapped pinned memory (16-byte aligned, sizes multiples of
+ *             16 bytes) are copied by one launch of an SM copy kernel;
+ *             other host memory by one copy per buffer.
  * On success *out_id names the circuit until sqc_unload. */
 SQC_API sqc_status sqc_load_subcircuit_outputs(sqc_ctx* ctx, const sqc_graph* graph,
                                                const void* const* probs, sqc_dtype dtype,
@@ -277,8 +280,8 @@ SQC_API sqc_status sqc_reconstruct(sqc_ctx* ctx, sqc_query_id q, sqc_precision p
  * staging copy and no synchronisation -- keep the buffers unchanged until
  * the stream has passed the call.  Other host memory fails with
  * SQC_EINVAL.  (On the 2^20-bin step this measured slower than staging,
- * 0.16 against 0.11 ms end to end: the attribution's latency-bound loads
- * each cross the host link.) 
+ * 0.16 against 0.09 ms end to end: the attribution's latency-bound loads
+ * each cross the host link.)
  * Applies when every subcircuit's roles follow the recursion's pattern
  * (data qubits in data_qubit order: the zoomed ones first, then the active
  * ones, then at most 8 merged ones -- what sqc_recursion_roles assigns),
