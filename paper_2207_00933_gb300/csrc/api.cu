@@ -1281,11 +1281,6 @@ bool build_attr_merge(const Circuit& c, const Query& q, const Plan& P, const voi
       *why = "a subcircuit's attribution tile does not fit shared memory";
       return false;
     }
-    // more, smaller tiles while a subcircuit has few: a tile's reads are
-    // latency-bound chains of 4^kin 2^(L1 + m) 2^kout loads over 256
-    // threads, so a small subcircuit spread over more CTAs finishes sooner
-    // (runs of 2 consecutive reads at least)
-    while (L1 > 1 && ((int64_t(1) << (a - L1)) << (2 * kout)) < 256) --L1;
     AttrMergeLaunch& L = launches->back();
     AttrMergeDesc& d = L.d[L.n];
     d.p = src[i];
@@ -1308,15 +1303,57 @@ bool build_attr_merge(const Circuit& c, const Query& q, const Plan& P, const voi
     d.kind = direct ? out_kind : P.tensors[i].kind;
     d.plane_stride = direct ? 0 : P.tensors[i].plane_stride;
     d.alpha = float(direct ? alpha : 1.0);
-    d.block_begin = blocks->back();
-    blocks->back() += (int64_t(1) << (a - L1)) << (2 * kout);
-    d.block_end = blocks->back();
-    smem->back() = std::max<int>(smem->back(), int(S << (L1 + m)) * 4);
     if (++L.n == kAttrPerLaunch && i + 1 < c.nC) {
       launches->push_back(AttrMergeLaunch{});
       blocks->push_back(0);
       smem->push_back(0);
     }
+  }
+  // Tile sizes per launch.  A tile's reads are latency-bound chains of
+  // 4^kin 2^(L1 + m) 2^kout loads over 256 threads, and the launch ends
+  // with its slowest CTA: starting from the fewest tiles, the subcircuit
+  // with the longest tiles is split in two (L1 - 1) while the launch still
+  // fits one wave of resident CTAs, down to runs of 2 consecutive reads
+  // (L1 = 1) and no further once a tile is one load per thread.
+  for (size_t j = 0; j < launches->size(); ++j) {
+    AttrMergeLaunch& L = (*launches)[j];
+    auto tiles = [&](const AttrMergeDesc& d) { return (int64_t(1) << (d.a - d.L1)) << (2 * d.kout); };
+    auto work = [&](const AttrMergeDesc& d) { return (int64_t(1) << (2 * d.kin + d.L1 + d.L2)) << d.kout; };
+    auto tile_smem = [&](const AttrMergeDesc& d) { return int((int64_t(1) << (2 * d.kin + d.L1 + d.L2)) * 4); };
+    int64_t total = 0;
+    for (int u = 0; u < L.n; ++u) total += tiles(L.d[u]);
+    bool any64 = false;
+    for (int u = 0; u < L.n; ++u) any64 = any64 || L.d[u].in_f64;
+    for (;;) {
+      int best = -1;
+      int64_t best_work = 256;
+      for (int u = 0; u < L.n; ++u) {
+        const AttrMergeDesc& d = L.d[u];
+        if (d.L1 > 1 && work(d) > best_work) {
+          // the split must keep the launch within one wave
+          int sm = 0;
+          for (int v = 0; v < L.n; ++v) sm = std::max(sm, v == u ? tile_smem(d) / 2 : tile_smem(L.d[v]));
+          if (total + tiles(d) <= attr_merge_wave(any64, sm)) {
+            best = u;
+            best_work = work(d);
+          }
+        }
+      }
+      if (best < 0) break;
+      total += tiles(L.d[best]);
+      --L.d[best].L1;
+    }
+    int64_t b = 0;
+    int sm = 0;
+    for (int u = 0; u < L.n; ++u) {
+      AttrMergeDesc& d = L.d[u];
+      d.block_begin = b;
+      b += tiles(d);
+      d.block_end = b;
+      sm = std::max(sm, tile_smem(d));
+    }
+    (*blocks)[j] = b;
+    (*smem)[j] = sm;
   }
   return true;
 }

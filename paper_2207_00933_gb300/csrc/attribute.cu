@@ -11,6 +11,8 @@
 // low data qubits, merged = high), a bin's states are one contiguous run.
 #include "common.cuh"
 
+#include <atomic>
+
 namespace sqc {
 
 namespace {
@@ -788,22 +790,38 @@ cudaError_t launch_stage_copy(const StageCopy& c, cudaStream_t s) {
   return launch_k(stage_copy_kernel, dim3(gx, unsigned(c.n)), dim3(256), 0, s, false, c);
 }
 
-cudaError_t launch_attr_merge(const AttrMergeLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s) {
-  if (L.n <= 0 || blocks <= 0) return cudaSuccess;
+int attr_merge_wave(bool f64, int smem_bytes) {
   static const int sms = [] {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
     return n;
   }();
+  // per power of two of the shared memory (the tiles' sizes are powers of
+  // two): computed once, read by any thread
+  static std::atomic<int> cache[2][32];
+  int lg = 0;
+  while (lg < 31 && (1 << lg) < smem_bytes) ++lg;
+  std::atomic<int>& slot = cache[f64 ? 1 : 0][lg];
+  int per_sm = slot.load(std::memory_order_relaxed);
+  if (per_sm <= 0) {
+    const void* fn = f64 ? reinterpret_cast<const void*>(attr_merge_kernel<true>)
+                         : reinterpret_cast<const void*>(attr_merge_kernel<false>);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 1 << lg) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+    slot.store(per_sm, std::memory_order_relaxed);
+  }
+  return sms * per_sm;
+}
+
+cudaError_t launch_attr_merge(const AttrMergeLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s) {
+  if (L.n <= 0 || blocks <= 0) return cudaSuccess;
   bool any64 = false;
   for (int i = 0; i < L.n; ++i) any64 = any64 || L.d[i].in_f64;
-  const void* fn = any64 ? reinterpret_cast<const void*>(attr_merge_kernel<true>)
-                         : reinterpret_cast<const void*>(attr_merge_kernel<false>);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem_bytes) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
-  const int64_t grid = blocks < int64_t(sms) * per_sm ? blocks : int64_t(sms) * per_sm;
+  const int64_t wave = attr_merge_wave(any64, smem_bytes);
+  const int64_t grid = blocks < wave ? blocks : wave;
   if (any64)
     return launch_k(attr_merge_kernel<true>, dim3(unsigned(grid)), dim3(256), size_t(smem_bytes), s, false, L, blocks);
   return launch_k(attr_merge_kernel<false>, dim3(unsigned(grid)), dim3(256), size_t(smem_bytes), s, false, L, blocks);

@@ -97,6 +97,9 @@ struct AttrMergeLaunch {
   int n;
 };
 cudaError_t launch_attr_merge(const AttrMergeLaunch& L, int64_t blocks, int smem_bytes, cudaStream_t s);
+// CTAs of the attribution-merge kernel resident on the device at once with
+// smem_bytes of dynamic shared memory each (one wave).
+int attr_merge_wave(bool f64, int smem_bytes);
 
 // Staging of host inputs by the SMs: every buffer's 16-byte words copied
 // from memory the device can read (mapped pinned host memory) to device

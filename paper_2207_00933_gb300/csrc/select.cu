@@ -1040,6 +1040,47 @@ __device__ __noinline__ void tail_tile_apart(const GemmArgs& a, int64_t m0, int6
   gemm_tile<BM, BM, TMN, TMN, false, BK, kRThreads, true>(a, m0, n0, stage, stage + BK * (BM + 4), a.C);
 }
 
+// A 32 x 32 tile of an FP32 step with K <= 64 on the whole CTA, one output
+// per thread: both operand tiles and the output's two layout-map entries
+// are loaded in one round (the general tile loads A, then B, then reads the
+// maps in its epilogue: three dependent round trips).  The multiply-adds
+// run over k = 0..63 ascending with zeros past K, as the general tile with
+// a 64-deep stage does, so the values are the same bit for bit.
+__device__ __forceinline__ void tail_tile32(const GemmArgs& a, int64_t m0, int64_t n0, float* stage) {
+  static_assert(kRThreads == 1024, "one output per thread");
+  float (*As)[32 + 4] = reinterpret_cast<float (*)[32 + 4]>(stage);
+  float (*Bs)[32 + 4] = reinterpret_cast<float (*)[32 + 4]>(stage + 64 * (32 + 4));
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  float ra[2], rb[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int idx = tid + u * kRThreads;
+    const int r = idx >> 6, kk = idx & 63;
+    ra[u] = (m0 + r < a.M && kk < a.K) ? __ldcg(a.A + (m0 + r) * a.K + kk) : 0.f;
+    rb[u] = (n0 + r < a.N && kk < a.K) ? __ldcg(a.B + (n0 + r) * a.K + kk) : 0.f;
+  }
+  const int64_t row = m0 + ty, col = n0 + tx;
+  const bool in = row < a.M && col < a.N;
+  uint64_t off = 0;
+  if (in) off = __ldg(a.rowmap + row) + __ldg(a.colmap + col);
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int idx = tid + u * kRThreads;
+    As[idx & 63][idx >> 6] = ra[u];
+    Bs[idx & 63][idx >> 6] = rb[u];
+  }
+  __syncthreads();
+  float acc = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < 64; ++kk) acc = fmaf(As[kk][ty], Bs[kk][tx], acc);
+  __syncthreads();
+  if (in) {
+    const float v = acc * pow2_to_float(a.alpha);
+    float* dst = static_cast<float*>(a.C) + off;
+    *dst = a.accumulate ? *dst + v : v;
+  }
+}
+
 __device__ __forceinline__ bool tail_pre_steps(const TailArgs& T, ResWork& w, unsigned nb, unsigned& bar,
                                               float* stage) {
   int lb = 0;
@@ -1069,7 +1110,9 @@ __device__ __forceinline__ bool tail_pre_steps(const TailArgs& T, ResWork& w, un
       // operands may come from the level before (written in this launch):
       // read them from L2.  Each stage of gemm_tile ends with a CTA
       // barrier, so the next tile may reuse the shared memory at once.
-      if (ts.cfg == 0)
+      if (ts.cfg == 0 && a.K <= 64 && a.kind == OUT_F32)
+        tail_tile32(a, m0, n0, stage);
+      else if (ts.cfg == 0)
         gemm_tile<32, 32, 1, 1, false, 64, kRThreads, true>(a, m0, n0, stage, stage + 64 * (32 + 4), a.C);
       else if (ts.cfg == 1)
         tail_tile_apart<64, 2, 32>(a, m0, n0, stage);
@@ -1240,10 +1283,10 @@ __device__ __forceinline__ unsigned rank_bucket(unsigned long long key, unsigned
 
 // Bytes of shared memory (after the histogram) the ranking needs: bucket
 // starts and the candidates grouped by bucket (FP32: the key packed with
-// the bin; FP64: key and bin), FP32 also every candidate's key word kept
-// between the passes over the list.
+// the bin; FP64: key and bin), FP32 also the whole list's key and bin words
+// in list order (read from global memory once).
 __host__ __device__ constexpr unsigned rank_region_bytes(bool f64) {
-  return unsigned(kRRadix) * 4u + unsigned(kMaxSort) * (f64 ? 16u : 12u);
+  return unsigned(kRRadix) * 4u + unsigned(kMaxSort) * 16u;
 }
 
 // Final order of the nc candidates (value descending, bin ascending) and
@@ -1268,25 +1311,34 @@ __device__ __forceinline__ void rank_candidates(const ResWork& w, unsigned nc, u
   unsigned* bstart = reinterpret_cast<unsigned*>(rsm + kRHistBytes);                  // [kRRadix]
   unsigned long long* gk = reinterpret_cast<unsigned long long*>(bstart + kRRadix);     // [kMaxSort]
   unsigned long long* gi = gk + kMaxSort;                                               // [kMaxSort] (FP64)
-  unsigned* kc = reinterpret_cast<unsigned*>(F64 ? gi + kMaxSort : gi);                 // [kMaxSort] (FP32)
+  unsigned* kc = reinterpret_cast<unsigned*>(gi);                                      // [kMaxSort] (FP32)
+  unsigned* ic = kc + kMaxSort;                                                         // [kMaxSort] (FP32)
   for (int d = tid; d < kRRadix; d += kRThreads) sh[d] = 0u;
   __syncthreads();
-  // the CTAs read the same list: each starts at its own offset
+  // the CTAs read the same list: each starts at its own offset.  FP32 keeps
+  // the list's key and bin words in shared memory in list order, so that
+  // the passes below read global memory no more.
   const unsigned rot = (blockIdx.x * nc) / nb;
   auto at = [&](unsigned e) { const unsigned f = e + rot; return f >= nc ? f - nc : f; };
   for (unsigned e0 = 0; e0 < nc; e0 += 4 * kRThreads) {
-    unsigned long long kk[4];
+    unsigned long long kk[4], ii[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const unsigned e = e0 + u * kRThreads + tid;
-      if (e < nc) kk[u] = __ldcg(w.cand_key + at(e));
+      if (e < nc) {
+        kk[u] = __ldcg(w.cand_key + at(e));
+        if (!F64) ii[u] = __ldcg(w.cand_idx + at(e));
+      }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const unsigned e = e0 + u * kRThreads + tid;
       if (e < nc) {
         atomicAdd(&sh[rank_bucket<F64>(kk[u], tmin)], 1u);
-        if (!F64) kc[e] = unsigned(kk[u]);
+        if constexpr (!F64) {
+          kc[at(e)] = unsigned(kk[u]);
+          ic[at(e)] = unsigned(ii[u]);
+        }
       }
     }
   }
@@ -1332,9 +1384,13 @@ __device__ __forceinline__ void rank_candidates(const ResWork& w, unsigned nc, u
     for (int u = 0; u < 4; ++u) {
       const unsigned e = e0 + u * kRThreads + tid;
       if (e < nc) {
-        const unsigned f = at(e);
-        kk[u] = F64 ? __ldcg(w.cand_key + f) : (unsigned long long)kc[e];
-        ii[u] = __ldcg(w.cand_idx + f);
+        if constexpr (F64) {
+          kk[u] = __ldcg(w.cand_key + at(e));
+          ii[u] = __ldcg(w.cand_idx + at(e));
+        } else {
+          kk[u] = kc[e];
+          ii[u] = ic[e];
+        }
       }
     }
 #pragma unroll
@@ -1357,8 +1413,8 @@ __device__ __forceinline__ void rank_candidates(const ResWork& w, unsigned nc, u
   const unsigned per = (nc + nb - 1) / nb;
   const unsigned p0 = blockIdx.x * per, p1 = p0 + per < nc ? p0 + per : nc;
   for (unsigned f = p0 + unsigned(warp); f < p1; f += kRWarps) {
-    const unsigned long long key = __ldcg(w.cand_key + f);
-    const unsigned long long bin = __ldcg(w.cand_idx + f);
+    const unsigned long long key = F64 ? __ldcg(w.cand_key + f) : (unsigned long long)kc[f];
+    const unsigned long long bin = F64 ? __ldcg(w.cand_idx + f) : (unsigned long long)ic[f];
     if (tie_by_pos && key == tie_key) continue;     // written by position below
     const unsigned long long kp = F64 ? key : ((key << 32) | (0xffffffffull - bin));
     const unsigned long long xp = F64 ? bin : 0ull;
