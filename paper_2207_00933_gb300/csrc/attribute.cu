@@ -453,6 +453,34 @@ __device__ __forceinline__ void v4_issue(const AttrDesc& d, const AttrTileCtx& t
   for (int s = int(threadIdx.x) >> 6; s < S; s += 4) cp_async16(buf + s * 256 + pos, p + (in_digits(tc, s) << n) + x0);
 }
 
+// the incoming edges' expansion of one state slot held in registers: the
+// 4^KIN values of slot p (stride 256), each digit q in turn, with the same
+// operations per element as the shared-memory passes
+template <int KIN>
+__device__ __forceinline__ void v4_expand_slot(float* val, int p) {
+  constexpr int S = 1 << (2 * KIN);
+  float v[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) v[s] = val[s * 256 + p];
+#pragma unroll
+  for (int q = 0; q < KIN; ++q) {
+    const int st = 1 << (2 * q);
+#pragma unroll
+    for (int g = 0; g < S / 4; ++g) {
+      const int lowmask = st - 1;
+      const int s0 = ((g & ~lowmask) << 2) | (g & lowmask);
+      const float v0 = v[s0], v1 = v[s0 + st], v2 = v[s0 + 2 * st], v3 = v[s0 + 3 * st];
+      const float sum = v0 + v1;
+      v[s0] = sum;                  // I
+      v[s0 + st] = 2.f * v2 - sum;  // X
+      v[s0 + 2 * st] = 2.f * v3 - sum;  // Y
+      v[s0 + 3 * st] = v0 - v1;     // Z
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) val[s * 256 + p] = v[s];
+}
+
 // expansion of the incoming edges and the bit-reversed write of tile t
 template <int L1>
 __device__ __forceinline__ void v4_finish(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
@@ -460,27 +488,11 @@ __device__ __forceinline__ void v4_finish(const AttrDesc& d, const AttrTileCtx& 
   const uint64_t xm = uint64_t(t);
   const int S = 1 << (2 * d.kin), n = d.n;
   const int g = int(threadIdx.x) & 63;
-  const int pos = v4_pos<L1>(4 * g);
-  for (int q = 0; q < d.kin; ++q) {
-    const int lowmask = (1 << (2 * q)) - 1;
-    const int st = 256 << (2 * q);
-    for (int gg = int(threadIdx.x) >> 6; gg < (S >> 2); gg += 4) {
-      const int s0 = ((gg & ~lowmask) << 2) | (gg & lowmask);
-      float* a = val + s0 * 256 + pos;
-      const float4 v0 = *reinterpret_cast<const float4*>(a);
-      const float4 v1 = *reinterpret_cast<const float4*>(a + st);
-      const float4 v2 = *reinterpret_cast<const float4*>(a + 2 * st);
-      const float4 v3 = *reinterpret_cast<const float4*>(a + 3 * st);
-      const float4 sm = make_float4(v0.x + v1.x, v0.y + v1.y, v0.z + v1.z, v0.w + v1.w);
-      *reinterpret_cast<float4*>(a) = sm;
-      *reinterpret_cast<float4*>(a + st) =
-          make_float4(2.f * v2.x - sm.x, 2.f * v2.y - sm.y, 2.f * v2.z - sm.z, 2.f * v2.w - sm.w);
-      *reinterpret_cast<float4*>(a + 2 * st) =
-          make_float4(2.f * v3.x - sm.x, 2.f * v3.y - sm.y, 2.f * v3.z - sm.z, 2.f * v3.w - sm.w);
-      *reinterpret_cast<float4*>(a + 3 * st) = make_float4(v0.x - v1.x, v0.y - v1.y, v0.z - v1.z, v0.w - v1.w);
-    }
-    __syncthreads();
-  }
+  // one pass: thread i expands the 4^kin values of state slot i (the 256
+  // slots of the tile, 256 threads) in registers, one CTA barrier in all
+  if (d.kin == 1) v4_expand_slot<1>(val, int(threadIdx.x));
+  else v4_expand_slot<2>(val, int(threadIdx.x));
+  __syncthreads();
   // thread g writes storage offsets r0 .. r0+3 (top state bits jh = the
   // L2-bit reversal of the offset) of the low state bits jl
   constexpr int kPerJl = (1 << L2) / 4;             // threads per low-bit value
@@ -533,6 +545,11 @@ __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kern
   int head = 0;
   for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     if (threadIdx.x == 0) {
+      // the descriptor search (parameter reads) only when the tile leaves
+      // the current descriptor's range
+      if (cur >= 0 && tile >= d.block_begin && tile < d.block_end) {
+        changed = 0;
+      } else {
       int di = 0;
 #pragma unroll
       for (int i = 1; i < kAttrPerLaunch; ++i)
@@ -548,6 +565,7 @@ __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kern
           default: break;
         }
         cur = di;
+      }
       }
     }
     __syncthreads();
