@@ -4,8 +4,8 @@ state tiles: the 4-states-per-thread form for 16-byte aligned FP32 inputs,
 the one-state-per-thread form for FP64 inputs and for FP32 inputs that are
 not 16-byte aligned.  The cases cover subcircuits with 1, 2 or 3 outgoing
 cut edges and none, with incoming edges and without (every form of the
-kernel), each checked through the whole reconstruction against the FP64
-oracle."""
+kernel, the double-buffered one with one and with two incoming edges),
+each checked through the whole reconstruction against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -23,6 +23,7 @@ CASES = {
     "kout3": ([18, 6], [3], [8, 4]),        # 15 data qubits, 3 outgoing edges
     "kout2_kin2": ([20, 22], [2], [10, 10]),  # 18 + 22 data qubits, 2 cuts
     "kin1_kout1": ([6, 21, 6], [1, 1], [3, 8, 3]),  # a middle subcircuit of 20 data qubits
+    "kin1_kout0": ([6, 20], [1], [3, 8]),   # 5 + 20 data qubits: the double-buffered form with one incoming edge
 }
 
 
