@@ -474,24 +474,27 @@ sqc_status attribute_all(sqc_ctx* ctx, Circuit* c, const void* const* probs, sqc
       d.L2 = L2;
       d.vec = L1 == 5 && L2 == 3 && dtype != SQC_F64 && (reinterpret_cast<uintptr_t>(src[i]) % 16) == 0;
       d.async2 = d.vec && kout == 0 && kin >= 1 && S <= 32;
-      // without outgoing edges A_i is as large as p_i, and the 32 x 8
-      // split's 32-byte bit-reversed write runs leave much of the DRAM
-      // bandwidth unused: the double-buffered form takes the 16 x 16 split
-      // (64-byte read and write runs).  With outgoing edges the reads
+      // without outgoing edges A_i is as large as p_i and the bit-reversed
+      // write runs (2^L2 states) set the speed: the double-buffered form
+      // takes 16 x 32 tiles (64-byte reads, 128-byte writes) in a ring of
+      // two buffers, three CTAs per SM.  At 592 MB per step: 136.2 us,
+      // against 149.4 us for 8 x 32 (32-byte reads), 148.5 us for 16 x 32
+      // in a ring of three (two CTAs per SM), 167.1 us for 16 x 16 and
+      // 248 us for 32 x 8 (32-byte writes).  With outgoing edges the reads
       // dominate and the 128-byte read runs of 32 x 8 measured faster.
       if (d.async2) {
-        d.L1 = 4;
-        d.L2 = 4;
+        d.L1 = kRingL1;
+        d.L2 = kRingL2;
       }
       for (int t = 0; t < kin; ++t) d.inshift[t] = digit_shift(*c, i, c->ins[i][t]);
       for (int u = 0; u < kout; ++u) d.outshift[u] = digit_shift(*c, i, c->outs[i][u]);
       d.block_begin = blocks;
       // a 4-state-per-thread CTA takes 4 tiles at once when there is a
       // single prepared-state row (no incoming edges): one per 64 threads
-      const int64_t tiles_i = (int64_t(1) << (n - L1 - L2)) << (2 * kout);
+      const int64_t tiles_i = (int64_t(1) << (n - d.L1 - d.L2)) << (2 * kout);
       blocks += (d.vec && kin == 0) ? tiles_i / 4 : tiles_i;
       d.block_end = blocks;
-      smem = std::max(smem, int((d.vec && kin == 0 ? 4 : (d.async2 ? kAttrRing * S : S)) << (L1 + L2)) * 4);
+      smem = std::max(smem, int((d.vec && kin == 0 ? 4 : (d.async2 ? kAttrRing * S : S)) << (d.L1 + d.L2)) * 4);
       if (++L.n == kAttrPerLaunch) {
         sqc_status st = flush();
         if (st != SQC_OK) return st;

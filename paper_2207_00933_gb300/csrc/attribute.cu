@@ -427,8 +427,15 @@ __device__ __forceinline__ void attr_tiles_v4_kin0(const AttrDesc& d, int64_t t,
 }
 
 // ---- double-buffered form (no outgoing edges, 4^kin <= 32): the rows of
-// the next tile are copied into the other half of shared memory by
-// cp.async while this tile is expanded and written
+// the next tiles are copied into other buffers of a ring in shared memory
+// by cp.async while this tile is expanded and written.  A tile is 2^L1 low
+// x 2^L2 top data states (4 consecutive states per thread and row), so the
+// reads of p run over 2^L1 consecutive states and the bit-reversed writes
+// of A over 2^L2 consecutive storage addresses.  This form writes as many
+// bytes as it reads, and its write runs set its speed.  Measured at 592 MB
+// per step with one side of the traffic cut out: the writes alone took 115
+// us in 64-byte runs and 95 us in 128- or 256-byte runs; the reads alone 95
+// us in 64- or 128-byte runs, 110 us in 32-byte and 124 us in 16-byte runs.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(uint32_t(__cvta_generic_to_shared(smem))),
                "l"(gmem)
@@ -440,28 +447,29 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// the 4^kin rows of tile t into buf (states in the slots of v4_pos)
-template <int L1>
-__device__ __forceinline__ void v4_issue(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* buf) {
-  constexpr int L2 = 8 - L1;
+// the 4^kin rows of tile t into buf, state j of a row at buf + row * 2^(L1+L2) + j
+template <int L1, int L2>
+__device__ __forceinline__ void ring_issue(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* buf) {
+  constexpr int TS = 1 << (L1 + L2);                // states per tile
+  constexpr int TPR = TS / 4;                       // threads per row
+  constexpr int RPP = 256 / TPR;                    // rows per pass of 256 threads
   const uint64_t xm = uint64_t(t);                  // no outgoing edges: tile = x middle bits
   const int S = 1 << (2 * d.kin), n = d.n;
-  const int j0 = 4 * (int(threadIdx.x) & 63);
+  const int j0 = 4 * (int(threadIdx.x) % TPR);
   const uint64_t x0 = uint64_t(j0 & ((1 << L1) - 1)) | (xm << L1) | (uint64_t(j0 >> L1) << (n - L2));
-  const int pos = v4_pos<L1>(j0);
   const float* p = static_cast<const float*>(d.p);
-  for (int s = int(threadIdx.x) >> 6; s < S; s += 4) cp_async16(buf + s * 256 + pos, p + (in_digits(tc, s) << n) + x0);
+  for (int s = int(threadIdx.x) / TPR; s < S; s += RPP) cp_async16(buf + s * TS + j0, p + (in_digits(tc, s) << n) + x0);
 }
 
 // the incoming edges' expansion of one state slot held in registers: the
-// 4^KIN values of slot p (stride 256), each digit q in turn, with the same
+// 4^KIN values of slot p (stride TS), each digit q in turn, with the same
 // operations per element as the shared-memory passes
-template <int KIN>
-__device__ __forceinline__ void v4_expand_slot(float* val, int p) {
+template <int KIN, int TS>
+__device__ __forceinline__ void ring_expand_slot(float* val, int p) {
   constexpr int S = 1 << (2 * KIN);
   float v[S];
 #pragma unroll
-  for (int s = 0; s < S; ++s) v[s] = val[s * 256 + p];
+  for (int s = 0; s < S; ++s) v[s] = val[s * TS + p];
 #pragma unroll
   for (int q = 0; q < KIN; ++q) {
     const int st = 1 << (2 * q);
@@ -478,31 +486,35 @@ __device__ __forceinline__ void v4_expand_slot(float* val, int p) {
     }
   }
 #pragma unroll
-  for (int s = 0; s < S; ++s) val[s * 256 + p] = v[s];
+  for (int s = 0; s < S; ++s) val[s * TS + p] = v[s];
 }
 
 // expansion of the incoming edges and the bit-reversed write of tile t
-template <int L1>
-__device__ __forceinline__ void v4_finish(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
-  constexpr int L2 = 8 - L1;
+template <int L1, int L2>
+__device__ __forceinline__ void ring_finish(const AttrDesc& d, const AttrTileCtx& tc, int64_t t, float* val) {
+  constexpr int TS = 1 << (L1 + L2);
+  constexpr int TPR = TS / 4;
+  constexpr int RPP = 256 / TPR;
   const uint64_t xm = uint64_t(t);
   const int S = 1 << (2 * d.kin), n = d.n;
-  const int g = int(threadIdx.x) & 63;
-  // one pass: thread i expands the 4^kin values of state slot i (the 256
-  // slots of the tile, 256 threads) in registers, one CTA barrier in all
-  if (d.kin == 1) v4_expand_slot<1>(val, int(threadIdx.x));
-  else v4_expand_slot<2>(val, int(threadIdx.x));
+  // thread i expands the 4^kin values of state slots i, i + 256, ... in
+  // registers, one CTA barrier in all
+  for (int j = int(threadIdx.x); j < TS; j += 256) {
+    if (d.kin == 1) ring_expand_slot<1, TS>(val, j);
+    else ring_expand_slot<2, TS>(val, j);
+  }
   __syncthreads();
   // thread g writes storage offsets r0 .. r0+3 (top state bits jh = the
   // L2-bit reversal of the offset) of the low state bits jl
   constexpr int kPerJl = (1 << L2) / 4;             // threads per low-bit value
+  const int g = int(threadIdx.x) % TPR;
   const int jl = g / kPerJl, r0 = (g % kPerJl) * 4;
   int pw[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) pw[q] = v4_pos<L1>(jl | (int(__brev(uint32_t(r0 + q)) >> (32 - L2)) << L1));
+  for (int q = 0; q < 4; ++q) pw[q] = jl | (int(__brev(uint32_t(r0 + q)) >> (32 - L2)) << L1);
   const uint64_t xw = rev_bits(uint32_t(uint64_t(jl) | (xm << L1)), n) + uint64_t(r0);
-  for (int s = int(threadIdx.x) >> 6; s < S; s += 4) {
-    const float* v = val + s * 256;
+  for (int s = int(threadIdx.x) / TPR; s < S; s += RPP) {
+    const float* v = val + s * TS;
     *reinterpret_cast<float4*>(d.A + (in_digits(tc, s) << n) + xw) = make_float4(v[pw[0]], v[pw[1]], v[pw[2]], v[pw[3]]);
   }
 }
@@ -580,12 +592,11 @@ __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kern
       // subcircuit are requested (cp.async) before the current one is
       // expanded, so up to kAttrRing - 1 loads are in flight meanwhile
       const int64_t t = tile - d.block_begin;
-      const int rows = (1 << (2 * d.kin)) * 256;
-      const bool sq = d.L1 == 4;                     // 4/4 tile shape
+      const int rows = (1 << (2 * d.kin)) << (kRingL1 + kRingL2);
       while (ahead < kAttrRing && tile + int64_t(ahead) * gridDim.x < d.block_end) {
         float* b = val + ((head + ahead) % kAttrRing) * rows;
         const int64_t ta = t + int64_t(ahead) * gridDim.x;
-        if (sq) v4_issue<4>(d, tc, ta, b); else v4_issue<5>(d, tc, ta, b);
+        ring_issue<kRingL1, kRingL2>(d, tc, ta, b);
         cp_async_commit();
         ++ahead;
       }
@@ -595,11 +606,11 @@ __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kern
       else cp_async_wait<0>();
       __syncthreads();
       float* cur_buf = val + head * rows;
-      if (sq) v4_finish<4>(d, tc, t, cur_buf); else v4_finish<5>(d, tc, t, cur_buf);
+      ring_finish<kRingL1, kRingL2>(d, tc, t, cur_buf);
       head = (head + 1) % kAttrRing;
       --ahead;
     } else if (d.vec && d.kin == 0) {
-      // (the host gives the 16 x 16 split to the double-buffered form only)
+      // (the host gives the 16 x 32 split to the double-buffered form only)
       attr_tiles_v4_kin0<5>(d, tile - d.block_begin, val);
     } else if (MODE == kAttrVec || d.vec) {
       attr_tile_v4<5>(d, tc, tile - d.block_begin, val);

@@ -43,7 +43,8 @@ cudaError_t launch_mix(const MixArgs& a, cudaStream_t s);
 // fused fold + mix, shared-memory tiled (subcircuits with kin <= 7)
 constexpr int kMaxFusedIn = 7;
 constexpr int kAttrSmemMax = 64 * 1024;
-constexpr int kAttrRing = 3;               // tile buffers of the ring-buffered attribution form
+constexpr int kAttrRing = 2;               // tile buffers of the ring-buffered attribution form
+constexpr int kRingL1 = 4, kRingL2 = 5;     // its tiles: 2^kRingL1 low x 2^kRingL2 top data states
 constexpr int kAttrPerLaunch = 16;
 struct AttrDesc {
   const void* p;
