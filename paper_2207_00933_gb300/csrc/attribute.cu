@@ -538,11 +538,17 @@ __device__ void fill_tile_ctx(const Desc& d, AttrTileCtx& t) {
 // kernel that covers its descriptors (fewer registers, and for small
 // subcircuits fewer instruction-cache misses):
 //   kAttrAll  -- every form;
-//   kAttrVec  -- every descriptor takes a 4-state-per-thread form;
+//   kAttrVec  -- every descriptor takes a 4-state-per-thread form (at most
+//                40 registers, for six CTAs per SM);
+//   kAttrVec3 -- the same forms, for launches whose shared memory allows
+//                three CTAs per SM at most (the double-buffered form's
+//                ring): up to 80 registers, where kAttrVec spills (at 592
+//                MB per step 125.5 us against 134.1 us);
 //   kAttrOne  -- every descriptor takes the one-state form with FP32 input.
-enum : int { kAttrAll = 0, kAttrVec = 1, kAttrOne = 2 };
+enum : int { kAttrAll = 0, kAttrVec = 1, kAttrOne = 2, kAttrVec3 = 3 };
 template <int MODE>
-__global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
+__global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : (MODE == kAttrVec3 ? 3 : 4))
+    attr_fused_kernel(AttrLaunch L, int64_t total_tiles) {
   pdl_wait();      // the previous kernel on the stream has completed
   pdl_trigger();   // the next one may start launching
   extern __shared__ float val[];
@@ -612,8 +618,9 @@ __global__ void __launch_bounds__(256, MODE == kAttrVec ? 6 : 4) attr_fused_kern
     } else if (d.vec && d.kin == 0) {
       // (the host gives the 16 x 32 split to the double-buffered form only)
       attr_tiles_v4_kin0<5>(d, tile - d.block_begin, val);
-    } else if (MODE == kAttrVec || d.vec) {
-      attr_tile_v4<5>(d, tc, tile - d.block_begin, val);
+    } else if (MODE == kAttrVec || MODE == kAttrVec3 || d.vec) {
+      // (with incoming edges the host gives the 16 x 16 split)
+      attr_tile_v4<4>(d, tc, tile - d.block_begin, val);
     } else {
       attr_tile<true>(d, tc, tile - d.block_begin, val);
     }
@@ -778,8 +785,15 @@ cudaError_t launch_attr_fused(const AttrLaunch& L, int64_t blocks, int smem_byte
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem_bytes) != cudaSuccess || per_sm < 1)
     per_sm = 1;
+  // shared memory already holds the launch to three CTAs per SM: the
+  // variant with more registers costs no occupancy
+  const bool vec3 = all_vec && per_sm <= 3;
+  if (vec3 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, attr_fused_kernel<kAttrVec3>, 256, smem_bytes) !=
+                   cudaSuccess || per_sm < 1))
+    per_sm = 1;
   const int64_t grid = blocks < int64_t(sms) * per_sm ? blocks : int64_t(sms) * per_sm;
   const dim3 g(unsigned(grid), 1, 1);
+  if (vec3) return launch_k(attr_fused_kernel<kAttrVec3>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
   if (all_vec) return launch_k(attr_fused_kernel<kAttrVec>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
   if (all_one) return launch_k(attr_fused_kernel<kAttrOne>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
   return launch_k(attr_fused_kernel<kAttrAll>, g, dim3(256), size_t(smem_bytes), s, false, L, blocks);
@@ -863,6 +877,8 @@ cudaError_t attr_configure() {
     e = cudaFuncSetAttribute(attr_fused_kernel<kAttrVec>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(attr_fused_kernel<kAttrOne>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(attr_fused_kernel<kAttrVec3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(attr_merge_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAttrSmemMax);
   if (e == cudaSuccess)
